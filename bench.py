@@ -1,0 +1,419 @@
+"""Benchmark of the CP-MDP GridWorld hot path on GB300.
+
+Workload: 3-D GridWorld 64^3 (262,144 states), 6 actions, p = 0.8 (0.05 to
+each perpendicular move), 5 % seeded obstacles, 8 goal cells with reward
+U(0.5, 1), step reward -0.01, gamma = 0.99; FP32 value tensor.
+
+One step = the whole hot path on that instance, inputs resident on the
+device: fused value iteration from zeros to max|dV| < 1e-6 with the FP64
+certifying sweep and policy extraction, then fused policy iteration from
+zeros with its FP64 certifying sweep. The metric is state-action backups
+per second over the step (|S| |A| per VI / improvement sweep, |S| per
+evaluation sweep); time-to-1e-6 of the fused VI is reported next to the
+plain unfused FP32 VI (one kernel per action, separate max and residual
+kernels, residual checked on the host every sweep) on the same GPU.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU FP64 oracle (plain C, OpenMP) on the same
+instance instead. Under torchrun each rank solves its own instance
+(replicas: the path has no exchange step), value = all ranks' backups over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "state-action backups/s and time to |dV|inf<1e-6 vs plain FP32 VI, same GB300"
+UNIT = "state-action backups/s"
+SIDE = 64
+TOL = 1e-6
+BYTES_VI = 13      # per state per VI sweep: V 4 + R 4 + code 1 + V' 4
+BYTES_EVAL = 14    # + policy read
+BYTES_IMPROVE = 10 # V 4 + R 4 + code 1 + policy 1
+
+
+def workload(seed):
+    import cpmdp_inputs as ci
+    return ci.config_3d(side=SIDE, seed=seed)
+
+
+def config_dict(extra=None):
+    d = {"workload": f"gridworld-3d-{SIDE}^3-A6-p0.8-obst5%-goals8-gamma0.99-fp32",
+         "states": SIDE ** 3, "actions": 6, "tol": TOL,
+         "step": "fused VI to 1e-6 + FP64 certify + fused PI + FP64 certify, zero init",
+         "l2": "flushed between timed steps (256 MiB write)",
+         "parallelism": "replicas (independent instance per rank)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        mhz, maxmhz, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                maxmhz.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(maxmhz), "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = os.environ.get("CPMDP_BENCH_BACKEND", "nccl")
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def aggregate(pg, units, ms, device=None):
+    """Sum of units over ranks and max of the timed milliseconds."""
+    if pg is None:
+        return units, ms
+    import torch
+    dev = device if device is not None else "cpu"
+    t = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    m = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    pg.all_reduce(m, op=pg.ReduceOp.MAX)
+    return float(t.item()), float(m.item())
+
+
+def traffic_from_profile(kernel_file):
+    """DRAM bytes per launch of the solve kernel from the committed ncu
+    summary, if it was taken on the current kernel source (hash match)."""
+    src = os.path.join(ROOT, "paper_2103_00331_gb300", "csrc", "banded.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", kernel_file)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for ln in open(path):
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("banded_cu_sha256_16") != h:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_scaled"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_oracle_sample(gw, budget_s=12.0, max_reps=50):
+    """The FP64 C oracle (as it stands) on the same instance: repeated full
+    value-iteration solves to 1e-6 from zeros until ~budget_s of CPU time."""
+    from oracle import cpfactor as oc
+    oc.build()
+    S, A = gw.nstates, 2 * len(gw.shape)
+    t0 = time.perf_counter()
+    backups, reps = 0, 0
+    while True:
+        _, _, k, _ = oc.value_iteration(gw, tol=TOL, max_iter=5000)
+        backups += k * S * A
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= max_reps:
+            break
+    return {"value": backups / el, "unit": UNIT, "cores": oc.threads(), "kind": "oracle",
+            "sample": f"{reps} full FP64 VI solves to 1e-6 of the 64^3 instance ({k} sweeps each), "
+                      f"{el:.1f} s on {oc.threads()} OpenMP threads"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    gw = workload(0)
+    from oracle import cpfactor as oc
+    oc.build()
+    S, A = gw.nstates, 2 * len(gw.shape)
+    # each step: one full oracle VI solve to 1e-6 from zeros (a bounded sample of the step)
+    for _ in range(args.warmup):
+        oc.value_iteration(gw, tol=TOL, max_iter=5000)
+    t0 = time.perf_counter()
+    backups = 0
+    for _ in range(args.steps):
+        _, _, k, _ = oc.value_iteration(gw, tol=TOL, max_iter=5000)
+        backups += k * S * A
+    el = time.perf_counter() - t0
+    value = backups / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict({"step": "CPU FP64 oracle VI solve to 1e-6 from zeros"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oc.threads(), "kind": "oracle",
+                             "sample": f"{args.steps} FP64 VI solves of the 64^3 instance ({k} sweeps each)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local, pg):
+    import torch
+    import paper_2103_00331_gb300 as cp
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    gw = workload(rank)
+    S, A = gw.nstates, 2 * len(gw.shape)
+    f = cp.build_factors(gw, device=local)
+    V = torch.zeros(S, dtype=torch.float32, device=dev)
+    pi = torch.zeros(S, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    vi_opts = cp.default_opts(tol=TOL, max_iter=5000)
+    pi_opts = cp.default_opts(tol=TOL, max_iter=5000)
+
+    def step(timers=None):
+        V.zero_()
+        if timers:
+            timers[0].record(stream)
+        rv = cp.value_iteration(f, cp.F32, V, pi, opts=vi_opts, stream=stream)
+        if timers:
+            timers[1].record(stream)
+        V.zero_()
+        if timers:
+            timers[2].record(stream)
+        rp = cp.policy_iteration(f, cp.F32, V, pi, opts=pi_opts, stream=stream)
+        if timers:
+            timers[3].record(stream)
+        return rv, rp
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    if pg is not None:
+        pg.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    total_ms, vi_ms, pi_ms, backups, launches = 0.0, [], [], 0, 0
+    vi_bytes, pi_bytes, vi_iters, pi_iters = 0, 0, [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        rv, rp = step(ev)
+        torch.cuda.synchronize()
+        a, b = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+        vi_ms.append(a)
+        pi_ms.append(b)
+        total_ms += ev[0].elapsed_time(ev[3])
+        backups += rv["backups"] + rp["backups"]
+        launches += 4   # persistent VI solve + certify sweep, persistent PI solve + certify sweep
+        vi_iters.append(rv["iterations"])
+        pi_iters.append(rp["iterations"])
+        vi_bytes += rv["iterations"] * S * BYTES_VI
+        pi_bytes += rp["eval_sweeps"] * S * BYTES_EVAL + (rp["rounds"] + 1) * S * BYTES_IMPROVE
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if pg is not None:
+        pg.barrier()
+    units, ms_max = aggregate(pg, backups, total_ms, device=dev)
+    value = units / (ms_max / 1e3)
+
+    # plain unfused FP32 VI on the same instance (the comparator of the metric)
+    plain_opts = cp.default_opts(tol=TOL, max_iter=5000, fused=0, certify=0)
+    plain_ms = []
+    rpl = {"iterations": None}
+    for i in range(0 if args.skip_plain else max(3, min(args.steps, 10)) + 1):
+        V.zero_()
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rpl = cp.value_iteration(f, cp.F32, V, None, opts=plain_opts, stream=stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            plain_ms.append((time.perf_counter() - t0) * 1e3)
+    fused_vi_ms = statistics.median(vi_ms)
+    plain_vi_ms = statistics.median(plain_ms) if plain_ms else None
+
+    # roofline of the dominant kernel (the persistent solve kernel): algorithmic
+    # bytes of its launches over their event-timed durations
+    solve_ms = sum(vi_ms) + sum(pi_ms)
+    achieved = (vi_bytes + pi_bytes) / (solve_ms / 1e3) / 1e9
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    hbm = peaks.get("hbm_gbs")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm or 6800.0, "unit": "GB/s",
+            "frac": achieved / (hbm or 6800.0),
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6.8 TB/s",
+            "traffic": traffic_from_profile("solve_kernel_gridworld64.txt"),
+            "kernel": "solve_kernel<float,3,4> (persistent VI/PI, FP32)",
+            "note": "64^3 working set (3.4 MB) is L2-resident; per-sweep grid barrier bound"}
+
+    # HBM-bound sweep: one fused backup of a 512^3 instance, event-timed
+    large = None
+    if not args.skip_large:
+        large = hbm_sweep(cp, dev, stream, hbm or 6800.0)
+
+    # end to end through the public API with host buffers: build_factors
+    # (host -> device), VI + PI, device -> host of V and the policy
+    e2e_ms = []
+    e2e_units = 0
+    for i in range(max(2, min(args.steps, 5)) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fe = cp.build_factors(gw, device=local)
+        Ve = torch.zeros(S, dtype=torch.float32, device=dev)
+        pe = torch.empty(S, dtype=torch.uint8, device=dev)
+        r1 = cp.value_iteration(fe, cp.F32, Ve, pe, opts=vi_opts, stream=stream)
+        Vh, ph = Ve.cpu(), pe.cpu()
+        Ve.zero_()
+        r2 = cp.policy_iteration(fe, cp.F32, Ve, pe, opts=pi_opts, stream=stream)
+        Vh2, ph2 = Ve.cpu(), pe.cpu()
+        fe.close()
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+            e2e_units += r1["backups"] + r2["backups"]
+    e2e_total, e2e_max = aggregate(pg, e2e_units, sum(e2e_ms), device=dev)
+    e2e = {"value": e2e_total / (e2e_max / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": S * (4 + 8 + 1 + 1),   # R32, R64, cell, code uploaded by build_factors
+           "d2h_bytes_per_step": 2 * S * (4 + 1),       # V and policy after VI and after PI
+           "ms_per_step": statistics.median(e2e_ms)}
+
+    cpu = None
+    if rank == 0 and world >= 1 and not args.skip_cpu:
+        cpu = cpu_oracle_sample(gw, budget_s=args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks,
+                "time_to_tol_ms": fused_vi_ms, "plain_fp32_vi_ms": plain_vi_ms,
+                "speedup_vs_plain_fp32_vi": plain_vi_ms / fused_vi_ms if plain_vi_ms else None,
+                "vi_sweeps": statistics.median(vi_iters), "plain_vi_sweeps": rpl["iterations"],
+                "pi_sweeps": statistics.median(pi_iters), "pi_ms": statistics.median(pi_ms),
+                "certified_residual": rv["certified_residual"], "error_bound": rv["error_bound"],
+                "hbm_sweep_512": large}
+        print(json.dumps(line), flush=True)
+    f.close()
+    return 0
+
+
+def hbm_sweep(cp, dev, stream, peak):
+    """One fused FP32 backup sweep of a 512^3 GridWorld (134M states, out of
+    L2): algorithmic bytes (13 per state) over the event-timed duration."""
+    import torch
+    import cpmdp_inputs as ci
+    n = 512
+    gw = ci.gridworld((n, n, n), p=0.8, gamma=0.99, step_reward=-0.01,
+                      goal_rewards=list(ci.uniform(0, 12, 8, 0.5, 1.0)), obstacle_rate=0.05, seed=2)
+    f = cp.build_factors(gw, device=dev.index)
+    S = gw.nstates
+    Va = torch.zeros(S, dtype=torch.float32, device=dev)
+    Vb = torch.zeros(S, dtype=torch.float32, device=dev)
+    res = torch.zeros(1, dtype=torch.float64, device=dev)
+    times = []
+    for i in range(13):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cp.bellman_backup(f, cp.F32, Va, Vb, None, res, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if i >= 3:
+            times.append(e0.elapsed_time(e1))
+        Va, Vb = Vb, Va
+    ms = statistics.median(times)
+    ach = S * BYTES_VI / (ms / 1e3) / 1e9
+    f.close()
+    del Va, Vb
+    torch.cuda.empty_cache()
+    return {"kernel": "sweep_kernel<float,float,3,4>", "states": S, "ms": ms,
+            "bytes_per_state": BYTES_VI, "achieved_gbs": ach, "peak_gbs": peak, "frac": ach / peak,
+            "note": "inputs 1.7 GB > L2; residual fused, policy not written"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--skip-large", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    rank, world, local, pg = dist_setup(args.gpus)
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+    else:
+        rc = run_ours(args, rank, world, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

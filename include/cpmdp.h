@@ -1,0 +1,235 @@
+/*
+ * cpmdp.h -- C ABI of the GB300 CP-MDP library (libcpmdp.so).
+ *
+ * CP-MDP (Kuinchtner, Sales and Meneguzzi, AAAI 2021) solves a Markov
+ * decision process <S, A, P, R, gamma> (background section, "Markov Decision
+ * Process") whose states are the tuples of an n-dimensional grid
+ * (Definitions 1 and 2) and whose transition model P is held as CANDECOMP-
+ * PARAFAC components: per action, a sum of rank-1 terms, each an outer
+ * product of small per-dimension factor matrices (background section,
+ * "Tensor Decomposition", Fig. 1; Definition 3). The library computes the
+ * Bellman backup of Eq. 1,
+ *     V'(s) = R(s) + gamma * max_a sum_{s'} P(s'|s,a) V(s'),
+ * without ever expanding P to an |S| x |S| matrix, and runs value iteration
+ * and policy iteration (background section) entirely on one GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - States are flat indices in C order over (N_1, ..., N_D): the last
+ *   dimension varies fastest (Definition 2). Every per-state array (cell
+ *   codes, rewards, values, policies) uses this layout, densely packed.
+ * - GridWorld actions (scenario section: two actions per axis, |A| = 2D):
+ *   action a = 2*d + (sigma > 0) moves by sigma = -1 or +1 along dimension
+ *   d (d = 0 is the slowest dimension). In 2-D: N, S on the first axis and
+ *   W, E on the second.
+ * - Slip model: the intended move happens with probability p_success; the
+ *   remaining mass is split evenly over the 2(D-1) perpendicular unit
+ *   moves (for D = 1 the agent stays put instead). A move that leaves the
+ *   grid or enters an obstacle leaves the agent in place.
+ * - Cell codes: 0 free, 1 obstacle (never entered, not a state: value 0,
+ *   policy 255), 2 terminal (the interaction ends: V(t) = R(t), policy 255).
+ * - Values are float (CPMDP_F32, CPMDP_BF16X3) or double (CPMDP_F64), in
+ *   caller-owned DEVICE memory. Policies are uint8 action indices in
+ *   caller-owned device memory, 255 where no action applies.
+ * - Device buffers passed in must be at least 16-byte aligned for the
+ *   vectorised kernels (PyTorch allocations are); other alignments are
+ *   accepted and take a scalar path.
+ * - Every call that takes a stream enqueues its kernels on that stream
+ *   (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ *   Calls that fill a cpmdp_result synchronise with the stream before they
+ *   return. Two calls that use the same cpmdp_factors object must not run
+ *   concurrently: the object owns the scratch buffers of the solvers.
+ * - No call throws or aborts. Each returns a cpmdp_status; on failure
+ *   cpmdp_last_error() gives a message (per host thread).
+ */
+#ifndef CPMDP_H
+#define CPMDP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CPMDP_MAX_DIM 9
+
+typedef enum {
+    CPMDP_OK = 0,
+    CPMDP_EINVAL = 1,    /* invalid argument: nothing was enqueued */
+    CPMDP_ENOMEM = 2,    /* host or device allocation failed */
+    CPMDP_ECUDA = 3,     /* a CUDA runtime call failed (message has details) */
+    CPMDP_ENOCONV = 4,   /* max_iter sweeps done without reaching tol; outputs hold the last iterate */
+    CPMDP_ETIMEOUT = 5   /* a device-side wait gave up after timeout_s; outputs undefined */
+} cpmdp_status;
+
+typedef enum {
+    CPMDP_F32 = 0,       /* float values, float arithmetic */
+    CPMDP_F64 = 1,       /* double values, double arithmetic */
+    CPMDP_BF16X3 = 2     /* dense CP only: float values, mode products as three bf16 tensor-core products */
+} cpmdp_precision;
+
+typedef enum {
+    CPMDP_GRIDWORLD = 0, /* banded factors from the slip model above */
+    CPMDP_DENSE_CP = 1   /* general dense rank-R factors */
+} cpmdp_kind;
+
+enum { CPMDP_CELL_FREE = 0, CPMDP_CELL_OBSTACLE = 1, CPMDP_CELL_TERMINAL = 2 };
+
+/*
+ * The MDP tuple <S, A, P, R, gamma> (background section).
+ *   ndim, shape[0..ndim-1]  S = N_1 x ... x N_D (Definitions 1-2), each N_d >= 1,
+ *                           1 <= ndim <= CPMDP_MAX_DIM, |S| < 2^31.
+ *   nactions                GridWorld: must equal 2*ndim. Dense: 1..64.
+ *   kind                    cpmdp_kind.
+ *   p_success               GridWorld: probability of the intended move, in [0, 1].
+ *   cell                    host, |S| codes (see above); NULL = all free. Dense: must be NULL.
+ *   reward                  host, |S| state rewards R(s) (finite).
+ *   rank                    dense: R >= 1 terms per action (GridWorld: ignored).
+ *   factors                 dense, host: U[a][r][d] as N_d x N_d row-major blocks,
+ *                           packed in the order a, r, d; U[a][r][d][i][j] is the
+ *                           factor of moving coordinate d from i to j. Rows must be
+ *                           non-negative; P_a is row-stochastic when every row sums
+ *                           to 1 and lambda[a][.] sums to 1 (checked to 1e-9).
+ *   lambda                  dense, host: [A][R] rank weights.
+ *   gamma                   discount in [0, 1]; gamma == 1 needs terminals reachable
+ *                           (value iteration then stops only through tol or max_iter).
+ * The library copies everything it needs; the caller may free these
+ * buffers after cpmdp_build_factors returns.
+ */
+typedef struct {
+    int32_t ndim;
+    int64_t shape[CPMDP_MAX_DIM];
+    int32_t nactions;
+    int32_t kind;
+    double p_success;
+    const uint8_t *cell;
+    const double *reward;
+    int32_t rank;
+    const double *factors;
+    const double *lambda;
+    double gamma;
+} cpmdp_problem;
+
+/* Opaque, library-owned transition model plus its device copies and solver scratch. */
+typedef struct cpmdp_factors cpmdp_factors;
+
+typedef struct {
+    double tol;              /* stop when max |V' - V| over non-obstacle states < tol (default 1e-6) */
+    int32_t max_iter;        /* sweep limit (default 1000, the paper's maxIter) */
+    int32_t certify;         /* 1 (default): after F32 solves, one FP64 sweep of the result gives the
+                                certified residual and the policy (FP64 argmax) */
+    int32_t fused;           /* 1 (default): fused device-resident solver; 0: the plain
+                                unfused FP32/FP64 baseline (one kernel per action, separate max and
+                                residual kernels, residual checked on the host every sweep) */
+    double eval_tol;         /* policy iteration: evaluation stops below this residual
+                                (default: tol for F32, 1e-10 for F64) */
+    int32_t max_eval_iter;   /* policy iteration: evaluation sweep limit per round (default 100000) */
+    int32_t max_rounds;      /* policy iteration: improvement round limit (default 1000) */
+    double timeout_s;        /* limit of every device-side wait (default 2 s) */
+    double *trace;           /* optional device buffer of max_iter doubles: residual of each sweep
+                                (value iteration, fused path only) */
+    int32_t inject_stall;    /* testing aid (default 0): 1 makes one block of the fused GridWorld
+                                solver leave without arriving at its first grid barrier, so the other
+                                blocks' bounded waits run out after timeout_s and the call returns
+                                CPMDP_ETIMEOUT; the device stays usable */
+} cpmdp_solve_opts;
+
+typedef struct {
+    int32_t status;              /* cpmdp_status of the solve */
+    int32_t iterations;          /* sweeps: VI backups, or PI evaluation + improvement sweeps */
+    int32_t rounds;              /* policy iteration improvement rounds (0 for VI) */
+    int32_t eval_sweeps;         /* policy iteration evaluation sweeps (0 for VI) */
+    double residual;             /* last max |V' - V| in working precision */
+    double certified_residual;   /* FP64 max |T(V) - V| of the returned V (-1 if not computed) */
+    double error_bound;          /* certified_residual / (1 - gamma): bound on max |V - V*| (-1 if n/a) */
+    int64_t backups;             /* state-action backups done: |S|*|A| per VI sweep, |S| per evaluation sweep */
+    double elapsed_ms;           /* device time of the solve, CUDA events on the stream */
+} cpmdp_result;
+
+/* Fill *opts with the defaults listed above. */
+void cpmdp_default_opts(cpmdp_solve_opts *opts);
+
+/*
+ * Validate the problem and build its CP factors (background section, Fig. 1;
+ * Definition 3): GridWorld -> per action the 2D-1 rank-1 terms (intended
+ * move, perpendicular slips; 2 terms for D = 1) with banded shift/identity
+ * factors, plus the obstacle and terminal correction, encoded per state;
+ * dense -> the given factors. Copies rewards, codes and factors to device
+ * `device` and allocates the solvers' scratch there (about 8 bytes per
+ * state; dense adds 2 value tensors). device = -1 builds a host-only object
+ * usable by cpmdp_factors_info and cpmdp_components only.
+ * On success *out owns everything; release it with cpmdp_free_factors.
+ * Errors: EINVAL (problem invalid), ENOMEM, ECUDA.
+ */
+cpmdp_status cpmdp_build_factors(const cpmdp_problem *problem, int device, cpmdp_factors **out);
+
+/* Release a factors object and its device memory (NULL is ignored). */
+void cpmdp_free_factors(cpmdp_factors *factors);
+
+/* Sizes of a built model. Any output pointer may be NULL. */
+cpmdp_status cpmdp_factors_info(const cpmdp_factors *factors, int64_t *nstates, int32_t *nactions,
+                                int32_t *rank, int32_t *ndim);
+
+/*
+ * Definition 3, for one (state, action): the successor states s' with
+ * P(s'|s,a) > 0 and their probabilities, expanded on the host from the
+ * factors (successors in increasing index order, duplicates merged).
+ * Writes up to `cap` entries to next[] / prob[] and the full count to
+ * *count. Obstacle and terminal states have no components (count 0).
+ * GridWorld only (dense models: EINVAL). Host memory only.
+ */
+cpmdp_status cpmdp_components(const cpmdp_factors *factors, int64_t state, int32_t action,
+                              int64_t *next, double *prob, int32_t cap, int32_t *count);
+
+/*
+ * One Bellman backup, Eq. 1, fused: E_a[V] for every action from the CP
+ * factors, + R, x gamma, max/argmax over actions, and the infinity-norm
+ * residual.
+ *   V_in, V_out     device, |S| values (float or double per precision); may not alias.
+ *   policy_out      device, |S| uint8 argmax (lowest action on exact ties), or NULL.
+ *   residual_out    device, one double: max |V_out - V_in| over non-obstacle states, or NULL.
+ * Asynchronous on `stream`. Errors: EINVAL, ECUDA.
+ */
+cpmdp_status cpmdp_bellman_backup(const cpmdp_factors *factors, cpmdp_precision precision,
+                                  const void *V_in, void *V_out, uint8_t *policy_out,
+                                  double *residual_out, void *stream);
+
+/*
+ * Value iteration (background section): from V (device, in: warm start or
+ * zeros, out: the last iterate), repeat the fused backup until the residual
+ * falls below opts->tol or opts->max_iter sweeps; the loop, its residual
+ * test and the buffer swaps stay on the device (one persistent launch).
+ * policy_out (device, |S|, may be NULL) receives the greedy policy of the
+ * returned V (FP64 argmax when certify is on). opts may be NULL (defaults);
+ * info may be NULL. Synchronises with `stream` before returning.
+ * Errors: EINVAL, ECUDA, ENOCONV (max_iter reached), ETIMEOUT.
+ */
+cpmdp_status cpmdp_value_iteration(const cpmdp_factors *factors, cpmdp_precision precision,
+                                   void *V, uint8_t *policy_out, const cpmdp_solve_opts *opts,
+                                   cpmdp_result *info, void *stream);
+
+/*
+ * Policy iteration (background section): start from the greedy policy of
+ * the input V (device, in/out), then alternate evaluation of the fixed
+ * policy (backup sweeps without the max, until opts->eval_tol) and greedy
+ * improvement (an action changes only when another beats it by more than
+ * 1e-6 (F32) or 1e-12 (F64) times 1 + |Q|); stop when no action changes.
+ * V receives the value of the final policy, policy (device, |S|, not NULL)
+ * the final policy. Synchronises with `stream` before returning.
+ * Errors: EINVAL, ECUDA, ENOCONV (round or evaluation limit), ETIMEOUT.
+ */
+cpmdp_status cpmdp_policy_iteration(const cpmdp_factors *factors, cpmdp_precision precision,
+                                    void *V, uint8_t *policy, const cpmdp_solve_opts *opts,
+                                    cpmdp_result *info, void *stream);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *cpmdp_last_error(void);
+
+/* Library version string. */
+const char *cpmdp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPMDP_H */

@@ -193,3 +193,26 @@ int oracle_gw_evaluate(int D, const int64_t *shape, double p, double gamma,
     if (res_out) *res_out = res;
     return k;
 }
+
+/*
+ * Q(s, a) for a list of states only (sampled checks at sizes where a full
+ * sweep is too slow): Q_out[i * A + a] for states[i]; obstacles and
+ * terminals get 0. Returns 0.
+ */
+int oracle_gw_q_states(int D, const int64_t *shape, double p, double gamma, const uint8_t *cell,
+                       const double *R, const double *V, const int64_t *states, int64_t n,
+                       double *Q_out) {
+    int64_t S = 1, stride[MAXD];
+    for (int d = D - 1; d >= 0; d--) { stride[d] = S; S *= shape[d]; }
+    int A = 2 * D;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t s = states[i];
+        uint8_t kind = cell ? cell[s] : CELL_FREE;
+        for (int a = 0; a < A; a++) Q_out[i * A + a] = 0.0;
+        if (kind != CELL_FREE) continue;
+        int64_t c[MAXD], rem = s;
+        for (int d = 0; d < D; d++) { c[d] = rem / stride[d]; rem -= c[d] * stride[d]; }
+        for (int a = 0; a < A; a++) Q_out[i * A + a] = q_value(D, shape, stride, p, gamma, cell, R, V, s, c, a);
+    }
+    return 0;
+}

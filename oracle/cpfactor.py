@@ -52,6 +52,9 @@ def _load():
         lib.oracle_gw_evaluate.restype = ctypes.c_int
         lib.oracle_gw_evaluate.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double,
                                            u8p, dp, u8p, dp, ctypes.c_double, ctypes.c_int, dp]
+        lib.oracle_gw_q_states.restype = ctypes.c_int
+        lib.oracle_gw_q_states.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_double,
+                                           u8p, dp, dp, dp, ctypes.c_int64, dp]
         lib.oracle_threads.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -153,3 +156,16 @@ def policy_iteration(gw, eval_tol=1e-12, max_rounds=1000, keep_margin=1e-12, pi0
             break
         pi = newpi
     return V, pi, rounds
+
+
+def q_states(gw, V, states):
+    """Q(s, .) in FP64 for the given flat states only: array (len(states), A)."""
+    lib = _load()
+    shape, cell, R = _prep(gw)
+    V = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(-1))
+    st = np.ascontiguousarray(np.asarray(states, dtype=np.int64).reshape(-1))
+    A = 2 * len(gw.shape)
+    Q = np.empty(st.size * A)
+    lib.oracle_gw_q_states(len(gw.shape), shape.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                           gw.p, gw.gamma, _ptr(cell), _ptr(R), _ptr(V), _ptr(st), st.size, _ptr(Q))
+    return Q.reshape(st.size, A)

@@ -1,0 +1,459 @@
+// C ABI entry points of libcpmdp: problem validation, CP factor
+// construction (host), device upload, and dispatch to the solvers.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+
+#include "internal.h"
+
+namespace cpmdp {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+cpmdp_status cuda_fail(cudaError_t e, const char *what) {
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return CPMDP_ECUDA;
+}
+
+// Makes F.device current for the scope and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+SolveOpts resolve_opts(const cpmdp_solve_opts *o, cpmdp_precision prec) {
+    cpmdp_solve_opts d;
+    cpmdp_default_opts(&d);
+    if (!o) o = &d;
+    SolveOpts r;
+    r.tol = o->tol;
+    r.max_iter = o->max_iter;
+    r.certify = o->certify;
+    r.fused = o->fused;
+    r.eval_tol = o->eval_tol > 0 ? o->eval_tol : (prec == CPMDP_F64 ? 1e-10 : o->tol);
+    r.max_eval_iter = o->max_eval_iter;
+    r.max_rounds = o->max_rounds;
+    r.timeout_s = o->timeout_s;
+    r.trace = o->trace;
+    r.inject_stall = o->inject_stall;
+    return r;
+}
+
+static void free_device(Factors &F) {
+    void *ptrs[] = {F.d_code, F.d_R32, F.d_R64, F.d_cell, F.d_scratch, F.d_q, F.d_ctrl,
+                    F.d_U32, F.d_U64, F.d_Ubf, F.d_lam32, F.d_lam64, F.d_dense_work};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    F.d_code = nullptr; F.d_R32 = nullptr; F.d_R64 = nullptr; F.d_cell = nullptr;
+    F.d_scratch = nullptr; F.d_q = nullptr; F.d_ctrl = nullptr; F.d_U32 = nullptr;
+    F.d_U64 = nullptr; F.d_Ubf = nullptr; F.d_lam32 = nullptr; F.d_lam64 = nullptr;
+    F.d_dense_work = nullptr;
+}
+
+// Build the banded GridWorld factors: the slip weights of the rank-1 terms
+// and, per state, the code of blocked moves (walls: the shift factor's
+// reflecting rows; obstacles: the non-separable correction).
+static void build_gridworld(Factors &F) {
+    const int D = F.ndim;
+    F.rank = D == 1 ? 2 : 2 * D - 1;
+    F.w_move = F.p;
+    F.w_perp = D >= 2 ? (1.0 - F.p) / (2.0 * (D - 1)) : 0.0;
+    F.w_stay = D == 1 ? 1.0 - F.p : 0.0;
+    F.code_bytes = code_bytes_for(D);
+    const int64_t S = F.nstates;
+    F.code.assign((size_t)S, 0u);
+    const uint32_t all_dirs = (uint32_t)((1ull << (2 * D)) - 1);
+    for (int64_t s = 0; s < S; s++) {
+        const uint8_t k = F.cell[(size_t)s];
+        if (k == CPMDP_CELL_OBSTACLE) { F.code[(size_t)s] = all_dirs | (1u << (2 * D)); continue; }
+        if (k == CPMDP_CELL_TERMINAL) { F.code[(size_t)s] = all_dirs | (1u << (2 * D + 1)); continue; }
+        uint32_t c = 0;
+        int64_t rem = s;
+        for (int d = 0; d < D; d++) {
+            const int64_t x = rem / F.stride[d];
+            rem -= x * F.stride[d];
+            for (int sg = 0; sg < 2; sg++) {
+                const int64_t y = x + (sg ? 1 : -1);
+                bool blocked = y < 0 || y >= F.shape[d];
+                if (!blocked) {
+                    const int64_t t = s + (sg ? F.stride[d] : -F.stride[d]);
+                    blocked = F.cell[(size_t)t] == CPMDP_CELL_OBSTACLE;
+                }
+                if (blocked) c |= 1u << (2 * d + sg);
+            }
+        }
+        F.code[(size_t)s] = c;
+    }
+}
+
+static cpmdp_status validate(const cpmdp_problem *p) {
+    if (!p) { set_error("problem is NULL"); return CPMDP_EINVAL; }
+    if (p->ndim < 1 || p->ndim > CPMDP_MAX_DIM) { set_error("ndim %d outside [1, %d]", p->ndim, CPMDP_MAX_DIM); return CPMDP_EINVAL; }
+    double S = 1;
+    for (int d = 0; d < p->ndim; d++) {
+        if (p->shape[d] < 1) { set_error("shape[%d] = %lld < 1", d, (long long)p->shape[d]); return CPMDP_EINVAL; }
+        S *= (double)p->shape[d];
+    }
+    if (S >= 2147483648.0) { set_error("|S| = %.0f exceeds 2^31 - 1", S); return CPMDP_EINVAL; }
+    if (!(p->gamma >= 0.0 && p->gamma <= 1.0)) { set_error("gamma %g outside [0, 1]", p->gamma); return CPMDP_EINVAL; }
+    if (!p->reward) { set_error("reward is NULL"); return CPMDP_EINVAL; }
+    for (int64_t s = 0; s < (int64_t)S; s++)
+        if (!isfinite(p->reward[s])) { set_error("reward[%lld] is not finite", (long long)s); return CPMDP_EINVAL; }
+    if (p->kind == CPMDP_GRIDWORLD) {
+        if (p->nactions != 2 * p->ndim) { set_error("GridWorld needs nactions = 2*ndim = %d (got %d)", 2 * p->ndim, p->nactions); return CPMDP_EINVAL; }
+        if (!(p->p_success >= 0.0 && p->p_success <= 1.0)) { set_error("p_success %g outside [0, 1]", p->p_success); return CPMDP_EINVAL; }
+        if (p->cell)
+            for (int64_t s = 0; s < (int64_t)S; s++)
+                if (p->cell[s] > CPMDP_CELL_TERMINAL) { set_error("cell[%lld] = %d is not 0, 1 or 2", (long long)s, p->cell[s]); return CPMDP_EINVAL; }
+    } else if (p->kind == CPMDP_DENSE_CP) {
+        if (p->nactions < 1 || p->nactions > 64) { set_error("dense nactions %d outside [1, 64]", p->nactions); return CPMDP_EINVAL; }
+        if (p->rank < 1 || p->rank > 64) { set_error("dense rank %d outside [1, 64]", p->rank); return CPMDP_EINVAL; }
+        if (!p->factors || !p->lambda) { set_error("dense factors or lambda is NULL"); return CPMDP_EINVAL; }
+        if (p->cell) { set_error("dense models take no cell codes"); return CPMDP_EINVAL; }
+        for (int d = 0; d < p->ndim; d++)
+            if (p->shape[d] > 4096) { set_error("dense mode size %lld > 4096", (long long)p->shape[d]); return CPMDP_EINVAL; }
+    } else {
+        set_error("unknown kind %d", p->kind);
+        return CPMDP_EINVAL;
+    }
+    return CPMDP_OK;
+}
+
+static cpmdp_status upload(Factors &F) {
+    DeviceGuard g(F.device);
+    if (!g.ok) { set_error("cannot select CUDA device %d", F.device); return CPMDP_ECUDA; }
+    CPMDP_CUDA(cudaDeviceGetAttribute(&F.num_sms, cudaDevAttrMultiProcessorCount, F.device));
+    const size_t S = (size_t)F.nstates;
+    std::vector<float> r32(S);
+    for (size_t s = 0; s < S; s++) r32[s] = (float)F.reward[s];
+    CPMDP_CUDA(cudaMalloc(&F.d_R32, S * sizeof(float)));
+    CPMDP_CUDA(cudaMalloc(&F.d_R64, S * sizeof(double)));
+    CPMDP_CUDA(cudaMemcpy(F.d_R32, r32.data(), S * sizeof(float), cudaMemcpyHostToDevice));
+    CPMDP_CUDA(cudaMemcpy(F.d_R64, F.reward.data(), S * sizeof(double), cudaMemcpyHostToDevice));
+    CPMDP_CUDA(cudaMalloc(&F.d_cell, S));
+    CPMDP_CUDA(cudaMemcpy(F.d_cell, F.cell.data(), S, cudaMemcpyHostToDevice));
+    F.scratch_bytes = S * sizeof(double);
+    CPMDP_CUDA(cudaMalloc(&F.d_scratch, F.scratch_bytes));
+    CPMDP_CUDA(cudaMalloc(&F.d_ctrl, sizeof(Ctrl)));
+    CPMDP_CUDA(cudaMemset(F.d_ctrl, 0, sizeof(Ctrl)));
+    if (F.kind == CPMDP_GRIDWORLD) {
+        const size_t cb = (size_t)F.code_bytes;
+        std::vector<uint8_t> packed(S * cb);
+        for (size_t s = 0; s < S; s++) {
+            const uint32_t c = F.code[s];
+            if (cb == 1) packed[s] = (uint8_t)c;
+            else if (cb == 2) { uint16_t v = (uint16_t)c; memcpy(&packed[2 * s], &v, 2); }
+            else memcpy(&packed[4 * s], &c, 4);
+        }
+        CPMDP_CUDA(cudaMalloc(&F.d_code, S * cb));
+        CPMDP_CUDA(cudaMemcpy(F.d_code, packed.data(), S * cb, cudaMemcpyHostToDevice));
+    } else {
+        cpmdp_status st = dense_prepare(F);
+        if (st != CPMDP_OK) return st;
+    }
+    return CPMDP_OK;
+}
+
+}  // namespace cpmdp
+
+using namespace cpmdp;
+
+extern "C" {
+
+void cpmdp_default_opts(cpmdp_solve_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->tol = 1e-6;
+    o->max_iter = 1000;
+    o->certify = 1;
+    o->fused = 1;
+    o->eval_tol = 0.0;
+    o->max_eval_iter = 100000;
+    o->max_rounds = 1000;
+    o->timeout_s = 2.0;
+    o->trace = nullptr;
+}
+
+const char *cpmdp_last_error(void) { return g_err; }
+
+const char *cpmdp_version(void) { return "cpmdp-gb300 0.1 (sm_103a)"; }
+
+cpmdp_status cpmdp_build_factors(const cpmdp_problem *p, int device, cpmdp_factors **out) {
+    g_err[0] = 0;
+    if (!out) { set_error("out is NULL"); return CPMDP_EINVAL; }
+    *out = nullptr;
+    cpmdp_status st = validate(p);
+    if (st != CPMDP_OK) return st;
+    cpmdp_factors *h = new (std::nothrow) cpmdp_factors();
+    if (!h) { set_error("host allocation failed"); return CPMDP_ENOMEM; }
+    Factors &F = h->f;
+    try {
+        F.device = device;
+        F.kind = p->kind;
+        F.ndim = p->ndim;
+        int64_t S = 1;
+        for (int d = p->ndim - 1; d >= 0; d--) { F.stride[d] = S; S *= p->shape[d]; }
+        for (int d = 0; d < p->ndim; d++) F.shape[d] = p->shape[d];
+        F.nstates = S;
+        F.nactions = p->nactions;
+        F.p = p->p_success;
+        F.gamma = p->gamma;
+        F.reward.assign(p->reward, p->reward + S);
+        if (p->cell) F.cell.assign(p->cell, p->cell + S);
+        else F.cell.assign((size_t)S, (uint8_t)CPMDP_CELL_FREE);
+        if (F.kind == CPMDP_GRIDWORLD) {
+            build_gridworld(F);
+        } else {
+            F.rank = p->rank;
+            int64_t off = 0;
+            for (int a = 0; a < F.nactions; a++)
+                for (int r = 0; r < F.rank; r++)
+                    for (int d = 0; d < F.ndim; d++) { F.factor_off.push_back(off); off += F.shape[d] * F.shape[d]; }
+            F.dense_factors.assign(p->factors, p->factors + off);
+            F.lambda.assign(p->lambda, p->lambda + (size_t)F.nactions * F.rank);
+            for (int64_t i = 0; i < off; i++)
+                if (!(F.dense_factors[(size_t)i] >= 0.0) || !isfinite(F.dense_factors[(size_t)i])) {
+                    set_error("factor entry %lld is negative or not finite", (long long)i);
+                    delete h;
+                    return CPMDP_EINVAL;
+                }
+            for (int a = 0; a < F.nactions; a++) {
+                double ls = 0;
+                for (int r = 0; r < F.rank; r++) {
+                    const double l = F.lambda[(size_t)a * F.rank + r];
+                    if (!(l >= 0.0) || !isfinite(l)) { set_error("lambda[%d][%d] invalid", a, r); delete h; return CPMDP_EINVAL; }
+                    ls += l;
+                    for (int d = 0; d < F.ndim; d++) {
+                        const int64_t n = F.shape[d];
+                        const double *U = &F.dense_factors[(size_t)F.factor_off[((size_t)a * F.rank + r) * F.ndim + d]];
+                        for (int64_t i = 0; i < n; i++) {
+                            double rs = 0;
+                            for (int64_t j = 0; j < n; j++) rs += U[i * n + j];
+                            if (fabs(rs - 1.0) > 1e-9) {
+                                set_error("factor (a=%d, r=%d, d=%d) row %lld sums to %.12g, not 1", a, r, d, (long long)i, rs);
+                                delete h;
+                                return CPMDP_EINVAL;
+                            }
+                        }
+                    }
+                }
+                if (fabs(ls - 1.0) > 1e-9) { set_error("lambda of action %d sums to %.12g, not 1", a, ls); delete h; return CPMDP_EINVAL; }
+            }
+        }
+    } catch (const std::bad_alloc &) {
+        delete h;
+        set_error("host allocation failed");
+        return CPMDP_ENOMEM;
+    }
+    if (device >= 0) {
+        st = upload(F);
+        if (st != CPMDP_OK) {
+            free_device(F);
+            delete h;
+            return st;
+        }
+    }
+    *out = h;
+    return CPMDP_OK;
+}
+
+void cpmdp_free_factors(cpmdp_factors *h) {
+    if (!h) return;
+    if (h->f.device >= 0) {
+        DeviceGuard g(h->f.device);
+        free_device(h->f);
+    }
+    delete h;
+}
+
+cpmdp_status cpmdp_factors_info(const cpmdp_factors *h, int64_t *nstates, int32_t *nactions,
+                                int32_t *rank, int32_t *ndim) {
+    if (!h) { set_error("factors is NULL"); return CPMDP_EINVAL; }
+    if (nstates) *nstates = h->f.nstates;
+    if (nactions) *nactions = h->f.nactions;
+    if (rank) *rank = h->f.rank;
+    if (ndim) *ndim = h->f.ndim;
+    return CPMDP_OK;
+}
+
+cpmdp_status cpmdp_components(const cpmdp_factors *h, int64_t s, int32_t a, int64_t *next, double *prob,
+                              int32_t cap, int32_t *count) {
+    if (!h || !count) { set_error("factors or count is NULL"); return CPMDP_EINVAL; }
+    const Factors &F = h->f;
+    if (F.kind != CPMDP_GRIDWORLD) { set_error("components are listed for GridWorld models only"); return CPMDP_EINVAL; }
+    if (s < 0 || s >= F.nstates || a < 0 || a >= F.nactions) { set_error("state or action out of range"); return CPMDP_EINVAL; }
+    if (cap > 0 && (!next || !prob)) { set_error("next/prob NULL with cap > 0"); return CPMDP_EINVAL; }
+    *count = 0;
+    if (F.cell[(size_t)s] != CPMDP_CELL_FREE) return CPMDP_OK;
+    const int D = F.ndim;
+    const uint32_t code = F.code[(size_t)s];
+    std::map<int64_t, double> acc;
+    auto move = [&](int d, int sg, double w) {
+        const int j = 2 * d + sg;
+        const int64_t t = ((code >> j) & 1u) ? s : s + (sg ? F.stride[d] : -F.stride[d]);
+        acc[t] += w;
+    };
+    const int d0 = a / 2, s0 = a & 1;
+    move(d0, s0, F.w_move);
+    if (D == 1) acc[s] += F.w_stay;
+    else
+        for (int d = 0; d < D; d++)
+            if (d != d0) { move(d, 0, F.w_perp); move(d, 1, F.w_perp); }
+    int n = 0;
+    for (const auto &kv : acc) {
+        if (kv.second <= 0.0) continue;
+        if (n < cap) { next[n] = kv.first; prob[n] = kv.second; }
+        n++;
+    }
+    *count = n;
+    return CPMDP_OK;
+}
+
+static cpmdp_status check_solver_args(const cpmdp_factors *h, cpmdp_precision prec, const void *V) {
+    if (!h) { set_error("factors is NULL"); return CPMDP_EINVAL; }
+    if (h->f.device < 0) { set_error("factors were built host-only (device -1)"); return CPMDP_EINVAL; }
+    if (!V) { set_error("value buffer is NULL"); return CPMDP_EINVAL; }
+    if (prec != CPMDP_F32 && prec != CPMDP_F64 && prec != CPMDP_BF16X3) { set_error("unknown precision %d", (int)prec); return CPMDP_EINVAL; }
+    if (prec == CPMDP_BF16X3 && h->f.kind != CPMDP_DENSE_CP) { set_error("BF16X3 applies to dense CP models only"); return CPMDP_EINVAL; }
+    return CPMDP_OK;
+}
+
+cpmdp_status cpmdp_bellman_backup(const cpmdp_factors *h, cpmdp_precision prec, const void *Vin, void *Vout,
+                                  uint8_t *pi, double *res, void *stream) {
+    g_err[0] = 0;
+    cpmdp_status st = check_solver_args(h, prec, Vin);
+    if (st != CPMDP_OK) return st;
+    if (!Vout) { set_error("V_out is NULL"); return CPMDP_EINVAL; }
+    if (Vin == Vout) { set_error("V_in and V_out must not alias"); return CPMDP_EINVAL; }
+    DeviceGuard g(h->f.device);
+    if (!g.ok) { set_error("cannot select CUDA device %d", h->f.device); return CPMDP_ECUDA; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->f.kind == CPMDP_GRIDWORLD) return banded_backup(h->f, prec, Vin, Vout, pi, res, s);
+    return dense_backup(h->f, prec, Vin, Vout, pi, res, s);
+}
+
+static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, bool pi_mode, void *V,
+                               uint8_t *pi, const cpmdp_solve_opts *opts, cpmdp_result *info, void *stream) {
+    g_err[0] = 0;
+    cpmdp_status st = check_solver_args(h, prec, V);
+    if (st != CPMDP_OK) return st;
+    if (pi_mode && !pi) { set_error("policy iteration needs a policy buffer"); return CPMDP_EINVAL; }
+    const Factors &F = h->f;
+    SolveOpts o = resolve_opts(opts, prec);
+    if (!(o.tol > 0) || o.max_iter < 1 || o.max_eval_iter < 1 || o.max_rounds < 1 || !(o.timeout_s > 0)) {
+        set_error("invalid solve options (tol > 0, max_iter >= 1, timeout_s > 0 required)");
+        return CPMDP_EINVAL;
+    }
+    if (pi_mode && !o.fused) { set_error("the plain baseline implements value iteration only"); return CPMDP_EINVAL; }
+    DeviceGuard g(F.device);
+    if (!g.ok) { set_error("cannot select CUDA device %d", F.device); return CPMDP_ECUDA; }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    CPMDP_CUDA(cudaEventCreate(&e0));
+    CPMDP_CUDA(cudaEventCreate(&e1));
+    CPMDP_CUDA(cudaEventRecord(e0, s));
+    Ctrl hc;
+    memset(&hc, 0, sizeof(hc));
+    bool have_ctrl = false;
+    if (F.kind == CPMDP_GRIDWORLD) {
+        if (o.fused) {
+            st = banded_solve(F, prec, pi_mode, V, pi, o, s);
+        } else {
+            if (!F.d_q) {
+                Factors &Fm = const_cast<Factors &>(F);
+                Fm.q_bytes = (size_t)F.nactions * F.nstates * sizeof(double);
+                CPMDP_CUDA(cudaMalloc(&Fm.d_q, Fm.q_bytes));
+            }
+            st = banded_plain_vi(F, prec, V, pi, o, &hc, s);
+            have_ctrl = true;
+        }
+    } else {
+        st = dense_solve(F, prec, pi_mode, V, pi, o, &hc, s);
+        have_ctrl = true;
+    }
+    if (st != CPMDP_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+    // certifying FP64 sweep (banded F32 / F64 fused path)
+    double *cert = (double *)((char *)F.d_ctrl + offsetof(Ctrl, certify_residual));
+    const bool do_cert = o.certify && F.kind == CPMDP_GRIDWORLD;
+    if (do_cert) {
+        if (prec == CPMDP_F64) {
+            // one FP64 backup into scratch: residual + policy of the returned V
+            uint8_t *pout = pi_mode ? nullptr : pi;
+            st = banded_backup(F, CPMDP_F64, V, F.d_scratch, pout, cert, s);
+        } else {
+            st = banded_certify(F, (const float *)V, pi_mode ? nullptr : pi, cert, s);
+        }
+        if (st != CPMDP_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+    } else if (!pi_mode && pi && F.kind == CPMDP_GRIDWORLD && o.fused) {
+        st = banded_backup(F, prec, V, F.d_scratch, pi, nullptr, s);
+        if (st != CPMDP_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+    }
+    CPMDP_CUDA(cudaEventRecord(e1, s));
+    Ctrl dc;
+    CPMDP_CUDA(cudaMemcpyAsync(&dc, F.d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    CPMDP_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!have_ctrl) {
+        hc = dc;
+    } else {
+        hc.certify_residual = dc.certify_residual;
+    }
+    if (dc.status != 0 && !have_ctrl) {
+        set_error("a device-side wait exceeded %.3g s; results are undefined", o.timeout_s);
+        if (info) { memset(info, 0, sizeof(*info)); info->status = dc.status; }
+        return (cpmdp_status)dc.status;
+    }
+    cpmdp_result r;
+    memset(&r, 0, sizeof(r));
+    r.iterations = hc.iterations;
+    r.rounds = hc.rounds;
+    r.eval_sweeps = hc.eval_sweeps;
+    r.residual = hc.last_residual;
+    r.certified_residual = do_cert ? hc.certify_residual : -1.0;
+    r.error_bound = (do_cert && F.gamma < 1.0) ? hc.certify_residual / (1.0 - F.gamma) : -1.0;
+    r.backups = hc.backups;
+    r.elapsed_ms = ms;
+    r.status = hc.converged ? CPMDP_OK : CPMDP_ENOCONV;
+    if (info) *info = r;
+    if (!hc.converged) {
+        set_error("not converged: %d sweeps, residual %.3g", hc.iterations, hc.last_residual);
+        return CPMDP_ENOCONV;
+    }
+    return CPMDP_OK;
+}
+
+cpmdp_status cpmdp_value_iteration(const cpmdp_factors *h, cpmdp_precision prec, void *V, uint8_t *pi,
+                                   const cpmdp_solve_opts *opts, cpmdp_result *info, void *stream) {
+    return run_solver(h, prec, false, V, pi, opts, info, stream);
+}
+
+cpmdp_status cpmdp_policy_iteration(const cpmdp_factors *h, cpmdp_precision prec, void *V, uint8_t *pi,
+                                    const cpmdp_solve_opts *opts, cpmdp_result *info, void *stream) {
+    return run_solver(h, prec, true, V, pi, opts, info, stream);
+}
+
+}  // extern "C"

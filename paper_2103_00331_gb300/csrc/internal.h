@@ -1,0 +1,129 @@
+// Internal declarations of libcpmdp (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cpmdp.h"
+
+namespace cpmdp {
+
+constexpr int kMaxDim = CPMDP_MAX_DIM;
+
+// Per-state code of the banded GridWorld factors. Bit j (j = 2d + (sigma>0),
+// j < 2D) is set when the unit move in direction j is blocked: it would
+// leave the grid (the shift factor's reflecting row) or enter an obstacle
+// (the non-separable correction). Bit 2D marks an obstacle, bit 2D+1 a
+// terminal state. 8 bits hold D <= 3, 16 bits D <= 7, 32 bits D <= 9.
+inline int code_bytes_for(int D) { return D <= 3 ? 1 : (D <= 7 ? 2 : 4); }
+
+// Device control block of the persistent solvers (zeroed before a launch).
+struct Ctrl {
+    unsigned long long bar[2];     // grid barrier counters (arrivals | flags << 32)
+    int status;                    // 0 ok, CPMDP_ETIMEOUT, ...
+    int iterations;                // sweeps done
+    int rounds;                    // PI improvement rounds
+    int eval_sweeps;               // PI evaluation sweeps
+    int converged;                 // 1 when the stopping rule was met
+    unsigned int changed_total;    // PI: actions changed over all rounds
+    unsigned long long res_slot[3];  // residual of sweep k in slot k % 3 (bits of a double)
+    unsigned int changed_slot[3];  // dense PI: changed actions of the current round
+    double last_residual;          // residual of the last sweep
+    double certify_residual;       // FP64 certifying sweep
+    long long backups;             // state-action backups done
+};
+
+struct Factors {
+    int device = -1;
+    int kind = CPMDP_GRIDWORLD;
+    int ndim = 0;
+    int64_t shape[kMaxDim] = {0};
+    int64_t stride[kMaxDim] = {0};   // element strides, C order
+    int64_t nstates = 0;
+    int nactions = 0;
+    int rank = 0;
+    double p = 1.0;
+    double gamma = 0.9;
+    // GridWorld slip weights: intended move, each perpendicular move, stay (D = 1 only)
+    double w_move = 1.0, w_perp = 0.0, w_stay = 0.0;
+    int code_bytes = 1;
+
+    // host copies
+    std::vector<uint8_t> cell;
+    std::vector<double> reward;
+    std::vector<uint32_t> code;        // banded code per state (host, widened)
+    std::vector<double> dense_factors; // [a][r][d] blocks
+    std::vector<double> lambda;        // [a][r]
+    std::vector<int64_t> factor_off;   // offset of block (a, r, d) in dense_factors
+
+    // device copies
+    void *d_code = nullptr;
+    float *d_R32 = nullptr;
+    double *d_R64 = nullptr;
+    uint8_t *d_cell = nullptr;
+    void *d_scratch = nullptr;         // |S| doubles: ping-pong value buffer
+    size_t scratch_bytes = 0;
+    void *d_q = nullptr;               // plain baseline: |A| x |S| Q values (lazily allocated)
+    size_t q_bytes = 0;
+    Ctrl *d_ctrl = nullptr;
+    int num_sms = 0;
+
+    // dense CP device data
+    float *d_U32 = nullptr;            // factors as float
+    double *d_U64 = nullptr;           // factors as double
+    void *d_Ubf = nullptr;             // bf16 hi/lo split of the factors (tensor-core path)
+    float *d_lam32 = nullptr;
+    double *d_lam64 = nullptr;
+    void *d_dense_work = nullptr;      // dense chain intermediates
+    size_t dense_work_bytes = 0;
+};
+
+// Thread-local error message.
+void set_error(const char *fmt, ...);
+cpmdp_status cuda_fail(cudaError_t e, const char *what);
+
+#define CPMDP_CUDA(call)                                              \
+    do {                                                              \
+        cudaError_t e__ = (call);                                     \
+        if (e__ != cudaSuccess) return ::cpmdp::cuda_fail(e__, #call); \
+    } while (0)
+
+struct SolveOpts {
+    double tol;
+    int max_iter;
+    int certify;
+    int fused;
+    double eval_tol;
+    int max_eval_iter;
+    int max_rounds;
+    double timeout_s;
+    double *trace;
+    int inject_stall;
+};
+SolveOpts resolve_opts(const cpmdp_solve_opts *o, cpmdp_precision prec);
+
+// banded.cu
+cpmdp_status banded_backup(const Factors &F, cpmdp_precision prec, const void *Vin, void *Vout,
+                           uint8_t *pi, double *res, cudaStream_t st);
+cpmdp_status banded_certify(const Factors &F, const float *V, uint8_t *pi, double *res,
+                            cudaStream_t st);
+cpmdp_status banded_solve(const Factors &F, cpmdp_precision prec, bool policy_iteration, void *V,
+                          uint8_t *pi, const SolveOpts &o, cudaStream_t st);
+cpmdp_status banded_plain_vi(const Factors &F, cpmdp_precision prec, void *V, uint8_t *pi,
+                             const SolveOpts &o, Ctrl *host_ctrl, cudaStream_t st);
+
+// dense.cu
+cpmdp_status dense_backup(const Factors &F, cpmdp_precision prec, const void *Vin, void *Vout,
+                          uint8_t *pi, double *res, cudaStream_t st);
+cpmdp_status dense_solve(const Factors &F, cpmdp_precision prec, bool policy_iteration, void *V,
+                         uint8_t *pi, const SolveOpts &o, Ctrl *host_ctrl, cudaStream_t st);
+cpmdp_status dense_prepare(Factors &F);
+
+}  // namespace cpmdp
+
+struct cpmdp_factors {
+    cpmdp::Factors f;
+};

@@ -320,3 +320,15 @@ def test_dense_uniform_and_identity_closed_forms():
     dc = ci.DenseCP(shape=shape, factors=ident, lam=np.ones((3, 1)), reward=R, gamma=gamma)
     V, _, _, _ = OD.value_iteration(dc, tol=1e-13, max_iter=5000)
     np.testing.assert_allclose(V, (R / (1 - gamma)).reshape(-1), atol=1e-11)
+
+
+def test_c_oracle_sampled_q_matches_full(oracle_c):
+    gw = ci.gridworld((5, 6, 7), p=0.7, gamma=0.9, step_reward=-0.04, goal_rewards=[1.0, -1.0],
+                      obstacle_rate=0.1, seed=9)
+    V = ci.random_values(gw.shape, seed=2).reshape(-1)
+    _, _, _, Q = oracle_c.backup(gw, V, want_q=True)
+    states = np.array([0, 17, 101, gw.nstates - 1, 55])
+    Qs = oracle_c.q_states(gw, V, states)
+    free = gw.cell.reshape(-1)[states] == FREE
+    np.testing.assert_array_equal(Qs[free], Q[:, states].T[free])
+    assert np.all(Qs[~free] == 0)
