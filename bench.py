@@ -394,6 +394,39 @@ def hbm_sweep(cp, dev, stream, peak):
             "note": "inputs 1.7 GB > L2; residual fused, policy not written"}
 
 
+def kernel_case(name, reps=3):
+    """Run one kernel workload a few times and exit (for ncu captures):
+    sweep512 = fused FP32 backup of a 512^3 GridWorld; solve64 = fused FP32
+    value iteration of the 64^3 instance."""
+    import torch
+    import paper_2103_00331_gb300 as cp
+    import cpmdp_inputs as ci
+    dev = torch.device("cuda", 0)
+    if name == "sweep512":
+        n = 512
+        gw = ci.gridworld((n, n, n), p=0.8, gamma=0.99, step_reward=-0.01,
+                          goal_rewards=list(ci.uniform(0, 12, 8, 0.5, 1.0)), obstacle_rate=0.05, seed=2)
+        f = cp.build_factors(gw, device=0)
+        Va = torch.zeros(gw.nstates, dtype=torch.float32, device=dev)
+        Vb = torch.zeros_like(Va)
+        res = torch.zeros(1, dtype=torch.float64, device=dev)
+        for _ in range(reps):
+            cp.bellman_backup(f, cp.F32, Va, Vb, None, res)
+            Va, Vb = Vb, Va
+    elif name == "solve64":
+        gw = workload(0)
+        f = cp.build_factors(gw, device=0)
+        V = torch.zeros(gw.nstates, dtype=torch.float32, device=dev)
+        for _ in range(reps):
+            V.zero_()
+            cp.value_iteration(f, cp.F32, V, None, opts=cp.default_opts(max_iter=5000, certify=0))
+    else:
+        raise SystemExit(f"unknown kernel case {name}")
+    torch.cuda.synchronize()
+    print(f"kernel case {name}: ok")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,7 +437,11 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--kernel-case", choices=["sweep512", "solve64"], default=None,
+                    help="run one kernel workload a few times (profiling) and exit")
     args = ap.parse_args()
+    if args.kernel_case:
+        return kernel_case(args.kernel_case)
     rank, world, local, pg = dist_setup(args.gpus)
     if args.impl == "reference":
         rc = run_reference(args, rank, world)
