@@ -222,6 +222,31 @@ cpmdp_status cpmdp_policy_iteration(const cpmdp_factors *factors, cpmdp_precisio
                                     void *V, uint8_t *policy, const cpmdp_solve_opts *opts,
                                     cpmdp_result *info, void *stream);
 
+/*
+ * Value iteration that allocates nothing (the paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, such as code
+ * running under an arena or pool that owns all device memory of the process,
+ * or loops that forbid allocation after start-up).
+ *   ndim, shape      1 <= ndim <= 3, |S| = prod(shape) <= 2,097,152 states; larger
+ *                    grids are rejected with CPMDP_EINVAL.
+ *   p_success, gamma the GridWorld slip model and discount as in cpmdp_problem.
+ *   cell             device, |S| cell codes (0 free, 1 obstacle, 2 terminal), or NULL.
+ *   reward           device, |S| float state rewards.
+ *   V                device, |S| floats: start values in, last iterate out.
+ *   tol, max_iter    stopping rule of cpmdp_value_iteration (FP32 arithmetic).
+ *   iterations_out, residual_out  host, may be NULL: sweeps done, last residual.
+ * All scratch (second value buffer, move codes, barrier words: about 10 MiB)
+ * is one static device array that every GPU loading this library keeps until
+ * the process exits. All calls share it: calls that overlap on the GPU race,
+ * so serialise them. The first call on each device looks up the array's
+ * address and loads its module; make it before any stream capture. Device
+ * waits give up after 2 s (CPMDP_ETIMEOUT). Synchronises with `stream`.
+ */
+cpmdp_status cpmdp_value_iteration_static(int32_t ndim, const int64_t *shape, double p_success,
+                                          double gamma, const uint8_t *cell, const float *reward,
+                                          float *V, double tol, int32_t max_iter,
+                                          int32_t *iterations_out, double *residual_out, void *stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *cpmdp_last_error(void);
 

@@ -85,6 +85,10 @@ def _load():
     lib.cpmdp_policy_iteration.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(SolveOpts),
                                            ctypes.POINTER(Result), vp]
     lib.cpmdp_policy_iteration.restype = ctypes.c_int
+    lib.cpmdp_value_iteration_static.argtypes = [i32, ctypes.POINTER(i64), ctypes.c_double,
+                                                 ctypes.c_double, vp, vp, vp, ctypes.c_double, i32,
+                                                 ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double), vp]
+    lib.cpmdp_value_iteration_static.restype = ctypes.c_int
     lib.cpmdp_last_error.argtypes = []
     lib.cpmdp_last_error.restype = ctypes.c_char_p
     lib.cpmdp_version.argtypes = []
@@ -96,7 +100,8 @@ lib = _load()
 
 EXPORTED = ["cpmdp_default_opts", "cpmdp_build_factors", "cpmdp_free_factors", "cpmdp_factors_info",
             "cpmdp_components", "cpmdp_bellman_backup", "cpmdp_value_iteration",
-            "cpmdp_policy_iteration", "cpmdp_last_error", "cpmdp_version"]
+            "cpmdp_policy_iteration", "cpmdp_value_iteration_static", "cpmdp_last_error",
+            "cpmdp_version"]
 
 
 def last_error() -> str:
@@ -256,3 +261,19 @@ def policy_iteration(f: Factors, precision, V, policy, opts=None, stream=None,
     if st != OK and not (st == ENOCONV and not raise_on_noconv):
         _check(st)
     return res.as_dict()
+
+
+def value_iteration_static(shape, p_success, gamma, cell, reward, V, tol=1e-6, max_iter=1000,
+                           stream=None):
+    """``cpmdp_value_iteration_static``: FP32 GridWorld value iteration with no
+    device allocation (scratch in a fixed static device array). ``cell`` (uint8
+    or None), ``reward`` (float32) and ``V`` (float32) are device tensors.
+    Returns (iterations, residual); raises on any status but OK."""
+    shape = tuple(int(n) for n in shape)
+    sh = (ctypes.c_int64 * len(shape))(*shape)
+    it, res = ctypes.c_int32(), ctypes.c_double()
+    _check(lib.cpmdp_value_iteration_static(len(shape), sh, float(p_success), float(gamma),
+                                            _ptr(cell), _ptr(reward), _ptr(V), float(tol),
+                                            int(max_iter), ctypes.byref(it), ctypes.byref(res),
+                                            _stream(stream)))
+    return it.value, res.value
