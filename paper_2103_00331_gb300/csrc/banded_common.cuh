@@ -1,0 +1,425 @@
+// Device code shared by the banded (GridWorld) kernels.
+//
+// For a GridWorld every rank-1 CP term of an action is an outer product of
+// identity factors and one shift factor (a unit move along one dimension,
+// reflecting at the walls). E_a[V](s) therefore needs only the 2D face
+// neighbours of s: with N_j the value reached by the unit move in direction
+// j (V(s) itself when the move is blocked by a wall or an obstacle, the
+// non-separable correction) and P_d = N_{2d} + N_{2d+1},
+//     E_{(d,sigma)} = w_move N_{(d,sigma)} + w_perp sum_{d' != d} P_{d'} + w_stay V(s)
+// (w_move = p, w_perp = (1-p)/(2(D-1)), w_stay = 1-p only for D = 1), and
+// Eq. 1 gives Q_a = R(s) + gamma E_a, V'(s) = max_a Q_a. Work is
+// O(|S| |C(s)| |A|) as in the paper's complexity section, with the pair
+// sums shared by all actions.
+//
+// Layout: V, R, the per-state code and the policy are flat C-order arrays
+// (Definition 2). A thread takes VEC consecutive states of one row of the
+// last (contiguous) dimension: one 16-byte load per row neighbour, two
+// scalar halo loads, the codes as one packed load.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace cpmdp {
+
+template <int D> struct CodeType { using type = uint32_t; };
+template <> struct CodeType<1> { using type = uint8_t; };
+template <> struct CodeType<2> { using type = uint8_t; };
+template <> struct CodeType<3> { using type = uint8_t; };
+template <> struct CodeType<4> { using type = uint16_t; };
+template <> struct CodeType<5> { using type = uint16_t; };
+template <> struct CodeType<6> { using type = uint16_t; };
+template <> struct CodeType<7> { using type = uint16_t; };
+
+struct BandArgs {
+    int nstates;
+    int nlast;
+    int stride[kMaxDim];
+    double w_move, w_perp, w_stay, gamma;
+    const void *code;
+    const float *R32;
+    const double *R64;
+};
+
+enum Mode : int { M_VI = 0, M_EVAL = 1, M_IMPROVE = 2, M_GREEDY = 3 };
+
+template <typename T, int VEC> struct alignas(sizeof(T) * VEC) VPack { T v[VEC]; };
+
+template <typename T, int VEC>
+__device__ __forceinline__ void load_pack(const T *p, T (&out)[VEC]) {
+    VPack<T, VEC> pk = *reinterpret_cast<const VPack<T, VEC> *>(p);
+#pragma unroll
+    for (int k = 0; k < VEC; k++) out[k] = pk.v[k];
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void store_pack(T *p, const T (&in)[VEC]) {
+    VPack<T, VEC> pk;
+#pragma unroll
+    for (int k = 0; k < VEC; k++) pk.v[k] = in[k];
+    *reinterpret_cast<VPack<T, VEC> *>(p) = pk;
+}
+
+template <typename TA> __device__ __forceinline__ TA rew(const BandArgs &a, int s);
+template <> __device__ __forceinline__ float rew<float>(const BandArgs &a, int s) { return a.R32[s]; }
+template <> __device__ __forceinline__ double rew<double>(const BandArgs &a, int s) { return a.R64[s]; }
+
+// One row segment: states s0 .. s0+VEC-1 of a row of the last dimension.
+// load() issues every global load of the segment at once: the neighbour
+// addresses are clamped into [0, |S|) arithmetically instead of being chosen
+// from the per-state code, so no load waits for another. A clamped address
+// only differs from the true neighbour where that neighbour does not exist,
+// and there the code marks the move as blocked and V(s) is used instead.
+template <typename T, typename TA, int D, int VEC>
+struct Segment {
+    using C = typename CodeType<D>::type;
+    static constexpr int NB = 2 * D;
+    static constexpr unsigned OBST = 1u << (2 * D);
+    static constexpr unsigned TERM = 1u << (2 * D + 1);
+    C code[VEC];
+    T vs[VEC];
+    T rows[D > 1 ? 2 * (D - 1) : 1][VEC];
+    T halo_m, halo_p;
+    TA r[VEC];
+    uint8_t act[VEC];
+
+    template <int MODE>
+    __device__ __forceinline__ void load(const BandArgs &a, const T *V, const uint8_t *pi, int s0) {
+        load_pack<C, VEC>(static_cast<const C *>(a.code) + s0, code);
+        load_pack<T, VEC>(V + s0, vs);
+        const int last = a.nstates - VEC;
+#pragma unroll
+        for (int d = 0; d < D - 1; d++) {
+            int lo = s0 - a.stride[d], hi = s0 + a.stride[d];
+            lo = lo < 0 ? 0 : lo;
+            hi = hi > last ? last : hi;
+            load_pack<T, VEC>(V + lo, rows[2 * d]);
+            load_pack<T, VEC>(V + hi, rows[2 * d + 1]);
+        }
+        halo_m = V[s0 > 0 ? s0 - 1 : 0];
+        halo_p = V[s0 + VEC < a.nstates ? s0 + VEC : a.nstates - 1];
+#pragma unroll
+        for (int k = 0; k < VEC; k++) r[k] = rew<TA>(a, s0 + k);
+        if (MODE == M_EVAL || MODE == M_IMPROVE) {
+#pragma unroll
+            for (int k = 0; k < VEC; k++) act[k] = pi[s0 + k];
+        }
+    }
+
+    // Neighbour values with the blocked moves replaced by V(s).
+    __device__ __forceinline__ void neighbours(TA (&self)[VEC], TA (&nb)[NB][VEC]) const {
+#pragma unroll
+        for (int k = 0; k < VEC; k++) self[k] = (TA)vs[k];
+#pragma unroll
+        for (int j = 0; j < 2 * (D - 1); j++)
+#pragma unroll
+            for (int k = 0; k < VEC; k++) nb[j][k] = ((code[k] >> j) & 1u) ? self[k] : (TA)rows[j][k];
+        const int jm = 2 * (D - 1), jp = jm + 1;
+#pragma unroll
+        for (int k = 0; k < VEC; k++) {
+            const TA left = (k == 0) ? (TA)halo_m : self[k > 0 ? k - 1 : 0];
+            const TA right = (k == VEC - 1) ? (TA)halo_p : self[k < VEC - 1 ? k + 1 : 0];
+            nb[jm][k] = ((code[k] >> jm) & 1u) ? self[k] : left;
+            nb[jp][k] = ((code[k] >> jp) & 1u) ? self[k] : right;
+        }
+    }
+
+    // perp[d] = sum over d' != d of the pair sums (prefix + suffix sums).
+    __device__ __forceinline__ static void perp_sums(const TA (&nb)[NB][VEC], int k, TA (&perp)[D]) {
+        TA P[D];
+#pragma unroll
+        for (int d = 0; d < D; d++) P[d] = nb[2 * d][k] + nb[2 * d + 1][k];
+        TA acc = 0;
+#pragma unroll
+        for (int d = 0; d < D; d++) { perp[d] = acc; acc += P[d]; }
+        acc = 0;
+#pragma unroll
+        for (int d = D - 1; d >= 0; d--) { perp[d] += acc; acc += P[d]; }
+    }
+
+    // Value-iteration backup. Because w_move, w_perp and gamma are >= 0 and
+    // rounding is monotone, max_sigma E_(d,sigma) is E at max(N_{d,-}, N_{d,+})
+    // and max_a fl(R + gamma E_a) = fl(R + gamma max_a E_a): the same values
+    // (and the same lowest-index argmax) as evaluating every action, with D
+    // instead of 2D expectation chains. Returns max |V' - V| over
+    // non-obstacle states; writes V' to W (if not null) and the policy to pi
+    // (WITH_PI).
+    template <bool WITH_PI>
+    __device__ __forceinline__ TA finish_vi(const BandArgs &a, T *W, uint8_t *pi, int s0) const {
+        TA self[VEC], nb[NB][VEC];
+        neighbours(self, nb);
+        const TA wm = (TA)a.w_move, wp = (TA)a.w_perp, wst = (TA)a.w_stay, g = (TA)a.gamma;
+        TA out[VEC];
+        TA res = 0;
+#pragma unroll
+        for (int k = 0; k < VEC; k++) {
+            const unsigned c = code[k];
+            TA perp[D];
+            perp_sums(nb, k, perp);
+            const TA stay = (D == 1) ? wst * self[k] : (TA)0;
+            TA bestE = 0;
+            int arg = 0;
+#pragma unroll
+            for (int d = 0; d < D; d++) {
+                const bool up = nb[2 * d + 1][k] > nb[2 * d][k];
+                const TA m = up ? nb[2 * d + 1][k] : nb[2 * d][k];
+                const TA e = wm * m + wp * perp[d] + stay;
+                if (d == 0 || e > bestE) { bestE = e; arg = 2 * d + (up ? 1 : 0); }
+            }
+            TA v = r[k] + g * bestE;
+            if (c & TERM) v = r[k];
+            if (c & OBST) v = 0;
+            out[k] = v;
+            if (WITH_PI) pi[s0 + k] = (c & (OBST | TERM)) ? (uint8_t)255 : (uint8_t)arg;
+            if (!(c & OBST)) {
+                const TA dv = v > self[k] ? v - self[k] : self[k] - v;
+                res = dv > res ? dv : res;
+            }
+        }
+        if (W) {
+            T o[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; k++) o[k] = (T)out[k];
+            store_pack<T, VEC>(W + s0, o);
+        }
+        return res;
+    }
+
+    // Policy-iteration sweeps: EVAL (V' = Q of the fixed action, returns the
+    // residual), IMPROVE (switch to the argmax when it beats the current
+    // action by more than margin (1 + |Q|), count switches) and GREEDY
+    // (policy = argmax, lowest index on ties).
+    template <int MODE>
+    __device__ __forceinline__ TA finish_pi(const BandArgs &a, T *W, uint8_t *pi, TA margin, int s0,
+                                            unsigned &changed) const {
+        TA self[VEC], nb[NB][VEC];
+        neighbours(self, nb);
+        const TA wm = (TA)a.w_move, wp = (TA)a.w_perp, wst = (TA)a.w_stay, g = (TA)a.gamma;
+        TA out[VEC];
+        TA res = 0;
+#pragma unroll
+        for (int k = 0; k < VEC; k++) {
+            const int s = s0 + k;
+            const unsigned c = code[k];
+            const TA rk = r[k];
+            TA perp[D];
+            perp_sums(nb, k, perp);
+            const TA stay = wst * self[k];
+            TA v = self[k];
+            if (MODE == M_EVAL) {
+                const int ak = act[k];
+                TA nbv = nb[0][k], pv = perp[0];
+#pragma unroll
+                for (int j = 1; j < NB; j++)
+                    if (ak == j) { nbv = nb[j][k]; pv = perp[j / 2]; }
+                v = rk + g * (wm * nbv + wp * pv + stay);
+                if (c & TERM) v = rk;
+                if (c & OBST) v = 0;
+                if (!(c & OBST)) {
+                    const TA dv = v > self[k] ? v - self[k] : self[k] - v;
+                    res = dv > res ? dv : res;
+                }
+            } else if (!(c & (OBST | TERM))) {
+                TA best = rk + g * (wm * nb[0][k] + wp * perp[0] + stay);
+                int arg = 0;
+                TA qold = best;
+                const int old = (MODE == M_IMPROVE) ? (int)act[k] : 0;
+#pragma unroll
+                for (int j = 1; j < NB; j++) {
+                    const TA q = rk + g * (wm * nb[j][k] + wp * perp[j / 2] + stay);
+                    if (q > best) { best = q; arg = j; }
+                    if (j == old) qold = q;
+                }
+                if (MODE == M_IMPROVE) {
+                    const TA thr = margin * ((TA)1 + (qold < 0 ? -qold : qold));
+                    if (arg != old && best > qold + thr) { pi[s] = (uint8_t)arg; changed++; }
+                } else {
+                    pi[s] = (uint8_t)arg;
+                }
+            } else if (MODE == M_GREEDY) {
+                pi[s] = 255;
+            }
+            out[k] = v;
+        }
+        if (MODE == M_EVAL) {
+            T o[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; k++) o[k] = (T)out[k];
+            store_pack<T, VEC>(W + s0, o);
+        }
+        return res;
+    }
+};
+
+// All segments of one sweep, grid-stride, two segments in flight per thread.
+// With a grid of co-resident blocks, the states being worked on at any time
+// form one compact window, so the row neighbours one plane away are still in
+// L2 when their own window comes.
+template <typename T, typename TA, int D, int VEC, int MODE, bool WITH_PI>
+__device__ __forceinline__ TA sweep_all(const BandArgs &a, const T *V, T *W, uint8_t *pi, TA margin,
+                                        unsigned &changed) {
+    const int nitems = a.nstates / VEC;
+    const int step = gridDim.x * blockDim.x;
+    TA res = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nitems; i += 2 * step) {
+        Segment<T, TA, D, VEC> s0, s1;
+        const bool two = i + step < nitems;
+        s0.template load<MODE>(a, V, pi, i * VEC);
+        if (two) s1.template load<MODE>(a, V, pi, (i + step) * VEC);
+        TA r;
+        if (MODE == M_VI) r = s0.template finish_vi<WITH_PI>(a, W, pi, i * VEC);
+        else r = s0.template finish_pi<MODE>(a, W, pi, margin, i * VEC, changed);
+        res = r > res ? r : res;
+        if (two) {
+            if (MODE == M_VI) r = s1.template finish_vi<WITH_PI>(a, W, pi, (i + step) * VEC);
+            else r = s1.template finish_pi<MODE>(a, W, pi, margin, (i + step) * VEC, changed);
+            res = r > res ? r : res;
+        }
+    }
+    return res;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ unsigned warp_sum(unsigned v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// Block-wide max (result valid in thread 0). blockDim must be a multiple of 32.
+__device__ __forceinline__ double block_max(double v, double *sh) {
+    v = warp_max(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+        v = warp_max(v);
+    }
+    __syncthreads();
+    return v;
+}
+
+__device__ __forceinline__ unsigned block_sum(unsigned v, unsigned *sh) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0u;
+        v = warp_sum(v);
+    }
+    __syncthreads();
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void red_add_release(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of a co-resident (cooperative) grid that also counts
+// how many blocks raised `flag` (thread 0's value) in the step it closes.
+// Barrier number n uses counter bar[n % 2]: the low 32 bits count arrivals
+// ((n/2 + 1) * nblocks once everyone has arrived), the high 32 bits count
+// raised flags. A block cannot reach barrier n+2 before every block has left
+// barrier n+1, so the value read when barrier n completes holds exactly the
+// arrivals up to barrier n; the flags of step n are its high part minus the
+// high part seen at barrier n-2 (prev0 / prev1 for even / odd n, kept by
+// thread 0). Every wait gives up after timeout_ns or when another block has
+// recorded a status: returns -1 (CPMDP_ETIMEOUT stored in the status word).
+// stall: testing aid, this block leaves without arriving.
+__device__ __forceinline__ long long grid_sync_count(Ctrl *c, int n, unsigned nblocks, int flag,
+                                                     unsigned long long timeout_ns, unsigned long long &prev0,
+                                                     unsigned long long &prev1, bool stall) {
+    __shared__ long long result;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        result = 0;
+        if (stall) {
+            if (nblocks == 1) atomicCAS(&c->status, 0, (int)CPMDP_ETIMEOUT);
+            result = -1;
+        } else {
+            unsigned long long *ctr = &c->bar[n & 1];
+            red_add_release(ctr, 1ull | ((unsigned long long)(flag != 0) << 32));
+            const unsigned long long target = (unsigned long long)(n / 2 + 1) * nblocks;
+            unsigned long long v = ld_acquire(ctr);
+            if ((v & 0xFFFFFFFFull) < target) {
+                const unsigned long long t0 = global_ns();
+                unsigned spins = 0;
+                do {
+                    __nanosleep(32);
+                    v = ld_acquire(ctr);
+                    if ((++spins & 15u) == 0 && (v & 0xFFFFFFFFull) < target) {
+                        if (*(volatile int *)&c->status != 0) { result = -1; break; }
+                        if (global_ns() - t0 > timeout_ns) {
+                            atomicCAS(&c->status, 0, (int)CPMDP_ETIMEOUT);
+                            result = -1;
+                            break;
+                        }
+                    }
+                } while ((v & 0xFFFFFFFFull) < target);
+            }
+            if (result == 0) {
+                const unsigned long long hi = v >> 32;
+                const unsigned long long prev = (n & 1) ? prev1 : prev0;
+                result = (long long)(hi - prev);
+                if (n & 1) prev1 = hi;
+                else prev0 = hi;
+            }
+        }
+    }
+    __syncthreads();
+    return result;
+}
+
+struct SolveParams {
+    int max_iter;
+    int max_eval_iter;
+    int max_rounds;
+    double tol;
+    double eval_tol;
+    double margin;
+    unsigned long long timeout_ns;
+    int nactions;
+    int inject_stall;
+};
+
+BandArgs make_band_args(const Factors &F);
+int band_pick_vec(const Factors &F, size_t elem, const void *p0, const void *p1);
+
+#define CPMDP_DISPATCH_D(D_, ...)                             \
+    switch (D_) {                                             \
+        case 1: { constexpr int DD = 1; __VA_ARGS__; } break; \
+        case 2: { constexpr int DD = 2; __VA_ARGS__; } break; \
+        case 3: { constexpr int DD = 3; __VA_ARGS__; } break; \
+        case 4: { constexpr int DD = 4; __VA_ARGS__; } break; \
+        case 5: { constexpr int DD = 5; __VA_ARGS__; } break; \
+        case 6: { constexpr int DD = 6; __VA_ARGS__; } break; \
+        case 7: { constexpr int DD = 7; __VA_ARGS__; } break; \
+        case 8: { constexpr int DD = 8; __VA_ARGS__; } break; \
+        case 9: { constexpr int DD = 9; __VA_ARGS__; } break; \
+        default: break;                                       \
+    }
+
+}  // namespace cpmdp

@@ -1,0 +1,215 @@
+// Device-resident value iteration and policy iteration for GridWorld
+// factors (background section: value iteration repeats Eq. 1 until it
+// converges; policy iteration alternates evaluation of a fixed policy with
+// greedy improvement until no action changes).
+//
+// Each solve is one cooperative launch of co-resident blocks. Every sweep
+// ends in a grid barrier whose arrival atomic also reports whether the
+// block's residual is still >= tol (VI, evaluation) or whether the block
+// changed an action (improvement): every block learns the stopping decision
+// from the barrier itself, with no extra round trip. The residual value goes
+// to res_slot[k % 3] by atomic max (slot k+1 is cleared by block 0 during
+// sweep k, after every block has passed the barrier of sweep k-1, so nobody
+// still reads it); it is read for the trace and at the end. The host reads
+// back the control block once, after the launch.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "banded_common.cuh"
+
+namespace cpmdp {
+
+template <typename T, int D, int VEC>
+__global__ void __launch_bounds__(256) solve_vi_kernel(BandArgs a, T *V, T *Wbuf, SolveParams sp, Ctrl *ctrl,
+                                                       double *trace) {
+    typedef T TA;
+    __shared__ double shd[32];
+    const unsigned nb = gridDim.x;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const bool stall = sp.inject_stall && blockIdx.x == 0;
+    T *cur = V, *nxt = Wbuf;
+    int k = 0, converged = 0;
+    unsigned dummy = 0;
+    unsigned long long ph0 = 0ull, ph1 = 0ull;
+    while (k < sp.max_iter) {
+        const TA r = sweep_all<T, TA, D, VEC, M_VI, false>(a, cur, nxt, nullptr, (TA)0, dummy);
+        const double m = block_max((double)r, shd);
+        int flag = 0;
+        if (threadIdx.x == 0) {
+            if (m > 0.0) atomicMax(&ctrl->res_slot[k % 3], (unsigned long long)__double_as_longlong(m));
+            flag = !(m < sp.tol);
+        }
+        if (lead) ctrl->res_slot[(k + 1) % 3] = 0ull;
+        const long long open = grid_sync_count(ctrl, k, nb, flag, sp.timeout_ns, ph0, ph1, stall && k == 0);
+        if (open < 0) return;
+        if (trace && lead)
+            trace[k] = __longlong_as_double((long long)*(volatile unsigned long long *)&ctrl->res_slot[k % 3]);
+        k++;
+        T *t = cur; cur = nxt; nxt = t;
+        if (open == 0) { converged = 1; break; }
+    }
+    if (cur != V) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nstates; i += gridDim.x * blockDim.x) V[i] = cur[i];
+    }
+    if (lead) {
+        ctrl->iterations = k;
+        ctrl->converged = converged;
+        ctrl->last_residual =
+            k > 0 ? __longlong_as_double((long long)*(volatile unsigned long long *)&ctrl->res_slot[(k - 1) % 3]) : 0.0;
+        ctrl->backups = (long long)k * a.nstates * sp.nactions;
+    }
+}
+
+template <typename T, int D, int VEC>
+__global__ void __launch_bounds__(256) solve_pi_kernel(BandArgs a, T *V, T *Wbuf, uint8_t *pi, SolveParams sp,
+                                                       Ctrl *ctrl) {
+    typedef T TA;
+    __shared__ double shd[32];
+    __shared__ unsigned shu[32];
+    const unsigned nb = gridDim.x;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    const bool stall = sp.inject_stall && blockIdx.x == 0;
+    T *cur = V, *nxt = Wbuf;
+    int ks = 0, total = 0, nbar = 0, round = 0, evals = 0, converged = 0;
+    long long backups = 0;
+    unsigned dummy = 0;
+    unsigned long long ph0 = 0ull, ph1 = 0ull;
+
+    // initial policy: greedy with respect to the input V
+    sweep_all<T, TA, D, VEC, M_GREEDY, true>(a, cur, nullptr, pi, (TA)0, dummy);
+    if (grid_sync_count(ctrl, nbar++, nb, 0, sp.timeout_ns, ph0, ph1, stall) < 0) return;
+    total++;
+    backups += (long long)a.nstates * sp.nactions;
+    while (round < sp.max_rounds) {
+        int e = 0, eval_ok = 0;
+        while (e < sp.max_eval_iter) {
+            const TA r = sweep_all<T, TA, D, VEC, M_EVAL, true>(a, cur, nxt, pi, (TA)0, dummy);
+            const double m = block_max((double)r, shd);
+            int flag = 0;
+            if (threadIdx.x == 0) {
+                if (m > 0.0) atomicMax(&ctrl->res_slot[ks % 3], (unsigned long long)__double_as_longlong(m));
+                flag = !(m < sp.eval_tol);
+            }
+            if (lead) ctrl->res_slot[(ks + 1) % 3] = 0ull;
+            const long long open = grid_sync_count(ctrl, nbar++, nb, flag, sp.timeout_ns, ph0, ph1, false);
+            if (open < 0) return;
+            ks++; e++; total++;
+            backups += a.nstates;
+            T *t = cur; cur = nxt; nxt = t;
+            if (open == 0) { eval_ok = 1; break; }
+        }
+        evals += e;
+        unsigned changed = 0;
+        sweep_all<T, TA, D, VEC, M_IMPROVE, true>(a, cur, nullptr, pi, (TA)sp.margin, changed);
+        const unsigned c = block_sum(changed, shu);
+        if (threadIdx.x == 0 && c) atomicAdd(&ctrl->changed_total, c);
+        const long long moved = grid_sync_count(ctrl, nbar++, nb, threadIdx.x == 0 && c > 0, sp.timeout_ns,
+                                                ph0, ph1, false);
+        if (moved < 0) return;
+        total++;
+        round++;
+        backups += (long long)a.nstates * sp.nactions;
+        if (moved == 0) { converged = eval_ok; break; }
+        if (!eval_ok) break;
+    }
+    if (cur != V) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nstates; i += gridDim.x * blockDim.x) V[i] = cur[i];
+    }
+    if (lead) {
+        ctrl->rounds = round;
+        ctrl->eval_sweeps = evals;
+        ctrl->iterations = total;
+        ctrl->converged = converged;
+        ctrl->last_residual =
+            ks > 0 ? __longlong_as_double((long long)*(volatile unsigned long long *)&ctrl->res_slot[(ks - 1) % 3]) : 0.0;
+        ctrl->backups = backups;
+    }
+}
+
+template <typename K>
+static cudaError_t coop_grid(K kern, const Factors &F, int nitems, int &cache, int &grid) {
+    if (cache <= 0) {
+        int o = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 256, 0);
+        if (e != cudaSuccess) return e;
+        cache = o;
+    }
+    // Barrier cost grows with the number of blocks: use one block per SM as
+    // long as two segments per thread cover the grid, more only for large
+    // (bandwidth-bound) grids, never more than can be co-resident.
+    const int cap = cache * F.num_sms;
+    if (cap < 1) return cudaErrorCooperativeLaunchTooLarge;
+    grid = (nitems + 511) / 512;
+    if (grid < F.num_sms) grid = F.num_sms;
+    if (grid > (nitems + 255) / 256) grid = (nitems + 255) / 256;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    return cudaSuccess;
+}
+
+template <typename T, int D, int VEC>
+static cudaError_t launch_vi(const Factors &F, T *V, T *W, const SolveParams &sp, double *trace, cudaStream_t st) {
+    static int occ = 0;
+    BandArgs a = make_band_args(F);
+    auto kern = solve_vi_kernel<T, D, VEC>;
+    int grid = 1;
+    cudaError_t e = coop_grid(kern, F, (int)(F.nstates / VEC), occ, grid);
+    if (e != cudaSuccess) return e;
+    Ctrl *ctrl = F.d_ctrl;
+    SolveParams spc = sp;
+    void *args[] = {(void *)&a, (void *)&V, (void *)&W, (void *)&spc, (void *)&ctrl, (void *)&trace};
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(256), args, 0, st);
+}
+
+template <typename T, int D, int VEC>
+static cudaError_t launch_pi(const Factors &F, T *V, T *W, uint8_t *pi, const SolveParams &sp, cudaStream_t st) {
+    static int occ = 0;
+    BandArgs a = make_band_args(F);
+    auto kern = solve_pi_kernel<T, D, VEC>;
+    int grid = 1;
+    cudaError_t e = coop_grid(kern, F, (int)(F.nstates / VEC), occ, grid);
+    if (e != cudaSuccess) return e;
+    Ctrl *ctrl = F.d_ctrl;
+    SolveParams spc = sp;
+    void *args[] = {(void *)&a, (void *)&V, (void *)&W, (void *)&pi, (void *)&spc, (void *)&ctrl};
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(256), args, 0, st);
+}
+
+template <typename T>
+static cudaError_t solve_t(const Factors &F, bool pim, T *V, uint8_t *pi, const SolveParams &sp, double *trace,
+                           cudaStream_t st) {
+    T *W = (T *)F.d_scratch;
+    const int vec = band_pick_vec(F, sizeof(T), V, W);
+    constexpr int V2 = (int)(16 / sizeof(T));
+    cudaError_t e = cudaErrorInvalidValue;
+    if (pim) {
+        if (vec == 1) { CPMDP_DISPATCH_D(F.ndim, e = (launch_pi<T, DD, 1>(F, V, W, pi, sp, st))); }
+        else { CPMDP_DISPATCH_D(F.ndim, e = (launch_pi<T, DD, V2>(F, V, W, pi, sp, st))); }
+    } else {
+        if (vec == 1) { CPMDP_DISPATCH_D(F.ndim, e = (launch_vi<T, DD, 1>(F, V, W, sp, trace, st))); }
+        else { CPMDP_DISPATCH_D(F.ndim, e = (launch_vi<T, DD, V2>(F, V, W, sp, trace, st))); }
+    }
+    return e;
+}
+
+cpmdp_status banded_solve(const Factors &F, cpmdp_precision prec, bool policy_iteration, void *V,
+                          uint8_t *pi, const SolveOpts &o, cudaStream_t st) {
+    SolveParams sp;
+    sp.max_iter = o.max_iter;
+    sp.max_eval_iter = o.max_eval_iter;
+    sp.max_rounds = o.max_rounds;
+    sp.tol = o.tol;
+    sp.eval_tol = o.eval_tol;
+    sp.margin = prec == CPMDP_F64 ? 1e-12 : 1e-6;
+    sp.timeout_ns = (unsigned long long)(o.timeout_s * 1e9);
+    sp.nactions = F.nactions;
+    sp.inject_stall = o.inject_stall;
+    CPMDP_CUDA(cudaMemsetAsync(F.d_ctrl, 0, sizeof(Ctrl), st));
+    cudaError_t e;
+    if (prec == CPMDP_F64) e = solve_t<double>(F, policy_iteration, (double *)V, pi, sp, o.trace, st);
+    else e = solve_t<float>(F, policy_iteration, (float *)V, pi, sp, o.trace, st);
+    CPMDP_CUDA(e);
+    return CPMDP_OK;
+}
+
+}  // namespace cpmdp
