@@ -428,6 +428,23 @@ def kernel_case(name, reps=3):
         for _ in range(reps):
             cp.bellman_backup(f, cp.F32, Va, Vb, None, res)
             Va, Vb = Vb, Va
+    elif name == "dense64tc":
+        dc = ci.config_dense_4d(side=64, seed=0)
+        f = cp.build_factors(dc, device=0)
+        Va = torch.as_tensor(ci.random_values(dc.shape, seed=2).reshape(-1).astype(np.float32)).to(dev)
+        Vb = torch.empty_like(Va)
+        res = torch.zeros(1, dtype=torch.float64, device=dev)
+        for i in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            cp.bellman_backup(f, cp.BF16X3, Va, Vb, None, res)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            flops = 2.0 * 64 * 4 * dc.nstates * dc.nactions * dc.rank
+            print(f"dense 64^4 BF16x3 tcgen05 sweep: {ms:.3f} ms, {flops / ms / 1e9:.1f} TFLOP/s (FP32-equivalent), "
+                  f"{3 * flops / ms / 1e9:.1f} TFLOP/s bf16")
+            Va, Vb = Vb, Va
     elif name == "dense64":
         dc = ci.config_dense_4d(side=64, seed=0)
         f = cp.build_factors(dc, device=0)
@@ -470,7 +487,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--kernel-case", choices=["sweep512", "solve64", "pi64", "dense64"], default=None,
+    ap.add_argument("--kernel-case", choices=["sweep512", "solve64", "pi64", "dense64", "dense64tc"], default=None,
                     help="run one kernel workload a few times (profiling) and exit")
     args = ap.parse_args()
     if args.kernel_case:

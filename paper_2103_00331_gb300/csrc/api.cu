@@ -62,13 +62,15 @@ SolveOpts resolve_opts(const cpmdp_solve_opts *o, cpmdp_precision prec) {
 
 static void free_device(Factors &F) {
     void *ptrs[] = {F.d_code, F.d_R32, F.d_R64, F.d_cell, F.d_scratch, F.d_q, F.d_ctrl,
-                    F.d_U32, F.d_U64, F.d_Ubf, F.d_lam32, F.d_lam64, F.d_dense_work};
+                    F.d_U32, F.d_U64, F.d_Ubf, F.d_lam32, F.d_lam64, F.d_dense_work, F.d_Vd,
+                    F.d_RB, F.d_T, F.d_EB, F.d_Vbase, F.d_tc_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     F.d_code = nullptr; F.d_R32 = nullptr; F.d_R64 = nullptr; F.d_cell = nullptr;
     F.d_scratch = nullptr; F.d_q = nullptr; F.d_ctrl = nullptr; F.d_U32 = nullptr;
     F.d_U64 = nullptr; F.d_Ubf = nullptr; F.d_lam32 = nullptr; F.d_lam64 = nullptr;
-    F.d_dense_work = nullptr;
+    F.d_dense_work = nullptr; F.d_Vd = nullptr; F.d_RB = nullptr; F.d_T = nullptr;
+    F.d_EB = nullptr; F.d_Vbase = nullptr; F.d_tc_err = nullptr;
 }
 
 // Build the banded GridWorld factors: the slip weights of the rank-1 terms
@@ -396,6 +398,8 @@ static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, boo
     // certifying FP64 sweep (banded F32 / F64 fused path)
     double *cert = (double *)((char *)F.d_ctrl + offsetof(Ctrl, certify_residual));
     const bool do_cert = o.certify && F.kind == CPMDP_GRIDWORLD;
+    // the dense BF16X3 solver runs its own FP64 certifying sweep
+    const bool dense_cert = o.certify && F.kind == CPMDP_DENSE_CP && prec == CPMDP_BF16X3 && !pi_mode;
     if (do_cert) {
         if (prec == CPMDP_F64) {
             // one FP64 backup into scratch: residual + policy of the returned V
@@ -422,6 +426,7 @@ static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, boo
     } else {
         hc.certify_residual = dc.certify_residual;
     }
+    if (dense_cert) hc.certify_residual = dc.certify_residual;
     if (dc.status != 0 && !have_ctrl) {
         set_error("a device-side wait exceeded %.3g s; results are undefined", o.timeout_s);
         if (info) { memset(info, 0, sizeof(*info)); info->status = dc.status; }
@@ -433,8 +438,9 @@ static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, boo
     r.rounds = hc.rounds;
     r.eval_sweeps = hc.eval_sweeps;
     r.residual = hc.last_residual;
-    r.certified_residual = do_cert ? hc.certify_residual : -1.0;
-    r.error_bound = (do_cert && F.gamma < 1.0) ? hc.certify_residual / (1.0 - F.gamma) : -1.0;
+    const bool have_cert = do_cert || dense_cert;
+    r.certified_residual = have_cert ? hc.certify_residual : -1.0;
+    r.error_bound = (have_cert && F.gamma < 1.0) ? hc.certify_residual / (1.0 - F.gamma) : -1.0;
     r.backups = hc.backups;
     r.elapsed_ms = ms;
     r.status = hc.converged ? CPMDP_OK : CPMDP_ENOCONV;

@@ -22,7 +22,7 @@
 
 namespace cpmdp {
 
-enum DenseMode : int { DM_VI = 0, DM_EVAL = 1, DM_IMPROVE = 2, DM_GREEDY = 3 };
+enum DenseMode : int { DM_VI = 0, DM_EVAL = 1, DM_IMPROVE = 2, DM_GREEDY = 3, DM_STORE_E = 4 };
 
 struct Epilogue {
     int enabled;           // 0: plain store of Y (intermediate mode)
@@ -114,6 +114,11 @@ __global__ void __launch_bounds__(256) mode_product_kernel(const T *__restrict__
             T *E = (T *)ep.E;
             const T e = (ep.first_rank ? (T)0 : E[s]) + (T)ep.lambda * acc[a][b];
             if (!ep.last_rank) { E[s] = e; continue; }
+            if (ep.mode == DM_STORE_E) {
+                // E_a in the tensor-core pass-B layout (64^4): [a][(i3,i4)][(i1,i2)]
+                ((T *)ep.Vout)[(long long)ep.action * ncols * N + (s % 4096) * 4096 + s / 4096] = e;
+                continue;
+            }
             const T q = ((const T *)ep.R)[s] + (T)ep.gamma * e;
             T *best = (T *)ep.best;
             T b0;
@@ -149,7 +154,7 @@ __global__ void __launch_bounds__(256) mode_product_kernel(const T *__restrict__
             }
         }
     }
-    if (ep.enabled && ep.last_rank && ep.last_action) {
+    if (ep.enabled && ep.last_rank && ep.last_action && ep.mode != DM_STORE_E) {
         __shared__ double shd[8];
         __shared__ unsigned shc[8];
 #pragma unroll
@@ -240,6 +245,26 @@ static cpmdp_status dense_sweep(const Factors &F, const T *Vin, T *Vout, uint8_t
     return CPMDP_OK;
 }
 
+cpmdp_status dense_store_expectation(const Factors &F, const float *V, float *EB, cudaStream_t st) {
+    return dense_sweep<float>(F, V, EB, nullptr, DM_STORE_E, 0.0, nullptr, nullptr, st);
+}
+
+__global__ void widen_kernel(const float *__restrict__ x, double *__restrict__ y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (double)x[i];
+}
+
+// FP64 backup of a float value tensor: certified residual and FP64 argmax.
+cpmdp_status dense_certify(const Factors &F, const float *V, uint8_t *pi, double *res, cudaStream_t st) {
+    Factors &Fm = const_cast<Factors &>(F);
+    if (!Fm.d_Vd) CPMDP_CUDA(cudaMalloc(&Fm.d_Vd, (size_t)F.nstates * sizeof(double)));
+    widen_kernel<<<1024, 256, 0, st>>>(V, Fm.d_Vd, F.nstates);
+    CPMDP_CUDA(cudaGetLastError());
+    unsigned long long *rb = reinterpret_cast<unsigned long long *>(res);
+    CPMDP_CUDA(cudaMemsetAsync(rb, 0, sizeof(double), st));
+    return dense_sweep<double>(F, Fm.d_Vd, nullptr, pi, DM_VI, 0.0, rb, nullptr, st);
+}
+
 cpmdp_status dense_backup(const Factors &F, cpmdp_precision prec, const void *Vin, void *Vout, uint8_t *pi,
                           double *res, cudaStream_t st) {
     unsigned long long *rb = reinterpret_cast<unsigned long long *>(res);
@@ -248,8 +273,7 @@ cpmdp_status dense_backup(const Factors &F, cpmdp_precision prec, const void *Vi
         return dense_sweep<double>(F, (const double *)Vin, (double *)Vout, pi, DM_VI, 0.0, rb, nullptr, st);
     if (prec == CPMDP_F32)
         return dense_sweep<float>(F, (const float *)Vin, (float *)Vout, pi, DM_VI, 0.0, rb, nullptr, st);
-    set_error("dense BF16X3 path is not available in this build");
-    return CPMDP_EINVAL;
+    return dense_tc_backup(F, (const float *)Vin, (float *)Vout, pi, res, st);
 }
 
 // Value / policy iteration for dense models: each sweep is A*R*D launches
@@ -328,8 +352,11 @@ cpmdp_status dense_solve(const Factors &F, cpmdp_precision prec, bool pim, void 
                          const SolveOpts &o, Ctrl *hc, cudaStream_t st) {
     if (prec == CPMDP_F64) return dense_solve_t<double>(F, pim, (double *)V, pi, o, hc, st);
     if (prec == CPMDP_F32) return dense_solve_t<float>(F, pim, (float *)V, pi, o, hc, st);
-    set_error("dense BF16X3 path is not available in this build");
-    return CPMDP_EINVAL;
+    if (pim) {
+        set_error("BF16X3 runs value iteration only; use F32 or F64 for dense policy iteration");
+        return CPMDP_EINVAL;
+    }
+    return dense_tc_solve(F, (float *)V, pi, o, hc, st);
 }
 
 }  // namespace cpmdp

@@ -1,0 +1,493 @@
+// Dense CP backup on the tcgen05 tensor cores, BF16x3 (shapes 64^4).
+//
+// E_a[V] = sum_r lambda_{a,r} V x_1 U_{a,r,1} x_2 U_{a,r,2} x_3 U_{a,r,3} x_4 U_{a,r,4}
+// (the CP form applied per action; Eq. 1 then takes R + gamma max_a E_a).
+// Matricise V as a 4096 x 4096 matrix with rows (i1,i2) and columns (i3,i4):
+// E = (U_1 (x) U_2) V (U_3 (x) U_4)^T. Two passes, each applying two modes
+// to 64 x 64 slabs entirely on chip:
+//
+//  pass A, per chain c = (a, r) and slab b = (i1,i2) of V (rows i3, cols i4):
+//    Z = X U_4^T            (GEMM 1, M = 2 slabs x 64 rows, N = 64, K = 64)
+//    Y^T = Z^T U_3^T        (GEMM 2, A operand = Z^T written by the threads)
+//    T_c[(i3',i4')][(i1,i2)] = Y[i3',i4']   (bf16 hi/lo pairs, 4 bytes)
+//  pass B, per slab q = (i3',i4') of T_c (rows i1, cols i2), ranks of one
+//  action accumulated in TMEM (lambda is folded into U_1):
+//    W = Z U_2^T, E^T += W^T (lambda U_1)^T
+//    then max / argmax over actions in registers, V' = R + gamma max_a E_a
+//    (exact: rounding is monotone and gamma >= 0), residual max |V' - V|.
+//
+// Each GEMM is D = A B^T with K-major 128B-swizzled tiles, run as BF16x3
+// (A_hi B_hi + A_hi B_lo + A_lo B_hi, FP32 accumulation in TMEM): about 16
+// significant bits per operand. Value iteration corrects the remaining error
+// against a base expectation E_a(V_base) computed in FP32 (defect
+// correction: E_a(V) = E_a(V_base) + E_a^{bf16x3}(V - V_base)); the base is
+// refreshed when the residual stops falling. One FP64 sweep certifies the
+// result.
+//
+// One warpgroup per CTA (thread t owns TMEM lane t). Every mbarrier wait is
+// bounded; a wait that runs out sets the error word and the CTA stops.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace cpmdp {
+
+constexpr int kN = 64;
+constexpr int kSlab = 4096;               // elements of one 64 x 64 slab
+constexpr long long kS = 16777216LL;      // 64^4 states
+constexpr int kTileBytes = 8192;          // 64 x 64 bf16 tile
+constexpr int kPairBytes = 16384;         // 128 x 64 bf16 tile
+constexpr long long kWaitCycles = 4000000000LL;   // about 2 s at 2 GHz
+
+// U tiles in global memory, pre-split and pre-swizzled:
+// ((c * 4 + d) * 2 + part) * 8192 bytes, part 0 = hi, 1 = lo; d = 0 holds lambda U_1.
+__device__ __forceinline__ const uint8_t *utile(const uint8_t *U, int c, int d, int part) {
+    return U + ((size_t)(c * 4 + d) * 2 + part) * kTileBytes;
+}
+
+__device__ __forceinline__ void copy_tile(uint8_t *dst, const uint8_t *src, int tid) {
+    const uint4 *s = reinterpret_cast<const uint4 *>(src);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < kTileBytes / 16 / 128; i++) d[tid + 128 * i] = s[tid + 128 * i];
+}
+
+__device__ __forceinline__ void put_bf16(uint8_t *tile, uint32_t row, uint32_t k, uint16_t v) {
+    *reinterpret_cast<uint16_t *>(tile + tc::sw128_off(row, k)) = v;
+}
+
+// Uniform wait: every thread waits; the CTA continues only if all succeeded.
+__device__ __forceinline__ bool wait_all(uint64_t *mbar, uint32_t &phase, int *err) {
+    const bool ok = tc::mbar_wait(mbar, phase, kWaitCycles);
+    phase ^= 1u;
+    const int all = __syncthreads_and(ok ? 1 : 0);
+    if (!all && threadIdx.x == 0) atomicExch(err, (int)CPMDP_ETIMEOUT);
+    return all != 0;
+}
+
+__device__ __forceinline__ void sync_for_async() {
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+}
+
+// ---------------------------------------------------------------------------
+// pass A: slabs of V (minus V_base when given) -> T_c for every chain c
+
+constexpr int kAOffX = 0;                          // 2 pairs x {hi, lo} x 16 KB
+constexpr int kAOffA2 = 4 * kPairBytes;            // {hi, lo} x 16 KB
+constexpr int kAOffU = kAOffA2 + 2 * kPairBytes;   // U4 hi, lo, U3 hi, lo (4 x 8 KB)
+constexpr int kAOffStage = kAOffU + 4 * kTileBytes;// 4 slabs x 4096 x 4 B
+constexpr int kAOffBar = kAOffStage + 4 * kSlab * 4;
+constexpr int kASmem = kAOffBar + 64 + 1024;
+
+__global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__ V, const float *__restrict__ Vbase,
+                                                       const uint8_t *__restrict__ U, uint32_t *__restrict__ T,
+                                                       int nchains, int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sX = sm + kAOffX;
+    uint8_t *sA2 = sm + kAOffA2;
+    uint8_t *sU = sm + kAOffU;
+    uint32_t *stage = reinterpret_cast<uint32_t *>(sm + kAOffStage);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kAOffBar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kAOffBar + 8);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) tc::mbar_init(mbar, 1);
+    if (warp == 0) tc::tmem_alloc(tslot, 128);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sync_for_async();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    uint32_t phase = 0;
+    bool alive = true;
+    const uint32_t aX = tc::smem_u32(sX), aA2 = tc::smem_u32(sA2), aU = tc::smem_u32(sU);
+
+    for (int g = blockIdx.x; g < kSlab / 4 && alive; g += gridDim.x) {
+        const int b0 = 4 * g;
+        // stage the 4 slabs as 2 pair tiles: row = (s % 2) * 64 + i3, k = i4
+        for (int e = tid; e < 4 * kSlab; e += 128) {
+            const int s = e >> 12, rem = e & (kSlab - 1);
+            const size_t gi = (size_t)(b0 + s) * kSlab + rem;
+            const float x = Vbase ? V[gi] - Vbase[gi] : V[gi];
+            __nv_bfloat16 h, l;
+            tc::split_bf16(x, h, l);
+            uint8_t *tile = sX + (s >> 1) * 2 * kPairBytes;
+            const uint32_t row = (uint32_t)((s & 1) * 64 + (rem >> 6)), k = (uint32_t)(rem & 63);
+            put_bf16(tile, row, k, __bfloat16_as_ushort(h));
+            put_bf16(tile + kPairBytes, row, k, __bfloat16_as_ushort(l));
+        }
+        for (int c = 0; c < nchains && alive; c++) {
+            copy_tile(sU + 0 * kTileBytes, utile(U, c, 3, 0), tid);
+            copy_tile(sU + 1 * kTileBytes, utile(U, c, 3, 1), tid);
+            copy_tile(sU + 2 * kTileBytes, utile(U, c, 2, 0), tid);
+            copy_tile(sU + 3 * kTileBytes, utile(U, c, 2, 1), tid);
+            sync_for_async();
+            for (int p = 0; p < 2 && alive; p++) {
+                const uint32_t xa = aX + p * 2 * kPairBytes;
+                if (tid == 0) {
+                    tc::mma_bf16x3(tmem, xa, xa + kPairBytes, aU, aU + kTileBytes, 0);
+                    tc::commit(mbar);
+                }
+                if (!wait_all(mbar, phase, err)) { alive = false; break; }
+                tc::fence_after();
+                float z[64];
+                tc::tmem_ld64(tmem + lane_off, z);   // row tid = (s2, i3), cols i4'
+                {
+                    const uint32_t s2 = tid >> 6, i3 = tid & 63;
+#pragma unroll
+                    for (int j = 0; j < 64; j++) {
+                        __nv_bfloat16 h, l;
+                        tc::split_bf16(z[j], h, l);
+                        put_bf16(sA2, s2 * 64 + j, i3, __bfloat16_as_ushort(h));
+                        put_bf16(sA2 + kPairBytes, s2 * 64 + j, i3, __bfloat16_as_ushort(l));
+                    }
+                }
+                sync_for_async();
+                if (tid == 0) {
+                    tc::mma_bf16x3(tmem + 64, aA2, aA2 + kPairBytes, aU + 2 * kTileBytes, aU + 3 * kTileBytes, 0);
+                    tc::commit(mbar);
+                }
+                if (!wait_all(mbar, phase, err)) { alive = false; break; }
+                tc::fence_after();
+                float y[64];
+                tc::tmem_ld64(tmem + lane_off + 64, y);   // row tid = (s2, i4'), cols i3'
+                {
+                    const int s = 2 * p + (tid >> 6), i4 = tid & 63;
+#pragma unroll
+                    for (int j = 0; j < 64; j++) stage[s * kSlab + j * 64 + i4] = tc::pack_hilo(y[j]);
+                }
+                tc::fence_before();
+                __syncthreads();
+                tc::fence_after();
+            }
+            if (!alive) break;
+            // T_c row q = i3' * 64 + i4', columns b0 .. b0+3 (16 bytes)
+            uint32_t *Tc = T + (size_t)c * kS;
+            for (int q = tid; q < kSlab; q += 128) {
+                uint4 v;
+                v.x = stage[0 * kSlab + q];
+                v.y = stage[1 * kSlab + q];
+                v.z = stage[2 * kSlab + q];
+                v.w = stage[3 * kSlab + q];
+                *reinterpret_cast<uint4 *>(Tc + (size_t)q * kSlab + b0) = v;
+            }
+            __syncthreads();
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// ---------------------------------------------------------------------------
+// pass B: slabs of T_c -> E_a accumulated over ranks -> max over actions
+
+constexpr int kBOffZ = 0;                         // {hi, lo} x 16 KB
+constexpr int kBOffA2 = 2 * kPairBytes;           // {hi, lo} x 16 KB
+constexpr int kBOffU = 4 * kPairBytes;            // U2 hi, lo, U1 hi, lo
+constexpr int kBOffArg = kBOffU + 4 * kTileBytes; // 64 x 128 argmax bytes
+constexpr int kBOffBar = kBOffArg + 64 * 128;
+constexpr int kBSmem = kBOffBar + 64 + 1024;
+
+__global__ void __launch_bounds__(128, 1) dense_pass_b(const uint32_t *__restrict__ T, const uint8_t *__restrict__ U,
+                                                       const float *__restrict__ RB, const float *__restrict__ EB,
+                                                       const float *__restrict__ Vin, float *__restrict__ Vout,
+                                                       uint8_t *__restrict__ pi, int nact, int nrank, float gamma,
+                                                       unsigned long long *res, int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sZ = sm + kBOffZ;
+    uint8_t *sA2 = sm + kBOffA2;
+    uint8_t *sU = sm + kBOffU;
+    uint8_t *sArg = sm + kBOffArg;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kBOffBar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kBOffBar + 8);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) tc::mbar_init(mbar, 1);
+    if (warp == 0) tc::tmem_alloc(tslot, 128);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sync_for_async();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    uint32_t phase = 0;
+    bool alive = true;
+    const uint32_t aZ = tc::smem_u32(sZ), aA2 = tc::smem_u32(sA2), aU = tc::smem_u32(sU);
+    double local_res = 0.0;
+
+    for (int P = blockIdx.x; P < kSlab / 2 && alive; P += gridDim.x) {
+        const int q0 = 2 * P;
+        float best[64];
+#pragma unroll
+        for (int j = 0; j < 64; j++) best[j] = 0.f;
+        for (int a = 0; a < nact && alive; a++) {
+            for (int r = 0; r < nrank && alive; r++) {
+                const int c = a * nrank + r;
+                const uint32_t *Tc = T + (size_t)c * kS + (size_t)q0 * kSlab;
+                for (int e = tid; e < 2 * kSlab; e += 128) {
+                    const uint32_t w = Tc[e];
+                    const int s2 = e >> 12, rem = e & (kSlab - 1);
+                    const uint32_t row = (uint32_t)(s2 * 64 + (rem >> 6)), k = (uint32_t)(rem & 63);
+                    put_bf16(sZ, row, k, (uint16_t)(w & 0xFFFFu));
+                    put_bf16(sZ + kPairBytes, row, k, (uint16_t)(w >> 16));
+                }
+                copy_tile(sU + 0 * kTileBytes, utile(U, c, 1, 0), tid);
+                copy_tile(sU + 1 * kTileBytes, utile(U, c, 1, 1), tid);
+                copy_tile(sU + 2 * kTileBytes, utile(U, c, 0, 0), tid);
+                copy_tile(sU + 3 * kTileBytes, utile(U, c, 0, 1), tid);
+                sync_for_async();
+                if (tid == 0) {
+                    tc::mma_bf16x3(tmem, aZ, aZ + kPairBytes, aU, aU + kTileBytes, 0);
+                    tc::commit(mbar);
+                }
+                if (!wait_all(mbar, phase, err)) { alive = false; break; }
+                tc::fence_after();
+                float w1[64];
+                tc::tmem_ld64(tmem + lane_off, w1);   // row tid = (s2, i1), cols i2'
+                {
+                    const uint32_t s2 = tid >> 6, i1 = tid & 63;
+#pragma unroll
+                    for (int j = 0; j < 64; j++) {
+                        __nv_bfloat16 h, l;
+                        tc::split_bf16(w1[j], h, l);
+                        put_bf16(sA2, s2 * 64 + j, i1, __bfloat16_as_ushort(h));
+                        put_bf16(sA2 + kPairBytes, s2 * 64 + j, i1, __bfloat16_as_ushort(l));
+                    }
+                }
+                sync_for_async();
+                if (tid == 0) {
+                    tc::mma_bf16x3(tmem + 64, aA2, aA2 + kPairBytes, aU + 2 * kTileBytes, aU + 3 * kTileBytes,
+                                   r > 0 ? 1u : 0u);
+                    tc::commit(mbar);
+                }
+                if (!wait_all(mbar, phase, err)) { alive = false; break; }
+            }
+            if (!alive) break;
+            tc::fence_after();
+            float e[64];
+            tc::tmem_ld64(tmem + lane_off + 64, e);   // row tid = (s2, i2'), cols i1'
+            const int q = q0 + (tid >> 6), i2 = tid & 63;
+            if (EB) {
+                const float *eb = EB + (size_t)a * kS + (size_t)q * kSlab + i2;
+#pragma unroll
+                for (int j = 0; j < 64; j++) e[j] += eb[j * 64];
+            }
+#pragma unroll
+            for (int j = 0; j < 64; j++) {
+                if (a == 0 || e[j] > best[j]) {
+                    best[j] = e[j];
+                    sArg[j * 128 + tid] = (uint8_t)a;
+                }
+            }
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
+        }
+        if (!alive) break;
+        // V'(s) = R(s) + gamma max_a E_a(s); state s = (i1' * 64 + i2') * 4096 + q
+        const int q = q0 + (tid >> 6), i2 = tid & 63;
+        const float *rb = RB + (size_t)q * kSlab + i2;
+#pragma unroll
+        for (int j = 0; j < 64; j++) {
+            const size_t s = (size_t)(j * 64 + i2) * kSlab + q;
+            const float v = rb[j * 64] + gamma * best[j];
+            if (Vout) Vout[s] = v;
+            if (pi) pi[s] = sArg[j * 128 + tid];
+            if (res) local_res = fmax(local_res, fabs((double)v - (double)Vin[s]));
+        }
+        __syncthreads();
+    }
+    if (res) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) local_res = fmax(local_res, __shfl_xor_sync(0xFFFFFFFFu, local_res, o));
+        if ((tid & 31) == 0 && local_res > 0.0) atomicMax(res, (unsigned long long)__double_as_longlong(local_res));
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+static uint16_t host_bf16_rn(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return (uint16_t)(u >> 16);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+static float host_bf16_to_f(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+bool dense_tc_supported(const Factors &F) {
+    if (F.kind != CPMDP_DENSE_CP || F.ndim != 4 || F.nactions > 16) return false;
+    for (int d = 0; d < 4; d++)
+        if (F.shape[d] != kN) return false;
+    return true;
+}
+
+// Device buffers of the tensor-core path, allocated on first use.
+static cpmdp_status tc_prepare(Factors &F) {
+    if (F.d_Ubf) return CPMDP_OK;
+    const int C = F.nactions * F.rank;
+    // factor tiles: hi / lo split, swizzled; mode 1 carries lambda
+    std::vector<uint8_t> tiles((size_t)C * 4 * 2 * kTileBytes, 0);
+    for (int c = 0; c < C; c++) {
+        const int a = c / F.rank, r = c % F.rank;
+        const double lam = F.lambda[(size_t)a * F.rank + r];
+        for (int d = 0; d < 4; d++) {
+            const double *Ud = &F.dense_factors[(size_t)F.factor_off[((size_t)a * F.rank + r) * 4 + d]];
+            uint8_t *hi = &tiles[((size_t)(c * 4 + d) * 2 + 0) * kTileBytes];
+            uint8_t *lo = &tiles[((size_t)(c * 4 + d) * 2 + 1) * kTileBytes];
+            for (int i = 0; i < kN; i++)
+                for (int k = 0; k < kN; k++) {
+                    const float x = (float)(d == 0 ? lam * Ud[i * kN + k] : Ud[i * kN + k]);
+                    const uint16_t h = host_bf16_rn(x);
+                    const uint16_t l = host_bf16_rn(x - host_bf16_to_f(h));
+                    const uint32_t off = tc::sw128_off((uint32_t)i, (uint32_t)k);
+                    memcpy(hi + off, &h, 2);
+                    memcpy(lo + off, &l, 2);
+                }
+        }
+    }
+    // rewards in the pass-B layout: RB[q * 4096 + (i1,i2)] = R[(i1,i2) * 4096 + q]
+    std::vector<float> rb((size_t)kS);
+    for (long long col = 0; col < kSlab; col++)
+        for (long long q = 0; q < kSlab; q++) rb[(size_t)(q * kSlab + col)] = (float)F.reward[(size_t)(col * kSlab + q)];
+    Factors &Fm = F;
+    CPMDP_CUDA(cudaMalloc(&Fm.d_Ubf, tiles.size()));
+    CPMDP_CUDA(cudaMemcpy(Fm.d_Ubf, tiles.data(), tiles.size(), cudaMemcpyHostToDevice));
+    CPMDP_CUDA(cudaMalloc(&Fm.d_RB, (size_t)kS * sizeof(float)));
+    CPMDP_CUDA(cudaMemcpy(Fm.d_RB, rb.data(), (size_t)kS * sizeof(float), cudaMemcpyHostToDevice));
+    CPMDP_CUDA(cudaMalloc(&Fm.d_T, (size_t)C * kS * sizeof(uint32_t)));
+    CPMDP_CUDA(cudaMalloc(&Fm.d_EB, (size_t)F.nactions * kS * sizeof(float)));
+    CPMDP_CUDA(cudaMalloc(&Fm.d_Vbase, (size_t)kS * sizeof(float)));
+    CPMDP_CUDA(cudaMalloc(&Fm.d_tc_err, sizeof(int)));
+    CPMDP_CUDA(cudaFuncSetAttribute(dense_pass_a, cudaFuncAttributeMaxDynamicSharedMemorySize, kASmem));
+    CPMDP_CUDA(cudaFuncSetAttribute(dense_pass_b, cudaFuncAttributeMaxDynamicSharedMemorySize, kBSmem));
+    return CPMDP_OK;
+}
+
+// One BF16x3 backup: Vout = R + gamma max_a (EB_a + E_a(Vin - Vbase)).
+static cpmdp_status tc_sweep(const Factors &F, const float *Vin, float *Vout, uint8_t *pi, bool use_base,
+                             unsigned long long *res, cudaStream_t st) {
+    const int C = F.nactions * F.rank;
+    int *err = F.d_tc_err;
+    const int grid = F.num_sms > 0 ? F.num_sms : 148;
+    dense_pass_a<<<grid, 128, kASmem, st>>>(Vin, use_base ? F.d_Vbase : nullptr, (const uint8_t *)F.d_Ubf,
+                                            (uint32_t *)F.d_T, C, err);
+    CPMDP_CUDA(cudaGetLastError());
+    dense_pass_b<<<grid, 128, kBSmem, st>>>((const uint32_t *)F.d_T, (const uint8_t *)F.d_Ubf, F.d_RB,
+                                            use_base ? F.d_EB : nullptr, Vin, Vout, pi, F.nactions, F.rank,
+                                            (float)F.gamma, res, err);
+    CPMDP_CUDA(cudaGetLastError());
+    return CPMDP_OK;
+}
+
+static cpmdp_status tc_check_err(const Factors &F, cudaStream_t st) {
+    int h = 0;
+    CPMDP_CUDA(cudaMemcpyAsync(&h, F.d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CPMDP_CUDA(cudaStreamSynchronize(st));
+    if (h != 0) {
+        set_error("a tensor-core wait exceeded its limit; results are undefined");
+        return CPMDP_ETIMEOUT;
+    }
+    return CPMDP_OK;
+}
+
+cpmdp_status dense_tc_backup(const Factors &F, const float *Vin, float *Vout, uint8_t *pi, double *res,
+                             cudaStream_t st) {
+    if (!dense_tc_supported(F)) {
+        set_error("BF16X3 needs a dense model with 4 dimensions of size 64 and at most 16 actions");
+        return CPMDP_EINVAL;
+    }
+    cpmdp_status s = tc_prepare(const_cast<Factors &>(F));
+    if (s != CPMDP_OK) return s;
+    CPMDP_CUDA(cudaMemsetAsync(F.d_tc_err, 0, sizeof(int), st));
+    unsigned long long *rb = reinterpret_cast<unsigned long long *>(res);
+    if (rb) CPMDP_CUDA(cudaMemsetAsync(rb, 0, sizeof(double), st));
+    s = tc_sweep(F, Vin, Vout, pi, false, rb, st);
+    if (s != CPMDP_OK) return s;
+    return tc_check_err(F, st);
+}
+
+// FP32 SIMT expectation of every action, stored in the pass-B layout (dense.cu).
+cpmdp_status dense_store_expectation(const Factors &F, const float *V, float *EB, cudaStream_t st);
+// FP64 SIMT backup of a float value tensor (dense.cu).
+cpmdp_status dense_certify(const Factors &F, const float *V, uint8_t *pi, double *res, cudaStream_t st);
+
+// Value iteration with BF16x3 sweeps and defect correction against an FP32
+// base expectation; FP64 certifying sweep at the end.
+cpmdp_status dense_tc_solve(const Factors &F, float *V, uint8_t *pi, const SolveOpts &o, Ctrl *hc, cudaStream_t st) {
+    if (!dense_tc_supported(F)) {
+        set_error("BF16X3 needs a dense model with 4 dimensions of size 64 and at most 16 actions");
+        return CPMDP_EINVAL;
+    }
+    cpmdp_status s = tc_prepare(const_cast<Factors &>(F));
+    if (s != CPMDP_OK) return s;
+    CPMDP_CUDA(cudaMemsetAsync(F.d_tc_err, 0, sizeof(int), st));
+    float *W = (float *)F.d_scratch;
+    unsigned long long *rb = &F.d_ctrl->res_slot[0];
+    float *cur = V, *nxt = W;
+    std::vector<double> hist;
+    int k = 0, conv = 0, last_rebase = 0, rebases = 0;
+    bool base = false;
+    double res = INFINITY;
+    while (k < o.max_iter) {
+        CPMDP_CUDA(cudaMemsetAsync(rb, 0, sizeof(*rb), st));
+        s = tc_sweep(F, cur, nxt, nullptr, base, rb, st);
+        if (s != CPMDP_OK) return s;
+        unsigned long long bits = 0;
+        CPMDP_CUDA(cudaMemcpyAsync(&bits, rb, sizeof(bits), cudaMemcpyDeviceToHost, st));
+        s = tc_check_err(F, st);
+        if (s != CPMDP_OK) return s;
+        memcpy(&res, &bits, sizeof(res));
+        if (o.trace) CPMDP_CUDA(cudaMemcpyAsync(o.trace + k, &res, sizeof(double), cudaMemcpyHostToDevice, st));
+        hist.push_back(res);
+        float *t = cur; cur = nxt; nxt = t;
+        k++;
+        if (res < o.tol) { conv = 1; break; }
+        // the residual stopped falling: the BF16x3 error of the correction
+        // dominates; refresh the FP32 base at the current iterate
+        if (k - last_rebase >= 6 && res > 0.9 * hist[k - 6] && rebases < 64) {
+            CPMDP_CUDA(cudaMemcpyAsync(F.d_Vbase, cur, (size_t)kS * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            s = dense_store_expectation(F, cur, F.d_EB, st);
+            if (s != CPMDP_OK) return s;
+            base = true;
+            last_rebase = k;
+            rebases++;
+        }
+    }
+    if (cur != V) CPMDP_CUDA(cudaMemcpyAsync(V, cur, (size_t)kS * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    double *cert = (double *)((char *)F.d_ctrl + offsetof(Ctrl, certify_residual));
+    if (o.certify) {
+        s = dense_certify(F, V, pi, cert, st);
+        if (s != CPMDP_OK) return s;
+    } else if (pi) {
+        s = tc_sweep(F, V, W, pi, base, nullptr, st);
+        if (s != CPMDP_OK) return s;
+    }
+    hc->iterations = k;
+    hc->rounds = rebases;
+    hc->converged = conv;
+    hc->last_residual = res;
+    hc->backups = (long long)k * kS * F.nactions;
+    return CPMDP_OK;
+}
+
+}  // namespace cpmdp

@@ -79,6 +79,13 @@ struct Factors {
     double *d_lam64 = nullptr;
     void *d_dense_work = nullptr;      // dense chain intermediates
     size_t dense_work_bytes = 0;
+    double *d_Vd = nullptr;            // dense FP64 certify: the float values as doubles
+    // dense tensor-core path (64^4), allocated on first BF16X3 use
+    float *d_RB = nullptr;             // rewards in the pass-B layout
+    void *d_T = nullptr;               // per-chain intermediates (bf16 hi/lo pairs)
+    float *d_EB = nullptr;             // base expectation per action, pass-B layout
+    float *d_Vbase = nullptr;          // base value tensor of the defect correction
+    int *d_tc_err = nullptr;           // error word of the tensor-core kernels
 };
 
 // Thread-local error message.
@@ -121,6 +128,11 @@ cpmdp_status dense_backup(const Factors &F, cpmdp_precision prec, const void *Vi
 cpmdp_status dense_solve(const Factors &F, cpmdp_precision prec, bool policy_iteration, void *V,
                          uint8_t *pi, const SolveOpts &o, Ctrl *host_ctrl, cudaStream_t st);
 cpmdp_status dense_prepare(Factors &F);
+// dense_tc.cu
+bool dense_tc_supported(const Factors &F);
+cpmdp_status dense_tc_backup(const Factors &F, const float *Vin, float *Vout, uint8_t *pi, double *res,
+                             cudaStream_t st);
+cpmdp_status dense_tc_solve(const Factors &F, float *V, uint8_t *pi, const SolveOpts &o, Ctrl *hc, cudaStream_t st);
 
 }  // namespace cpmdp
 
