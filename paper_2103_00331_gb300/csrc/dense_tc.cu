@@ -78,39 +78,56 @@ __device__ __forceinline__ void sync_for_async() {
     tc::fence_after();
 }
 
+// Intermediate layout: for chain c and pass-B slab q = (i3', i4'), a 16 KB
+// tile of 64 rows (i1) x 16 quads; quad j of row i1 (16 bytes at
+// (c * 4096 + q) * 16384 + (i1 * 16 + j) * 16) holds the bf16 hi parts of
+// k = i2 = 4j .. 4j+3 followed by their lo parts. Pass A writes whole quads,
+// pass B copies a slab pair (32 KB, contiguous) with one bulk copy.
+constexpr int kQuadTileBytes = 16384;
+
 // ---------------------------------------------------------------------------
 // pass A: slabs of V (minus V_base when given) -> T_c for every chain c
 
-constexpr int kAOffX = 0;                          // 2 pairs x {hi, lo} x 16 KB
-constexpr int kAOffA2 = 4 * kPairBytes;            // {hi, lo} x 16 KB
-constexpr int kAOffU = kAOffA2 + 2 * kPairBytes;   // U4 hi, lo, U3 hi, lo (4 x 8 KB)
-constexpr int kAOffStage = kAOffU + 4 * kTileBytes;// 4 slabs x 4096 x 4 B
+constexpr int kAOffX = 0;                            // 2 pairs x {hi, lo} x 16 KB
+constexpr int kAOffA2 = 4 * kPairBytes;              // {hi, lo} x 16 KB
+constexpr int kAOffU = kAOffA2 + 2 * kPairBytes;     // 2 buffers x (U3 hi, lo, U4 hi, lo)
+constexpr int kAOffStage = kAOffU + 2 * 4 * kTileBytes;  // 4 slabs x 4096 x 4 B
 constexpr int kAOffBar = kAOffStage + 4 * kSlab * 4;
 constexpr int kASmem = kAOffBar + 64 + 1024;
 
 __global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__ V, const float *__restrict__ Vbase,
-                                                       const uint8_t *__restrict__ U, uint32_t *__restrict__ T,
+                                                       const uint8_t *__restrict__ U, uint8_t *__restrict__ T,
                                                        int nchains, int *err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sX = sm + kAOffX;
     uint8_t *sA2 = sm + kAOffA2;
-    uint8_t *sU = sm + kAOffU;
     uint32_t *stage = reinterpret_cast<uint32_t *>(sm + kAOffStage);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kAOffBar);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kAOffBar + 8);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + kAOffBar);       // [2]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kAOffBar + 16);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kAOffBar + 24);
     const int tid = threadIdx.x, warp = tid >> 5;
-    if (tid == 0) tc::mbar_init(mbar, 1);
+    if (tid == 0) {
+        tc::mbar_init(&full[0], 1);
+        tc::mbar_init(&full[1], 1);
+        tc::mbar_init(mbar, 1);
+    }
     if (warp == 0) tc::tmem_alloc(tslot, 128);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sync_for_async();
     const uint32_t tmem = *tslot;
     const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
-    uint32_t phase = 0;
+    uint32_t phase = 0, fph0 = 0, fph1 = 0;
     bool alive = true;
-    const uint32_t aX = tc::smem_u32(sX), aA2 = tc::smem_u32(sA2), aU = tc::smem_u32(sU);
-
-    for (int g = blockIdx.x; g < kSlab / 4 && alive; g += gridDim.x) {
+    const uint32_t aX = tc::smem_u32(sX), aA2 = tc::smem_u32(sA2), aU = tc::smem_u32(sm + kAOffU);
+    const int ngroups = kSlab / 4;
+    // items in order (group g, chain c); U tiles of item it go to buffer it % 2
+    int it = 0;
+    if (tid == 0 && blockIdx.x < ngroups) {
+        tc::mbar_expect_tx(&full[0], 4 * kTileBytes);
+        tc::bulk_g2s(aU, utile(U, 0, 2, 0), 4 * kTileBytes, &full[0]);
+    }
+    for (int g = blockIdx.x; g < ngroups && alive; g += gridDim.x) {
         const int b0 = 4 * g;
         // stage the 4 slabs as 2 pair tiles: row = (s % 2) * 64 + i3, k = i4
         for (int e = tid; e < 4 * kSlab; e += 128) {
@@ -124,16 +141,26 @@ __global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__
             put_bf16(tile, row, k, __bfloat16_as_ushort(h));
             put_bf16(tile + kPairBytes, row, k, __bfloat16_as_ushort(l));
         }
-        for (int c = 0; c < nchains && alive; c++) {
-            copy_tile(sU + 0 * kTileBytes, utile(U, c, 3, 0), tid);
-            copy_tile(sU + 1 * kTileBytes, utile(U, c, 3, 1), tid);
-            copy_tile(sU + 2 * kTileBytes, utile(U, c, 2, 0), tid);
-            copy_tile(sU + 3 * kTileBytes, utile(U, c, 2, 1), tid);
+        for (int c = 0; c < nchains && alive; c++, it++) {
+            const int buf = it & 1;
+            // prefetch the next item's factor tiles into the other buffer (its
+            // previous reader, item it-1, has completed)
+            if (tid == 0) {
+                int nc = c + 1, ng = g;
+                if (nc == nchains) { nc = 0; ng = g + gridDim.x; }
+                if (ng < ngroups) {
+                    tc::mbar_expect_tx(&full[buf ^ 1], 4 * kTileBytes);
+                    tc::bulk_g2s(aU + (buf ^ 1) * 4 * kTileBytes, utile(U, nc, 2, 0), 4 * kTileBytes, &full[buf ^ 1]);
+                }
+            }
+            uint32_t &fph = buf ? fph1 : fph0;
+            if (!wait_all(&full[buf], fph, err)) { alive = false; break; }
             sync_for_async();
+            const uint32_t u3 = aU + buf * 4 * kTileBytes, u4 = u3 + 2 * kTileBytes;
             for (int p = 0; p < 2 && alive; p++) {
                 const uint32_t xa = aX + p * 2 * kPairBytes;
                 if (tid == 0) {
-                    tc::mma_bf16x3(tmem, xa, xa + kPairBytes, aU, aU + kTileBytes, 0);
+                    tc::mma_bf16x3(tmem, xa, xa + kPairBytes, u4, u4 + kTileBytes, 0);
                     tc::commit(mbar);
                 }
                 if (!wait_all(mbar, phase, err)) { alive = false; break; }
@@ -152,7 +179,7 @@ __global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__
                 }
                 sync_for_async();
                 if (tid == 0) {
-                    tc::mma_bf16x3(tmem + 64, aA2, aA2 + kPairBytes, aU + 2 * kTileBytes, aU + 3 * kTileBytes, 0);
+                    tc::mma_bf16x3(tmem + 64, aA2, aA2 + kPairBytes, u3, u3 + kTileBytes, 0);
                     tc::commit(mbar);
                 }
                 if (!wait_all(mbar, phase, err)) { alive = false; break; }
@@ -169,18 +196,24 @@ __global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__
                 tc::fence_after();
             }
             if (!alive) break;
-            // T_c row q = i3' * 64 + i4', columns b0 .. b0+3 (16 bytes)
-            uint32_t *Tc = T + (size_t)c * kS;
+            // quad (i1, j = i2_0 / 4) of every tile q of chain c
+            uint8_t *Tc = T + (size_t)c * kSlab * kQuadTileBytes + (size_t)((b0 >> 6) * 16 + ((b0 & 63) >> 2)) * 16;
             for (int q = tid; q < kSlab; q += 128) {
+                const uint32_t w0 = stage[q], w1 = stage[kSlab + q], w2 = stage[2 * kSlab + q], w3 = stage[3 * kSlab + q];
                 uint4 v;
-                v.x = stage[0 * kSlab + q];
-                v.y = stage[1 * kSlab + q];
-                v.z = stage[2 * kSlab + q];
-                v.w = stage[3 * kSlab + q];
-                *reinterpret_cast<uint4 *>(Tc + (size_t)q * kSlab + b0) = v;
+                v.x = (w0 & 0xFFFFu) | (w1 << 16);
+                v.y = (w2 & 0xFFFFu) | (w3 << 16);
+                v.z = (w0 >> 16) | (w1 & 0xFFFF0000u);
+                v.w = (w2 >> 16) | (w3 & 0xFFFF0000u);
+                *reinterpret_cast<uint4 *>(Tc + (size_t)q * kQuadTileBytes) = v;
             }
             __syncthreads();
         }
+    }
+    // a prefetch may still be in flight when this CTA stopped early: wait for it
+    if (!alive && tid == 0) {
+        tc::mbar_wait(&full[0], fph0, kWaitCycles);
+        tc::mbar_wait(&full[1], fph1, kWaitCycles);
     }
     tc::fence_before();
     __syncthreads();
@@ -191,14 +224,15 @@ __global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__
 // ---------------------------------------------------------------------------
 // pass B: slabs of T_c -> E_a accumulated over ranks -> max over actions
 
-constexpr int kBOffZ = 0;                         // {hi, lo} x 16 KB
-constexpr int kBOffA2 = 2 * kPairBytes;           // {hi, lo} x 16 KB
-constexpr int kBOffU = 4 * kPairBytes;            // U2 hi, lo, U1 hi, lo
-constexpr int kBOffArg = kBOffU + 4 * kTileBytes; // 64 x 128 argmax bytes
+constexpr int kBOffBuf = 0;                        // 2 x (raw slab pair 32 KB + U1 hi, lo, U2 hi, lo 32 KB)
+constexpr int kBBufBytes = 2 * kQuadTileBytes + 4 * kTileBytes;
+constexpr int kBOffZ = 2 * kBBufBytes;             // {hi, lo} x 16 KB
+constexpr int kBOffA2 = kBOffZ + 2 * kPairBytes;   // {hi, lo} x 16 KB
+constexpr int kBOffArg = kBOffA2 + 2 * kPairBytes; // 64 x 128 argmax bytes
 constexpr int kBOffBar = kBOffArg + 64 * 128;
 constexpr int kBSmem = kBOffBar + 64 + 1024;
 
-__global__ void __launch_bounds__(128, 1) dense_pass_b(const uint32_t *__restrict__ T, const uint8_t *__restrict__ U,
+__global__ void __launch_bounds__(128, 1) dense_pass_b(const uint8_t *__restrict__ T, const uint8_t *__restrict__ U,
                                                        const float *__restrict__ RB, const float *__restrict__ EB,
                                                        const float *__restrict__ Vin, float *__restrict__ Vout,
                                                        uint8_t *__restrict__ pi, int nact, int nrank, float gamma,
@@ -207,45 +241,68 @@ __global__ void __launch_bounds__(128, 1) dense_pass_b(const uint32_t *__restric
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sZ = sm + kBOffZ;
     uint8_t *sA2 = sm + kBOffA2;
-    uint8_t *sU = sm + kBOffU;
     uint8_t *sArg = sm + kBOffArg;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kBOffBar);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kBOffBar + 8);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + kBOffBar);       // [2]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kBOffBar + 16);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kBOffBar + 24);
     const int tid = threadIdx.x, warp = tid >> 5;
-    if (tid == 0) tc::mbar_init(mbar, 1);
+    if (tid == 0) {
+        tc::mbar_init(&full[0], 1);
+        tc::mbar_init(&full[1], 1);
+        tc::mbar_init(mbar, 1);
+    }
     if (warp == 0) tc::tmem_alloc(tslot, 128);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sync_for_async();
     const uint32_t tmem = *tslot;
     const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
-    uint32_t phase = 0;
+    uint32_t phase = 0, fph0 = 0, fph1 = 0;
     bool alive = true;
-    const uint32_t aZ = tc::smem_u32(sZ), aA2 = tc::smem_u32(sA2), aU = tc::smem_u32(sU);
+    const uint32_t aBuf = tc::smem_u32(sm + kBOffBuf), aZ = tc::smem_u32(sZ), aA2 = tc::smem_u32(sA2);
+    const int npairs = kSlab / 2, nchains = nact * nrank;
     double local_res = 0.0;
 
-    for (int P = blockIdx.x; P < kSlab / 2 && alive; P += gridDim.x) {
+    // item = (pair P, chain c); its raw slab pair and U1/U2 tiles go to buffer it % 2
+    auto issue = [&](int P, int c, int b) {
+        tc::mbar_expect_tx(&full[b], kBBufBytes);
+        const uint32_t dst = aBuf + b * kBBufBytes;
+        tc::bulk_g2s(dst, T + ((size_t)c * kSlab + 2 * P) * kQuadTileBytes, 2 * kQuadTileBytes, &full[b]);
+        tc::bulk_g2s(dst + 2 * kQuadTileBytes, utile(U, c, 0, 0), 4 * kTileBytes, &full[b]);
+    };
+    int it = 0;
+    if (tid == 0 && blockIdx.x < npairs) issue(blockIdx.x, 0, 0);
+    for (int P = blockIdx.x; P < npairs && alive; P += gridDim.x) {
         const int q0 = 2 * P;
         float best[64];
 #pragma unroll
         for (int j = 0; j < 64; j++) best[j] = 0.f;
         for (int a = 0; a < nact && alive; a++) {
-            for (int r = 0; r < nrank && alive; r++) {
-                const int c = a * nrank + r;
-                const uint32_t *Tc = T + (size_t)c * kS + (size_t)q0 * kSlab;
-                for (int e = tid; e < 2 * kSlab; e += 128) {
-                    const uint32_t w = Tc[e];
-                    const int s2 = e >> 12, rem = e & (kSlab - 1);
-                    const uint32_t row = (uint32_t)(s2 * 64 + (rem >> 6)), k = (uint32_t)(rem & 63);
-                    put_bf16(sZ, row, k, (uint16_t)(w & 0xFFFFu));
-                    put_bf16(sZ + kPairBytes, row, k, (uint16_t)(w >> 16));
-                }
-                copy_tile(sU + 0 * kTileBytes, utile(U, c, 1, 0), tid);
-                copy_tile(sU + 1 * kTileBytes, utile(U, c, 1, 1), tid);
-                copy_tile(sU + 2 * kTileBytes, utile(U, c, 0, 0), tid);
-                copy_tile(sU + 3 * kTileBytes, utile(U, c, 0, 1), tid);
-                sync_for_async();
+            for (int r = 0; r < nrank && alive; r++, it++) {
+                const int c = a * nrank + r, buf = it & 1;
                 if (tid == 0) {
-                    tc::mma_bf16x3(tmem, aZ, aZ + kPairBytes, aU, aU + kTileBytes, 0);
+                    int nc = c + 1, nP = P;
+                    if (nc == nchains) { nc = 0; nP = P + gridDim.x; }
+                    if (nP < npairs) issue(nP, nc, buf ^ 1);
+                }
+                uint32_t &fph = buf ? fph1 : fph0;
+                if (!wait_all(&full[buf], fph, err)) { alive = false; break; }
+                // de-interleave the raw quads into the swizzled hi / lo pair tiles
+                {
+                    const uint4 *raw = reinterpret_cast<const uint4 *>(sm + kBOffBuf + buf * kBBufBytes);
+#pragma unroll 4
+                    for (int idx = tid; idx < 2 * 1024; idx += 128) {
+                        const uint4 w = raw[idx];
+                        const uint32_t s2 = idx >> 10, rem = idx & 1023;
+                        const uint32_t row = s2 * 64 + (rem >> 4), k = (rem & 15) * 4;
+                        const uint32_t off = tc::sw128_off(row, k);
+                        *reinterpret_cast<uint2 *>(sZ + off) = make_uint2(w.x, w.y);
+                        *reinterpret_cast<uint2 *>(sZ + kPairBytes + off) = make_uint2(w.z, w.w);
+                    }
+                }
+                sync_for_async();
+                const uint32_t u1 = aBuf + buf * kBBufBytes + 2 * kQuadTileBytes, u2 = u1 + 2 * kTileBytes;
+                if (tid == 0) {
+                    tc::mma_bf16x3(tmem, aZ, aZ + kPairBytes, u2, u2 + kTileBytes, 0);
                     tc::commit(mbar);
                 }
                 if (!wait_all(mbar, phase, err)) { alive = false; break; }
@@ -264,8 +321,7 @@ __global__ void __launch_bounds__(128, 1) dense_pass_b(const uint32_t *__restric
                 }
                 sync_for_async();
                 if (tid == 0) {
-                    tc::mma_bf16x3(tmem + 64, aA2, aA2 + kPairBytes, aU + 2 * kTileBytes, aU + 3 * kTileBytes,
-                                   r > 0 ? 1u : 0u);
+                    tc::mma_bf16x3(tmem + 64, aA2, aA2 + kPairBytes, u1, u1 + kTileBytes, r > 0 ? 1u : 0u);
                     tc::commit(mbar);
                 }
                 if (!wait_all(mbar, phase, err)) { alive = false; break; }
@@ -309,6 +365,11 @@ __global__ void __launch_bounds__(128, 1) dense_pass_b(const uint32_t *__restric
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) local_res = fmax(local_res, __shfl_xor_sync(0xFFFFFFFFu, local_res, o));
         if ((tid & 31) == 0 && local_res > 0.0) atomicMax(res, (unsigned long long)__double_as_longlong(local_res));
+    }
+    // a prefetch may still be in flight when this CTA stopped early: wait for it
+    if (!alive && tid == 0) {
+        tc::mbar_wait(&full[0], fph0, kWaitCycles);
+        tc::mbar_wait(&full[1], fph1, kWaitCycles);
     }
     tc::fence_before();
     __syncthreads();
@@ -390,9 +451,9 @@ static cpmdp_status tc_sweep(const Factors &F, const float *Vin, float *Vout, ui
     int *err = F.d_tc_err;
     const int grid = F.num_sms > 0 ? F.num_sms : 148;
     dense_pass_a<<<grid, 128, kASmem, st>>>(Vin, use_base ? F.d_Vbase : nullptr, (const uint8_t *)F.d_Ubf,
-                                            (uint32_t *)F.d_T, C, err);
+                                            (uint8_t *)F.d_T, C, err);
     CPMDP_CUDA(cudaGetLastError());
-    dense_pass_b<<<grid, 128, kBSmem, st>>>((const uint32_t *)F.d_T, (const uint8_t *)F.d_Ubf, F.d_RB,
+    dense_pass_b<<<grid, 128, kBSmem, st>>>((const uint8_t *)F.d_T, (const uint8_t *)F.d_Ubf, F.d_RB,
                                             use_base ? F.d_EB : nullptr, Vin, Vout, pi, F.nactions, F.rank,
                                             (float)F.gamma, res, err);
     CPMDP_CUDA(cudaGetLastError());
