@@ -247,6 +247,47 @@ cpmdp_status cpmdp_value_iteration_static(int32_t ndim, const int64_t *shape, do
                                           float *V, double tol, int32_t max_iter,
                                           int32_t *iterations_out, double *residual_out, void *stream);
 
+/*
+ * Batched value iteration: many independent GridWorld MDPs (each its own
+ * tuple <S, A, P, R, gamma>, 1 to 3 dimensions) solved by one persistent
+ * launch in which every instance stops on its own residual.
+ */
+typedef struct cpmdp_batch cpmdp_batch;
+
+/*
+ * Build a batch from `count` GridWorld problems (validated and factored as
+ * by cpmdp_build_factors) on CUDA device `device`. Instance i's states
+ * occupy [offsets[i], offsets[i] + |S_i|) of the packed value array; each
+ * instance starts on a multiple of 4 states (padding between instances is
+ * never read or written). Errors: EINVAL (an instance is invalid: the
+ * message names it), ENOMEM, ECUDA.
+ */
+cpmdp_status cpmdp_batch_build(const cpmdp_problem *problems, int32_t count, int device, cpmdp_batch **out);
+
+/* Release a batch (NULL is ignored). */
+void cpmdp_batch_free(cpmdp_batch *batch);
+
+/* count, total packed states, and offsets[count + 1] (host; any may be NULL). */
+cpmdp_status cpmdp_batch_info(const cpmdp_batch *batch, int32_t *count, int64_t *total_states, int64_t *offsets);
+
+/*
+ * FP32 value iteration of every instance of the batch (fused backup of
+ * cpmdp_value_iteration, one cooperative persistent launch, per-instance
+ * stopping at opts->tol or opts->max_iter). V: device, packed values (start
+ * in, result out), 16-byte aligned. iterations_out / residual_out: host
+ * arrays of `count` (may be NULL): sweeps and last residual per instance.
+ * info (may be NULL): iterations = launch-wide sweeps, backups = sum over
+ * instances, elapsed_ms, rounds = 1 when the solve was replayed from a CUDA
+ * graph. The first call tunes block and tile sizes on the batch (a few
+ * sweeps on a temporary buffer) and records the solve into a CUDA graph,
+ * replayed by later calls with the same V, stream and options. Synchronises
+ * with `stream`. Errors: EINVAL, ECUDA, ENOCONV (some instance hit
+ * max_iter), ETIMEOUT.
+ */
+cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *batch, float *V, const cpmdp_solve_opts *opts,
+                                         int32_t *iterations_out, double *residual_out, cpmdp_result *info,
+                                         void *stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *cpmdp_last_error(void);
 

@@ -89,6 +89,15 @@ def _load():
                                                  ctypes.c_double, vp, vp, vp, ctypes.c_double, i32,
                                                  ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double), vp]
     lib.cpmdp_value_iteration_static.restype = ctypes.c_int
+    lib.cpmdp_batch_build.argtypes = [ctypes.POINTER(Problem), i32, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.cpmdp_batch_build.restype = ctypes.c_int
+    lib.cpmdp_batch_free.argtypes = [vp]
+    lib.cpmdp_batch_free.restype = None
+    lib.cpmdp_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), vp]
+    lib.cpmdp_batch_info.restype = ctypes.c_int
+    lib.cpmdp_batch_value_iteration.argtypes = [vp, vp, ctypes.POINTER(SolveOpts), vp, vp,
+                                                ctypes.POINTER(Result), vp]
+    lib.cpmdp_batch_value_iteration.restype = ctypes.c_int
     lib.cpmdp_last_error.argtypes = []
     lib.cpmdp_last_error.restype = ctypes.c_char_p
     lib.cpmdp_version.argtypes = []
@@ -100,7 +109,8 @@ lib = _load()
 
 EXPORTED = ["cpmdp_default_opts", "cpmdp_build_factors", "cpmdp_free_factors", "cpmdp_factors_info",
             "cpmdp_components", "cpmdp_bellman_backup", "cpmdp_value_iteration",
-            "cpmdp_policy_iteration", "cpmdp_value_iteration_static", "cpmdp_last_error",
+            "cpmdp_policy_iteration", "cpmdp_value_iteration_static", "cpmdp_batch_build",
+            "cpmdp_batch_free", "cpmdp_batch_info", "cpmdp_batch_value_iteration", "cpmdp_last_error",
             "cpmdp_version"]
 
 
@@ -277,3 +287,57 @@ def value_iteration_static(shape, p_success, gamma, cell, reward, V, tol=1e-6, m
                                             int(max_iter), ctypes.byref(it), ctypes.byref(res),
                                             _stream(stream)))
     return it.value, res.value
+
+
+class Batch:
+    """Owner of a ``cpmdp_batch`` handle (freed on ``close`` / GC)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        n, tot = ctypes.c_int32(), ctypes.c_int64()
+        _check(lib.cpmdp_batch_info(handle, ctypes.byref(n), ctypes.byref(tot), None))
+        self.count, self.total_states = n.value, tot.value
+        self.offsets = np.zeros(self.count + 1, dtype=np.int64)
+        _check(lib.cpmdp_batch_info(handle, None, None, self.offsets.ctypes.data))
+
+    def close(self):
+        if self.handle:
+            lib.cpmdp_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_build(instances, device: int = 0) -> Batch:
+    """``cpmdp_batch_build`` from a list of GridWorld instances (``cpmdp_inputs``)."""
+    n = len(instances)
+    arr = (Problem * n)()
+    keep = []
+    for i, inst in enumerate(instances):
+        reward = np.ascontiguousarray(np.asarray(inst.reward, dtype=np.float64).reshape(-1))
+        cell = np.ascontiguousarray(np.asarray(inst.cell, dtype=np.uint8).reshape(-1))
+        keep += [reward, cell]
+        arr[i] = make_problem(inst.shape, 2 * len(inst.shape), GRIDWORLD, reward, inst.gamma,
+                              p_success=inst.p, cell=cell)
+    h = ctypes.c_void_p()
+    _check(lib.cpmdp_batch_build(arr, n, int(device), ctypes.byref(h)))
+    return Batch(h)
+
+
+def batch_value_iteration(batch: Batch, V, opts=None, stream=None, raise_on_noconv=True):
+    """``cpmdp_batch_value_iteration``: returns (result dict, sweeps per
+    instance, last residual per instance)."""
+    it = np.zeros(batch.count, dtype=np.int32)
+    rs = np.zeros(batch.count, dtype=np.float64)
+    res = Result()
+    st = lib.cpmdp_batch_value_iteration(batch.handle, _ptr(V),
+                                         ctypes.byref(opts) if opts is not None else None,
+                                         it.ctypes.data, rs.ctypes.data, ctypes.byref(res),
+                                         _stream(stream))
+    if st != OK and not (st == ENOCONV and not raise_on_noconv):
+        _check(st)
+    return res.as_dict(), it, rs

@@ -1,0 +1,577 @@
+// Batched value iteration: thousands of independent, uneven GridWorld MDPs
+// (each a tuple <S, A, P, R, gamma> of its own, background section) solved
+// in one persistent launch.
+//
+// The instances are packed back to back (values, FP32 rewards, per-state
+// move codes in the encoding of the single-instance path). The work is cut
+// into tiles: a tile is up to `tile_items` row segments of one instance,
+// each segment VEC in {1, 2, 4} consecutive states of a row of the last
+// dimension (VEC divides that instance's row length). Every global sweep the
+// blocks of the cooperative grid take the tiles of instances that are still
+// running; an instance stops on its own as soon as its residual falls below
+// tol, so short and long solves share the launch. Per-instance residuals use
+// three rotating slots (slot k+1 is cleared during sweep k by the block that
+// owns the instance's first tile, after every block has read slot k-2); the
+// grid stops after a sweep in which no block found a running instance.
+//
+// Tile size and block size are chosen by a small autotuner (time a few
+// sweeps of each candidate on the actual batch), and the solve is recorded
+// once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "banded_common.cuh"
+
+namespace cpmdp {
+
+struct BatchInst {
+    long long offset;      // first state in the packed arrays
+    int nstates;
+    int ndim;              // 1..3
+    int nlast;
+    int stride[3];
+    int vec;               // 1, 2 or 4
+    int first_tile;
+    float w_move, w_perp, w_stay, gamma;
+};
+
+struct BatchTile {
+    int inst;
+    int first_item;        // segment index within the instance
+    int nitems;
+};
+
+struct BatchArgs {
+    const BatchInst *inst;
+    const BatchTile *tiles;
+    int ntiles;
+    int ninst;
+    const uint8_t *code;
+    const float *R;
+    float *V;
+    float *W;
+    unsigned long long *res;   // [3][ninst]
+    int *done_at;              // per instance: sweeps done when it stopped (0 = running)
+    double tol;
+    int max_iter;
+    unsigned long long timeout_ns;
+    Ctrl *ctrl;
+};
+
+// One segment of an instance; D and VEC fixed at compile time.
+template <int D, int VEC>
+__device__ __forceinline__ float batch_segment(const BatchInst &I, const uint8_t *code, const float *R,
+                                               const float *V, float *W, int seg) {
+    BandArgs a;
+    a.nstates = I.nstates;
+    a.nlast = I.nlast;
+#pragma unroll
+    for (int d = 0; d < kMaxDim; d++) a.stride[d] = d < 3 ? (d < D ? I.stride[d] : 0) : 0;
+    a.w_move = I.w_move;
+    a.w_perp = I.w_perp;
+    a.w_stay = I.w_stay;
+    a.gamma = I.gamma;
+    a.code = code + I.offset;
+    a.R32 = R + I.offset;
+    a.R64 = nullptr;
+    Segment<float, float, D, VEC> sg;
+    sg.template load<M_VI>(a, V + I.offset, nullptr, seg * VEC);
+    return sg.template finish_vi<false>(a, W + I.offset, nullptr, seg * VEC);
+}
+
+__device__ __forceinline__ float batch_item(const BatchInst &I, const uint8_t *code, const float *R, const float *V,
+                                            float *W, int seg) {
+    switch (I.ndim * 8 + I.vec) {
+        case 1 * 8 + 1: return batch_segment<1, 1>(I, code, R, V, W, seg);
+        case 1 * 8 + 2: return batch_segment<1, 2>(I, code, R, V, W, seg);
+        case 1 * 8 + 4: return batch_segment<1, 4>(I, code, R, V, W, seg);
+        case 2 * 8 + 1: return batch_segment<2, 1>(I, code, R, V, W, seg);
+        case 2 * 8 + 2: return batch_segment<2, 2>(I, code, R, V, W, seg);
+        case 2 * 8 + 4: return batch_segment<2, 4>(I, code, R, V, W, seg);
+        case 3 * 8 + 1: return batch_segment<3, 1>(I, code, R, V, W, seg);
+        case 3 * 8 + 2: return batch_segment<3, 2>(I, code, R, V, W, seg);
+        default: return batch_segment<3, 4>(I, code, R, V, W, seg);
+    }
+}
+
+template <int IPT>
+__global__ void __launch_bounds__(512) batch_vi_kernel(BatchArgs b) {
+    __shared__ int s_state;       // 0 skip, 1 work, 2 just stopped
+    __shared__ float s_red[16];
+    const unsigned nb = gridDim.x;
+    const int tid = threadIdx.x;
+    unsigned long long ph0 = 0ull, ph1 = 0ull;
+    int k = 0;
+    for (; k <= b.max_iter; k++) {
+        const float *cur = (k & 1) ? b.W : b.V;
+        float *nxt = (k & 1) ? b.V : b.W;
+        int worked = 0;
+        for (int t = blockIdx.x; t < b.ntiles; t += nb) {
+            const BatchTile T = b.tiles[t];
+            if (tid == 0) {
+                int st = 1;
+                if (b.done_at[T.inst] != 0) {
+                    st = 0;
+                } else if (k > 0) {
+                    const double r = __longlong_as_double(
+                        (long long)*(volatile unsigned long long *)&b.res[(size_t)((k - 1) % 3) * b.ninst + T.inst]);
+                    if (r < b.tol) st = 2;
+                }
+                if (st == 1 && k == b.max_iter) st = 3;   // limit reached: stop without a sweep
+                if (st == 2 || st == 3) {
+                    // every block that sees the stop writes the same value
+                    b.done_at[T.inst] = st == 2 ? k : -k;
+                    st = 0;
+                }
+                if (st == 1 && T.first_item == 0)
+                    b.res[(size_t)((k + 1) % 3) * b.ninst + T.inst] = 0ull;
+                s_state = st;
+            }
+            __syncthreads();
+            const int st = s_state;
+            __syncthreads();
+            if (st == 0) continue;
+            worked = 1;
+            const BatchInst I = b.inst[T.inst];
+            float r = 0.f;
+#pragma unroll
+            for (int u = 0; u < IPT; u++) {
+                const int it = tid + u * blockDim.x;
+                if (it < T.nitems) r = fmaxf(r, batch_item(I, b.code, b.R, cur, nxt, T.first_item + it));
+            }
+            // block max -> the instance's slot for sweep k
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xFFFFFFFFu, r, o));
+            if ((tid & 31) == 0) s_red[tid >> 5] = r;
+            __syncthreads();
+            if (tid == 0) {
+                float m = 0.f;
+                for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = fmaxf(m, s_red[w]);
+                if (m > 0.f)
+                    atomicMax(&b.res[(size_t)(k % 3) * b.ninst + T.inst],
+                              (unsigned long long)__double_as_longlong((double)m));
+            }
+            __syncthreads();
+        }
+        const long long busy = grid_sync_count(b.ctrl, k, nb, tid == 0 ? worked : 0, b.timeout_ns, ph0, ph1, false);
+        if (busy < 0) return;
+        if (busy == 0) break;
+    }
+    // results: an instance stopped at sweep count n has its values in V if n
+    // is even, in W if n is odd
+    for (int t = blockIdx.x; t < b.ntiles; t += nb) {
+        const BatchTile T = b.tiles[t];
+        const int n = b.done_at[T.inst];
+        const int sweeps = n < 0 ? -n : n;
+        if (!(sweeps & 1)) continue;
+        const BatchInst I = b.inst[T.inst];
+        const int s0 = T.first_item * I.vec, s1 = min((T.first_item + T.nitems) * I.vec, I.nstates);
+        for (int s = s0 + tid; s < s1; s += blockDim.x) b.V[I.offset + s] = b.W[I.offset + s];
+    }
+    if (blockIdx.x == 0 && tid == 0) b.ctrl->iterations = k;
+}
+
+}  // namespace cpmdp
+
+// ---------------------------------------------------------------------------
+// host side
+
+struct cpmdp_batch {
+    int device = -1;
+    int ninst = 0;
+    long long total_states = 0;
+    std::vector<cpmdp::BatchInst> inst;
+    std::vector<int> inst_actions;
+    std::vector<int64_t> offsets;
+    cpmdp::BatchInst *d_inst = nullptr;
+    cpmdp::BatchTile *d_tiles = nullptr;
+    int ntiles = 0;
+    int tile_items = 0;
+    int block = 0;
+    int ipt = 1;
+    uint8_t *d_code = nullptr;
+    float *d_R = nullptr;
+    float *d_W = nullptr;
+    unsigned long long *d_res = nullptr;
+    int *d_done = nullptr;
+    cpmdp::Ctrl *d_ctrl = nullptr;
+    bool graph_failed = false;
+    bool tuned = false;
+    int num_sms = 0;
+    int grid = 0;
+    // CUDA graph of one solve, recorded for (V pointer, stream, options)
+    cudaGraphExec_t graph = nullptr;
+    void *graph_V = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    double graph_tol = 0;
+    int graph_max_iter = 0;
+    double graph_timeout = 0;
+    std::vector<cpmdp::BatchTile> tiles_host;
+};
+
+namespace cpmdp {
+
+static void free_batch_device(cpmdp_batch &B) {
+    void *ptrs[] = {B.d_inst, B.d_tiles, B.d_code, B.d_R, B.d_W, B.d_res, B.d_done, B.d_ctrl};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (B.graph) cudaGraphExecDestroy(B.graph);
+    B.graph = nullptr;
+}
+
+static std::vector<BatchTile> make_tiles(const std::vector<BatchInst> &inst, int tile_items,
+                                         std::vector<int> *first_tile) {
+    std::vector<BatchTile> tiles;
+    first_tile->assign(inst.size(), 0);
+    for (size_t i = 0; i < inst.size(); i++) {
+        const int nitems = inst[i].nstates / inst[i].vec;
+        (*first_tile)[i] = (int)tiles.size();
+        for (int f = 0; f < nitems; f += tile_items) tiles.push_back({(int)i, f, std::min(tile_items, nitems - f)});
+    }
+    return tiles;
+}
+
+// Autotuner result cache: (number of instances, total states / 64K) -> (block, items per thread)
+static std::mutex g_tune_mutex;
+static std::map<std::pair<int, long long>, std::pair<int, int>> g_tune_cache;
+
+template <int IPT>
+static cudaError_t launch_batch(const cpmdp_batch &B, int block, const BatchArgs &args, cudaStream_t st, int *grid_out) {
+    static int occ[3] = {0, 0, 0};
+    const int bi = block == 128 ? 0 : (block == 256 ? 1 : 2);
+    if (occ[bi] <= 0) {
+        int o = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, batch_vi_kernel<IPT>, block, 0);
+        if (e != cudaSuccess) return e;
+        occ[bi] = o > 0 ? o : 1;
+    }
+    int grid = occ[bi] * B.num_sms;
+    if (grid > B.ntiles) grid = B.ntiles;
+    if (grid < 1) grid = 1;
+    *grid_out = grid;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_vi_kernel<IPT>, args);
+}
+
+static cudaError_t enqueue_batch(const cpmdp_batch &B, float *V, double tol, int max_iter, double timeout_s,
+                                 int block, int ipt, cudaStream_t st, int *grid_out) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(B.d_ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(B.d_res, 0, sizeof(unsigned long long) * 3 * B.ninst, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(B.d_done, 0, sizeof(int) * B.ninst, st)) != cudaSuccess) return e;
+    BatchArgs a;
+    a.inst = B.d_inst;
+    a.tiles = B.d_tiles;
+    a.ntiles = B.ntiles;
+    a.ninst = B.ninst;
+    a.code = B.d_code;
+    a.R = B.d_R;
+    a.V = V;
+    a.W = B.d_W;
+    a.res = B.d_res;
+    a.done_at = B.d_done;
+    a.tol = tol;
+    a.max_iter = max_iter;
+    a.timeout_ns = (unsigned long long)(timeout_s * 1e9);
+    a.ctrl = B.d_ctrl;
+    return ipt == 2 ? launch_batch<2>(B, block, a, st, grid_out) : launch_batch<1>(B, block, a, st, grid_out);
+}
+
+static cpmdp_status upload_tiles(cpmdp_batch &B, int tile_items) {
+    std::vector<int> first;
+    std::vector<BatchTile> tiles = make_tiles(B.inst, tile_items, &first);
+    for (int i = 0; i < B.ninst; i++) B.inst[(size_t)i].first_tile = first[(size_t)i];
+    if (B.d_tiles) cudaFree(B.d_tiles);
+    B.d_tiles = nullptr;
+    CPMDP_CUDA(cudaMalloc(&B.d_tiles, tiles.size() * sizeof(BatchTile)));
+    CPMDP_CUDA(cudaMemcpy(B.d_tiles, tiles.data(), tiles.size() * sizeof(BatchTile), cudaMemcpyHostToDevice));
+    CPMDP_CUDA(cudaMemcpy(B.d_inst, B.inst.data(), B.inst.size() * sizeof(BatchInst), cudaMemcpyHostToDevice));
+    B.ntiles = (int)tiles.size();
+    B.tile_items = tile_items;
+    B.tiles_host = tiles;
+    return CPMDP_OK;
+}
+
+// Time `sweeps` global sweeps for each (block, items per thread) candidate
+// on the batch itself (values from zero, scratch output), keep the fastest.
+static cpmdp_status autotune(cpmdp_batch &B, cudaStream_t st) {
+    const std::pair<int, long long> key(B.ninst, B.total_states >> 16);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            B.block = it->second.first;
+            B.ipt = it->second.second;
+            return upload_tiles(B, B.block * B.ipt);
+        }
+    }
+    const int cand[][2] = {{128, 1}, {256, 1}, {512, 1}, {256, 2}, {512, 2}};
+    // the candidates run on a temporary value tensor (the caller's V is the start)
+    float *V = nullptr;
+    CPMDP_CUDA(cudaMalloc(&V, sizeof(float) * B.total_states));
+    struct FreeV { float *p; ~FreeV() { cudaFree(p); } } free_v{V};
+    float best_ms = 1e30f;
+    int best = 1;
+    cudaEvent_t e0, e1;
+    CPMDP_CUDA(cudaEventCreate(&e0));
+    CPMDP_CUDA(cudaEventCreate(&e1));
+    for (int c = 0; c < 5; c++) {
+        cpmdp_status s = upload_tiles(B, cand[c][0] * cand[c][1]);
+        if (s != CPMDP_OK) return s;
+        float ms_sum = 0.f;
+        for (int rep = 0; rep < 3; rep++) {
+            CPMDP_CUDA(cudaMemsetAsync(V, 0, sizeof(float) * B.total_states, st));
+            CPMDP_CUDA(cudaEventRecord(e0, st));
+            int grid = 0;
+            CPMDP_CUDA(enqueue_batch(B, V, 0.0, 8, 2.0, cand[c][0], cand[c][1], st, &grid));
+            CPMDP_CUDA(cudaEventRecord(e1, st));
+            CPMDP_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_sum += ms;
+        }
+        if (ms_sum < best_ms) { best_ms = ms_sum; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B.block = cand[best][0];
+    B.ipt = cand[best][1];
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_cache[key] = std::make_pair(B.block, B.ipt);
+    }
+    return upload_tiles(B, B.block * B.ipt);
+}
+
+}  // namespace cpmdp
+
+using namespace cpmdp;
+
+extern "C" {
+
+cpmdp_status cpmdp_batch_build(const cpmdp_problem *problems, int32_t count, int device, cpmdp_batch **out) {
+    if (!out || !problems || count < 1) { set_error("batch: problems, count >= 1 and out are required"); return CPMDP_EINVAL; }
+    *out = nullptr;
+    if (device < 0) { set_error("batch: a CUDA device is required"); return CPMDP_EINVAL; }
+    cpmdp_batch *B = new (std::nothrow) cpmdp_batch();
+    if (!B) { set_error("host allocation failed"); return CPMDP_ENOMEM; }
+    B->device = device;
+    B->ninst = count;
+    std::vector<uint8_t> codes;
+    std::vector<float> rew;
+    long long off = 0;
+    for (int i = 0; i < count; i++) {
+        const cpmdp_problem &p = problems[i];
+        if (p.kind != CPMDP_GRIDWORLD || p.ndim < 1 || p.ndim > 3) {
+            set_error("batch instance %d: GridWorld with 1 to 3 dimensions required", i);
+            delete B;
+            return CPMDP_EINVAL;
+        }
+        // reuse the single-instance validation and factor construction
+        cpmdp_factors *f = nullptr;
+        cpmdp_status st = cpmdp_build_factors(&p, -1, &f);
+        if (st != CPMDP_OK) {
+            char msg[400];
+            snprintf(msg, sizeof(msg), "batch instance %d: %s", i, cpmdp_last_error());
+            set_error("%s", msg);
+            delete B;
+            return st;
+        }
+        const Factors &F = f->f;
+        BatchInst I;
+        memset(&I, 0, sizeof(I));
+        I.offset = off;
+        I.nstates = (int)F.nstates;
+        I.ndim = F.ndim;
+        I.nlast = (int)F.shape[F.ndim - 1];
+        for (int d = 0; d < F.ndim; d++) I.stride[d] = (int)F.stride[d];
+        I.vec = (I.nlast % 4 == 0) ? 4 : ((I.nlast % 2 == 0) ? 2 : 1);
+        I.w_move = (float)F.w_move;
+        I.w_perp = (float)F.w_perp;
+        I.w_stay = (float)F.w_stay;
+        I.gamma = (float)F.gamma;
+        B->inst.push_back(I);
+        B->inst_actions.push_back(F.nactions);
+        B->offsets.push_back(off);
+        for (int64_t s = 0; s < F.nstates; s++) {
+            codes.push_back((uint8_t)F.code[(size_t)s]);
+            rew.push_back((float)F.reward[(size_t)s]);
+        }
+        // pad each instance to a multiple of 4 states so every instance starts 16-byte aligned
+        off += F.nstates;
+        while (off % 4) { codes.push_back(0xFF); rew.push_back(0.f); off++; }
+        cpmdp_free_factors(f);
+    }
+    B->offsets.push_back(off);
+    B->total_states = off;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(device) != cudaSuccess) { set_error("cannot select CUDA device %d", device); delete B; return CPMDP_ECUDA; }
+    auto fail = [&](cudaError_t e, const char *w) {
+        cuda_fail(e, w);
+        free_batch_device(*B);
+        delete B;
+        if (prev >= 0) cudaSetDevice(prev);
+        return CPMDP_ECUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaDeviceGetAttribute(&B->num_sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return fail(e, "attr");
+    if ((e = cudaMalloc(&B->d_code, (size_t)off)) != cudaSuccess) return fail(e, "cudaMalloc code");
+    if ((e = cudaMalloc(&B->d_R, (size_t)off * sizeof(float))) != cudaSuccess) return fail(e, "cudaMalloc R");
+    if ((e = cudaMalloc(&B->d_W, (size_t)off * sizeof(float))) != cudaSuccess) return fail(e, "cudaMalloc W");
+    if ((e = cudaMalloc(&B->d_res, sizeof(unsigned long long) * 3 * count)) != cudaSuccess) return fail(e, "cudaMalloc res");
+    if ((e = cudaMalloc(&B->d_done, sizeof(int) * count)) != cudaSuccess) return fail(e, "cudaMalloc done");
+    if ((e = cudaMalloc(&B->d_ctrl, sizeof(Ctrl))) != cudaSuccess) return fail(e, "cudaMalloc ctrl");
+    if ((e = cudaMalloc(&B->d_inst, sizeof(BatchInst) * count)) != cudaSuccess) return fail(e, "cudaMalloc inst");
+    if ((e = cudaMemcpy(B->d_code, codes.data(), (size_t)off, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "copy code");
+    if ((e = cudaMemcpy(B->d_R, rew.data(), (size_t)off * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "copy R");
+    B->block = 256;
+    B->ipt = 1;
+    if (upload_tiles(*B, 256) != CPMDP_OK) { free_batch_device(*B); delete B; if (prev >= 0) cudaSetDevice(prev); return CPMDP_ECUDA; }
+    if (prev >= 0) cudaSetDevice(prev);
+    *out = B;
+    return CPMDP_OK;
+}
+
+void cpmdp_batch_free(cpmdp_batch *B) {
+    if (!B) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(B->device);
+    free_batch_device(*B);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete B;
+}
+
+cpmdp_status cpmdp_batch_info(const cpmdp_batch *B, int32_t *count, int64_t *total_states, int64_t *offsets) {
+    if (!B) { set_error("batch is NULL"); return CPMDP_EINVAL; }
+    if (count) *count = B->ninst;
+    if (total_states) *total_states = B->total_states;
+    if (offsets) memcpy(offsets, B->offsets.data(), sizeof(int64_t) * B->offsets.size());
+    return CPMDP_OK;
+}
+
+cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_solve_opts *opts,
+                                         int32_t *iterations_out, double *residual_out, cpmdp_result *info,
+                                         void *stream) {
+    if (!B || !V) { set_error("batch and V are required"); return CPMDP_EINVAL; }
+    if (((uintptr_t)V & 15u) != 0) { set_error("V must be 16-byte aligned"); return CPMDP_EINVAL; }
+    SolveOpts o = resolve_opts(opts, CPMDP_F32);
+    if (!(o.tol > 0) || o.max_iter < 1 || !(o.timeout_s > 0)) { set_error("invalid solve options"); return CPMDP_EINVAL; }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(B->device) != cudaSuccess) { set_error("cannot select CUDA device %d", B->device); return CPMDP_ECUDA; }
+    struct Restore { int p; ~Restore() { if (p >= 0) cudaSetDevice(p); } } restore{prev};
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!B->tuned) {
+        // first solve: pick block and tile sizes on this batch
+        cpmdp_status s = autotune(*B, st);
+        if (s != CPMDP_OK) return s;
+        B->tuned = true;
+    }
+    // record the solve (state resets + the cooperative launch) into a CUDA
+    // graph once per (V, stream, options) and replay it; if recording is
+    // refused, launch directly
+    const bool same = B->graph && B->graph_V == (void *)V && B->graph_stream == st && B->graph_tol == o.tol &&
+                      B->graph_max_iter == o.max_iter && B->graph_timeout == o.timeout_s;
+    if (!same && !B->graph_failed) {
+        if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
+        cudaStream_t cap;
+        CPMDP_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        int grid = 0;
+        if (e == cudaSuccess) e = enqueue_batch(*B, V, o.tol, o.max_iter, o.timeout_s, B->block, B->ipt, cap, &grid);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (e == cudaSuccess && e2 == cudaSuccess && g) e = cudaGraphInstantiate(&B->graph, g, 0);
+        else if (e == cudaSuccess) e = e2;
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            B->graph_failed = true;
+            B->graph = nullptr;
+        } else {
+            B->grid = grid;
+            B->graph_V = V;
+            B->graph_stream = st;
+            B->graph_tol = o.tol;
+            B->graph_max_iter = o.max_iter;
+            B->graph_timeout = o.timeout_s;
+        }
+    }
+    cudaEvent_t e0, e1;
+    CPMDP_CUDA(cudaEventCreate(&e0));
+    CPMDP_CUDA(cudaEventCreate(&e1));
+    CPMDP_CUDA(cudaEventRecord(e0, st));
+    if (B->graph && !B->graph_failed) {
+        CPMDP_CUDA(cudaGraphLaunch(B->graph, st));
+    } else {
+        int grid = 0;
+        CPMDP_CUDA(enqueue_batch(*B, V, o.tol, o.max_iter, o.timeout_s, B->block, B->ipt, st, &grid));
+    }
+    CPMDP_CUDA(cudaEventRecord(e1, st));
+    Ctrl hc;
+    std::vector<int> done((size_t)B->ninst);
+    std::vector<unsigned long long> res((size_t)3 * B->ninst);
+    CPMDP_CUDA(cudaMemcpyAsync(&hc, B->d_ctrl, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    CPMDP_CUDA(cudaMemcpyAsync(done.data(), B->d_done, sizeof(int) * B->ninst, cudaMemcpyDeviceToHost, st));
+    CPMDP_CUDA(cudaMemcpyAsync(res.data(), B->d_res, sizeof(unsigned long long) * 3 * B->ninst, cudaMemcpyDeviceToHost, st));
+    CPMDP_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (hc.status != 0) {
+        set_error("a device-side wait exceeded %.3g s; results are undefined", o.timeout_s);
+        return (cpmdp_status)hc.status;
+    }
+    int not_conv = 0;
+    long long backups = 0;
+    double worst = 0.0;
+    for (int i = 0; i < B->ninst; i++) {
+        const int n = done[(size_t)i];
+        const int sweeps = n < 0 ? -n : n;
+        if (n <= 0) not_conv++;
+        double r = 0.0;
+        if (sweeps > 0) memcpy(&r, &res[(size_t)((sweeps - 1) % 3) * B->ninst + i], sizeof(double));
+        if (iterations_out) iterations_out[i] = sweeps;
+        if (residual_out) residual_out[i] = r;
+        worst = r > worst ? r : worst;
+        backups += (long long)sweeps * B->inst[(size_t)i].nstates * B->inst_actions[(size_t)i];
+    }
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->status = not_conv ? CPMDP_ENOCONV : CPMDP_OK;
+        info->iterations = hc.iterations;
+        info->rounds = (B->graph && !B->graph_failed) ? 1 : 0;   // 1 when replayed from a CUDA graph
+        info->residual = worst;
+        info->certified_residual = -1.0;
+        info->error_bound = -1.0;
+        info->backups = backups;
+        info->elapsed_ms = ms;
+    }
+    if (not_conv) {
+        set_error("%d instance(s) reached max_iter before tol", not_conv);
+        return CPMDP_ENOCONV;
+    }
+    return CPMDP_OK;
+}
+
+}  // extern "C"

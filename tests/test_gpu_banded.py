@@ -12,6 +12,10 @@ Tolerances (derived from the arithmetic; u = 2^-24 for FP32):
 * one FP64 sweep: same with u = 2^-53 (we use 1e-13 (max|R| + max|V|)).
 * k FP32 sweeps from the same start: errors add up, contracted by gamma
   each sweep: <= eps (1 - gamma^k) / (1 - gamma) with eps the one-sweep bound.
+* FP32 and FP64 value iteration to the same tol: each result is within
+  gamma tol / (1 - gamma) of V*, so they differ by at most
+  (2 gamma tol + eps) / (1 - gamma); the sweep at which an FP32 residual
+  crosses tol is not compared (its rounding noise is of the size of tol).
 * policies are compared where the oracle's best/second-best Q gap exceeds
   twice the value tolerance (FP32) or 1e-6 (FP64), i.e. where rounding
   cannot flip the argmax.
@@ -205,11 +209,10 @@ def test_vi_3d_64_matches_oracle(cp, oc, prec):
         assert r["iterations"] == ko
         assert np.abs(g - Vo).max() <= 1e-12
     else:
-        assert abs(r["iterations"] - ko) <= 3
-        # k-sweep FP32 rounding bound plus a few final residuals for a
-        # stopping sweep that differs by up to 3
+        # both runs stop with a residual below tol: each is within
+        # gamma tol / (1 - gamma) of V*; FP32 rounding adds eps / (1 - gamma)
         eps = 14 * U32 * (np.abs(gw.reward).max() + np.abs(Vo).max())
-        bound = eps / (1 - gw.gamma) + 1e-5
+        bound = (2 * gw.gamma * 1e-6 + eps) / (1 - gw.gamma)
         err = np.abs(g - Vo).max()
         assert err <= bound, (err, bound)
     # certified residual and policy from the FP64 sweep of the returned V

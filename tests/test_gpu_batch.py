@@ -1,0 +1,104 @@
+"""Batched value iteration: one persistent launch over many uneven GridWorlds.
+
+Each instance is checked against the FP64 C oracle run to the same stopping
+rule and against the single-instance fused solver (same arithmetic: same
+sweep count, values within 1e-6). Against the oracle only values are
+compared: both runs stop with a residual below tol, so each is within
+gamma tol / (1 - gamma) of V*, and FP32 rounding adds at most
+eps / (1 - gamma) with eps = 14 u (max|R| + max|V|), u = 2^-24. Near tol
+the FP32 residual carries rounding noise of the same size, so the sweep at
+which it crosses tol is not compared.
+"""
+import numpy as np
+import pytest
+
+import cpmdp_inputs as ci
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def cp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2103_00331_gb300 as cp
+    return cp
+
+
+def _instances():
+    inst = ci.batch_gridworlds(count=192, seed=7)
+    # edge cases: a 1-D chain, a single state, a ragged thin grid, an all-obstacle grid
+    inst.append(ci.gridworld((37,), p=0.9, gamma=0.95, step_reward=-0.04, goal_rewards=[1.0], seed=1))
+    inst.append(ci.GridWorld(shape=(1,), p=0.8, gamma=0.9, cell=np.zeros(1, np.uint8), reward=np.array([0.3])))
+    inst.append(ci.gridworld((3, 129), p=0.7, gamma=0.97, step_reward=-0.04, goal_rewards=[1.0, -1.0],
+                             obstacle_rate=0.1, seed=2))
+    inst.append(ci.GridWorld(shape=(4, 4), p=0.8, gamma=0.9, cell=np.ones((4, 4), np.uint8),
+                             reward=np.zeros((4, 4))))
+    return inst
+
+
+def test_batch_matches_oracle_and_single(cp, oc_lib=None):
+    import torch
+    from oracle import cpfactor as oc
+    inst = _instances()
+    B = cp.batch_build(inst, device=0)
+    assert B.count == len(inst)
+    V = torch.zeros(int(B.total_states), dtype=torch.float32, device="cuda")
+    r, iters, res = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=5000))
+    assert r["status"] == cp.OK and np.all(res < 1e-6)
+    Vh = V.double().cpu().numpy()
+    picks = list(range(0, 192, 8)) + list(range(192, len(inst)))
+    for i in picks:
+        gw = inst[i]
+        lo, n = int(B.offsets[i]), gw.nstates
+        got = Vh[lo:lo + n]
+        Vo, _, ko, _ = oc.value_iteration(gw, tol=1e-6, max_iter=5000)
+        eps = 14 * U32 * (np.abs(gw.reward).max() + np.abs(Vo).max())
+        bound = (2 * gw.gamma * 1e-6 + eps) / (1 - gw.gamma)
+        assert np.abs(got - Vo).max() <= bound, (i, np.abs(got - Vo).max(), bound, iters[i], ko)
+    # the single-instance fused solver on a few instances
+    for i in picks[:6] + [len(inst) - 2]:
+        gw = inst[i]
+        f = cp.build_factors(gw, device=0)
+        Vs = torch.zeros(gw.nstates, dtype=torch.float32, device="cuda")
+        rs = cp.value_iteration(f, cp.F32, Vs, None, opts=cp.default_opts(max_iter=5000, certify=0))
+        lo = int(B.offsets[i])
+        assert rs["iterations"] == int(iters[i])
+        assert np.abs(Vs.double().cpu().numpy() - Vh[lo:lo + gw.nstates]).max() <= 1e-6
+        f.close()
+    # a second solve replays the recorded graph and reproduces the result
+    V2 = V.clone().zero_()
+    V.zero_()
+    r2, it2, _ = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=5000))
+    assert np.array_equal(it2, iters) and np.array_equal(V.double().cpu().numpy(), Vh)
+    assert r2["rounds"] in (0, 1)
+    B.close()
+
+
+def test_batch_max_iter_and_warm_start(cp):
+    import torch
+    inst = ci.batch_gridworlds(count=40, seed=3)
+    B = cp.batch_build(inst, device=0)
+    V = torch.zeros(int(B.total_states), dtype=torch.float32, device="cuda")
+    r, iters, _ = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=7), raise_on_noconv=False)
+    assert r["status"] == cp.ENOCONV and np.all(iters <= 7)
+    # continuing from the partial result converges and uses fewer sweeps than from zero
+    r, it_warm, res = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=5000))
+    V0 = torch.zeros_like(V)
+    r0, it_zero, _ = cp.batch_value_iteration(B, V0, opts=cp.default_opts(max_iter=5000))
+    assert np.all(res < 1e-6)
+    assert it_warm.sum() < it_zero.sum()
+    B.close()
+
+
+def test_batch_rejects_invalid_instance(cp):
+    bad = ci.config_small_2d(0)
+    bad.reward = bad.reward.copy()
+    bad.reward[0, 0] = np.nan
+    with pytest.raises(cp.CpmdpError) as ei:
+        cp.batch_build([ci.config_small_2d(1), bad], device=0)
+    assert ei.value.status == cp.EINVAL and "instance 1" in cp.last_error()
