@@ -288,6 +288,48 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *batch, float *V, const cpm
                                          int32_t *iterations_out, double *residual_out, cpmdp_result *info,
                                          void *stream);
 
+/*
+ * Learned warm start (no counterpart in the paper's method; it only changes
+ * where value iteration starts). A fully convolutional 3-D network works on
+ * a grid coarsened by 4 in every dimension. Activations are channels-last
+ * bf16 arrays [n][z][y][x][64] (as uint16), weights per layer FP32
+ * W[27][64][64] (tap, out, in; tap t = (dz+1)*9 + (dy+1)*3 + (dx+1) for
+ * offsets dilation * (dz, dy, dx)), "same" zero padding. All device memory
+ * caller-owned; all calls asynchronous on `stream`; errors EINVAL / ECUDA.
+ *
+ * cpmdp_ws_features: coarse features of batch instances first..first+count-1
+ *   (3-D, one shape, contiguous): per 4x4x4 cell the mean reward of its
+ *   non-obstacle states, its obstacle fraction, its largest terminal reward
+ *   (0 if none), -log(1 - gamma) / 5; channels 4..63 zero.
+ * cpmdp_ws_targets: per coarse cell the mean of V over its non-obstacle
+ *   states (float [count][cells]) and a mask (1 if it has any).
+ * cpmdp_ws_upsample: V (packed batch layout) = coarse estimate on free
+ *   states, R(t) on terminals, 0 on obstacles.
+ */
+cpmdp_status cpmdp_ws_features(const cpmdp_batch *batch, int32_t first, int32_t count, uint16_t *feat, void *stream);
+cpmdp_status cpmdp_ws_targets(const cpmdp_batch *batch, const float *V, int32_t first, int32_t count, float *target,
+                              float *mask, void *stream);
+cpmdp_status cpmdp_ws_upsample(const cpmdp_batch *batch, const float *coarse, int32_t first, int32_t count, float *V,
+                               void *stream);
+/* y = conv(x, W) + b (ReLU if relu); wf = W as [27][in][out] bf16; y0 (nullable) gets channel 0 in FP32. */
+cpmdp_status cpmdp_conv3d_forward(const uint16_t *x, const uint16_t *wf, const float *bias, uint16_t *y, float *y0,
+                                  int32_t n, int32_t z, int32_t y_, int32_t x_, int32_t dilation, int32_t relu,
+                                  void *stream);
+/* dx = conv^T(dy, W) times (act_in > 0) when act_in is given; wb = W as [27][out][in] bf16. */
+cpmdp_status cpmdp_conv3d_backward_data(const uint16_t *dy, const uint16_t *wb, const uint16_t *act_in, uint16_t *dx,
+                                        int32_t n, int32_t z, int32_t y_, int32_t x_, int32_t dilation, void *stream);
+/* dw += dL/dW (FP32 [27][64][64]), db += dL/db (FP32 [64], nullable). */
+cpmdp_status cpmdp_conv3d_backward_weight(const uint16_t *x, const uint16_t *dy, float *dw, float *db, int32_t n,
+                                          int32_t z, int32_t y_, int32_t x_, int32_t dilation, void *stream);
+/* Mean over nvox cells of mask (pred - target)^2: dy channel 0 = its gradient, other channels 0; *loss += value. */
+cpmdp_status cpmdp_ws_loss_grad(const float *pred, const float *target, const float *mask, int32_t nvox, uint16_t *dy,
+                                float *loss, void *stream);
+/* One Adam step (bias-corrected, step >= 1) on n FP32 parameters. */
+cpmdp_status cpmdp_adam_step(float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1,
+                             float beta2, float eps, int32_t step, void *stream);
+/* FP32 W[layers][27][64][64] -> bf16 wf (per tap [in][out]) and wb (per tap [out][in]). */
+cpmdp_status cpmdp_ws_cast_weights(const float *w, uint16_t *wf, uint16_t *wb, int32_t layers, void *stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char *cpmdp_last_error(void);
 

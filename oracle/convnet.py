@@ -69,32 +69,51 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
-DILATIONS = (1, 2, 4, 8, 1, 1)
+DILATIONS = (1, 2, 4, 2, 1, 1)
 
 
-def net_forward(x, params):
+def bf16_round(a):
+    """Round to the nearest bfloat16 (ties to even), via float32: keep the top
+    16 bits of the float32 pattern after adding 0x7FFF plus the lowest kept
+    bit. The network stores activations and gradients this way."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def net_forward(x, params, bf16=False):
     """Layers conv -> ReLU (all but the last); params = [(w, b, dilation)].
-    Returns the list of activations [x, a1, ..., out]."""
+    Returns the list of activations [x, a1, ..., out]. With bf16=True every
+    hidden activation is stored rounded to bf16 (the last output stays
+    unrounded, as the loss reads it in FP32)."""
     acts = [x]
     h = x
     for i, (w, b, d) in enumerate(params):
         z = conv_forward(h, w, b, d)
         h = z if i == len(params) - 1 else relu(z)
+        if bf16 and i < len(params) - 1:
+            h = bf16_round(h)
         acts.append(h)
     return acts
 
 
 def net_loss(out, target, mask):
-    """Mean squared error of output channel 0 over the masked coarse cells."""
+    """Squared error of output channel 0 on the masked coarse cells, averaged
+    over all coarse cells of the batch."""
     diff = (out[..., 0] - target) * mask
-    return float((diff ** 2).sum() / max(mask.sum(), 1.0))
+    return float((diff ** 2).sum() / diff.size)
 
 
-def net_backward(acts, params, target, mask):
-    """Gradients [(dW, db)] of net_loss, by the chain rule layer by layer."""
+def net_backward(acts, params, target, mask, bf16=False):
+    """Gradients [(dW, db)] of net_loss, by the chain rule layer by layer.
+    With bf16=True the gradient passed between layers is stored rounded to
+    bf16, as in the network's kernels."""
     out = acts[-1]
     g = np.zeros_like(out)
-    g[..., 0] = 2.0 * (out[..., 0] - target) * mask / max(mask.sum(), 1.0)
+    g[..., 0] = 2.0 * (out[..., 0] - target) * mask / mask.size
+    if bf16:
+        g = bf16_round(g)
     grads = []
     for i in range(len(params) - 1, -1, -1):
         w, b, d = params[i]
@@ -102,6 +121,8 @@ def net_backward(acts, params, target, mask):
         grads.append((dW, db))
         if i > 0:
             g = dxa * (acts[i] > 0)
+            if bf16:
+                g = bf16_round(g)
     return grads[::-1]
 
 

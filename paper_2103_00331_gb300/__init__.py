@@ -98,6 +98,19 @@ def _load():
     lib.cpmdp_batch_value_iteration.argtypes = [vp, vp, ctypes.POINTER(SolveOpts), vp, vp,
                                                 ctypes.POINTER(Result), vp]
     lib.cpmdp_batch_value_iteration.restype = ctypes.c_int
+    for name, args in [
+            ("cpmdp_ws_features", [vp, i32, i32, vp, vp]),
+            ("cpmdp_ws_targets", [vp, vp, i32, i32, vp, vp, vp]),
+            ("cpmdp_ws_upsample", [vp, vp, i32, i32, vp, vp]),
+            ("cpmdp_conv3d_forward", [vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, i32, vp]),
+            ("cpmdp_conv3d_backward_data", [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]),
+            ("cpmdp_conv3d_backward_weight", [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]),
+            ("cpmdp_ws_loss_grad", [vp, vp, vp, i32, vp, vp, vp]),
+            ("cpmdp_adam_step", [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, i32, vp]),
+            ("cpmdp_ws_cast_weights", [vp, vp, vp, i32, vp])]:
+        getattr(lib, name).argtypes = args
+        getattr(lib, name).restype = ctypes.c_int
     lib.cpmdp_last_error.argtypes = []
     lib.cpmdp_last_error.restype = ctypes.c_char_p
     lib.cpmdp_version.argtypes = []
@@ -110,8 +123,10 @@ lib = _load()
 EXPORTED = ["cpmdp_default_opts", "cpmdp_build_factors", "cpmdp_free_factors", "cpmdp_factors_info",
             "cpmdp_components", "cpmdp_bellman_backup", "cpmdp_value_iteration",
             "cpmdp_policy_iteration", "cpmdp_value_iteration_static", "cpmdp_batch_build",
-            "cpmdp_batch_free", "cpmdp_batch_info", "cpmdp_batch_value_iteration", "cpmdp_last_error",
-            "cpmdp_version"]
+            "cpmdp_batch_free", "cpmdp_batch_info", "cpmdp_batch_value_iteration", "cpmdp_ws_features",
+            "cpmdp_ws_targets", "cpmdp_ws_upsample", "cpmdp_conv3d_forward", "cpmdp_conv3d_backward_data",
+            "cpmdp_conv3d_backward_weight", "cpmdp_ws_loss_grad", "cpmdp_adam_step", "cpmdp_ws_cast_weights",
+            "cpmdp_last_error", "cpmdp_version"]
 
 
 def last_error() -> str:
@@ -341,3 +356,48 @@ def batch_value_iteration(batch: Batch, V, opts=None, stream=None, raise_on_noco
     if st != OK and not (st == ENOCONV and not raise_on_noconv):
         _check(st)
     return res.as_dict(), it, rs
+
+
+def ws_features(batch, first, count, feat, stream=None):
+    _check(lib.cpmdp_ws_features(batch.handle, int(first), int(count), _ptr(feat), _stream(stream)))
+
+
+def ws_targets(batch, V, first, count, target, mask, stream=None):
+    _check(lib.cpmdp_ws_targets(batch.handle, _ptr(V), int(first), int(count), _ptr(target), _ptr(mask),
+                                _stream(stream)))
+
+
+def ws_upsample(batch, coarse, first, count, V, stream=None):
+    _check(lib.cpmdp_ws_upsample(batch.handle, _ptr(coarse), int(first), int(count), _ptr(V), _stream(stream)))
+
+
+def conv3d_forward(x, wf, bias, y, y0, dims, dilation, relu, stream=None):
+    n, z, yy, xx = dims
+    _check(lib.cpmdp_conv3d_forward(_ptr(x), _ptr(wf), _ptr(bias), _ptr(y), _ptr(y0), n, z, yy, xx,
+                                    int(dilation), int(relu), _stream(stream)))
+
+
+def conv3d_backward_data(dy, wb, act_in, dx, dims, dilation, stream=None):
+    n, z, yy, xx = dims
+    _check(lib.cpmdp_conv3d_backward_data(_ptr(dy), _ptr(wb), _ptr(act_in), _ptr(dx), n, z, yy, xx,
+                                          int(dilation), _stream(stream)))
+
+
+def conv3d_backward_weight(x, dy, dw, db, dims, dilation, stream=None):
+    n, z, yy, xx = dims
+    _check(lib.cpmdp_conv3d_backward_weight(_ptr(x), _ptr(dy), _ptr(dw), _ptr(db), n, z, yy, xx,
+                                            int(dilation), _stream(stream)))
+
+
+def ws_loss_grad(pred, target, mask, nvox, dy, loss, stream=None):
+    _check(lib.cpmdp_ws_loss_grad(_ptr(pred), _ptr(target), _ptr(mask), int(nvox), _ptr(dy), _ptr(loss),
+                                  _stream(stream)))
+
+
+def adam_step(p, g, m, v, n, lr, beta1, beta2, eps, step, stream=None):
+    _check(lib.cpmdp_adam_step(_ptr(p), _ptr(g), _ptr(m), _ptr(v), int(n), lr, beta1, beta2, eps, int(step),
+                               _stream(stream)))
+
+
+def ws_cast_weights(w, wf, wb, layers, stream=None):
+    _check(lib.cpmdp_ws_cast_weights(_ptr(w), _ptr(wf), _ptr(wb), int(layers), _stream(stream)))

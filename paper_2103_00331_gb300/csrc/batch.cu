@@ -28,25 +28,9 @@
 #include <vector>
 
 #include "banded_common.cuh"
+#include "batch_internal.h"
 
 namespace cpmdp {
-
-struct BatchInst {
-    long long offset;      // first state in the packed arrays
-    int nstates;
-    int ndim;              // 1..3
-    int nlast;
-    int stride[3];
-    int vec;               // 1, 2 or 4
-    int first_tile;
-    float w_move, w_perp, w_stay, gamma;
-};
-
-struct BatchTile {
-    int inst;
-    int first_item;        // segment index within the instance
-    int nitems;
-};
 
 struct BatchArgs {
     const BatchInst *inst;
@@ -182,39 +166,6 @@ __global__ void __launch_bounds__(512) batch_vi_kernel(BatchArgs b) {
 
 // ---------------------------------------------------------------------------
 // host side
-
-struct cpmdp_batch {
-    int device = -1;
-    int ninst = 0;
-    long long total_states = 0;
-    std::vector<cpmdp::BatchInst> inst;
-    std::vector<int> inst_actions;
-    std::vector<int64_t> offsets;
-    cpmdp::BatchInst *d_inst = nullptr;
-    cpmdp::BatchTile *d_tiles = nullptr;
-    int ntiles = 0;
-    int tile_items = 0;
-    int block = 0;
-    int ipt = 1;
-    uint8_t *d_code = nullptr;
-    float *d_R = nullptr;
-    float *d_W = nullptr;
-    unsigned long long *d_res = nullptr;
-    int *d_done = nullptr;
-    cpmdp::Ctrl *d_ctrl = nullptr;
-    bool graph_failed = false;
-    bool tuned = false;
-    int num_sms = 0;
-    int grid = 0;
-    // CUDA graph of one solve, recorded for (V pointer, stream, options)
-    cudaGraphExec_t graph = nullptr;
-    void *graph_V = nullptr;
-    cudaStream_t graph_stream = nullptr;
-    double graph_tol = 0;
-    int graph_max_iter = 0;
-    double graph_timeout = 0;
-    std::vector<cpmdp::BatchTile> tiles_host;
-};
 
 namespace cpmdp {
 
@@ -400,7 +351,10 @@ cpmdp_status cpmdp_batch_build(const cpmdp_problem *problems, int32_t count, int
         I.nstates = (int)F.nstates;
         I.ndim = F.ndim;
         I.nlast = (int)F.shape[F.ndim - 1];
-        for (int d = 0; d < F.ndim; d++) I.stride[d] = (int)F.stride[d];
+        for (int d = 0; d < F.ndim; d++) {
+            I.stride[d] = (int)F.stride[d];
+            I.shape[d] = (int)F.shape[d];
+        }
         I.vec = (I.nlast % 4 == 0) ? 4 : ((I.nlast % 2 == 0) ? 2 : 1);
         I.w_move = (float)F.w_move;
         I.w_perp = (float)F.w_perp;

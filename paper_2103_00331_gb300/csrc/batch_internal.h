@@ -1,0 +1,66 @@
+// Internal layout of a packed batch of GridWorld instances (batch.cu),
+// shared with the warm-start kernels (warmstart.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace cpmdp {
+
+struct BatchInst {
+    long long offset;      // first state in the packed arrays
+    int nstates;
+    int ndim;              // 1..3
+    int nlast;
+    int stride[3];
+    int shape[3];
+    int vec;               // 1, 2 or 4
+    int first_tile;
+    float w_move, w_perp, w_stay, gamma;
+};
+
+struct BatchTile {
+    int inst;
+    int first_item;        // segment index within the instance
+    int nitems;
+};
+
+}  // namespace cpmdp
+
+struct cpmdp_batch {
+    int device = -1;
+    int ninst = 0;
+    long long total_states = 0;
+    std::vector<cpmdp::BatchInst> inst;
+    std::vector<int> inst_actions;
+    std::vector<int64_t> offsets;
+    cpmdp::BatchInst *d_inst = nullptr;
+    cpmdp::BatchTile *d_tiles = nullptr;
+    int ntiles = 0;
+    int tile_items = 0;
+    int block = 0;
+    int ipt = 1;
+    uint8_t *d_code = nullptr;
+    float *d_R = nullptr;
+    float *d_W = nullptr;
+    unsigned long long *d_res = nullptr;
+    int *d_done = nullptr;
+    cpmdp::Ctrl *d_ctrl = nullptr;
+    bool graph_failed = false;
+    bool tuned = false;
+    int num_sms = 0;
+    int grid = 0;
+    // CUDA graph of one solve, recorded for (V pointer, stream, options)
+    cudaGraphExec_t graph = nullptr;
+    void *graph_V = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    double graph_tol = 0;
+    int graph_max_iter = 0;
+    double graph_timeout = 0;
+    std::vector<cpmdp::BatchTile> tiles_host;
+};
+

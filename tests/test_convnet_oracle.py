@@ -89,3 +89,13 @@ def test_features_target_upsample():
     free = gw.cell == 0
     assert np.all(V0[(gw.cell == 1)] == 0) and np.all(V0[gw.cell == 2] == gw.reward[gw.cell == 2])
     assert V0[5, 6, 3] == (t[1, 1, 0] if free[5, 6, 3] else V0[5, 6, 3])
+
+
+def test_bf16_round_against_torch():
+    torch = pytest.importorskip("torch")
+    vals = np.concatenate([ci.random_values((4096,), seed=30, lo=-50, hi=50),
+                           [1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -2.5, 0.0, 1e-30, 3.0e38]])
+    want = torch.as_tensor(vals.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(N.bf16_round(vals), want)
+    assert N.bf16_round([1.0 + 2.0 ** -8])[0] == 1.0          # tie to even
+    assert N.bf16_round([1.0 + 3 * 2.0 ** -8])[0] == 1.0 + 2.0 ** -6

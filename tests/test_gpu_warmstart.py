@@ -1,0 +1,179 @@
+"""Warm-start network on the GPU against the FP64 oracle (oracle/convnet.py).
+
+Inputs and weights are rounded to bf16 on the host (round to nearest even,
+torch CPU) and the oracle evaluates the same rounded values in float64, so
+the only differences are FP32 accumulation and the bf16 rounding of outputs
+and intermediate activations:
+* one convolution: |y - y_ref| <= 2^-8 |y_ref| + 1e-5 sum|x||w| (bf16 output);
+* weight / bias gradients (FP32 outputs): <= 1e-4 of sum|dy||x|;
+* whole-network gradients against the oracle with the network's bf16
+  storage points (activations and inter-layer gradients rounded to bf16,
+  oracle/convnet.py bf16=True): what remains is FP32 vs FP64 accumulation
+  (about 1e-6) and the few elements whose accumulated value lands on the
+  other side of a bf16 rounding boundary (a 2^-8 relative step each, on a
+  small fraction f of elements, amplified through the remaining layers):
+  per-layer relative error (Frobenius) <= 5e-3.
+"""
+import numpy as np
+import pytest
+
+import cpmdp_inputs as ci
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2103_00331_gb300 as cp
+    from paper_2103_00331_gb300 import warmstart as ws
+    return cp, ws, torch
+
+
+def _bf16(a, torch):
+    """Round float64 values to bf16 on the host; returns (bf16 tensor, float64 values)."""
+    t = torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16)
+    return t, t.to(torch.float64).numpy()
+
+
+def test_conv_kernels_match_oracle(env):
+    cp, ws, torch = env
+    from oracle import convnet as N
+    dims = (2, 3, 4, 5)
+    shp = dims + (64,)
+    xb, x = _bf16(ci.random_values(shp, seed=1), torch)
+    dyb, dy = _bf16(ci.random_values(shp, seed=2), torch)
+    w32 = (ci.random_values((27, 64, 64), seed=3) * 0.1).astype(np.float32)
+    wq = torch.as_tensor(w32).to(torch.bfloat16).to(torch.float64).numpy()
+    b = (ci.random_values((64,), seed=4) * 0.1).astype(np.float32)
+    dev = torch.device("cuda")
+    wt = torch.as_tensor(w32).to(dev)
+    wf = torch.empty((27, 64, 64), dtype=torch.bfloat16, device=dev)
+    wb = torch.empty_like(wf)
+    cp.ws_cast_weights(wt, wf, wb, 1)
+    xg, dyg = xb.to(dev).reshape(-1, 64), dyb.to(dev).reshape(-1, 64)
+    for dil in (1, 2):
+        y = torch.empty_like(xg)
+        y0 = torch.empty(xg.shape[0], dtype=torch.float32, device=dev)
+        cp.conv3d_forward(xg, wf, torch.as_tensor(b).to(dev), y, y0, dims, dil, relu=False)
+        ref = N.conv_forward(x, wq, b.astype(np.float64), dil).reshape(-1, 64)
+        mag = N.conv_forward(np.abs(x), np.abs(wq), np.zeros(64), dil).reshape(-1, 64)
+        got = y.to(torch.float64).cpu().numpy()
+        assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-5 * mag + 1e-6)
+        np.testing.assert_allclose(y0.cpu().numpy(), ref[:, 0], rtol=1e-5, atol=1e-5)
+        # data gradient with the ReLU mask of an input activation
+        act = torch.as_tensor(np.asarray(ci.random_values(shp, seed=5), np.float32)).to(torch.bfloat16).to(dev)
+        act_mask = act.to(torch.float64).cpu().numpy().reshape(shp) > 0
+        dx = torch.empty_like(dyg)
+        cp.conv3d_backward_data(dyg, wb, act.reshape(-1, 64), dx, dims, dil)
+        dref, dWref, dbref = N.conv_backward(x, wq, dy, dil)
+        dref = (dref * act_mask).reshape(-1, 64)
+        dmag = N.conv_backward(np.abs(x), np.abs(wq), np.abs(dy), dil)[0].reshape(-1, 64)
+        got = dx.to(torch.float64).cpu().numpy()
+        assert np.all(np.abs(got - dref) <= 2.0 ** -8 * np.abs(dref) + 1e-5 * dmag + 1e-6)
+        dW = torch.zeros((27, 64, 64), dtype=torch.float32, device=dev)
+        db = torch.zeros(64, dtype=torch.float32, device=dev)
+        cp.conv3d_backward_weight(xg, dyg, dW, db, dims, dil)
+        wmag = N.conv_backward(np.abs(x), np.abs(wq), np.abs(dy), dil)[1]
+        assert np.all(np.abs(dW.cpu().numpy() - dWref) <= 1e-4 * wmag + 1e-6)
+        np.testing.assert_allclose(db.cpu().numpy(), dbref, rtol=1e-4, atol=1e-4)
+
+
+def test_network_gradient_matches_oracle(env):
+    cp, ws, torch = env
+    from oracle import convnet as N
+    net = ws.WarmStartNet(device=0, seed=3)
+    dims = (2, 6, 5, 6)
+    nv = int(np.prod(dims))
+    f = np.zeros(dims + (64,))
+    f[..., :4] = ci.random_values(dims + (4,), seed=8)
+    fb, fq = _bf16(f, torch)
+    tgt = ci.random_values(dims, seed=9).astype(np.float32)
+    msk = (ci.uniform(0, 10, nv, 0, 1) > 0.2).astype(np.float32).reshape(dims)
+    dev = net.dev
+    feat = fb.to(dev).reshape(nv, 64)
+    t = torch.as_tensor(tgt.reshape(-1)).to(dev)
+    m = torch.as_tensor(msk.reshape(-1)).to(dev)
+    w_before, b_before = net.numpy_params()
+    net.train_step(feat, t, m, dims, lr=0.0)
+    wq = [torch.as_tensor(w_before[i]).to(torch.bfloat16).to(torch.float64).numpy() for i in range(ws.LAYERS)]
+    params = [(wq[i], b_before[i].astype(np.float64), ws.DILATIONS[i]) for i in range(ws.LAYERS)]
+    acts = N.net_forward(fq, params, bf16=True)
+    acts[-1] = acts[-1].astype(np.float32).astype(np.float64)
+    grads = N.net_backward(acts, params, tgt.astype(np.float64), msk.astype(np.float64), bf16=True)
+    dW = net.dw.cpu().numpy()
+    dB = net.db.cpu().numpy()
+    for i in range(ws.LAYERS):
+        gw, gb = grads[i]
+        nrm = np.linalg.norm(gw)
+        if nrm > 0:
+            assert np.linalg.norm(dW[i] - gw) <= 5e-3 * nrm, (i, np.linalg.norm(dW[i] - gw) / nrm)
+        assert np.linalg.norm(dB[i] - gb) <= 5e-3 * max(np.linalg.norm(gb), 1e-12), i
+
+
+def test_features_targets_upsample(env):
+    cp, ws, torch = env
+    from oracle import convnet as N
+    inst = [ci.gridworld((9, 8, 5), p=0.8, gamma=g, step_reward=-0.01, goal_rewards=[0.7, 0.9],
+                         obstacle_rate=0.2, seed=s) for s, g in ((4, 0.95), (5, 0.9), (6, 0.99))]
+    B = cp.batch_build(inst, device=0)
+    dims = ws.coarse_dims(3, (9, 8, 5))
+    cells = int(np.prod(dims[1:]))
+    dev = torch.device("cuda")
+    feat = torch.empty((3 * cells, 64), dtype=torch.bfloat16, device=dev)
+    cp.ws_features(B, 0, 3, feat)
+    Vh = np.concatenate([ci.random_values(g.shape, seed=11 + i).reshape(-1) for i, g in enumerate(inst)])
+    V = torch.zeros(int(B.total_states), dtype=torch.float32, device=dev)
+    for i, g in enumerate(inst):
+        lo = int(B.offsets[i])
+        V[lo:lo + g.nstates] = torch.as_tensor(Vh[i * 360:(i + 1) * 360].astype(np.float32))
+    tgt = torch.empty(3 * cells, dtype=torch.float32, device=dev)
+    msk = torch.empty_like(tgt)
+    cp.ws_targets(B, V, 0, 3, tgt, msk)
+    coarse = torch.as_tensor(ci.random_values((3 * cells,), seed=21).astype(np.float32)).to(dev)
+    V0 = torch.zeros_like(V)
+    cp.ws_upsample(B, coarse, 0, 3, V0)
+    fh = feat.to(torch.float64).cpu().numpy().reshape(3, cells, 64)
+    for i, g in enumerate(inst):
+        fo = N.features(g).reshape(cells, 4)
+        assert np.all(np.abs(fh[i, :, :4] - fo) <= 2.0 ** -8 * np.abs(fo) + 1e-6)
+        assert np.all(fh[i, :, 4:] == 0)
+        Vi = Vh[i * 360:(i + 1) * 360].astype(np.float32).astype(np.float64)
+        to, mo = N.coarse_target(g, Vi)
+        np.testing.assert_allclose(tgt.cpu().numpy()[i * cells:(i + 1) * cells], to.reshape(-1), rtol=1e-5,
+                                   atol=1e-6)
+        assert np.array_equal(msk.cpu().numpy()[i * cells:(i + 1) * cells], mo.reshape(-1))
+        lo = int(B.offsets[i])
+        up = N.upsample(g, coarse.cpu().numpy()[i * cells:(i + 1) * cells].astype(np.float64).reshape(dims[1:]))
+        np.testing.assert_allclose(V0.cpu().numpy()[lo:lo + g.nstates], up.reshape(-1), rtol=1e-6, atol=1e-7)
+    B.close()
+
+
+def test_trained_network_saves_sweeps(env):
+    """Train on 256 solved 32^3 instances, then warm-start value iteration
+    on 24 held-out 32^3 instances: every instance still converges to
+    |dV|inf < 1e-6, and the warm start needs fewer sweeps in total than
+    zero initialisation on the same instances."""
+    cp, ws, torch = env
+    train_inst = ws.training_instances(256, 32, seed=1)
+    _, _, feat, target, mask, dims = ws.solved_dataset(train_inst)
+    net = ws.WarmStartNet(device=0, seed=0)
+    losses = ws.train(net, feat, target, mask, dims, epochs=30, batch=16, lr=2e-3, lr_final=2e-4)
+    assert losses[-1] < 0.2 * losses[0]
+    test_inst = ws.training_instances(24, 32, seed=777)
+    B = cp.batch_build(test_inst, device=0)
+    V = torch.zeros(int(B.total_states), dtype=torch.float32, device=net.dev)
+    _, it_zero, res0 = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=5000))
+    Vz = V.clone()
+    ws.warm_start_values(net, B, 24, (32, 32, 32), V)
+    _, it_warm, res1 = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=5000))
+    assert np.all(res0 < 1e-6) and np.all(res1 < 1e-6)
+    assert it_warm.sum() < it_zero.sum(), (it_warm.sum(), it_zero.sum())
+    # both end at the same fixed point (within the stopping bound)
+    g = max(x.gamma for x in test_inst)
+    assert (V - Vz).abs().max().item() <= (2 * g * 1e-6 + 4e-6) / (1 - g)
+    B.close()
