@@ -329,6 +329,13 @@ def run_ours(args, rank, world, local, pg):
     if not args.skip_large:
         large = hbm_sweep(cp, dev, stream, hbm or 6800.0)
 
+    batch = None
+    if not args.skip_batch:
+        batch = batch_measure(cp, dev, stream, seed=rank)
+    warm = None
+    if not args.skip_warmstart:
+        warm = warmstart_measure(local)
+
     # end to end through the public API with host buffers: build_factors
     # (host -> device), VI + PI, device -> host of V and the policy
     e2e_ms = []
@@ -370,10 +377,85 @@ def run_ours(args, rank, world, local, pg):
                 "vi_sweeps": statistics.median(vi_iters), "plain_vi_sweeps": rpl["iterations"],
                 "pi_sweeps": statistics.median(pi_iters), "pi_ms": statistics.median(pi_ms),
                 "certified_residual": rv["certified_residual"], "error_bound": rv["error_bound"],
-                "hbm_sweep_512": large, "roofline_vi": roof_vi}
+                "hbm_sweep_512": large, "roofline_vi": roof_vi, "batch_4096": batch,
+                "warmstart_512x64": warm}
         print(json.dumps(line), flush=True)
     f.close()
     return 0
+
+
+def batch_measure(cp, dev, stream, seed=0, count=4096, reps=3):
+    """4096 independent 2-D / 3-D GridWorlds (sides U{8..128} / U{8..48},
+    p ~ U(0.6, 0.95), gamma ~ U(0.9, 0.995)) solved to 1e-6 from zeros by one
+    batched persistent launch, next to the same instances solved one at a
+    time by the fused single-instance solver and by the plain FP32 VI (the
+    latter two on an evenly spaced sample, scaled by instance count: labelled)."""
+    import torch
+    import cpmdp_inputs as ci
+    inst = ci.batch_gridworlds(count=count, seed=seed)
+    B = cp.batch_build(inst, device=dev.index)
+    V = torch.zeros(int(B.total_states), dtype=torch.float32, device=dev)
+    opts = cp.default_opts(max_iter=5000)
+    r, iters, _ = cp.batch_value_iteration(B, V, opts=opts, stream=stream)   # tunes and records the graph
+    times, backups = [], 0
+    for _ in range(reps):
+        V.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r, iters, res = cp.batch_value_iteration(B, V, opts=opts, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        backups = r["backups"]
+    batched_ms = statistics.median(times)
+    # one instance at a time: fused persistent solver and plain FP32 VI, sampled
+    step = 16
+    sample = list(range(0, count, step))
+    fused_ms, plain_ms = 0.0, 0.0
+    popts = cp.default_opts(max_iter=5000, fused=0, certify=0)
+    fopts = cp.default_opts(max_iter=5000, certify=0)
+    for i in sample:
+        f = cp.build_factors(inst[i], device=dev.index)
+        Vi = torch.zeros(inst[i].nstates, dtype=torch.float32, device=dev)
+        for mode, o in (("fused", fopts), ("plain", popts)):
+            Vi.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cp.value_iteration(f, cp.F32, Vi, None, opts=o, stream=stream)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) * 1e3
+            if mode == "fused":
+                fused_ms += dt
+            else:
+                plain_ms += dt
+        f.close()
+    B.close()
+    scale = count / len(sample)
+    return {"instances": count, "states": int(inst_states(inst)), "backups": int(backups),
+            "batched_ms": batched_ms, "batched_backups_per_s": backups / (batched_ms / 1e3),
+            "launch_sweeps": r["iterations"], "max_instance_sweeps": int(iters.max()),
+            "graph_replay": bool(r["rounds"] == 1),
+            "one_at_a_time_fused_ms_est": fused_ms * scale, "plain_fp32_vi_ms_est": plain_ms * scale,
+            "speedup_vs_plain_fp32_vi": plain_ms * scale / batched_ms,
+            "note": f"one-at-a-time times measured on every {step}th instance ({len(sample)} of {count}) "
+                    f"and scaled by {scale:.0f}"}
+
+
+def warmstart_measure(device_index):
+    """Config 5: the committed network (trained on 20,000 solved 32^3
+    instances) warm-starts batched value iteration on 512 held-out 64^3
+    instances; zero initialisation on the same instances beside it."""
+    from paper_2103_00331_gb300 import warmstart as ws
+    path = os.path.join(ROOT, "paper_2103_00331_gb300", "data", "warmstart_weights.npz")
+    if not os.path.exists(path):
+        return None
+    net = ws.WarmStartNet.load(path, device=device_index)
+    return ws.evaluate(net, count=512, side=64)
+
+
+def inst_states(inst):
+    return sum(g.nstates for g in inst)
 
 
 def hbm_sweep(cp, dev, stream, peak):
@@ -486,6 +568,8 @@ def main():
     ap.add_argument("--skip-large", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-warmstart", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--kernel-case", choices=["sweep512", "solve64", "pi64", "dense64", "dense64tc"], default=None,
                     help="run one kernel workload a few times (profiling) and exit")

@@ -182,3 +182,102 @@ def warm_start_values(net, batch_obj, count, shape, V):
     pred = net.predict(feat, dims)
     ws_upsample(batch_obj, pred, 0, count, V)
     return pred
+
+
+def evaluate(net, count=512, side=64, seed=424242, device=0, log=None):
+    """Held-out instances (seeds disjoint from training): batched value
+    iteration to |dV|inf < 1e-6 from zeros and from the network's estimate.
+    Times come from CUDA events around each stage; returns a dict."""
+    import time
+    import torch
+    inst = training_instances(count, side, seed=seed)
+    B = batch_build(inst, device=device)
+    dev = net.dev
+    V = torch.zeros(int(B.total_states), dtype=torch.float32, device=dev)
+    opts = default_opts(tol=1e-6, max_iter=5000)
+    batch_value_iteration(B, V, opts=opts)                 # autotune and record the graph
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    V.zero_()
+    torch.cuda.synchronize()
+    ev[0].record()
+    r0, it0, res0 = batch_value_iteration(B, V, opts=opts)
+    ev[1].record()
+    torch.cuda.synchronize()
+    Vz = V.clone()
+    warm_start_values(net, B, count, (side,) * 3, V)      # warm-up of the network kernels
+    torch.cuda.synchronize()
+    ev[2].record()
+    warm_start_values(net, B, count, (side,) * 3, V)
+    ev[3].record()
+    r1, it1, res1 = batch_value_iteration(B, V, opts=opts)
+    ev[4].record()
+    torch.cuda.synchronize()
+    zero_ms = ev[0].elapsed_time(ev[1])
+    net_ms = ev[2].elapsed_time(ev[3])
+    vi_ms = ev[3].elapsed_time(ev[4])
+    diff = (V - Vz).abs().max().item()
+    out = {"instances": count, "side": side, "zero_init_ms": zero_ms, "net_ms": net_ms, "warm_vi_ms": vi_ms,
+           "warm_total_ms": net_ms + vi_ms, "speedup_total": zero_ms / (net_ms + vi_ms),
+           "mean_sweeps_zero": float(it0.mean()), "mean_sweeps_warm": float(it1.mean()),
+           "sweeps_saved_frac": float(1 - it1.sum() / it0.sum()),
+           "launch_sweeps_zero": r0["iterations"], "launch_sweeps_warm": r1["iterations"],
+           "all_converged": bool((res0 < 1e-6).all() and (res1 < 1e-6).all()),
+           "max_abs_diff_warm_vs_zero": diff}
+    B.close()
+    if log:
+        log(str(out))
+    return out
+
+
+def main(argv=None):
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser(description="train / evaluate the learned warm start")
+    ap.add_argument("mode", choices=["train", "eval"])
+    ap.add_argument("--instances", type=int, default=20000)
+    ap.add_argument("--side", type=int, default=32)
+    ap.add_argument("--epochs", type=int, default=12)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--lr-final", type=float, default=1e-4)
+    ap.add_argument("--weights", default=None)
+    ap.add_argument("--eval-instances", type=int, default=512)
+    ap.add_argument("--eval-side", type=int, default=64)
+    args = ap.parse_args(argv)
+    t0 = time.time()
+    if args.mode == "train":
+        inst = []
+        chunk = 2000
+        feats, targets, masks = [], [], []
+        dims = None
+        for lo in range(0, args.instances, chunk):
+            part = training_instances(min(chunk, args.instances - lo), args.side, seed=1 + lo // chunk)
+            B, V, f, t, m, d = solved_dataset(part)
+            feats.append(f)
+            targets.append(t)
+            masks.append(m)
+            dims = d
+            B.close()
+            del V
+            print(f"solved {lo + len(part)} / {args.instances} instances, {time.time() - t0:.1f} s", flush=True)
+        import torch
+        feat = torch.cat(feats)
+        target = torch.cat(targets)
+        mask = torch.cat(masks)
+        dims = (args.instances,) + tuple(dims[1:])
+        net = WarmStartNet(device=0, seed=0)
+        losses = train(net, feat, target, mask, dims, epochs=args.epochs, batch=args.batch, lr=args.lr,
+                       lr_final=args.lr_final, log=lambda s: print(s, flush=True))
+        if args.weights:
+            net.save(args.weights)
+        print(json.dumps({"train_instances": args.instances, "side": args.side, "epochs": args.epochs,
+                          "losses": losses, "seconds": time.time() - t0}), flush=True)
+    else:
+        net = WarmStartNet.load(args.weights)
+        out = evaluate(net, count=args.eval_instances, side=args.eval_side)
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
