@@ -19,12 +19,12 @@ template <typename T, typename TA, int D, int VEC, bool WITH_PI>
 __global__ void __launch_bounds__(256) sweep_kernel(BandArgs a, const T *__restrict__ V,
                                                     T *__restrict__ W, uint8_t *pi,
                                                     unsigned long long *res_out) {
-    __shared__ double shd[32];
+    __shared__ unsigned shm[64];
     unsigned dummy = 0;
     const TA r = sweep_all<T, TA, D, VEC, M_VI, WITH_PI>(a, V, W, pi, (TA)0, dummy);
     if (res_out) {
-        const double m = block_max((double)r, shd);
-        if (threadIdx.x == 0 && m > 0.0) atomicMax(res_out, (unsigned long long)__double_as_longlong(m));
+        const unsigned long long mb = block_max_bits(r, shm);
+        if (threadIdx.x == 0 && mb) atomicMax(res_out, mb);
     }
 }
 
@@ -111,6 +111,10 @@ BandArgs make_band_args(const Factors &F) {
     a.w_perp = F.w_perp;
     a.w_stay = F.w_stay;
     a.gamma = F.gamma;
+    a.wf_move = (float)F.w_move;
+    a.wf_perp = (float)F.w_perp;
+    a.wf_stay = (float)F.w_stay;
+    a.wf_gamma = (float)F.gamma;
     a.code = F.d_code;
     a.R32 = F.d_R32;
     a.R64 = F.d_R64;

@@ -40,6 +40,7 @@ struct BandArgs {
     int nlast;
     int stride[kMaxDim];
     double w_move, w_perp, w_stay, gamma;
+    float wf_move, wf_perp, wf_stay, wf_gamma;  // the same rounded to float, for the FP32 kernels
     const void *code;
     const float *R32;
     const double *R64;
@@ -64,9 +65,93 @@ __device__ __forceinline__ void store_pack(T *p, const T (&in)[VEC]) {
     *reinterpret_cast<VPack<T, VEC> *>(p) = pk;
 }
 
+// Transition weights and gamma in the working precision (no conversion in
+// the kernels: float <-> double conversions issue on GB300's narrow FP64 pipe).
+template <typename TA>
+__device__ __forceinline__ void weights(const BandArgs &a, TA &wm, TA &wp, TA &wst, TA &g);
+template <>
+__device__ __forceinline__ void weights<float>(const BandArgs &a, float &wm, float &wp, float &wst, float &g) {
+    wm = a.wf_move; wp = a.wf_perp; wst = a.wf_stay; g = a.wf_gamma;
+}
+template <>
+__device__ __forceinline__ void weights<double>(const BandArgs &a, double &wm, double &wp, double &wst, double &g) {
+    wm = a.w_move; wp = a.w_perp; wst = a.w_stay; g = a.gamma;
+}
+
+// |a - b| with the sign bit cleared (never -0), so that residual maxima can
+// be taken on bit patterns (block_max_bits).
+__device__ __forceinline__ float abs_diff(float a, float b) { return fabsf(a - b); }
+__device__ __forceinline__ double abs_diff(double a, double b) { return fabs(a - b); }
+
+// Residual m (bits of a non-negative double, or a NaN) below tol > 0: the
+// same order on the bits read as unsigned integers, with no FP64
+// instruction; a NaN is never below tol, as in floating point.
+__device__ __forceinline__ bool below_tol(unsigned long long mbits, double tol) {
+    return mbits < (unsigned long long)__double_as_longlong(tol);
+}
+
 template <typename TA> __device__ __forceinline__ TA rew(const BandArgs &a, int s);
 template <> __device__ __forceinline__ float rew<float>(const BandArgs &a, int s) { return a.R32[s]; }
 template <> __device__ __forceinline__ double rew<double>(const BandArgs &a, int s) { return a.R64[s]; }
+
+// perp[d] = sum over d' != d of the pair sums P_d' = N_{2d'} + N_{2d'+1}
+// (prefix + suffix sums).
+template <typename TA, int D>
+__device__ __forceinline__ void perp_of(const TA (&nb)[2 * D], TA (&perp)[D]) {
+    TA P[D];
+#pragma unroll
+    for (int d = 0; d < D; d++) P[d] = nb[2 * d] + nb[2 * d + 1];
+    TA acc = 0;
+#pragma unroll
+    for (int d = 0; d < D; d++) { perp[d] = acc; acc += P[d]; }
+    acc = 0;
+#pragma unroll
+    for (int d = D - 1; d >= 0; d--) { perp[d] += acc; acc += P[d]; }
+}
+
+// Value-iteration backup of one state from its blocked-move-resolved
+// neighbour values nb (Eq. 1). Because w_move, w_perp and gamma are >= 0 and
+// rounding is monotone, max_sigma E_(d,sigma) is E at max(N_{d,-}, N_{d,+})
+// and max_a fl(R + gamma E_a) = fl(R + gamma max_a E_a): the same value (and
+// the same lowest-index argmax) as evaluating every action, with D instead
+// of 2D expectation chains. Terminals keep R, obstacles 0.
+template <typename TA, int D>
+__device__ __forceinline__ TA vi_state(TA self, const TA (&nb)[2 * D], unsigned c, TA r, TA wm, TA wp, TA wst, TA g,
+                                       int &arg) {
+    TA perp[D];
+    perp_of<TA, D>(nb, perp);
+    const TA stay = (D == 1) ? wst * self : (TA)0;
+    TA bestE = 0;
+    arg = 0;
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+        const bool up = nb[2 * d + 1] > nb[2 * d];
+        const TA m = up ? nb[2 * d + 1] : nb[2 * d];
+        const TA e = wm * m + wp * perp[d] + stay;
+        if (d == 0 || e > bestE) { bestE = e; arg = 2 * d + (up ? 1 : 0); }
+    }
+    TA v = r + g * bestE;
+    if (c & (1u << (2 * D + 1))) v = r;
+    if (c & (1u << (2 * D))) v = 0;
+    return v;
+}
+
+// Policy-evaluation backup of one state for its fixed action `act`.
+template <typename TA, int D>
+__device__ __forceinline__ TA eval_state(TA self, const TA (&nb)[2 * D], unsigned c, TA r, int act, TA wm, TA wp,
+                                         TA wst, TA g) {
+    TA perp[D];
+    perp_of<TA, D>(nb, perp);
+    const TA stay = wst * self;
+    TA nbv = nb[0], pv = perp[0];
+#pragma unroll
+    for (int j = 1; j < 2 * D; j++)
+        if (act == j) { nbv = nb[j]; pv = perp[j / 2]; }
+    TA v = r + g * (wm * nbv + wp * pv + stay);
+    if (c & (1u << (2 * D + 1))) v = r;
+    if (c & (1u << (2 * D))) v = 0;
+    return v;
+}
 
 // One row segment: states s0 .. s0+VEC-1 of a row of the last dimension.
 // load() issues every global load of the segment at once: the neighbour
@@ -141,42 +226,29 @@ struct Segment {
         for (int d = D - 1; d >= 0; d--) { perp[d] += acc; acc += P[d]; }
     }
 
-    // Value-iteration backup. Because w_move, w_perp and gamma are >= 0 and
-    // rounding is monotone, max_sigma E_(d,sigma) is E at max(N_{d,-}, N_{d,+})
-    // and max_a fl(R + gamma E_a) = fl(R + gamma max_a E_a): the same values
-    // (and the same lowest-index argmax) as evaluating every action, with D
-    // instead of 2D expectation chains. Returns max |V' - V| over
-    // non-obstacle states; writes V' to W (if not null) and the policy to pi
-    // (WITH_PI).
+    // Value-iteration backup of the segment (vi_state per state). Writes V'
+    // to W (if not null) and the policy to pi (WITH_PI); returns the largest
+    // |V' - V| over non-obstacle states.
     template <bool WITH_PI>
     __device__ __forceinline__ TA finish_vi(const BandArgs &a, T *W, uint8_t *pi, int s0) const {
         TA self[VEC], nb[NB][VEC];
         neighbours(self, nb);
-        const TA wm = (TA)a.w_move, wp = (TA)a.w_perp, wst = (TA)a.w_stay, g = (TA)a.gamma;
+        TA wm, wp, wst, g;
+        weights<TA>(a, wm, wp, wst, g);
         TA out[VEC];
         TA res = 0;
 #pragma unroll
         for (int k = 0; k < VEC; k++) {
             const unsigned c = code[k];
-            TA perp[D];
-            perp_sums(nb, k, perp);
-            const TA stay = (D == 1) ? wst * self[k] : (TA)0;
-            TA bestE = 0;
-            int arg = 0;
+            TA nbk[NB];
 #pragma unroll
-            for (int d = 0; d < D; d++) {
-                const bool up = nb[2 * d + 1][k] > nb[2 * d][k];
-                const TA m = up ? nb[2 * d + 1][k] : nb[2 * d][k];
-                const TA e = wm * m + wp * perp[d] + stay;
-                if (d == 0 || e > bestE) { bestE = e; arg = 2 * d + (up ? 1 : 0); }
-            }
-            TA v = r[k] + g * bestE;
-            if (c & TERM) v = r[k];
-            if (c & OBST) v = 0;
+            for (int j = 0; j < NB; j++) nbk[j] = nb[j][k];
+            int arg;
+            const TA v = vi_state<TA, D>(self[k], nbk, c, r[k], wm, wp, wst, g, arg);
             out[k] = v;
             if (WITH_PI) pi[s0 + k] = (c & (OBST | TERM)) ? (uint8_t)255 : (uint8_t)arg;
             if (!(c & OBST)) {
-                const TA dv = v > self[k] ? v - self[k] : self[k] - v;
+                const TA dv = abs_diff(v, self[k]);
                 res = dv > res ? dv : res;
             }
         }
@@ -198,7 +270,8 @@ struct Segment {
                                             unsigned &changed) const {
         TA self[VEC], nb[NB][VEC];
         neighbours(self, nb);
-        const TA wm = (TA)a.w_move, wp = (TA)a.w_perp, wst = (TA)a.w_stay, g = (TA)a.gamma;
+        TA wm, wp, wst, g;
+        weights<TA>(a, wm, wp, wst, g);
         TA out[VEC];
         TA res = 0;
 #pragma unroll
@@ -211,16 +284,12 @@ struct Segment {
             const TA stay = wst * self[k];
             TA v = self[k];
             if (MODE == M_EVAL) {
-                const int ak = act[k];
-                TA nbv = nb[0][k], pv = perp[0];
+                TA nbk[NB];
 #pragma unroll
-                for (int j = 1; j < NB; j++)
-                    if (ak == j) { nbv = nb[j][k]; pv = perp[j / 2]; }
-                v = rk + g * (wm * nbv + wp * pv + stay);
-                if (c & TERM) v = rk;
-                if (c & OBST) v = 0;
+                for (int j = 0; j < NB; j++) nbk[j] = nb[j][k];
+                v = eval_state<TA, D>(self[k], nbk, c, rk, (int)act[k], wm, wp, wst, g);
                 if (!(c & OBST)) {
-                    const TA dv = v > self[k] ? v - self[k] : self[k] - v;
+                    const TA dv = abs_diff(v, self[k]);
                     res = dv > res ? dv : res;
                 }
             } else if (!(c & (OBST | TERM))) {
@@ -309,6 +378,47 @@ __device__ __forceinline__ double block_max(double v, double *sh) {
     return v;
 }
 
+// Largest of the block's non-negative residuals, as the bits of a double
+// (valid in thread 0; ready for an atomicMax on a residual slot). A
+// non-negative IEEE-754 value orders like its bit pattern read as an
+// unsigned integer (a NaN above +inf), so each warp step is one integer max
+// reduction (redux.sync) and no FP64 instruction is issued: GB300's FP64
+// pipe is narrow enough that a shuffle-and-fmax tree over doubles costs
+// microseconds per sweep. sh: 32 words of shared memory.
+__device__ __forceinline__ unsigned long long block_max_bits(float v, unsigned *sh) {
+    unsigned u = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(v));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = u;
+    __syncthreads();
+    if (w == 0) {
+        u = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0u;
+        u = __reduce_max_sync(0xFFFFFFFFu, u);
+    }
+    __syncthreads();
+    return (unsigned long long)__double_as_longlong((double)__uint_as_float(u));
+}
+
+// The same for double residuals: the high words first, then the low words
+// of the lanes holding the largest high word. sh: 64 words.
+__device__ __forceinline__ unsigned long long block_max_bits(double v, unsigned *sh) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    unsigned hm = __reduce_max_sync(0xFFFFFFFFu, hi);
+    unsigned lm = __reduce_max_sync(0xFFFFFFFFu, hi == hm ? lo : 0u);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sh[w] = hm; sh[32 + w] = lm; }
+    __syncthreads();
+    if (w == 0) {
+        const bool in = l < (int)(blockDim.x >> 5);
+        hi = in ? sh[l] : 0u;
+        lo = in ? sh[32 + l] : 0u;
+        hm = __reduce_max_sync(0xFFFFFFFFu, hi);
+        lm = __reduce_max_sync(0xFFFFFFFFu, hi == hm ? lo : 0u);
+    }
+    __syncthreads();
+    return ((unsigned long long)hm << 32) | lm;
+}
+
 __device__ __forceinline__ unsigned block_sum(unsigned v, unsigned *sh) {
     v = warp_sum(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -383,7 +493,7 @@ __device__ __forceinline__ long long grid_sync_count(Ctrl *c, int n, unsigned nb
             if (result == 0) {
                 const unsigned long long hi = v >> 32;
                 const unsigned long long prev = (n & 1) ? prev1 : prev0;
-                result = (long long)(hi - prev);
+                result = (long long)((hi - prev) & 0xFFFFFFFFull);
                 if (n & 1) prev1 = hi;
                 else prev0 = hi;
             }

@@ -23,7 +23,7 @@ template <typename T, int D, int VEC>
 __global__ void __launch_bounds__(256) solve_vi_kernel(BandArgs a, T *V, T *Wbuf, SolveParams sp, Ctrl *ctrl,
                                                        double *trace) {
     typedef T TA;
-    __shared__ double shd[32];
+    __shared__ unsigned shm[64];
     const unsigned nb = gridDim.x;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const bool stall = sp.inject_stall && blockIdx.x == 0;
@@ -33,11 +33,11 @@ __global__ void __launch_bounds__(256) solve_vi_kernel(BandArgs a, T *V, T *Wbuf
     unsigned long long ph0 = 0ull, ph1 = 0ull;
     while (k < sp.max_iter) {
         const TA r = sweep_all<T, TA, D, VEC, M_VI, false>(a, cur, nxt, nullptr, (TA)0, dummy);
-        const double m = block_max((double)r, shd);
+        const unsigned long long mb = block_max_bits(r, shm);
         int flag = 0;
         if (threadIdx.x == 0) {
-            if (m > 0.0) atomicMax(&ctrl->res_slot[k % 3], (unsigned long long)__double_as_longlong(m));
-            flag = !(m < sp.tol);
+            if (mb) atomicMax(&ctrl->res_slot[k % 3], mb);
+            flag = !below_tol(mb, sp.tol);
         }
         if (lead) ctrl->res_slot[(k + 1) % 3] = 0ull;
         const long long open = grid_sync_count(ctrl, k, nb, flag, sp.timeout_ns, ph0, ph1, stall && k == 0);
@@ -64,7 +64,7 @@ template <typename T, int D, int VEC>
 __global__ void __launch_bounds__(256) solve_pi_kernel(BandArgs a, T *V, T *Wbuf, uint8_t *pi, SolveParams sp,
                                                        Ctrl *ctrl) {
     typedef T TA;
-    __shared__ double shd[32];
+    __shared__ unsigned shm[64];
     __shared__ unsigned shu[32];
     const unsigned nb = gridDim.x;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
@@ -84,11 +84,11 @@ __global__ void __launch_bounds__(256) solve_pi_kernel(BandArgs a, T *V, T *Wbuf
         int e = 0, eval_ok = 0;
         while (e < sp.max_eval_iter) {
             const TA r = sweep_all<T, TA, D, VEC, M_EVAL, true>(a, cur, nxt, pi, (TA)0, dummy);
-            const double m = block_max((double)r, shd);
+            const unsigned long long mb = block_max_bits(r, shm);
             int flag = 0;
             if (threadIdx.x == 0) {
-                if (m > 0.0) atomicMax(&ctrl->res_slot[ks % 3], (unsigned long long)__double_as_longlong(m));
-                flag = !(m < sp.eval_tol);
+                if (mb) atomicMax(&ctrl->res_slot[ks % 3], mb);
+                flag = !below_tol(mb, sp.eval_tol);
             }
             if (lead) ctrl->res_slot[(ks + 1) % 3] = 0ull;
             const long long open = grid_sync_count(ctrl, nbar++, nb, flag, sp.timeout_ns, ph0, ph1, false);
@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(256) solve_pi_kernel(BandArgs a, T *V, T *Wbuf
         ctrl->backups = backups;
     }
 }
+
 
 template <typename K>
 static cudaError_t coop_grid(K kern, const Factors &F, int nitems, int &cache, int &grid) {
@@ -174,6 +175,7 @@ static cudaError_t launch_pi(const Factors &F, T *V, T *W, uint8_t *pi, const So
     void *args[] = {(void *)&a, (void *)&V, (void *)&W, (void *)&pi, (void *)&spc, (void *)&ctrl};
     return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(256), args, 0, st);
 }
+
 
 template <typename T>
 static cudaError_t solve_t(const Factors &F, bool pim, T *V, uint8_t *pi, const SolveParams &sp, double *trace,

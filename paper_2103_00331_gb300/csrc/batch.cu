@@ -58,10 +58,10 @@ __device__ __forceinline__ float batch_segment(const BatchInst &I, const uint8_t
     a.nlast = I.nlast;
 #pragma unroll
     for (int d = 0; d < kMaxDim; d++) a.stride[d] = d < 3 ? (d < D ? I.stride[d] : 0) : 0;
-    a.w_move = I.w_move;
-    a.w_perp = I.w_perp;
-    a.w_stay = I.w_stay;
-    a.gamma = I.gamma;
+    a.wf_move = I.w_move;
+    a.wf_perp = I.w_perp;
+    a.wf_stay = I.w_stay;
+    a.wf_gamma = I.gamma;
     a.code = code + I.offset;
     a.R32 = R + I.offset;
     a.R64 = nullptr;
@@ -88,7 +88,7 @@ __device__ __forceinline__ float batch_item(const BatchInst &I, const uint8_t *c
 template <int IPT>
 __global__ void __launch_bounds__(512) batch_vi_kernel(BatchArgs b) {
     __shared__ int s_state;       // 0 skip, 1 work, 2 just stopped
-    __shared__ float s_red[16];
+    __shared__ unsigned s_red[16];
     const unsigned nb = gridDim.x;
     const int tid = threadIdx.x;
     unsigned long long ph0 = 0ull, ph1 = 0ull;
@@ -104,9 +104,9 @@ __global__ void __launch_bounds__(512) batch_vi_kernel(BatchArgs b) {
                 if (b.done_at[T.inst] != 0) {
                     st = 0;
                 } else if (k > 0) {
-                    const double r = __longlong_as_double(
-                        (long long)*(volatile unsigned long long *)&b.res[(size_t)((k - 1) % 3) * b.ninst + T.inst]);
-                    if (r < b.tol) st = 2;
+                    const unsigned long long rb =
+                        *(volatile unsigned long long *)&b.res[(size_t)((k - 1) % 3) * b.ninst + T.inst];
+                    if (below_tol(rb, b.tol)) st = 2;
                 }
                 if (st == 1 && k == b.max_iter) st = 3;   // limit reached: stop without a sweep
                 if (st == 2 || st == 3) {
@@ -130,17 +130,17 @@ __global__ void __launch_bounds__(512) batch_vi_kernel(BatchArgs b) {
                 const int it = tid + u * blockDim.x;
                 if (it < T.nitems) r = fmaxf(r, batch_item(I, b.code, b.R, cur, nxt, T.first_item + it));
             }
-            // block max -> the instance's slot for sweep k
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xFFFFFFFFu, r, o));
-            if ((tid & 31) == 0) s_red[tid >> 5] = r;
+            // block max -> the instance's slot for sweep k (non-negative
+            // residuals: integer max of the bit patterns, one redux per warp)
+            const unsigned u = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(r));
+            if ((tid & 31) == 0) s_red[tid >> 5] = u;
             __syncthreads();
             if (tid == 0) {
-                float m = 0.f;
-                for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = fmaxf(m, s_red[w]);
-                if (m > 0.f)
+                unsigned m = 0u;
+                for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = m > s_red[w] ? m : s_red[w];
+                if (m)
                     atomicMax(&b.res[(size_t)(k % 3) * b.ninst + T.inst],
-                              (unsigned long long)__double_as_longlong((double)m));
+                              (unsigned long long)__double_as_longlong((double)__uint_as_float(m)));
             }
             __syncthreads();
         }

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kBlock) static_vi_kernel(StaticArgs a, const f
     StaticCtrl *c = reinterpret_cast<StaticCtrl *>(scratch);
     const uint8_t *code = scratch + kCtrlBytes;
     float *W = reinterpret_cast<float *>(scratch + kCtrlBytes + kMaxStates);
-    __shared__ double shm[kBlock / 32];
+    __shared__ unsigned shm[kBlock / 32];
     const int D = a.ndim;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     float *cur = V, *nxt = W;
@@ -179,15 +179,17 @@ __global__ void __launch_bounds__(kBlock) static_vi_kernel(StaticArgs a, const f
             nxt[s] = v;
             if (!(cs & (1u << (2 * D)))) m = fmaxf(m, fabsf(v - self));
         }
-        // block max of the residual
-        double dm = (double)m;
-        for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xFFFFFFFFu, dm, o));
-        if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = dm;
+        // block max of the residual: non-negative floats order like their
+        // bit patterns read as unsigned integers, so the warp step is one
+        // integer max reduction (no FP64 instruction)
+        unsigned um = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(m));
+        if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = um;
         __syncthreads();
         int flag = 0;
         if (threadIdx.x == 0) {
-            for (int w = 1; w < kBlock / 32; w++) dm = fmax(dm, shm[w]);
-            if (dm > 0.0) atomicMax(&c->res_slot[k % 3], (unsigned long long)__double_as_longlong(dm));
+            for (int w = 1; w < kBlock / 32; w++) um = um > shm[w] ? um : shm[w];
+            const double dm = (double)__uint_as_float(um);
+            if (um) atomicMax(&c->res_slot[k % 3], (unsigned long long)__double_as_longlong(dm));
             flag = !(dm < a.tol);
         }
         if (lead) c->res_slot[(k + 1) % 3] = 0ull;
