@@ -305,11 +305,7 @@ def run_ours(args, rank, world, local, pg):
     # roofline of the dominant kernel (the persistent policy-iteration kernel,
     # one launch per step): algorithmic bytes of its launches over their
     # event-timed durations; the value-iteration kernel beside it
-    peaks = {}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        peaks = json.load(open(pk))
-    hbm = peaks.get("hbm_gbs")
+    hbm = measured_peaks().get("hbm_gbs")
     peak = hbm or 6800.0
     src = "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm else "fallback 6.8 TB/s"
     ach_pi = (pi_bytes / len(pi_ms)) / (statistics.mean(pi_ms) / 1e3) / 1e9
@@ -432,7 +428,26 @@ def batch_measure(cp, dev, stream, seed=0, count=4096, reps=3):
         f.close()
     B.close()
     scale = count / len(sample)
+    # algorithmic bytes: every sweep of every instance reads V, R, code and
+    # writes V' (13 B per state); the floor takes each global sweep at the
+    # larger of its bytes at the measured HBM peak and the single-instance
+    # solver's per-sweep latency (2.5 us at 64^3)
+    sizes = np.array([g.nstates for g in inst], dtype=np.float64)
+    sweeps = np.asarray(iters, dtype=np.int64)
+    alg_bytes = float((sweeps * sizes).sum() * 13.0)
+    peak = measured_peaks().get("hbm_gbs") or 6800.0
+    order = np.argsort(sweeps)
+    active = np.concatenate([[sizes.sum()], sizes.sum() - np.cumsum(sizes[order])])
+    floor_ms = 0.0
+    prev = 0
+    for j, idx in enumerate(order):
+        n = int(sweeps[idx]) - prev
+        if n > 0:
+            floor_ms += n * max(active[j] * 13.0 / (peak * 1e9) * 1e3, 2.5e-3)
+            prev = int(sweeps[idx])
     return {"instances": count, "states": int(inst_states(inst)), "backups": int(backups),
+            "algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / (batched_ms * 1e6),
+            "hbm_frac": alg_bytes / (batched_ms * 1e6) / peak, "model_floor_ms": floor_ms,
             "batched_ms": batched_ms, "batched_backups_per_s": backups / (batched_ms / 1e3),
             "launch_sweeps": r["iterations"], "max_instance_sweeps": int(iters.max()),
             "graph_replay": bool(r["rounds"] == 1),
@@ -452,6 +467,11 @@ def warmstart_measure(device_index):
         return None
     net = ws.WarmStartNet.load(path, device=device_index)
     return ws.evaluate(net, count=512, side=64)
+
+
+def measured_peaks():
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(pk)) if os.path.exists(pk) else {}
 
 
 def inst_states(inst):

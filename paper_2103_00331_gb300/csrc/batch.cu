@@ -4,19 +4,19 @@
 //
 // The instances are packed back to back (values, FP32 rewards, per-state
 // move codes in the encoding of the single-instance path). The work is cut
-// into tiles: a tile is up to `tile_items` row segments of one instance,
+// into warp tiles: a tile is up to 32 x spl row segments of one instance,
 // each segment VEC in {1, 2, 4} consecutive states of a row of the last
 // dimension (VEC divides that instance's row length). Every global sweep the
-// blocks of the cooperative grid take the tiles of instances that are still
+// warps of the cooperative grid take the tiles of instances that are still
 // running; an instance stops on its own as soon as its residual falls below
 // tol, so short and long solves share the launch. Per-instance residuals use
 // three rotating slots (slot k+1 is cleared during sweep k by the block that
 // owns the instance's first tile, after every block has read slot k-2); the
 // grid stops after a sweep in which no block found a running instance.
 //
-// Tile size and block size are chosen by a small autotuner (time a few
-// sweeps of each candidate on the actual batch), and the solve is recorded
-// once into a CUDA graph and replayed.
+// The tile size (segments per lane) and block size are chosen by a small
+// autotuner (time a few sweeps of each candidate on the actual batch), and
+// the solve is recorded once into a CUDA graph and replayed.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -45,14 +45,53 @@ struct BatchArgs {
     int *done_at;              // per instance: sweeps done when it stopped (0 = running)
     double tol;
     int max_iter;
+    int spl;                   // segments per lane of a tile (tile = 32 spl segments)
     unsigned long long timeout_ns;
     Ctrl *ctrl;
 };
 
-// One segment of an instance; D and VEC fixed at compile time.
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// L2 prefetch of the 128-byte lines holding elements [lo, hi) of an array
+// of `esize`-byte elements (every line start lies inside the array).
+__device__ __forceinline__ void prefetch_span(const void *base, long long lo, long long hi, int esize) {
+    const char *p = static_cast<const char *>(base);
+    for (long long a = (lo * esize) & ~127ll; a < hi * esize; a += 128) prefetch_l2(p + a);
+}
+
+// Everything a tile's backups read: its states (plus the row halo) of V, R
+// and the codes, and the rows one stride away in each leading dimension.
+// Issued by the lane that found the tile running, for all running tiles of
+// a round at once, so that the warp, working through them one by one, waits
+// for HBM once per round instead of once per tile.
+__device__ __forceinline__ void prefetch_tile(const BatchInst &I, const BatchTile &T, const float *V, const float *R,
+                                              const uint8_t *code) {
+    const long long base = I.offset, end = I.offset + I.nstates;
+    const long long a0 = base + (long long)T.first_item * I.vec;
+    long long a1 = base + (long long)(T.first_item + T.nitems) * I.vec;
+    a1 = a1 < end ? a1 : end;
+    const long long h0 = a0 > base ? a0 - 1 : a0, h1 = a1 < end ? a1 + 1 : a1;
+    prefetch_span(V, h0, h1, 4);
+    prefetch_span(R, a0, a1, 4);
+    prefetch_span(code, a0, a1, 1);
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+        if (d >= I.ndim - 1) break;
+        const long long st = I.stride[d];
+        if (a0 - st >= base) prefetch_span(V, a0 - st, a1 - st, 4);
+        if (a1 + st <= end) prefetch_span(V, a0 + st, a1 + st, 4);
+    }
+}
+
+// One segment of a tile per lane (segment first + lane of the instance), D
+// and VEC fixed at compile time. (Two or more segments per lane in flight
+// were measured slower: with the nine shape classes compiled into one
+// kernel their register needs add up and spill.)
 template <int D, int VEC>
-__device__ __forceinline__ float batch_segment(const BatchInst &I, const uint8_t *code, const float *R,
-                                               const float *V, float *W, int seg) {
+__device__ __forceinline__ float batch_tile(const BatchInst &I, const uint8_t *code, const float *R, const float *V,
+                                            float *W, int first, int nitems, int lane) {
     BandArgs a;
     a.nstates = I.nstates;
     a.nlast = I.nlast;
@@ -65,41 +104,101 @@ __device__ __forceinline__ float batch_segment(const BatchInst &I, const uint8_t
     a.code = code + I.offset;
     a.R32 = R + I.offset;
     a.R64 = nullptr;
+    const float *Vi = V + I.offset;
+    float *Wi = W + I.offset;
+    if (lane >= nitems) return 0.f;
     Segment<float, float, D, VEC> sg;
-    sg.template load<M_VI>(a, V + I.offset, nullptr, seg * VEC);
-    return sg.template finish_vi<false>(a, W + I.offset, nullptr, seg * VEC);
+    sg.template load<M_VI>(a, Vi, nullptr, (first + lane) * VEC);
+    return sg.template finish_vi<false>(a, Wi, nullptr, (first + lane) * VEC);
 }
 
-__device__ __forceinline__ float batch_item(const BatchInst &I, const uint8_t *code, const float *R, const float *V,
-                                            float *W, int seg) {
-    switch (I.ndim * 8 + I.vec) {
-        case 1 * 8 + 1: return batch_segment<1, 1>(I, code, R, V, W, seg);
-        case 1 * 8 + 2: return batch_segment<1, 2>(I, code, R, V, W, seg);
-        case 1 * 8 + 4: return batch_segment<1, 4>(I, code, R, V, W, seg);
-        case 2 * 8 + 1: return batch_segment<2, 1>(I, code, R, V, W, seg);
-        case 2 * 8 + 2: return batch_segment<2, 2>(I, code, R, V, W, seg);
-        case 2 * 8 + 4: return batch_segment<2, 4>(I, code, R, V, W, seg);
-        case 3 * 8 + 1: return batch_segment<3, 1>(I, code, R, V, W, seg);
-        case 3 * 8 + 2: return batch_segment<3, 2>(I, code, R, V, W, seg);
-        default: return batch_segment<3, 4>(I, code, R, V, W, seg);
+// Broadcast lane src's instance record to the warp.
+__device__ __forceinline__ BatchInst shfl_inst(const BatchInst &x, int src) {
+    BatchInst y;
+    y.offset = __shfl_sync(0xFFFFFFFFu, x.offset, src);
+    y.nstates = __shfl_sync(0xFFFFFFFFu, x.nstates, src);
+    y.ndim = __shfl_sync(0xFFFFFFFFu, x.ndim, src);
+    y.nlast = __shfl_sync(0xFFFFFFFFu, x.nlast, src);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        y.stride[d] = __shfl_sync(0xFFFFFFFFu, x.stride[d], src);
+        y.shape[d] = 0;
+    }
+    y.vec = __shfl_sync(0xFFFFFFFFu, x.vec, src);
+    y.first_tile = 0;
+    y.w_move = __shfl_sync(0xFFFFFFFFu, x.w_move, src);
+    y.w_perp = __shfl_sync(0xFFFFFFFFu, x.w_perp, src);
+    y.w_stay = __shfl_sync(0xFFFFFFFFu, x.w_stay, src);
+    y.gamma = __shfl_sync(0xFFFFFFFFu, x.gamma, src);
+    return y;
+}
+
+// The running tiles of one shape class (D, VEC) among the warp's round:
+// cls is the lane's tile class, act the running lanes.
+template <int D, int VEC>
+__device__ __forceinline__ void batch_class(const BatchArgs &b, const BatchTile &T, const BatchInst &I, int cls,
+                                            unsigned act, const float *cur, float *nxt, int k, int lane) {
+    unsigned m = act & __ballot_sync(0xFFFFFFFFu, cls == D * 8 + VEC);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1u;
+        const int inst = __shfl_sync(0xFFFFFFFFu, T.inst, src);
+        const int first = __shfl_sync(0xFFFFFFFFu, T.first_item, src);
+        const int nitems = __shfl_sync(0xFFFFFFFFu, T.nitems, src);
+        const BatchInst Ib = shfl_inst(I, src);
+        // b.spl groups of 32 segments, one after another (their lines are
+        // already on their way to L2)
+        float r = 0.f;
+        for (int u = 0; u < b.spl; u++)
+            r = fmaxf(r, batch_tile<D, VEC>(Ib, b.code, b.R, cur, nxt, first + 32 * u, nitems - 32 * u, lane));
+        // non-negative residuals: integer max of the bit patterns
+        const unsigned mx = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(r));
+        if (lane == 0 && mx)
+            atomicMax(&b.res[(size_t)(k % 3) * b.ninst + inst],
+                      (unsigned long long)__double_as_longlong((double)__uint_as_float(mx)));
     }
 }
 
-template <int IPT>
-__global__ void __launch_bounds__(512) batch_vi_kernel(BatchArgs b) {
-    __shared__ int s_state;       // 0 skip, 1 work, 2 just stopped
-    __shared__ unsigned s_red[16];
+// One persistent launch. Every global sweep k, each warp takes the tiles
+// t = w + j NW (w its global warp index, NW the number of warps, j = 0, 1,
+// ...; consecutive tiles of an instance land on different warps), 32 at a
+// time: lane l classifies tile w + (j0 + l) NW itself (its instance stopped
+// earlier, stops now, or runs) and, if it runs, loads the instance record,
+// so one round of loads serves 32 tiles. A lane remembers in a register
+// which of its tiles belong to stopped instances (an instance never
+// restarts within a solve) and loads nothing for them again. The warp then
+// works through the running tiles of the round, each lane taking spl
+// segments one after another, and reduces the tile's residual
+// with one integer max (redux) and one atomicMax on the instance's slot.
+// Warps never wait for one another inside a sweep; the block meets the grid
+// barrier at the end, reporting whether any of its warps found a running
+// tile.
+__global__ void __launch_bounds__(512, 1) batch_vi_kernel(BatchArgs b) {
+    __shared__ int s_worked;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int wpb = blockDim.x >> 5;
+    const long long nw = (long long)gridDim.x * wpb;
+    const long long gw = (long long)blockIdx.x * wpb + (tid >> 5);
     const unsigned nb = gridDim.x;
-    const int tid = threadIdx.x;
     unsigned long long ph0 = 0ull, ph1 = 0ull;
+    unsigned stopped = 0u;   // bit r: this lane's tile of round r belongs to a stopped instance
     int k = 0;
     for (; k <= b.max_iter; k++) {
         const float *cur = (k & 1) ? b.W : b.V;
         float *nxt = (k & 1) ? b.V : b.W;
-        int worked = 0;
-        for (int t = blockIdx.x; t < b.ntiles; t += nb) {
-            const BatchTile T = b.tiles[t];
-            if (tid == 0) {
+        if (tid == 0) s_worked = 0;
+        __syncthreads();
+        bool worked = false;
+        int round = 0;
+        for (long long j0 = 0; gw + j0 * nw < b.ntiles; j0 += 32, round++) {
+            const long long tl = gw + (j0 + lane) * nw;
+            const bool known = round < 32 && ((stopped >> round) & 1u);
+            if (__all_sync(0xFFFFFFFFu, known || tl >= b.ntiles)) continue;
+            bool run = false;
+            BatchTile T = {0, 0, 0};
+            BatchInst I;
+            if (tl < b.ntiles && !known) {
+                T = b.tiles[tl];
                 int st = 1;
                 if (b.done_at[T.inst] != 0) {
                     st = 0;
@@ -109,42 +208,36 @@ __global__ void __launch_bounds__(512) batch_vi_kernel(BatchArgs b) {
                     if (below_tol(rb, b.tol)) st = 2;
                 }
                 if (st == 1 && k == b.max_iter) st = 3;   // limit reached: stop without a sweep
-                if (st == 2 || st == 3) {
-                    // every block that sees the stop writes the same value
-                    b.done_at[T.inst] = st == 2 ? k : -k;
-                    st = 0;
+                // every lane that sees the stop writes the same value
+                if (st >= 2) b.done_at[T.inst] = st == 2 ? k : -k;
+                run = st == 1;
+                if (!run && round < 32) stopped |= 1u << round;
+                if (run) {
+                    if (T.first_item == 0) b.res[(size_t)((k + 1) % 3) * b.ninst + T.inst] = 0ull;
+                    I = b.inst[T.inst];
+                    prefetch_tile(I, T, cur, b.R, b.code);
                 }
-                if (st == 1 && T.first_item == 0)
-                    b.res[(size_t)((k + 1) % 3) * b.ninst + T.inst] = 0ull;
-                s_state = st;
             }
-            __syncthreads();
-            const int st = s_state;
-            __syncthreads();
-            if (st == 0) continue;
-            worked = 1;
-            const BatchInst I = b.inst[T.inst];
-            float r = 0.f;
-#pragma unroll
-            for (int u = 0; u < IPT; u++) {
-                const int it = tid + u * blockDim.x;
-                if (it < T.nitems) r = fmaxf(r, batch_item(I, b.code, b.R, cur, nxt, T.first_item + it));
-            }
-            // block max -> the instance's slot for sweep k (non-negative
-            // residuals: integer max of the bit patterns, one redux per warp)
-            const unsigned u = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(r));
-            if ((tid & 31) == 0) s_red[tid >> 5] = u;
-            __syncthreads();
-            if (tid == 0) {
-                unsigned m = 0u;
-                for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = m > s_red[w] ? m : s_red[w];
-                if (m)
-                    atomicMax(&b.res[(size_t)(k % 3) * b.ninst + T.inst],
-                              (unsigned long long)__double_as_longlong((double)__uint_as_float(m)));
-            }
-            __syncthreads();
+            const unsigned act = __ballot_sync(0xFFFFFFFFu, run);
+            worked |= act != 0u;
+            if (!act) continue;
+            // the running tiles, one instance shape class (D, VEC) at a time:
+            // each class is its own loop, so the register needs of the nine
+            // tile variants do not add up
+            const int cls = run ? I.ndim * 8 + I.vec : 0;
+            batch_class<1, 1>(b, T, I, cls, act, cur, nxt, k, lane);
+            batch_class<1, 2>(b, T, I, cls, act, cur, nxt, k, lane);
+            batch_class<1, 4>(b, T, I, cls, act, cur, nxt, k, lane);
+            batch_class<2, 1>(b, T, I, cls, act, cur, nxt, k, lane);
+            batch_class<2, 2>(b, T, I, cls, act, cur, nxt, k, lane);
+            batch_class<2, 4>(b, T, I, cls, act, cur, nxt, k, lane);
+            batch_class<3, 1>(b, T, I, cls, act, cur, nxt, k, lane);
+            batch_class<3, 2>(b, T, I, cls, act, cur, nxt, k, lane);
+            batch_class<3, 4>(b, T, I, cls, act, cur, nxt, k, lane);
         }
-        const long long busy = grid_sync_count(b.ctrl, k, nb, tid == 0 ? worked : 0, b.timeout_ns, ph0, ph1, false);
+        if (worked && lane == 0) s_worked = 1;
+        __syncthreads();
+        const long long busy = grid_sync_count(b.ctrl, k, nb, tid == 0 ? s_worked : 0, b.timeout_ns, ph0, ph1, false);
         if (busy < 0) return;
         if (busy == 0) break;
     }
@@ -189,22 +282,23 @@ static std::vector<BatchTile> make_tiles(const std::vector<BatchInst> &inst, int
     return tiles;
 }
 
-// Autotuner result cache: (number of instances, total states / 64K) -> (block, items per thread)
+// Autotuner result cache: (number of instances, total states / 64K) -> (block, segments per lane)
 static std::mutex g_tune_mutex;
 static std::map<std::pair<int, long long>, std::pair<int, int>> g_tune_cache;
 
-template <int IPT>
 static cudaError_t launch_batch(const cpmdp_batch &B, int block, const BatchArgs &args, cudaStream_t st, int *grid_out) {
     static int occ[3] = {0, 0, 0};
     const int bi = block == 128 ? 0 : (block == 256 ? 1 : 2);
     if (occ[bi] <= 0) {
         int o = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, batch_vi_kernel<IPT>, block, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, batch_vi_kernel, block, 0);
         if (e != cudaSuccess) return e;
         occ[bi] = o > 0 ? o : 1;
     }
+    // all co-resident blocks, but no more warps than tiles
     int grid = occ[bi] * B.num_sms;
-    if (grid > B.ntiles) grid = B.ntiles;
+    const int wpb = block / 32;
+    if ((long long)grid * wpb > B.ntiles) grid = (B.ntiles + wpb - 1) / wpb;
     if (grid < 1) grid = 1;
     *grid_out = grid;
     cudaLaunchConfig_t cfg;
@@ -217,11 +311,11 @@ static cudaError_t launch_batch(const cpmdp_batch &B, int block, const BatchArgs
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, batch_vi_kernel<IPT>, args);
+    return cudaLaunchKernelEx(&cfg, batch_vi_kernel, args);
 }
 
 static cudaError_t enqueue_batch(const cpmdp_batch &B, float *V, double tol, int max_iter, double timeout_s,
-                                 int block, int ipt, cudaStream_t st, int *grid_out) {
+                                 int block, int spl, cudaStream_t st, int *grid_out) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(B.d_ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(B.d_res, 0, sizeof(unsigned long long) * 3 * B.ninst, st)) != cudaSuccess) return e;
@@ -239,9 +333,10 @@ static cudaError_t enqueue_batch(const cpmdp_batch &B, float *V, double tol, int
     a.done_at = B.d_done;
     a.tol = tol;
     a.max_iter = max_iter;
+    a.spl = spl;
     a.timeout_ns = (unsigned long long)(timeout_s * 1e9);
     a.ctrl = B.d_ctrl;
-    return ipt == 2 ? launch_batch<2>(B, block, a, st, grid_out) : launch_batch<1>(B, block, a, st, grid_out);
+    return launch_batch(B, block, a, st, grid_out);
 }
 
 static cpmdp_status upload_tiles(cpmdp_batch &B, int tile_items) {
@@ -259,7 +354,7 @@ static cpmdp_status upload_tiles(cpmdp_batch &B, int tile_items) {
     return CPMDP_OK;
 }
 
-// Time `sweeps` global sweeps for each (block, items per thread) candidate
+// Time 8 global sweeps for each (block, segments per lane) candidate
 // on the batch itself (values from zero, scratch output), keep the fastest.
 static cpmdp_status autotune(cpmdp_batch &B, cudaStream_t st) {
     const std::pair<int, long long> key(B.ninst, B.total_states >> 16);
@@ -268,11 +363,13 @@ static cpmdp_status autotune(cpmdp_batch &B, cudaStream_t st) {
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             B.block = it->second.first;
-            B.ipt = it->second.second;
-            return upload_tiles(B, B.block * B.ipt);
+            B.spl = it->second.second;
+            return upload_tiles(B, 32 * B.spl);
         }
     }
-    const int cand[][2] = {{128, 1}, {256, 1}, {512, 1}, {256, 2}, {512, 2}};
+    // (block size, segments per lane of a warp tile)
+    const int cand[][2] = {{128, 1}, {128, 2}, {128, 4}, {256, 1}, {256, 4}, {512, 1}};
+    const int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
     // the candidates run on a temporary value tensor (the caller's V is the start)
     float *V = nullptr;
     CPMDP_CUDA(cudaMalloc(&V, sizeof(float) * B.total_states));
@@ -282,8 +379,8 @@ static cpmdp_status autotune(cpmdp_batch &B, cudaStream_t st) {
     cudaEvent_t e0, e1;
     CPMDP_CUDA(cudaEventCreate(&e0));
     CPMDP_CUDA(cudaEventCreate(&e1));
-    for (int c = 0; c < 5; c++) {
-        cpmdp_status s = upload_tiles(B, cand[c][0] * cand[c][1]);
+    for (int c = 0; c < ncand; c++) {
+        cpmdp_status s = upload_tiles(B, 32 * cand[c][1]);
         if (s != CPMDP_OK) return s;
         float ms_sum = 0.f;
         for (int rep = 0; rep < 3; rep++) {
@@ -302,12 +399,12 @@ static cpmdp_status autotune(cpmdp_batch &B, cudaStream_t st) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     B.block = cand[best][0];
-    B.ipt = cand[best][1];
+    B.spl = cand[best][1];
     {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
-        g_tune_cache[key] = std::make_pair(B.block, B.ipt);
+        g_tune_cache[key] = std::make_pair(B.block, B.spl);
     }
-    return upload_tiles(B, B.block * B.ipt);
+    return upload_tiles(B, 32 * B.spl);
 }
 
 }  // namespace cpmdp
@@ -396,8 +493,8 @@ cpmdp_status cpmdp_batch_build(const cpmdp_problem *problems, int32_t count, int
     if ((e = cudaMemcpy(B->d_code, codes.data(), (size_t)off, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "copy code");
     if ((e = cudaMemcpy(B->d_R, rew.data(), (size_t)off * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "copy R");
     B->block = 256;
-    B->ipt = 1;
-    if (upload_tiles(*B, 256) != CPMDP_OK) { free_batch_device(*B); delete B; if (prev >= 0) cudaSetDevice(prev); return CPMDP_ECUDA; }
+    B->spl = 1;
+    if (upload_tiles(*B, 32) != CPMDP_OK) { free_batch_device(*B); delete B; if (prev >= 0) cudaSetDevice(prev); return CPMDP_ECUDA; }
     if (prev >= 0) cudaSetDevice(prev);
     *out = B;
     return CPMDP_OK;
@@ -451,7 +548,7 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         int grid = 0;
-        if (e == cudaSuccess) e = enqueue_batch(*B, V, o.tol, o.max_iter, o.timeout_s, B->block, B->ipt, cap, &grid);
+        if (e == cudaSuccess) e = enqueue_batch(*B, V, o.tol, o.max_iter, o.timeout_s, B->block, B->spl, cap, &grid);
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         cudaStreamDestroy(cap);
         if (e == cudaSuccess && e2 == cudaSuccess && g) e = cudaGraphInstantiate(&B->graph, g, 0);
@@ -478,7 +575,7 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
         CPMDP_CUDA(cudaGraphLaunch(B->graph, st));
     } else {
         int grid = 0;
-        CPMDP_CUDA(enqueue_batch(*B, V, o.tol, o.max_iter, o.timeout_s, B->block, B->ipt, st, &grid));
+        CPMDP_CUDA(enqueue_batch(*B, V, o.tol, o.max_iter, o.timeout_s, B->block, B->spl, st, &grid));
     }
     CPMDP_CUDA(cudaEventRecord(e1, st));
     Ctrl hc;

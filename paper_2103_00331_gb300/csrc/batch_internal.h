@@ -43,7 +43,7 @@ struct cpmdp_batch {
     int ntiles = 0;
     int tile_items = 0;
     int block = 0;
-    int ipt = 1;
+    int spl = 1;           // segments per lane of a warp tile
     uint8_t *d_code = nullptr;
     float *d_R = nullptr;
     float *d_W = nullptr;
