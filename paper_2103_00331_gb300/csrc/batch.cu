@@ -4,9 +4,10 @@
 //
 // The instances are packed back to back (values, FP32 rewards, per-state
 // move codes in the encoding of the single-instance path). The work is cut
-// into warp tiles: a tile is up to 32 x spl row segments of one instance,
-// each segment VEC in {1, 2, 4} consecutive states of a row of the last
-// dimension (VEC divides that instance's row length). Every global sweep the
+// into warp tiles: a tile is up to 32 x spl segments of one instance, each
+// segment 4 consecutive states (instances start 16-byte aligned and are
+// padded to a multiple of 4 states; a segment of an instance whose rows are
+// not a multiple of 4 long may span two rows). Every global sweep the
 // warps of the cooperative grid take the tiles of instances that are still
 // running; an instance stops on its own as soon as its residual falls below
 // tol, so short and long solves share the launch. Per-instance residuals use
@@ -33,7 +34,6 @@
 namespace cpmdp {
 
 struct BatchArgs {
-    const BatchInst *inst;
     const BatchTile *tiles;
     int ntiles;
     int ninst;
@@ -66,66 +66,101 @@ __device__ __forceinline__ void prefetch_span(const void *base, long long lo, lo
 // Issued by the lane that found the tile running, for all running tiles of
 // a round at once, so that the warp, working through them one by one, waits
 // for HBM once per round instead of once per tile.
-__device__ __forceinline__ void prefetch_tile(const BatchInst &I, const BatchTile &T, const float *V, const float *R,
-                                              const uint8_t *code) {
-    const long long base = I.offset, end = I.offset + I.nstates;
-    const long long a0 = base + (long long)T.first_item * I.vec;
-    long long a1 = base + (long long)(T.first_item + T.nitems) * I.vec;
+__device__ __forceinline__ void prefetch_tile(const BatchTile &T, const float *V, const float *R, const uint8_t *code) {
+    const long long base = T.offset, end = T.offset + T.nstates;
+    const long long a0 = base + 4ll * T.first_item;
+    long long a1 = base + 4ll * (T.first_item + T.nitems);
     a1 = a1 < end ? a1 : end;
     const long long h0 = a0 > base ? a0 - 1 : a0, h1 = a1 < end ? a1 + 1 : a1;
     prefetch_span(V, h0, h1, 4);
     prefetch_span(R, a0, a1, 4);
     prefetch_span(code, a0, a1, 1);
-#pragma unroll
-    for (int d = 0; d < 2; d++) {
-        if (d >= I.ndim - 1) break;
-        const long long st = I.stride[d];
+    const int ndim = T.cls >> 1;
+    if (ndim >= 2) {
+        const long long st = T.stride0;
+        if (a0 - st >= base) prefetch_span(V, a0 - st, a1 - st, 4);
+        if (a1 + st <= end) prefetch_span(V, a0 + st, a1 + st, 4);
+    }
+    if (ndim >= 3) {
+        const long long st = T.stride1;
         if (a0 - st >= base) prefetch_span(V, a0 - st, a1 - st, 4);
         if (a1 + st <= end) prefetch_span(V, a0 + st, a1 + st, 4);
     }
 }
 
-// One segment of a tile per lane (segment first + lane of the instance), D
-// and VEC fixed at compile time. (Two or more segments per lane in flight
-// were measured slower: with the nine shape classes compiled into one
-// kernel their register needs add up and spill.)
-template <int D, int VEC>
-__device__ __forceinline__ float batch_tile(const BatchInst &I, const uint8_t *code, const float *R, const float *V,
-                                            float *W, int first, int nitems, int lane) {
-    BandArgs a;
-    a.nstates = I.nstates;
-    a.nlast = I.nlast;
+// Loads of a 4-state segment whose rows are not a multiple of 4 states
+// long: the segment may end one row and start the next, and the neighbour
+// rows one stride away are not 16-byte aligned. The segment's own values,
+// rewards and codes are (instances start 16-byte aligned and are padded to
+// a multiple of 4 states with obstacle codes, so the last segment stays
+// inside the packed arrays); each neighbour is loaded on its own with its
+// index clamped into [0, npad). A clamped index only differs from the true
+// neighbour where that neighbour does not exist, and there the move is
+// blocked in the code (a wall at the end of a row included), so the backup
+// uses V(s) instead. Padding states are obstacles: value 0, no residual.
+template <int D>
+__device__ __forceinline__ void load_rows_any(Segment<float, float, D, 4> &sg, const BandArgs &a, const float *V,
+                                              int s0, int npad) {
+    load_pack<uint8_t, 4>(static_cast<const uint8_t *>(a.code) + s0, sg.code);
+    load_pack<float, 4>(V + s0, sg.vs);
 #pragma unroll
-    for (int d = 0; d < kMaxDim; d++) a.stride[d] = d < 3 ? (d < D ? I.stride[d] : 0) : 0;
-    a.wf_move = I.w_move;
-    a.wf_perp = I.w_perp;
-    a.wf_stay = I.w_stay;
-    a.wf_gamma = I.gamma;
-    a.code = code + I.offset;
-    a.R32 = R + I.offset;
+    for (int d = 0; d < D - 1; d++) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int lo = s0 + k - a.stride[d], hi = s0 + k + a.stride[d];
+            sg.rows[2 * d][k] = V[lo < 0 ? 0 : lo];
+            sg.rows[2 * d + 1][k] = V[hi >= npad ? npad - 1 : hi];
+        }
+    }
+    sg.halo_m = V[s0 > 0 ? s0 - 1 : 0];
+    sg.halo_p = V[s0 + 4 < npad ? s0 + 4 : npad - 1];
+    load_pack<float, 4>(a.R32 + s0, sg.r);
+}
+
+// One 4-state segment of a tile per lane (segment first + lane of the
+// instance), D fixed at compile time; ROWS4: rows a multiple of 4 states
+// long (16-byte neighbour-row loads), else load_rows_any. (Two or more
+// segments per lane in flight were measured slower: with every shape class
+// compiled into one kernel their register needs add up and spill.)
+template <int D, bool ROWS4>
+__device__ __forceinline__ float batch_tile(const BatchTile &T, const uint8_t *code, const float *R, const float *V,
+                                            float *W, int first, int nitems, int lane) {
+    constexpr int VEC = 4;
+    BandArgs a;
+    a.nstates = T.nstates;
+    a.nlast = T.nlast;
+#pragma unroll
+    for (int d = 0; d < kMaxDim; d++) a.stride[d] = 0;
+    if (D >= 2) a.stride[0] = T.stride0;
+    if (D >= 3) a.stride[1] = T.stride1;
+    a.wf_move = T.w_move;
+    a.wf_perp = T.w_perp;
+    a.wf_stay = T.w_stay;
+    a.wf_gamma = T.gamma;
+    a.code = code + T.offset;
+    a.R32 = R + T.offset;
     a.R64 = nullptr;
-    const float *Vi = V + I.offset;
-    float *Wi = W + I.offset;
+    const float *Vi = V + T.offset;
+    float *Wi = W + T.offset;
     if (lane >= nitems) return 0.f;
     Segment<float, float, D, VEC> sg;
-    sg.template load<M_VI>(a, Vi, nullptr, (first + lane) * VEC);
+    if (ROWS4) sg.template load<M_VI>(a, Vi, nullptr, (first + lane) * VEC);
+    else load_rows_any<D>(sg, a, Vi, (first + lane) * VEC, (T.nstates + 3) & ~3);
     return sg.template finish_vi<false>(a, Wi, nullptr, (first + lane) * VEC);
 }
 
-// Broadcast lane src's instance record to the warp.
-__device__ __forceinline__ BatchInst shfl_inst(const BatchInst &x, int src) {
-    BatchInst y;
+// Broadcast lane src's tile record to the warp.
+__device__ __forceinline__ BatchTile shfl_tile(const BatchTile &x, int src) {
+    BatchTile y;
     y.offset = __shfl_sync(0xFFFFFFFFu, x.offset, src);
+    y.inst = __shfl_sync(0xFFFFFFFFu, x.inst, src);
+    y.first_item = __shfl_sync(0xFFFFFFFFu, x.first_item, src);
+    y.nitems = __shfl_sync(0xFFFFFFFFu, x.nitems, src);
     y.nstates = __shfl_sync(0xFFFFFFFFu, x.nstates, src);
-    y.ndim = __shfl_sync(0xFFFFFFFFu, x.ndim, src);
+    y.cls = __shfl_sync(0xFFFFFFFFu, x.cls, src);
     y.nlast = __shfl_sync(0xFFFFFFFFu, x.nlast, src);
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        y.stride[d] = __shfl_sync(0xFFFFFFFFu, x.stride[d], src);
-        y.shape[d] = 0;
-    }
-    y.vec = __shfl_sync(0xFFFFFFFFu, x.vec, src);
-    y.first_tile = 0;
+    y.stride0 = __shfl_sync(0xFFFFFFFFu, x.stride0, src);
+    y.stride1 = __shfl_sync(0xFFFFFFFFu, x.stride1, src);
     y.w_move = __shfl_sync(0xFFFFFFFFu, x.w_move, src);
     y.w_perp = __shfl_sync(0xFFFFFFFFu, x.w_perp, src);
     y.w_stay = __shfl_sync(0xFFFFFFFFu, x.w_stay, src);
@@ -133,28 +168,26 @@ __device__ __forceinline__ BatchInst shfl_inst(const BatchInst &x, int src) {
     return y;
 }
 
-// The running tiles of one shape class (D, VEC) among the warp's round:
-// cls is the lane's tile class, act the running lanes.
-template <int D, int VEC>
-__device__ __forceinline__ void batch_class(const BatchArgs &b, const BatchTile &T, const BatchInst &I, int cls,
-                                            unsigned act, const float *cur, float *nxt, int k, int lane) {
-    unsigned m = act & __ballot_sync(0xFFFFFFFFu, cls == D * 8 + VEC);
+// The running tiles of one shape class (D, ROWS4) among the warp's round:
+// run marks the lanes whose tile runs.
+template <int D, bool ROWS4>
+__device__ __forceinline__ void batch_class(const BatchArgs &b, const BatchTile &T, bool run, const float *cur,
+                                            float *nxt, int k, int lane) {
+    unsigned m = __ballot_sync(0xFFFFFFFFu, run && T.cls == D * 2 + (ROWS4 ? 1 : 0));
     while (m) {
         const int src = __ffs(m) - 1;
         m &= m - 1u;
-        const int inst = __shfl_sync(0xFFFFFFFFu, T.inst, src);
-        const int first = __shfl_sync(0xFFFFFFFFu, T.first_item, src);
-        const int nitems = __shfl_sync(0xFFFFFFFFu, T.nitems, src);
-        const BatchInst Ib = shfl_inst(I, src);
+        const BatchTile Tb = shfl_tile(T, src);
         // b.spl groups of 32 segments, one after another (their lines are
         // already on their way to L2)
         float r = 0.f;
         for (int u = 0; u < b.spl; u++)
-            r = fmaxf(r, batch_tile<D, VEC>(Ib, b.code, b.R, cur, nxt, first + 32 * u, nitems - 32 * u, lane));
+            r = fmaxf(r, batch_tile<D, ROWS4>(Tb, b.code, b.R, cur, nxt, Tb.first_item + 32 * u, Tb.nitems - 32 * u,
+                                              lane));
         // non-negative residuals: integer max of the bit patterns
         const unsigned mx = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(r));
         if (lane == 0 && mx)
-            atomicMax(&b.res[(size_t)(k % 3) * b.ninst + inst],
+            atomicMax(&b.res[(size_t)(k % 3) * b.ninst + Tb.inst],
                       (unsigned long long)__double_as_longlong((double)__uint_as_float(mx)));
     }
 }
@@ -195,8 +228,9 @@ __global__ void __launch_bounds__(512, 1) batch_vi_kernel(BatchArgs b) {
             const bool known = round < 32 && ((stopped >> round) & 1u);
             if (__all_sync(0xFFFFFFFFu, known || tl >= b.ntiles)) continue;
             bool run = false;
-            BatchTile T = {0, 0, 0};
-            BatchInst I;
+            BatchTile T;
+            T.inst = 0;
+            T.cls = 0;
             if (tl < b.ntiles && !known) {
                 T = b.tiles[tl];
                 int st = 1;
@@ -214,26 +248,20 @@ __global__ void __launch_bounds__(512, 1) batch_vi_kernel(BatchArgs b) {
                 if (!run && round < 32) stopped |= 1u << round;
                 if (run) {
                     if (T.first_item == 0) b.res[(size_t)((k + 1) % 3) * b.ninst + T.inst] = 0ull;
-                    I = b.inst[T.inst];
-                    prefetch_tile(I, T, cur, b.R, b.code);
+                    prefetch_tile(T, cur, b.R, b.code);
                 }
             }
             const unsigned act = __ballot_sync(0xFFFFFFFFu, run);
             worked |= act != 0u;
             if (!act) continue;
-            // the running tiles, one instance shape class (D, VEC) at a time:
-            // each class is its own loop, so the register needs of the nine
-            // tile variants do not add up
-            const int cls = run ? I.ndim * 8 + I.vec : 0;
-            batch_class<1, 1>(b, T, I, cls, act, cur, nxt, k, lane);
-            batch_class<1, 2>(b, T, I, cls, act, cur, nxt, k, lane);
-            batch_class<1, 4>(b, T, I, cls, act, cur, nxt, k, lane);
-            batch_class<2, 1>(b, T, I, cls, act, cur, nxt, k, lane);
-            batch_class<2, 2>(b, T, I, cls, act, cur, nxt, k, lane);
-            batch_class<2, 4>(b, T, I, cls, act, cur, nxt, k, lane);
-            batch_class<3, 1>(b, T, I, cls, act, cur, nxt, k, lane);
-            batch_class<3, 2>(b, T, I, cls, act, cur, nxt, k, lane);
-            batch_class<3, 4>(b, T, I, cls, act, cur, nxt, k, lane);
+            // the running tiles, one instance shape class (D, rows of 4) at a
+            // time: each class is its own loop
+            batch_class<1, true>(b, T, run, cur, nxt, k, lane);
+            batch_class<1, false>(b, T, run, cur, nxt, k, lane);
+            batch_class<2, true>(b, T, run, cur, nxt, k, lane);
+            batch_class<2, false>(b, T, run, cur, nxt, k, lane);
+            batch_class<3, true>(b, T, run, cur, nxt, k, lane);
+            batch_class<3, false>(b, T, run, cur, nxt, k, lane);
         }
         if (worked && lane == 0) s_worked = 1;
         __syncthreads();
@@ -248,9 +276,8 @@ __global__ void __launch_bounds__(512, 1) batch_vi_kernel(BatchArgs b) {
         const int n = b.done_at[T.inst];
         const int sweeps = n < 0 ? -n : n;
         if (!(sweeps & 1)) continue;
-        const BatchInst I = b.inst[T.inst];
-        const int s0 = T.first_item * I.vec, s1 = min((T.first_item + T.nitems) * I.vec, I.nstates);
-        for (int s = s0 + tid; s < s1; s += blockDim.x) b.V[I.offset + s] = b.W[I.offset + s];
+        const int s0 = 4 * T.first_item, s1 = min(4 * (T.first_item + T.nitems), T.nstates);
+        for (int s = s0 + tid; s < s1; s += blockDim.x) b.V[T.offset + s] = b.W[T.offset + s];
     }
     if (blockIdx.x == 0 && tid == 0) b.ctrl->iterations = k;
 }
@@ -275,9 +302,27 @@ static std::vector<BatchTile> make_tiles(const std::vector<BatchInst> &inst, int
     std::vector<BatchTile> tiles;
     first_tile->assign(inst.size(), 0);
     for (size_t i = 0; i < inst.size(); i++) {
-        const int nitems = inst[i].nstates / inst[i].vec;
+        const BatchInst &I = inst[i];
+        const int nitems = (I.nstates + I.vec - 1) / I.vec;
         (*first_tile)[i] = (int)tiles.size();
-        for (int f = 0; f < nitems; f += tile_items) tiles.push_back({(int)i, f, std::min(tile_items, nitems - f)});
+        for (int f = 0; f < nitems; f += tile_items) {
+            BatchTile T;
+            memset(&T, 0, sizeof(T));
+            T.offset = I.offset;
+            T.inst = (int)i;
+            T.first_item = f;
+            T.nitems = std::min(tile_items, nitems - f);
+            T.nstates = I.nstates;
+            T.cls = I.ndim * 2 + I.rows4;
+            T.nlast = I.nlast;
+            T.stride0 = I.ndim >= 2 ? I.stride[0] : 0;
+            T.stride1 = I.ndim >= 3 ? I.stride[1] : 0;
+            T.w_move = I.w_move;
+            T.w_perp = I.w_perp;
+            T.w_stay = I.w_stay;
+            T.gamma = I.gamma;
+            tiles.push_back(T);
+        }
     }
     return tiles;
 }
@@ -321,7 +366,6 @@ static cudaError_t enqueue_batch(const cpmdp_batch &B, float *V, double tol, int
     if ((e = cudaMemsetAsync(B.d_res, 0, sizeof(unsigned long long) * 3 * B.ninst, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(B.d_done, 0, sizeof(int) * B.ninst, st)) != cudaSuccess) return e;
     BatchArgs a;
-    a.inst = B.d_inst;
     a.tiles = B.d_tiles;
     a.ntiles = B.ntiles;
     a.ninst = B.ninst;
@@ -452,7 +496,11 @@ cpmdp_status cpmdp_batch_build(const cpmdp_problem *problems, int32_t count, int
             I.stride[d] = (int)F.stride[d];
             I.shape[d] = (int)F.shape[d];
         }
-        I.vec = (I.nlast % 4 == 0) ? 4 : ((I.nlast % 2 == 0) ? 2 : 1);
+        // segments of 4 states for every instance (instances start 16-byte
+        // aligned and are padded to a multiple of 4 states); rows whose length
+        // is a multiple of 4 also take 16-byte loads of the neighbour rows
+        I.vec = 4;
+        I.rows4 = I.nlast % 4 == 0 ? 1 : 0;
         I.w_move = (float)F.w_move;
         I.w_perp = (float)F.w_perp;
         I.w_stay = (float)F.w_stay;

@@ -18,15 +18,24 @@ struct BatchInst {
     int nlast;
     int stride[3];
     int shape[3];
-    int vec;               // 1, 2 or 4
+    int vec;               // states per segment (4)
+    int rows4;             // 1: rows a multiple of 4 states long
     int first_tile;
     float w_move, w_perp, w_stay, gamma;
 };
 
-struct BatchTile {
+// One warp tile: up to 32 x spl 4-state segments of one instance, with the
+// instance fields the backups need (one 64-byte record, no second lookup).
+struct alignas(16) BatchTile {
+    long long offset;      // instance's first state in the packed arrays
     int inst;
-    int first_item;        // segment index within the instance
-    int nitems;
+    int first_item;        // first segment of the tile
+    int nitems;            // segments in the tile
+    int nstates;           // instance states
+    int cls;               // ndim * 2 + rows4
+    int nlast;
+    int stride0, stride1;  // strides of the leading dimensions (0 if absent)
+    float w_move, w_perp, w_stay, gamma;
 };
 
 }  // namespace cpmdp
