@@ -102,3 +102,31 @@ def test_batch_rejects_invalid_instance(cp):
     with pytest.raises(cp.CpmdpError) as ei:
         cp.batch_build([ci.config_small_2d(1), bad], device=0)
     assert ei.value.status == cp.EINVAL and "instance 1" in cp.last_error()
+
+
+@pytest.mark.parametrize("k", [1, 4, 9])
+def test_batch_k_sweeps_match_oracle(cp, k):
+    """k sweeps with tol too small to stop, on instances of every shape class:
+    row lengths not a multiple of 4 (4-state segments that span rows, single
+    neighbour loads), multiples of 4 (16-byte row loads), 1-D, 2-D and 3-D,
+    odd and even state counts (padding). Each instance equals k oracle sweeps
+    from zero within the FP32 bound eps (1 - gamma^k) / (1 - gamma)."""
+    import torch
+    from oracle import cpfactor as oc
+    shapes = [(5,), (8,), (3, 7), (6, 6), (4, 12), (5, 9, 3), (4, 4, 8), (7, 5, 11), (2, 3, 4), (9, 1, 6)]
+    inst = [ci.gridworld(s, p=0.75, gamma=0.93, step_reward=-0.04, goal_rewards=[1.0, -1.0][:min(2, int(np.prod(s)) - 1)],
+                         obstacle_rate=0.15, seed=50 + i) for i, s in enumerate(shapes)]
+    B = cp.batch_build(inst, device=0)
+    V = torch.zeros(int(B.total_states), dtype=torch.float32, device="cuda")
+    r, iters, _ = cp.batch_value_iteration(B, V, opts=cp.default_opts(tol=1e-30, max_iter=k), raise_on_noconv=False)
+    assert np.all(iters == k)
+    Vh = V.double().cpu().numpy()
+    for i, gw in enumerate(inst):
+        Vo = np.zeros(gw.nstates)
+        for _ in range(k):
+            Vo = oc.backup(gw, Vo)[0]
+        lo = int(B.offsets[i])
+        eps = 14 * U32 * (np.abs(gw.reward).max() + np.abs(Vo).max())
+        err = np.abs(Vh[lo:lo + gw.nstates] - Vo).max()
+        assert err <= eps * (1 - gw.gamma ** k) / (1 - gw.gamma) + 1e-30, (i, gw.shape, err)
+    B.close()
