@@ -223,16 +223,22 @@ __global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__
 
 // ---------------------------------------------------------------------------
 // pass B: slabs of T_c -> E_a accumulated over ranks -> max over actions
+//
+// About 106 KB of shared memory, so that two CTAs share an SM and each
+// fills the other's MMA and copy waits: one raw slab-pair buffer and one
+// factor buffer (each refilled as soon as it is consumed, each with its
+// own mbarrier), and one operand buffer that holds Z for the first GEMM and
+// then the second GEMM's A operand (Z is consumed once the first GEMM has
+// completed).
 
-constexpr int kBOffBuf = 0;                        // 2 x (raw slab pair 32 KB + U1 hi, lo, U2 hi, lo 32 KB)
-constexpr int kBBufBytes = 2 * kQuadTileBytes + 4 * kTileBytes;
-constexpr int kBOffZ = 2 * kBBufBytes;             // {hi, lo} x 16 KB
-constexpr int kBOffA2 = kBOffZ + 2 * kPairBytes;   // {hi, lo} x 16 KB
-constexpr int kBOffArg = kBOffA2 + 2 * kPairBytes; // 64 x 128 argmax bytes
+constexpr int kBOffRaw = 0;                              // raw slab pair, 32 KB
+constexpr int kBOffU = kBOffRaw + 2 * kQuadTileBytes;    // U1 hi, lo, U2 hi, lo: 32 KB
+constexpr int kBOffZ = kBOffU + 4 * kTileBytes;          // Z / A2 {hi, lo} x 16 KB
+constexpr int kBOffArg = kBOffZ + 2 * kPairBytes;        // 64 x 128 argmax bytes
 constexpr int kBOffBar = kBOffArg + 64 * 128;
 constexpr int kBSmem = kBOffBar + 64 + 1024;
 
-__global__ void __launch_bounds__(128, 1) dense_pass_b(const uint8_t *__restrict__ T, const uint8_t *__restrict__ U,
+__global__ void __launch_bounds__(128, 2) dense_pass_b(const uint8_t *__restrict__ T, const uint8_t *__restrict__ U,
                                                        const float *__restrict__ RB, const float *__restrict__ EB,
                                                        const float *__restrict__ Vin, float *__restrict__ Vout,
                                                        uint8_t *__restrict__ pi, int nact, int nrank, float gamma,
@@ -240,15 +246,15 @@ __global__ void __launch_bounds__(128, 1) dense_pass_b(const uint8_t *__restrict
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sZ = sm + kBOffZ;
-    uint8_t *sA2 = sm + kBOffA2;
     uint8_t *sArg = sm + kBOffArg;
-    uint64_t *full = reinterpret_cast<uint64_t *>(sm + kBOffBar);       // [2]
+    uint64_t *full_raw = reinterpret_cast<uint64_t *>(sm + kBOffBar);
+    uint64_t *full_u = reinterpret_cast<uint64_t *>(sm + kBOffBar + 8);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kBOffBar + 16);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kBOffBar + 24);
     const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
-        tc::mbar_init(&full[0], 1);
-        tc::mbar_init(&full[1], 1);
+        tc::mbar_init(full_raw, 1);
+        tc::mbar_init(full_u, 1);
         tc::mbar_init(mbar, 1);
     }
     if (warp == 0) tc::tmem_alloc(tslot, 128);
@@ -256,39 +262,44 @@ __global__ void __launch_bounds__(128, 1) dense_pass_b(const uint8_t *__restrict
     sync_for_async();
     const uint32_t tmem = *tslot;
     const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
-    uint32_t phase = 0, fph0 = 0, fph1 = 0;
-    bool alive = true;
-    const uint32_t aBuf = tc::smem_u32(sm + kBOffBuf), aZ = tc::smem_u32(sZ), aA2 = tc::smem_u32(sA2);
+    uint32_t mph = 0, rph = 0, uph = 0;
+    // a copy issued and not yet waited for (its phase is flipped already
+    // when its own wait ran out)
+    bool alive = true, raw_pending = false, u_pending = false, raw_failed = false, u_failed = false;
+    const uint32_t aRaw = tc::smem_u32(sm + kBOffRaw), aU = tc::smem_u32(sm + kBOffU), aZ = tc::smem_u32(sZ);
     const int npairs = kSlab / 2, nchains = nact * nrank;
     double local_res = 0.0;
 
-    // item = (pair P, chain c); its raw slab pair and U1/U2 tiles go to buffer it % 2
-    auto issue = [&](int P, int c, int b) {
-        tc::mbar_expect_tx(&full[b], kBBufBytes);
-        const uint32_t dst = aBuf + b * kBBufBytes;
-        tc::bulk_g2s(dst, T + ((size_t)c * kSlab + 2 * P) * kQuadTileBytes, 2 * kQuadTileBytes, &full[b]);
-        tc::bulk_g2s(dst + 2 * kQuadTileBytes, utile(U, c, 0, 0), 4 * kTileBytes, &full[b]);
+    auto issue_raw = [&](int P, int c) {
+        tc::mbar_expect_tx(full_raw, 2 * kQuadTileBytes);
+        tc::bulk_g2s(aRaw, T + ((size_t)c * kSlab + 2 * P) * kQuadTileBytes, 2 * kQuadTileBytes, full_raw);
     };
-    int it = 0;
-    if (tid == 0 && blockIdx.x < npairs) issue(blockIdx.x, 0, 0);
+    auto issue_u = [&](int c) {
+        tc::mbar_expect_tx(full_u, 4 * kTileBytes);
+        tc::bulk_g2s(aU, utile(U, c, 0, 0), 4 * kTileBytes, full_u);
+    };
+    if (tid == 0 && blockIdx.x < npairs) {
+        issue_raw(blockIdx.x, 0);
+        issue_u(0);
+    }
+    raw_pending = u_pending = blockIdx.x < npairs;
     for (int P = blockIdx.x; P < npairs && alive; P += gridDim.x) {
         const int q0 = 2 * P;
         float best[64];
 #pragma unroll
         for (int j = 0; j < 64; j++) best[j] = 0.f;
         for (int a = 0; a < nact && alive; a++) {
-            for (int r = 0; r < nrank && alive; r++, it++) {
-                const int c = a * nrank + r, buf = it & 1;
-                if (tid == 0) {
-                    int nc = c + 1, nP = P;
-                    if (nc == nchains) { nc = 0; nP = P + gridDim.x; }
-                    if (nP < npairs) issue(nP, nc, buf ^ 1);
-                }
-                uint32_t &fph = buf ? fph1 : fph0;
-                if (!wait_all(&full[buf], fph, err)) { alive = false; break; }
-                // de-interleave the raw quads into the swizzled hi / lo pair tiles
+            for (int r = 0; r < nrank && alive; r++) {
+                const int c = a * nrank + r;
+                int nc = c + 1, nP = P;
+                if (nc == nchains) { nc = 0; nP = P + gridDim.x; }
+                const bool has_next = nP < npairs;
+                // raw slab pair -> swizzled hi / lo Z tiles (the operand
+                // buffer is free: the previous item's second GEMM completed)
+                if (!wait_all(full_raw, rph, err)) { raw_failed = true; alive = false; break; }
+                raw_pending = false;
                 {
-                    const uint4 *raw = reinterpret_cast<const uint4 *>(sm + kBOffBuf + buf * kBBufBytes);
+                    const uint4 *raw = reinterpret_cast<const uint4 *>(sm + kBOffRaw);
 #pragma unroll 4
                     for (int idx = tid; idx < 2 * 1024; idx += 128) {
                         const uint4 w = raw[idx];
@@ -300,31 +311,44 @@ __global__ void __launch_bounds__(128, 1) dense_pass_b(const uint8_t *__restrict
                     }
                 }
                 sync_for_async();
-                const uint32_t u1 = aBuf + buf * kBBufBytes + 2 * kQuadTileBytes, u2 = u1 + 2 * kTileBytes;
+                // the raw buffer is free: fetch the next item's slab pair
+                if (has_next) {
+                    if (tid == 0) issue_raw(nP, nc);
+                    raw_pending = true;
+                }
+                if (!wait_all(full_u, uph, err)) { u_failed = true; alive = false; break; }
+                u_pending = false;
+                const uint32_t u1 = aU, u2 = aU + 2 * kTileBytes;
                 if (tid == 0) {
                     tc::mma_bf16x3(tmem, aZ, aZ + kPairBytes, u2, u2 + kTileBytes, 0);
                     tc::commit(mbar);
                 }
-                if (!wait_all(mbar, phase, err)) { alive = false; break; }
+                if (!wait_all(mbar, mph, err)) { alive = false; break; }
                 tc::fence_after();
                 float w1[64];
                 tc::tmem_ld64(tmem + lane_off, w1);   // row tid = (s2, i1), cols i2'
                 {
+                    // the second GEMM's A operand, into the operand buffer
                     const uint32_t s2 = tid >> 6, i1 = tid & 63;
 #pragma unroll
                     for (int j = 0; j < 64; j++) {
                         __nv_bfloat16 h, l;
                         tc::split_bf16(w1[j], h, l);
-                        put_bf16(sA2, s2 * 64 + j, i1, __bfloat16_as_ushort(h));
-                        put_bf16(sA2 + kPairBytes, s2 * 64 + j, i1, __bfloat16_as_ushort(l));
+                        put_bf16(sZ, s2 * 64 + j, i1, __bfloat16_as_ushort(h));
+                        put_bf16(sZ + kPairBytes, s2 * 64 + j, i1, __bfloat16_as_ushort(l));
                     }
                 }
                 sync_for_async();
                 if (tid == 0) {
-                    tc::mma_bf16x3(tmem + 64, aA2, aA2 + kPairBytes, u1, u1 + kTileBytes, r > 0 ? 1u : 0u);
+                    tc::mma_bf16x3(tmem + 64, aZ, aZ + kPairBytes, u1, u1 + kTileBytes, r > 0 ? 1u : 0u);
                     tc::commit(mbar);
                 }
-                if (!wait_all(mbar, phase, err)) { alive = false; break; }
+                if (!wait_all(mbar, mph, err)) { alive = false; break; }
+                // the factor buffer is free: fetch the next item's factors
+                if (has_next) {
+                    if (tid == 0) issue_u(nc);
+                    u_pending = true;
+                }
             }
             if (!alive) break;
             tc::fence_after();
@@ -366,10 +390,10 @@ __global__ void __launch_bounds__(128, 1) dense_pass_b(const uint8_t *__restrict
         for (int o = 16; o > 0; o >>= 1) local_res = fmax(local_res, __shfl_xor_sync(0xFFFFFFFFu, local_res, o));
         if ((tid & 31) == 0 && local_res > 0.0) atomicMax(res, (unsigned long long)__double_as_longlong(local_res));
     }
-    // a prefetch may still be in flight when this CTA stopped early: wait for it
+    // a copy may still be in flight when this CTA stopped early: wait for it
     if (!alive && tid == 0) {
-        tc::mbar_wait(&full[0], fph0, kWaitCycles);
-        tc::mbar_wait(&full[1], fph1, kWaitCycles);
+        if (raw_pending) tc::mbar_wait(full_raw, raw_failed ? rph ^ 1u : rph, kWaitCycles);
+        if (u_pending) tc::mbar_wait(full_u, u_failed ? uph ^ 1u : uph, kWaitCycles);
     }
     tc::fence_before();
     __syncthreads();
@@ -453,7 +477,8 @@ static cpmdp_status tc_sweep(const Factors &F, const float *Vin, float *Vout, ui
     dense_pass_a<<<grid, 128, kASmem, st>>>(Vin, use_base ? F.d_Vbase : nullptr, (const uint8_t *)F.d_Ubf,
                                             (uint8_t *)F.d_T, C, err);
     CPMDP_CUDA(cudaGetLastError());
-    dense_pass_b<<<grid, 128, kBSmem, st>>>((const uint8_t *)F.d_T, (const uint8_t *)F.d_Ubf, F.d_RB,
+    // pass B: two CTAs per SM (about 106 KB of shared memory each)
+    dense_pass_b<<<2 * grid, 128, kBSmem, st>>>((const uint8_t *)F.d_T, (const uint8_t *)F.d_Ubf, F.d_RB,
                                             use_base ? F.d_EB : nullptr, Vin, Vout, pi, F.nactions, F.rank,
                                             (float)F.gamma, res, err);
     CPMDP_CUDA(cudaGetLastError());
