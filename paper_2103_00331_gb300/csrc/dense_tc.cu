@@ -51,13 +51,6 @@ __device__ __forceinline__ const uint8_t *utile(const uint8_t *U, int c, int d, 
     return U + ((size_t)(c * 4 + d) * 2 + part) * kTileBytes;
 }
 
-__device__ __forceinline__ void copy_tile(uint8_t *dst, const uint8_t *src, int tid) {
-    const uint4 *s = reinterpret_cast<const uint4 *>(src);
-    uint4 *d = reinterpret_cast<uint4 *>(dst);
-#pragma unroll
-    for (int i = 0; i < kTileBytes / 16 / 128; i++) d[tid + 128 * i] = s[tid + 128 * i];
-}
-
 __device__ __forceinline__ void put_bf16(uint8_t *tile, uint32_t row, uint32_t k, uint16_t v) {
     *reinterpret_cast<uint16_t *>(tile + tc::sw128_off(row, k)) = v;
 }
@@ -95,7 +88,12 @@ constexpr int kAOffStage = kAOffU + 2 * 4 * kTileBytes;  // 4 slabs x 4096 x 4 B
 constexpr int kAOffBar = kAOffStage + 4 * kSlab * 4;
 constexpr int kASmem = kAOffBar + 64 + 1024;
 
-__global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__ V, const float *__restrict__ Vbase,
+// Two warpgroups: thread t reads accumulator row t % 128 (its warp's TMEM
+// lane quarter) and columns 32 (t / 128) .. +31, so every CUDA-core phase
+// between the GEMMs is split over 8 warps.
+constexpr int kAThreads = 256;
+
+__global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__restrict__ V, const float *__restrict__ Vbase,
                                                        const uint8_t *__restrict__ U, uint8_t *__restrict__ T,
                                                        int nchains, int *err) {
     extern __shared__ uint8_t smem_raw[];
@@ -107,6 +105,7 @@ __global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kAOffBar + 16);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kAOffBar + 24);
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int row = tid & 127, cbase = 32 * (tid >> 7);   // accumulator row, first column
     if (tid == 0) {
         tc::mbar_init(&full[0], 1);
         tc::mbar_init(&full[1], 1);
@@ -116,7 +115,7 @@ __global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sync_for_async();
     const uint32_t tmem = *tslot;
-    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     uint32_t phase = 0, fph0 = 0, fph1 = 0;
     bool alive = true;
     const uint32_t aX = tc::smem_u32(sX), aA2 = tc::smem_u32(sA2), aU = tc::smem_u32(sm + kAOffU);
@@ -130,7 +129,7 @@ __global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__
     for (int g = blockIdx.x; g < ngroups && alive; g += gridDim.x) {
         const int b0 = 4 * g;
         // stage the 4 slabs as 2 pair tiles: row = (s % 2) * 64 + i3, k = i4
-        for (int e = tid; e < 4 * kSlab; e += 128) {
+        for (int e = tid; e < 4 * kSlab; e += kAThreads) {
             const int s = e >> 12, rem = e & (kSlab - 1);
             const size_t gi = (size_t)(b0 + s) * kSlab + rem;
             const float x = Vbase ? V[gi] - Vbase[gi] : V[gi];
@@ -165,14 +164,15 @@ __global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__
                 }
                 if (!wait_all(mbar, phase, err)) { alive = false; break; }
                 tc::fence_after();
-                float z[64];
-                tc::tmem_ld64(tmem + lane_off, z);   // row tid = (s2, i3), cols i4'
+                float z[32];
+                tc::tmem_ld32(tmem + lane_off + cbase, z);   // row = (s2, i3), cols i4' = cbase ..
                 {
-                    const uint32_t s2 = tid >> 6, i3 = tid & 63;
+                    const uint32_t s2 = row >> 6, i3 = row & 63;
 #pragma unroll
-                    for (int j = 0; j < 64; j++) {
+                    for (int jj = 0; jj < 32; jj++) {
+                        const uint32_t j = cbase + jj;
                         __nv_bfloat16 h, l;
-                        tc::split_bf16(z[j], h, l);
+                        tc::split_bf16(z[jj], h, l);
                         put_bf16(sA2, s2 * 64 + j, i3, __bfloat16_as_ushort(h));
                         put_bf16(sA2 + kPairBytes, s2 * 64 + j, i3, __bfloat16_as_ushort(l));
                     }
@@ -184,12 +184,12 @@ __global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__
                 }
                 if (!wait_all(mbar, phase, err)) { alive = false; break; }
                 tc::fence_after();
-                float y[64];
-                tc::tmem_ld64(tmem + lane_off + 64, y);   // row tid = (s2, i4'), cols i3'
+                float y[32];
+                tc::tmem_ld32(tmem + lane_off + 64 + cbase, y);   // row = (s2, i4'), cols i3' = cbase ..
                 {
-                    const int s = 2 * p + (tid >> 6), i4 = tid & 63;
+                    const int s = 2 * p + (row >> 6), i4 = row & 63;
 #pragma unroll
-                    for (int j = 0; j < 64; j++) stage[s * kSlab + j * 64 + i4] = tc::pack_hilo(y[j]);
+                    for (int jj = 0; jj < 32; jj++) stage[s * kSlab + (cbase + jj) * 64 + i4] = tc::pack_hilo(y[jj]);
                 }
                 tc::fence_before();
                 __syncthreads();
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(128, 1) dense_pass_a(const float *__restrict__
             if (!alive) break;
             // quad (i1, j = i2_0 / 4) of every tile q of chain c
             uint8_t *Tc = T + (size_t)c * kSlab * kQuadTileBytes + (size_t)((b0 >> 6) * 16 + ((b0 & 63) >> 2)) * 16;
-            for (int q = tid; q < kSlab; q += 128) {
+            for (int q = tid; q < kSlab; q += kAThreads) {
                 const uint32_t w0 = stage[q], w1 = stage[kSlab + q], w2 = stage[2 * kSlab + q], w3 = stage[3 * kSlab + q];
                 uint4 v;
                 v.x = (w0 & 0xFFFFu) | (w1 << 16);
@@ -474,7 +474,7 @@ static cpmdp_status tc_sweep(const Factors &F, const float *Vin, float *Vout, ui
     const int C = F.nactions * F.rank;
     int *err = F.d_tc_err;
     const int grid = F.num_sms > 0 ? F.num_sms : 148;
-    dense_pass_a<<<grid, 128, kASmem, st>>>(Vin, use_base ? F.d_Vbase : nullptr, (const uint8_t *)F.d_Ubf,
+    dense_pass_a<<<grid, kAThreads, kASmem, st>>>(Vin, use_base ? F.d_Vbase : nullptr, (const uint8_t *)F.d_Ubf,
                                             (uint8_t *)F.d_T, C, err);
     CPMDP_CUDA(cudaGetLastError());
     // pass B: two CTAs per SM (about 106 KB of shared memory each)
