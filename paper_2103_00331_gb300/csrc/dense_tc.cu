@@ -78,8 +78,30 @@ __device__ __forceinline__ void sync_for_async() {
 // pass B copies a slab pair (32 KB, contiguous) with one bulk copy.
 constexpr int kQuadTileBytes = 16384;
 
+// Quads of one staged item (chain c, slab group starting at b0), those with
+// q in [q_lo, q_hi): written from the stage buffer ([slab][q], 32-bit hi/lo
+// words) as 16-byte units of the intermediate layout.
+__device__ __forceinline__ void write_quads(uint8_t *T, const uint32_t *stage, int c, int b0, int q_lo, int q_hi,
+                                            int tid, int nthreads) {
+    uint8_t *Tc = T + (size_t)c * kSlab * kQuadTileBytes + (size_t)((b0 >> 6) * 16 + ((b0 & 63) >> 2)) * 16;
+    for (int q = q_lo + tid; q < q_hi; q += nthreads) {
+        const uint32_t w0 = stage[q], w1 = stage[kSlab + q], w2 = stage[2 * kSlab + q], w3 = stage[3 * kSlab + q];
+        uint4 v;
+        v.x = (w0 & 0xFFFFu) | (w1 << 16);
+        v.y = (w2 & 0xFFFFu) | (w3 << 16);
+        v.z = (w0 >> 16) | (w1 & 0xFFFF0000u);
+        v.w = (w2 >> 16) | (w3 & 0xFFFF0000u);
+        *reinterpret_cast<uint4 *>(Tc + (size_t)q * kQuadTileBytes) = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // pass A: slabs of V (minus V_base when given) -> T_c for every chain c
+//
+// The scattered 16-byte stores of an item's intermediates are issued during
+// the next item's first two GEMMs (half after each is started), so the
+// tensor core works while the threads store; the stage buffer is only
+// overwritten after both halves.
 
 constexpr int kAOffX = 0;                            // 2 pairs x {hi, lo} x 16 KB
 constexpr int kAOffA2 = 4 * kPairBytes;              // {hi, lo} x 16 KB
@@ -126,6 +148,7 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
         tc::mbar_expect_tx(&full[0], 4 * kTileBytes);
         tc::bulk_g2s(aU, utile(U, 0, 2, 0), 4 * kTileBytes, &full[0]);
     }
+    int pend_c = -1, pend_b0 = 0;   // staged item whose quads are not yet stored
     for (int g = blockIdx.x; g < ngroups && alive; g += gridDim.x) {
         const int b0 = 4 * g;
         // stage the 4 slabs as 2 pair tiles: row = (s % 2) * 64 + i3, k = i4
@@ -162,6 +185,7 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
                     tc::mma_bf16x3(tmem, xa, xa + kPairBytes, u4, u4 + kTileBytes, 0);
                     tc::commit(mbar);
                 }
+                if (p == 0 && pend_c >= 0) write_quads(T, stage, pend_c, pend_b0, 0, kSlab / 2, tid, kAThreads);
                 if (!wait_all(mbar, phase, err)) { alive = false; break; }
                 tc::fence_after();
                 float z[32];
@@ -182,6 +206,12 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
                     tc::mma_bf16x3(tmem + 64, aA2, aA2 + kPairBytes, u3, u3 + kTileBytes, 0);
                     tc::commit(mbar);
                 }
+                if (p == 0 && pend_c >= 0) {
+                    write_quads(T, stage, pend_c, pend_b0, kSlab / 2, kSlab, tid, kAThreads);
+                    pend_c = -1;
+                }
+                // (the wait's barrier also orders every thread's reads of the
+                // stage buffer before it is overwritten below)
                 if (!wait_all(mbar, phase, err)) { alive = false; break; }
                 tc::fence_after();
                 float y[32];
@@ -196,20 +226,13 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
                 tc::fence_after();
             }
             if (!alive) break;
-            // quad (i1, j = i2_0 / 4) of every tile q of chain c
-            uint8_t *Tc = T + (size_t)c * kSlab * kQuadTileBytes + (size_t)((b0 >> 6) * 16 + ((b0 & 63) >> 2)) * 16;
-            for (int q = tid; q < kSlab; q += kAThreads) {
-                const uint32_t w0 = stage[q], w1 = stage[kSlab + q], w2 = stage[2 * kSlab + q], w3 = stage[3 * kSlab + q];
-                uint4 v;
-                v.x = (w0 & 0xFFFFu) | (w1 << 16);
-                v.y = (w2 & 0xFFFFu) | (w3 << 16);
-                v.z = (w0 >> 16) | (w1 & 0xFFFF0000u);
-                v.w = (w2 >> 16) | (w3 & 0xFFFF0000u);
-                *reinterpret_cast<uint4 *>(Tc + (size_t)q * kQuadTileBytes) = v;
-            }
-            __syncthreads();
+            // this item's quads go out during the next item's GEMMs
+            pend_c = c;
+            pend_b0 = b0;
         }
     }
+    // the last staged item
+    if (alive && pend_c >= 0) write_quads(T, stage, pend_c, pend_b0, 0, kSlab, tid, kAThreads);
     // a prefetch may still be in flight when this CTA stopped early: wait for it
     if (!alive && tid == 0) {
         tc::mbar_wait(&full[0], fph0, kWaitCycles);
