@@ -146,7 +146,7 @@ def aggregate(pg, units, ms, device=None):
     return float(t.item()), float(m.item())
 
 
-BANDED_SOURCES = ["banded_common.cuh", "banded.cu", "banded_solve.cu", "internal.h"]
+BANDED_SOURCES = ["banded_common.cuh", "banded.cu", "banded_solve.cu", "flow_solve.cu", "flow.h", "internal.h"]
 
 
 def banded_sources_hash():
@@ -302,6 +302,32 @@ def run_ours(args, rank, world, local, pg):
     fused_vi_ms = statistics.median(vi_ms)
     plain_vi_ms = statistics.median(plain_ms) if plain_ms else None
 
+    # the same step on the grid-barrier solver (one grid barrier per sweep),
+    # for comparison with the barrier-free solver timed above
+    gb_opts_vi = cp.default_opts(tol=TOL, max_iter=5000, fused=2)
+    gb_opts_pi = cp.default_opts(tol=TOL, max_iter=5000, fused=2)
+    gb_vi, gb_pi = [], []
+    for i in range(max(3, min(args.steps, 10)) + 1):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        V.zero_()
+        ev[0].record(stream)
+        gv = cp.value_iteration(f, cp.F32, V, pi, opts=gb_opts_vi, stream=stream)
+        ev[1].record(stream)
+        V.zero_()
+        ev[2].record(stream)
+        gp = cp.policy_iteration(f, cp.F32, V, pi, opts=gb_opts_pi, stream=stream)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            gb_vi.append(ev[0].elapsed_time(ev[1]))
+            gb_pi.append(ev[2].elapsed_time(ev[3]))
+    grid_barrier = {"kernels": "solve_vi_kernel<float,3,4> / solve_pi_kernel<float,3,4> (fused=2)",
+                    "vi_ms": statistics.median(gb_vi), "pi_ms": statistics.median(gb_pi),
+                    "vi_sweeps": gv["iterations"], "pi_sweeps": gp["iterations"],
+                    "same_sweeps": gv["iterations"] == rv["iterations"] and gp["iterations"] == rp["iterations"]}
+
     # roofline of the dominant kernel (the persistent policy-iteration kernel,
     # one launch per step): algorithmic bytes of its launches over their
     # event-timed durations; the value-iteration kernel beside it
@@ -311,13 +337,14 @@ def run_ours(args, rank, world, local, pg):
     ach_pi = (pi_bytes / len(pi_ms)) / (statistics.mean(pi_ms) / 1e3) / 1e9
     ach_vi = (vi_bytes / len(vi_ms)) / (statistics.mean(vi_ms) / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": ach_pi, "peak": peak, "unit": "GB/s", "frac": ach_pi / peak,
-            "traffic": traffic_from_profile("solve_pi_kernel_gridworld64.txt"),
-            "peak_source": src, "kernel": "solve_pi_kernel<float,3,4> (persistent PI, FP32)",
+            "traffic": traffic_from_profile("flow_pi_kernel_gridworld64.txt"),
+            "peak_source": src, "kernel": "flow_pi_kernel<3> (barrier-free persistent PI, FP32)",
             "algorithmic_bytes_per_launch": pi_bytes / len(pi_ms),
-            "note": "64^3 working set (3.4 MB) stays in L2 across sweeps; per-sweep grid-barrier latency bound"}
+            "note": "64^3 working set (3.4 MB) stays in L2 across sweeps; per-sweep latency bound "
+                    "(neighbour values through L2, no grid barrier)"}
     roof_vi = {"bound": "hbm", "achieved": ach_vi, "peak": peak, "unit": "GB/s", "frac": ach_vi / peak,
-               "traffic": traffic_from_profile("solve_vi_kernel_gridworld64.txt"),
-               "kernel": "solve_vi_kernel<float,3,4> (persistent VI, FP32)",
+               "traffic": traffic_from_profile("flow_vi_kernel_gridworld64.txt"),
+               "kernel": "flow_vi_kernel<3> (barrier-free persistent VI, FP32)",
                "algorithmic_bytes_per_launch": vi_bytes / len(vi_ms)}
 
     # HBM-bound sweep: one fused backup of a 512^3 instance, event-timed
@@ -373,6 +400,7 @@ def run_ours(args, rank, world, local, pg):
                 "vi_sweeps": statistics.median(vi_iters), "plain_vi_sweeps": rpl["iterations"],
                 "pi_sweeps": statistics.median(pi_iters), "pi_ms": statistics.median(pi_ms),
                 "certified_residual": rv["certified_residual"], "error_bound": rv["error_bound"],
+                "grid_barrier_solver": grid_barrier,
                 "hbm_sweep_512": large, "roofline_vi": roof_vi, "batch_4096": batch,
                 "warmstart_512x64": warm}
         print(json.dumps(line), flush=True)
@@ -514,7 +542,8 @@ def hbm_sweep(cp, dev, stream, peak):
 def kernel_case(name, reps=3):
     """Run one kernel workload a few times and exit (for ncu captures):
     sweep512 = fused FP32 backup of a 512^3 GridWorld; solve64 / pi64 = fused
-    FP32 value / policy iteration of the 64^3 instance."""
+    FP32 value / policy iteration of the 64^3 instance (barrier-free solver);
+    solve64b / pi64b = the same on the grid-barrier solver."""
     import torch
     import paper_2103_00331_gb300 as cp
     import cpmdp_inputs as ci
@@ -561,17 +590,18 @@ def kernel_case(name, reps=3):
             torch.cuda.synchronize()
             print(f"dense 64^4 FP32 SIMT sweep: {e0.elapsed_time(e1):.3f} ms")
             Va, Vb = Vb, Va
-    elif name in ("solve64", "pi64"):
+    elif name in ("solve64", "pi64", "solve64b", "pi64b"):
         gw = workload(0)
+        fused = 2 if name.endswith("b") else 1
         f = cp.build_factors(gw, device=0)
         V = torch.zeros(gw.nstates, dtype=torch.float32, device=dev)
         pi = torch.zeros(gw.nstates, dtype=torch.uint8, device=dev)
         for _ in range(reps):
             V.zero_()
-            if name == "solve64":
-                cp.value_iteration(f, cp.F32, V, None, opts=cp.default_opts(max_iter=5000, certify=0))
+            if name.startswith("solve64"):
+                cp.value_iteration(f, cp.F32, V, None, opts=cp.default_opts(max_iter=5000, certify=0, fused=fused))
             else:
-                cp.policy_iteration(f, cp.F32, V, pi, opts=cp.default_opts(max_iter=5000, certify=0))
+                cp.policy_iteration(f, cp.F32, V, pi, opts=cp.default_opts(max_iter=5000, certify=0, fused=fused))
     else:
         raise SystemExit(f"unknown kernel case {name}")
     torch.cuda.synchronize()
@@ -591,7 +621,8 @@ def main():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-warmstart", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--kernel-case", choices=["sweep512", "solve64", "pi64", "dense64", "dense64tc"], default=None,
+    ap.add_argument("--kernel-case", choices=["sweep512", "solve64", "pi64", "solve64b", "pi64b", "dense64", "dense64tc"],
+                    default=None,
                     help="run one kernel workload a few times (profiling) and exit")
     args = ap.parse_args()
     if args.kernel_case:

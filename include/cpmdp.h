@@ -118,19 +118,26 @@ typedef struct {
     int32_t max_iter;        /* sweep limit (default 1000, the paper's maxIter) */
     int32_t certify;         /* 1 (default): after F32 solves, one FP64 sweep of the result gives the
                                 certified residual and the policy (FP64 argmax) */
-    int32_t fused;           /* 1 (default): fused device-resident solver; 0: the plain
-                                unfused FP32/FP64 baseline (one kernel per action, separate max and
-                                residual kernels, residual checked on the host every sweep) */
+    int32_t fused;           /* 1 (default): fused device-resident solver; FP32 GridWorld solves of
+                                1 to 3 dimensions whose rows are a multiple of 4 states and that fit
+                                one co-resident grid at one thread per 4 states run barrier-free
+                                (sweeps synchronised through sweep-tagged values, the stopping rule
+                                checked two sweeps late; same values and sweep counts), the rest with
+                                a grid barrier per sweep; 2: always the grid-barrier solver; 0: the
+                                plain unfused FP32/FP64 baseline (one kernel per action, separate max
+                                and residual kernels, residual checked on the host every sweep) */
     double eval_tol;         /* policy iteration: evaluation stops below this residual
                                 (default: tol for F32, 1e-10 for F64) */
     int32_t max_eval_iter;   /* policy iteration: evaluation sweep limit per round (default 100000) */
     int32_t max_rounds;      /* policy iteration: improvement round limit (default 1000) */
     double timeout_s;        /* limit of every device-side wait (default 2 s) */
     double *trace;           /* optional device buffer of max_iter doubles: residual of each sweep
-                                (value iteration, fused path only) */
+                                (value iteration, fused path only; the barrier-free solver zeroes it
+                                first and also fills the entries of its two dropped sweeps) */
     int32_t inject_stall;    /* testing aid (default 0): 1 makes one block of the fused GridWorld
-                                solver leave without arriving at its first grid barrier, so the other
-                                blocks' bounded waits run out after timeout_s and the call returns
+                                solver leave at once (without arriving at its first grid barrier, or,
+                                barrier-free, without publishing its values), so the other blocks'
+                                bounded waits run out after timeout_s and the call returns
                                 CPMDP_ETIMEOUT; the device stays usable */
 } cpmdp_solve_opts;
 

@@ -63,7 +63,7 @@ SolveOpts resolve_opts(const cpmdp_solve_opts *o, cpmdp_precision prec) {
 static void free_device(Factors &F) {
     void *ptrs[] = {F.d_code, F.d_R32, F.d_R64, F.d_cell, F.d_scratch, F.d_q, F.d_ctrl,
                     F.d_U32, F.d_U64, F.d_Ubf, F.d_lam32, F.d_lam64, F.d_dense_work, F.d_Vd,
-                    F.d_RB, F.d_T, F.d_EB, F.d_Vbase, F.d_tc_err};
+                    F.d_RB, F.d_T, F.d_EB, F.d_Vbase, F.d_tc_err, F.d_flow};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     F.d_code = nullptr; F.d_R32 = nullptr; F.d_R64 = nullptr; F.d_cell = nullptr;
@@ -367,6 +367,7 @@ static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, boo
         set_error("invalid solve options (tol > 0, max_iter >= 1, timeout_s > 0 required)");
         return CPMDP_EINVAL;
     }
+    if (o.fused < 0 || o.fused > 2) { set_error("fused must be 0, 1 or 2"); return CPMDP_EINVAL; }
     if (pi_mode && !o.fused) { set_error("the plain baseline implements value iteration only"); return CPMDP_EINVAL; }
     DeviceGuard g(F.device);
     if (!g.ok) { set_error("cannot select CUDA device %d", F.device); return CPMDP_ECUDA; }
@@ -421,6 +422,10 @@ static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, boo
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (F.kind == CPMDP_GRIDWORLD && o.fused) {
+        st = banded_solve_finished(F, dc, s);
+        if (st != CPMDP_OK) return st;
+    }
     if (!have_ctrl) {
         hc = dc;
     } else {

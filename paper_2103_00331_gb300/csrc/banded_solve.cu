@@ -16,6 +16,7 @@
 #include <math.h>
 
 #include "banded_common.cuh"
+#include "flow.h"
 
 namespace cpmdp {
 
@@ -207,10 +208,42 @@ cpmdp_status banded_solve(const Factors &F, cpmdp_precision prec, bool policy_it
     sp.nactions = F.nactions;
     sp.inject_stall = o.inject_stall;
     CPMDP_CUDA(cudaMemsetAsync(F.d_ctrl, 0, sizeof(Ctrl), st));
+    // FP32 solves that fit one co-resident grid at one thread per 4 states
+    // run on the barrier-free solver (fused = 2 asks for this file's
+    // grid-barrier kernels instead).
+    if (prec == CPMDP_F32 && o.fused == 1 && flow_eligible(F, policy_iteration, V, pi, o)) {
+        Factors &M = const_cast<Factors &>(F);
+        if (!M.d_flow) {
+            CPMDP_CUDA(cudaMalloc(&M.d_flow, flow_bytes(F)));
+            CPMDP_CUDA(cudaMemsetAsync(static_cast<char *>(M.d_flow) + flow_counter_bytes(), 0xFF,
+                                       flow_bytes(F) - flow_counter_bytes(), st));
+            M.flow_base = 0;
+        }
+        M.flow_pending = true;
+        return flow_solve(F, policy_iteration, (float *)V, pi, sp, o.trace, st);
+    }
     cudaError_t e;
     if (prec == CPMDP_F64) e = solve_t<double>(F, policy_iteration, (double *)V, pi, sp, o.trace, st);
     else e = solve_t<float>(F, policy_iteration, (float *)V, pi, sp, o.trace, st);
     CPMDP_CUDA(e);
+    return CPMDP_OK;
+}
+
+cpmdp_status banded_solve_finished(const Factors &F, const Ctrl &dc, cudaStream_t st) {
+    Factors &M = const_cast<Factors &>(F);
+    if (!M.flow_pending) return CPMDP_OK;
+    M.flow_pending = false;
+    // Tags only grow, so a ring word can never look like one of a later
+    // sweep. After a failed launch (which may have left words with any tag
+    // above the base) and long before the tags wrap, the rings are cleared
+    // to the tag 0xFFFFFFFF, which is never used.
+    M.flow_base += dc.flow_tags + 2u;
+    if (dc.status != 0 || dc.flow_tags == 0 || M.flow_base > 0x40000000u) {
+        CPMDP_CUDA(cudaMemsetAsync(static_cast<char *>(M.d_flow) + flow_counter_bytes(), 0xFF,
+                                   flow_bytes(F) - flow_counter_bytes(), st));
+        CPMDP_CUDA(cudaStreamSynchronize(st));
+        M.flow_base = 0;
+    }
     return CPMDP_OK;
 }
 

@@ -34,6 +34,7 @@ struct Ctrl {
     double last_residual;          // residual of the last sweep
     double certify_residual;       // FP64 certifying sweep
     long long backups;             // state-action backups done
+    unsigned int flow_tags;        // barrier-free solver: tag sequences used by the launch
 };
 
 struct Factors {
@@ -86,6 +87,10 @@ struct Factors {
     float *d_EB = nullptr;             // base expectation per action, pass-B layout
     float *d_Vbase = nullptr;          // base value tensor of the defect correction
     int *d_tc_err = nullptr;           // error word of the tensor-core kernels
+    // barrier-free FP32 solver (flow_solve.cu), allocated on first use
+    void *d_flow = nullptr;            // arrival counters + three rings of |S| tagged words
+    unsigned flow_base = 0;            // first tag not written to the rings yet
+    bool flow_pending = false;         // a launch whose tags are not accounted for yet
 };
 
 // Thread-local error message.
@@ -119,6 +124,9 @@ cpmdp_status banded_certify(const Factors &F, const float *V, uint8_t *pi, doubl
                             cudaStream_t st);
 cpmdp_status banded_solve(const Factors &F, cpmdp_precision prec, bool policy_iteration, void *V,
                           uint8_t *pi, const SolveOpts &o, cudaStream_t st);
+// After the control block of a fused GridWorld solve was read back: account
+// for the barrier-free solver's tags (or clear its rings after a failure).
+cpmdp_status banded_solve_finished(const Factors &F, const Ctrl &dc, cudaStream_t st);
 cpmdp_status banded_plain_vi(const Factors &F, cpmdp_precision prec, void *V, uint8_t *pi,
                              const SolveOpts &o, Ctrl *host_ctrl, cudaStream_t st);
 

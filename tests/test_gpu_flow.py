@@ -1,0 +1,193 @@
+"""The barrier-free FP32 GridWorld solver (sweep-tagged values, stopping
+rule checked two sweeps late) against the grid-barrier solver and the
+oracle.
+
+Both solvers run the same Jacobi iterates with the same per-state
+arithmetic and stop at the same sweep, so their results must be equal bit
+for bit: values, policies, sweep counts, rounds, residuals and the
+per-sweep residual trace. fused=1 picks the barrier-free solver where it is
+eligible (1 to 3 dimensions, rows a multiple of 4 states, one thread per 4
+states in one co-resident grid); fused=2 always takes the grid-barrier
+solver. The oracle checks the k-sweep iterates directly.
+"""
+import numpy as np
+import pytest
+
+import cpmdp_inputs as ci
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def cp():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2103_00331_gb300 as cp
+    return cp
+
+
+@pytest.fixture(scope="module")
+def oc():
+    from oracle import cpfactor
+    cpfactor.build()
+    return cpfactor
+
+
+# shapes: 1-D chain; 2-D with rows of 3, 16 and 40 segments (row neighbours
+# inside and outside a warp); 3-D with a ragged last warp; the 64^3 bench size
+SHAPES = [(400,), (12, 20), (37, 64), (24, 160), (5, 9, 12), (20, 36, 8), (64, 64, 64)]
+
+
+def _world(shape, seed):
+    if len(shape) == 1:
+        return ci.gridworld(shape, p=0.8, gamma=0.95, step_reward=-0.04, goal_rewards=[1.0, -1.0],
+                            obstacle_rate=0.05, seed=seed)
+    if len(shape) == 2:
+        return ci.gridworld(shape, p=0.8, gamma=0.97, step_reward=-0.04, goal_rewards=[1.0, -1.0],
+                            obstacle_rate=0.05, seed=seed)
+    return ci.gridworld(shape, p=0.8, gamma=0.99, step_reward=-0.01,
+                        goal_rewards=list(ci.uniform(seed, 99, 8, 0.5, 1.0)), obstacle_rate=0.05, seed=seed)
+
+
+def _vi(cp, f, gw, fused, **kw):
+    import torch
+    V = torch.zeros(gw.nstates, dtype=torch.float32, device="cuda")
+    pi = torch.zeros(gw.nstates, dtype=torch.uint8, device="cuda")
+    mi = kw.pop("max_iter", 5000)
+    trace = torch.full((mi,), -1.0, dtype=torch.float64, device="cuda")
+    r = cp.value_iteration(f, cp.F32, V, pi, opts=cp.default_opts(fused=fused, max_iter=mi,
+                                                                     trace=trace.data_ptr(), **kw),
+                           raise_on_noconv=False)
+    return V.cpu().numpy(), pi.cpu().numpy(), trace.cpu().numpy(), r
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_vi_equals_grid_barrier_solver(cp, shape):
+    gw = _world(shape, seed=len(shape) * 7 + shape[-1])
+    f = cp.build_factors(gw, device=0)
+    Va, pa, ta, ra = _vi(cp, f, gw, 1)
+    Vb, pb, tb, rb = _vi(cp, f, gw, 2)
+    assert ra["status"] == cp.OK and rb["status"] == cp.OK
+    assert ra["iterations"] == rb["iterations"]
+    assert ra["residual"] == rb["residual"]
+    assert ra["backups"] == rb["backups"]
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+    assert np.array_equal(pa, pb)
+    k = ra["iterations"]
+    assert np.array_equal(ta[:k], tb[:k])
+    assert ra["certified_residual"] == rb["certified_residual"]
+    f.close()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 7, 30])
+def test_k_sweeps_match_oracle(cp, oc, k):
+    """max_iter = k with an unreachable tol: exactly k Jacobi sweeps from
+    zero, equal to the grid-barrier solver bit for bit and to k oracle
+    sweeps within the FP32 k-sweep bound."""
+    gw = _world((20, 36, 8), seed=3)
+    f = cp.build_factors(gw, device=0)
+    Va, _, ta, ra = _vi(cp, f, gw, 1, max_iter=k, tol=1e-30, certify=0)
+    Vb, _, tb, rb = _vi(cp, f, gw, 2, max_iter=k, tol=1e-30, certify=0)
+    assert ra["status"] == cp.ENOCONV and ra["iterations"] == k
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+    assert np.array_equal(ta, tb)
+    Vo = np.zeros(gw.nstates)
+    for _ in range(k):
+        Vo, _, _, _ = oc.backup(gw, Vo)
+    eps = 14 * U32 * (np.abs(gw.reward).max() + np.abs(Vo).max() + 1.0)
+    bound = eps * (1 - gw.gamma ** k) / (1 - gw.gamma)
+    assert np.abs(Va.astype(np.float64) - Vo).max() <= bound
+    f.close()
+
+
+@pytest.mark.parametrize("shape", [(12, 20), (37, 64), (5, 9, 12), (64, 64, 64)])
+def test_pi_equals_grid_barrier_solver(cp, shape):
+    import torch
+    gw = _world(shape, seed=11 + shape[0])
+    f = cp.build_factors(gw, device=0)
+    out = {}
+    for fused in (1, 2):
+        V = torch.zeros(gw.nstates, dtype=torch.float32, device="cuda")
+        pi = torch.zeros(gw.nstates, dtype=torch.uint8, device="cuda")
+        r = cp.policy_iteration(f, cp.F32, V, pi, opts=cp.default_opts(fused=fused))
+        out[fused] = (V.cpu().numpy(), pi.cpu().numpy(), r)
+    (Va, pa, ra), (Vb, pb, rb) = out[1], out[2]
+    for key in ("status", "iterations", "rounds", "eval_sweeps", "residual", "backups", "certified_residual"):
+        assert ra[key] == rb[key], (key, ra[key], rb[key])
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+    assert np.array_equal(pa, pb)
+    f.close()
+
+
+def test_pi_round_and_eval_limits(cp):
+    """Evaluation and round limits end the solve the same way in both
+    solvers (ENOCONV, same partial results)."""
+    import torch
+    gw = _world((20, 36, 8), seed=5)
+    f = cp.build_factors(gw, device=0)
+    for kw in (dict(max_eval_iter=1), dict(max_eval_iter=2), dict(max_eval_iter=3),
+               dict(max_rounds=1), dict(max_rounds=2, max_eval_iter=5)):
+        out = {}
+        for fused in (1, 2):
+            V = torch.zeros(gw.nstates, dtype=torch.float32, device="cuda")
+            pi = torch.zeros(gw.nstates, dtype=torch.uint8, device="cuda")
+            r = cp.policy_iteration(f, cp.F32, V, pi, opts=cp.default_opts(fused=fused, **kw),
+                                    raise_on_noconv=False)
+            out[fused] = (V.cpu().numpy(), pi.cpu().numpy(), r)
+        (Va, pa, ra), (Vb, pb, rb) = out[1], out[2]
+        for key in ("status", "iterations", "rounds", "eval_sweeps", "residual", "backups"):
+            assert ra[key] == rb[key], (kw, key, ra[key], rb[key])
+        assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32)), kw
+        assert np.array_equal(pa, pb), kw
+    f.close()
+
+
+def test_warm_start_and_repeated_calls(cp):
+    """Many solves on one factors object (the tag base moves on each time)
+    and warm starts give the same results as the grid-barrier solver."""
+    import torch
+    gw = _world((37, 64), seed=8)
+    f = cp.build_factors(gw, device=0)
+    V0 = torch.as_tensor(ci.random_values(gw.shape, seed=4, lo=-1, hi=1).reshape(-1)).float().cuda()
+    ref = None
+    for rep in range(6):
+        outs = []
+        for fused in (1, 2):
+            V = V0.clone()
+            pi = torch.zeros(gw.nstates, dtype=torch.uint8, device="cuda")
+            if rep % 2:
+                r = cp.policy_iteration(f, cp.F32, V, pi, opts=cp.default_opts(fused=fused))
+            else:
+                r = cp.value_iteration(f, cp.F32, V, pi, opts=cp.default_opts(fused=fused))
+            outs.append((V.cpu().numpy().view(np.uint32), pi.cpu().numpy(), r["iterations"]))
+        assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+        assert outs[0][2] == outs[1][2]
+    f.close()
+
+
+def test_timeout_then_recovery(cp):
+    """A stalled block makes the barrier-free solver's bounded waits run out
+    (CPMDP_ETIMEOUT, no hang); the rings are cleared and the next solve on
+    the same factors object is exact again."""
+    import torch
+    gw = _world((20, 36, 8), seed=9)
+    f = cp.build_factors(gw, device=0)
+    for pim in (False, True):
+        V = torch.zeros(gw.nstates, dtype=torch.float32, device="cuda")
+        pi = torch.zeros(gw.nstates, dtype=torch.uint8, device="cuda")
+        with pytest.raises(cp.CpmdpError) as ei:
+            if pim:
+                cp.policy_iteration(f, cp.F32, V, pi, opts=cp.default_opts(timeout_s=0.2, inject_stall=1))
+            else:
+                cp.value_iteration(f, cp.F32, V, pi, opts=cp.default_opts(timeout_s=0.2, inject_stall=1))
+        assert ei.value.status == cp.ETIMEOUT
+    Va, pa, _, ra = _vi(cp, f, gw, 1)
+    Vb, pb, _, rb = _vi(cp, f, gw, 2)
+    assert ra["iterations"] == rb["iterations"]
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+    f.close()
