@@ -75,6 +75,15 @@ typedef enum {
 
 enum { CPMDP_CELL_FREE = 0, CPMDP_CELL_OBSTACLE = 1, CPMDP_CELL_TERMINAL = 2 };
 
+/* Which solver ran (cpmdp_result.solver). */
+typedef enum {
+    CPMDP_SOLVER_PLAIN = 0,         /* plain unfused baseline (fused = 0) */
+    CPMDP_SOLVER_GRID_BARRIER = 1,  /* fused GridWorld solver, one grid barrier per sweep */
+    CPMDP_SOLVER_BARRIER_FREE = 2,  /* fused FP32 GridWorld solver without a barrier in its sweep loop */
+    CPMDP_SOLVER_DENSE = 3,         /* dense CP solver */
+    CPMDP_SOLVER_BATCH = 4          /* batched value iteration */
+} cpmdp_solver;
+
 /*
  * The MDP tuple <S, A, P, R, gamma> (background section).
  *   ndim, shape[0..ndim-1]  S = N_1 x ... x N_D (Definitions 1-2), each N_d >= 1,
@@ -151,6 +160,7 @@ typedef struct {
     double error_bound;          /* certified_residual / (1 - gamma): bound on max |V - V*| (-1 if n/a) */
     int64_t backups;             /* state-action backups done: |S|*|A| per VI sweep, |S| per evaluation sweep */
     double elapsed_ms;           /* device time of the solve, CUDA events on the stream */
+    int32_t solver;              /* cpmdp_solver: which solver ran */
 } cpmdp_result;
 
 /* Fill *opts with the defaults listed above. */

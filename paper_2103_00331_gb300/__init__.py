@@ -23,6 +23,7 @@ MAX_DIM = 9
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT = 0, 1, 2, 3, 4, 5
 F32, F64, BF16X3 = 0, 1, 2
 GRIDWORLD, DENSE_CP = 0, 1
+SOLVER_PLAIN, SOLVER_GRID_BARRIER, SOLVER_BARRIER_FREE, SOLVER_DENSE, SOLVER_BATCH = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT"}
 
 
@@ -54,7 +55,7 @@ class Result(ctypes.Structure):
                 ("rounds", ctypes.c_int32), ("eval_sweeps", ctypes.c_int32),
                 ("residual", ctypes.c_double), ("certified_residual", ctypes.c_double),
                 ("error_bound", ctypes.c_double), ("backups", ctypes.c_int64),
-                ("elapsed_ms", ctypes.c_double)]
+                ("elapsed_ms", ctypes.c_double), ("solver", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("_")}

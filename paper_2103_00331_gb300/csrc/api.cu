@@ -422,6 +422,9 @@ static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, boo
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    const int solver = F.kind != CPMDP_GRIDWORLD ? CPMDP_SOLVER_DENSE
+                       : !o.fused ? CPMDP_SOLVER_PLAIN
+                       : F.flow_pending ? CPMDP_SOLVER_BARRIER_FREE : CPMDP_SOLVER_GRID_BARRIER;
     if (F.kind == CPMDP_GRIDWORLD && o.fused) {
         st = banded_solve_finished(F, dc, s);
         if (st != CPMDP_OK) return st;
@@ -434,7 +437,7 @@ static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, boo
     if (dense_cert) hc.certify_residual = dc.certify_residual;
     if (dc.status != 0 && !have_ctrl) {
         set_error("a device-side wait exceeded %.3g s; results are undefined", o.timeout_s);
-        if (info) { memset(info, 0, sizeof(*info)); info->status = dc.status; }
+        if (info) { memset(info, 0, sizeof(*info)); info->status = dc.status; info->solver = solver; }
         return (cpmdp_status)dc.status;
     }
     cpmdp_result r;
@@ -448,6 +451,7 @@ static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, boo
     r.error_bound = (have_cert && F.gamma < 1.0) ? hc.certify_residual / (1.0 - F.gamma) : -1.0;
     r.backups = hc.backups;
     r.elapsed_ms = ms;
+    r.solver = solver;
     r.status = hc.converged ? CPMDP_OK : CPMDP_ENOCONV;
     if (info) *info = r;
     if (!hc.converged) {

@@ -665,6 +665,7 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
         info->error_bound = -1.0;
         info->backups = backups;
         info->elapsed_ms = ms;
+        info->solver = CPMDP_SOLVER_BATCH;
     }
     if (not_conv) {
         set_error("%d instance(s) reached max_iter before tol", not_conv);

@@ -53,7 +53,8 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int kSlots = 8;            // arrival slots (arrival i uses slot i % kSlots)
 constexpr int kNC = 8;               // counters per slot (warp w adds to counter w % kNC)
 constexpr int kLineWords = 16;       // 64-bit words per 128-byte line
-constexpr int kWarps = 8;            // warps per block (256 threads)
+constexpr int kMaxWarps = 14;        // warps per block at most (one block per SM, 448 threads)
+constexpr int kMaxThreads = 32 * kMaxWarps;
 
 __device__ __forceinline__ u64 ld_rlx(const u64 *p) {
     u64 v;
@@ -127,17 +128,21 @@ struct Arrivals {
         return lane < kNC ? ld_rlx(ctr + ((i % kSlots) * kNC + lane) * kLineWords) : 0ull;
     }
     // Warps that raised their flag at arrival i, or -1 if some warp has not
-    // reported it yet (then nothing is recorded).
+    // reported it yet (then nothing is recorded). After A arrivals with F
+    // raised flags a counter holds A + F * 2^32 as a 64-bit integer, carries
+    // from the low half included, so with A known from i the check needs
+    // only the low halves and F = (v - A) >> 32.
     __device__ __forceinline__ int settle(u64 v, unsigned i) {
         const int lane = threadIdx.x & 31;
-        const bool ok = lane >= kNC || (unsigned)v == (i / kSlots + 1u) * nw_lane;
+        const u64 A = ((u64)(i / kSlots) + 1ull) * nw_lane;
+        const bool ok = lane >= kNC || (unsigned)v == (unsigned)A;
         if (!__all_sync(FULL, ok)) return -1;
         unsigned d = 0;
         if (lane < kNC) {
             unsigned *ph = prevhi + (i % kSlots) * kNC + lane;
-            const unsigned hi = (unsigned)(v >> 32);
-            d = hi - *ph;
-            *ph = hi;
+            const unsigned F = (unsigned)((v - A) >> 32);
+            d = F - *ph;
+            *ph = F;
         }
         return (int)__reduce_add_sync(FULL, d);
     }
@@ -170,10 +175,9 @@ struct FlowSeg {
     int s0;
     bool valid;
     unsigned code;        // the 4 codes, state k in byte k
-    unsigned need;        // words to read from memory: bit 2j + h (row j, half h), HM, HP
-    int off[NR];          // state offset of row direction j
-    int src[NR];          // shuffle source lane of row direction j
-    bool shrow[NR];       // warp-uniform: direction j is less than 32 segments away
+    unsigned inw;         // served by a shuffle in this warp: bits 2j, 2j+1 (row j), HM, HP
+    unsigned need;        // needed from memory: bit 2j + h (row j, half h), HM, HP
+    int own;              // first ring word of this segment (a lane without one: the last segment's)
     float R[4], cur[4], prev[4];
     unsigned act;         // policy iteration: 4 actions, state k in byte k
 
@@ -183,24 +187,26 @@ struct FlowSeg {
         s0 = seg * 4;
         code = 0;
         act = 0;
-        unsigned inw = 0;
+        inw = 0;
+        int off[NR];
 #pragma unroll
         for (int j = 0; j < NR; j++) {
-            off[j] = 0; src[j] = lane; shrow[j] = false;
+            off[j] = 0;
             if (j < NRR) {
                 const int st = a.stride[j / 2];
                 const int so = st / 4;
                 const bool up = (j & 1) != 0;
                 off[j] = up ? st : -st;
-                shrow[j] = so < 32;
-                src[j] = up ? lane + so : lane - so;
-                if (shrow[j] && (up ? lane + so < 32 : lane >= so)) inw |= 3u << (2 * j);
+                if (so < 32 && (up ? lane + so < 32 : lane >= so)) inw |= 3u << (2 * j);
             }
         }
         if (lane >= 1) inw |= 1u << HM;
         if (lane <= 30) inw |= 1u << HP;
 #pragma unroll
         for (int k = 0; k < 4; k++) { R[k] = 0.f; cur[k] = 0.f; prev[k] = 0.f; }
+        // A lane without a segment reads the last segment's words, which
+        // its owner (the last valid lane of this warp) writes every sweep.
+        own = valid ? s0 : a.nstates - 4;
         need = 0;
         if (!valid) return;
         code = *reinterpret_cast<const unsigned *>(static_cast<const uint8_t *>(a.code) + s0);
@@ -222,6 +228,15 @@ struct FlowSeg {
         need = nd & ~inw;
     }
 
+    // Ring word read for row j, half h: the neighbours' pair when it is
+    // needed from memory, else this segment's own pair (already written).
+    __device__ __forceinline__ int wo(const BandArgs &a, int j, int h) const {
+        const int st = a.stride[j / 2];
+        return own + 2 * h + (((need >> (2 * j + h)) & 1u) ? ((j & 1) ? st : -st) : 0);
+    }
+    __device__ __forceinline__ int wol() const { return own - (int)((need >> HM) & 1u); }
+    __device__ __forceinline__ int wor() const { return own + (int)(((need >> HP) & 1u) << 2); }
+
     __device__ __forceinline__ void publish(const FlowArgs &f, unsigned q, unsigned base, const float (&v)[4]) const {
         if (!valid) return;
         u64 *out = ring(f, q);
@@ -233,65 +248,87 @@ struct FlowSeg {
     // Neighbour values of sweep q (tag base + q, buffer q mod 3) for the
     // values `self` (this segment's values of sweep q): rows[j][k] is the
     // value one move in direction j from state k, hl / hr the states just
-    // left of state 0 and right of state 3. Only what the codes mark as
-    // reachable is read from memory; entries for blocked moves are left as
-    // they are. Returns false when the warp must stop (status recorded).
+    // left of state 0 and right of state 3 (for blocked moves: anything).
+    // Every lane reads all its ring words at once (words it does not need
+    // are its own, already written), checks all tags with one OR and
+    // re-reads only on a mismatch. Returns false when the warp must stop
+    // (status recorded).
     __device__ __forceinline__ bool gather(const FlowArgs &f, unsigned q, unsigned base, const float (&self)[4],
                                            float (&rows)[NR][4], float &hl, float &hr, Ctrl *ctrl,
                                            u64 timeout_ns) const {
         const unsigned tg = base + q;
         const u64 *in = ring(f, q);
-#pragma unroll
-        for (int j = 0; j < NR; j++) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) rows[j][k] = 0.f;
-            if (j < NRR && shrow[j]) {
-#pragma unroll
-                for (int k = 0; k < 4; k++) rows[j][k] = __shfl_sync(FULL, self[k], src[j] & 31);
-            }
-        }
-        hl = __shfl_up_sync(FULL, self[3], 1);
-        hr = __shfl_down_sync(FULL, self[0], 1);
-        unsigned pend = valid ? need : 0u;
         u64 w[NR][2][2];
-        u64 wl = 0, wr = 0;
+        u64 wl, wr;
+        // The neighbours' words of sweep q are usually stored just as this
+        // warp finishes sweep q - 1; a read that reaches L2 before them costs
+        // a second round trip. A short pause first lowers that share
+        // (measured at 64^3 and 32^3: about 2 % and 4 % faster sweeps).
+        __nanosleep(100);
 #pragma unroll
-        for (int j = 0; j < NR; j++) { w[j][0][0] = w[j][0][1] = w[j][1][0] = w[j][1][1] = 0; }
-        u64 t0 = 0;
-        unsigned spins = 0;
-        for (;;) {
+        for (int j = 0; j < NRR; j++)
 #pragma unroll
-            for (int j = 0; j < NRR; j++)
+            for (int h = 0; h < 2; h++) ld_rlx2(in + wo(f.a, j, h), w[j][h][0], w[j][h][1]);
+        wl = ld_rlx(in + wol());
+        wr = ld_rlx(in + wor());
+        // rows less than 32 segments away: the lanes holding them (the
+        // stride is the same for every thread, so this branch is uniform)
+        const int lane = threadIdx.x & 31;
+        float sh[NR][4];
 #pragma unroll
-                for (int h = 0; h < 2; h++)
-                    if ((pend >> (2 * j + h)) & 1u) ld_rlx2(in + s0 + off[j] + 2 * h, w[j][h][0], w[j][h][1]);
-            if ((pend >> HM) & 1u) wl = ld_rlx(in + s0 - 1);
-            if ((pend >> HP) & 1u) wr = ld_rlx(in + s0 + 4);
-            unsigned still = 0;
+        for (int j = 0; j < NRR; j++) {
+            const int so = f.a.stride[j / 2] >> 2;
+            if (so < 32) {
+                const int src = ((j & 1) ? lane + so : lane - so) & 31;
 #pragma unroll
-            for (int j = 0; j < NRR; j++)
-#pragma unroll
-                for (int h = 0; h < 2; h++)
-                    if ((pend >> (2 * j + h)) & 1u) {
-                        if (has(w[j][h][0], tg) && has(w[j][h][1], tg)) {
-                            rows[j][2 * h] = val(w[j][h][0]);
-                            rows[j][2 * h + 1] = val(w[j][h][1]);
-                        } else {
-                            still |= 1u << (2 * j + h);
-                        }
-                    }
-            if ((pend >> HM) & 1u) {
-                if (has(wl, tg)) hl = val(wl);
-                else still |= 1u << HM;
+                for (int k = 0; k < 4; k++) sh[j][k] = __shfl_sync(FULL, self[k], src);
             }
-            if ((pend >> HP) & 1u) {
-                if (has(wr, tg)) hr = val(wr);
-                else still |= 1u << HP;
-            }
-            pend = still;
-            if (!__any_sync(FULL, pend != 0u)) return true;
-            if ((++spins & 15u) == 0 && give_up(ctrl, t0, timeout_ns)) return false;
         }
+        const float sl = __shfl_up_sync(FULL, self[3], 1);
+        const float sr = __shfl_down_sync(FULL, self[0], 1);
+        unsigned bad = ((unsigned)(wl >> 32) ^ tg) | ((unsigned)(wr >> 32) ^ tg);
+#pragma unroll
+        for (int j = 0; j < NRR; j++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) bad |= ((unsigned)(w[j][h][0] >> 32) ^ tg) | ((unsigned)(w[j][h][1] >> 32) ^ tg);
+        if (__any_sync(FULL, bad != 0u)) {
+            // slow path: re-read the words whose tag is not there yet
+            u64 t0 = 0;
+            unsigned spins = 0;
+            for (;;) {
+                unsigned pend = 0;
+#pragma unroll
+                for (int j = 0; j < NRR; j++)
+#pragma unroll
+                    for (int h = 0; h < 2; h++)
+                        if (!has(w[j][h][0], tg) || !has(w[j][h][1], tg)) pend |= 1u << (2 * j + h);
+                if (!has(wl, tg)) pend |= 1u << HM;
+                if (!has(wr, tg)) pend |= 1u << HP;
+                if (!__any_sync(FULL, pend != 0u)) break;
+                if ((++spins & 15u) == 0 && give_up(ctrl, t0, timeout_ns)) return false;
+#pragma unroll
+                for (int j = 0; j < NRR; j++)
+#pragma unroll
+                    for (int h = 0; h < 2; h++)
+                        if ((pend >> (2 * j + h)) & 1u) ld_rlx2(in + wo(f.a, j, h), w[j][h][0], w[j][h][1]);
+                if ((pend >> HM) & 1u) wl = ld_rlx(in + wol());
+                if ((pend >> HP) & 1u) wr = ld_rlx(in + wor());
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NRR; j++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const float m = val(w[j][k >> 1][k & 1]);
+                rows[j][k] = ((inw >> (2 * j)) & 1u) ? sh[j][k] : m;
+            }
+        if (NRR == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) rows[0][k] = 0.f;
+        }
+        hl = ((inw >> HM) & 1u) ? sl : val(wl);
+        hr = ((inw >> HP) & 1u) ? sr : val(wr);
+        return true;
     }
 
     // Neighbour values of state k with blocked moves replaced by V(s), in
@@ -370,8 +407,8 @@ __device__ __forceinline__ void flow_finish(Ctrl *ctrl, float rres, u64 timeout_
 }
 
 template <int D>
-__global__ void __launch_bounds__(256, 2) flow_vi_kernel(FlowArgs f, SolveParams sp, Ctrl *ctrl) {
-    __shared__ unsigned prevhi_all[kWarps][kSlots * kNC];
+__global__ void __launch_bounds__(kMaxThreads, 1) flow_vi_kernel(FlowArgs f, SolveParams sp, Ctrl *ctrl) {
+    __shared__ unsigned prevhi_all[kMaxWarps][kSlots * kNC];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int NW = gridDim.x * (blockDim.x >> 5);
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -472,8 +509,8 @@ __global__ void __launch_bounds__(256, 2) flow_vi_kernel(FlowArgs f, SolveParams
 }
 
 template <int D>
-__global__ void __launch_bounds__(256, 2) flow_pi_kernel(FlowArgs f, SolveParams sp, Ctrl *ctrl) {
-    __shared__ unsigned prevhi_all[kWarps][kSlots * kNC];
+__global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, SolveParams sp, Ctrl *ctrl) {
+    __shared__ unsigned prevhi_all[kMaxWarps][kSlots * kNC];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int NW = gridDim.x * (blockDim.x >> 5);
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -515,12 +552,8 @@ __global__ void __launch_bounds__(256, 2) flow_pi_kernel(FlowArgs f, SolveParams
         }
         sg.act = act;
     }
-    int total = 1, evals = 0, round = 0, conv = 0;
-    long long backups = (long long)f.a.nstates * sp.nactions;
-    float res[4];
+    int evals = 0, round = 0, conv = 0;
     float rres = 0.f;
-#pragma unroll
-    for (int k = 0; k < 4; k++) res[k] = sg.cur[k];
     while (round < sp.max_rounds) {
         // evaluation of the current policy from V_q (tag base + q)
         const unsigned q0 = q;
@@ -553,7 +586,7 @@ __global__ void __launch_bounds__(256, 2) flow_pi_kernel(FlowArgs f, SolveParams
                 if (nf < 0) return;
                 if (nf == 0) {  // sweep q - 2 met eval_tol: its result is V_{q-1}
 #pragma unroll
-                    for (int k = 0; k < 4; k++) res[k] = sg.prev[k];
+                    for (int k = 0; k < 4; k++) sg.cur[k] = sg.prev[k];
                     rres = r2;
                     rq = q - 1;
                     eval_ok = 1;
@@ -569,8 +602,6 @@ __global__ void __launch_bounds__(256, 2) flow_pi_kernel(FlowArgs f, SolveParams
             q++;
             e++;
             if (e == sp.max_eval_iter) {
-#pragma unroll
-                for (int k = 0; k < 4; k++) res[k] = sg.cur[k];
                 rres = r1;
                 rq = q;
                 // arrivals of this phase are its sweeps q0, q0 + 1, ... in order
@@ -584,7 +615,7 @@ __global__ void __launch_bounds__(256, 2) flow_pi_kernel(FlowArgs f, SolveParams
                         rq = sweep + 1;
                         const bool older = sweep + 2 == q;
 #pragma unroll
-                        for (int k = 0; k < 4; k++) res[k] = older ? sg.prev[k] : sg.cur[k];
+                        for (int k = 0; k < 4; k++) sg.cur[k] = older ? sg.prev[k] : sg.cur[k];
                         rres = older ? r2 : r1;
                     }
                 }
@@ -592,14 +623,11 @@ __global__ void __launch_bounds__(256, 2) flow_pi_kernel(FlowArgs f, SolveParams
             }
         }
         evals += (int)(rq - q0);
-        total += (int)(rq - q0);
-        backups += (long long)(rq - q0) * f.a.nstates;
         // every earlier arrival is settled before the improvement's own
         while (arv.nchk < arv.na)
             if (arv.check_next(ctrl, sp.timeout_ns) < 0) return;
         const unsigned hq = q;  // highest tag sequence written so far
-#pragma unroll
-        for (int k = 0; k < 4; k++) sg.cur[k] = res[k];
+        // sg.cur now holds V_rq, the values of this evaluation
         // improvement on V_rq (tag base + rq, buffer rq mod 3)
         unsigned changed = 0;
         {
@@ -627,70 +655,58 @@ __global__ void __launch_bounds__(256, 2) flow_pi_kernel(FlowArgs f, SolveParams
         arv.arrive(wc > 0);
         const int moved = arv.check_next(ctrl, sp.timeout_ns);
         if (moved < 0) return;
-        total++;
         round++;
-        backups += (long long)f.a.nstates * sp.nactions;
         if (moved == 0) { conv = eval_ok; break; }
         if (!eval_ok) break;
     }
     if (sg.valid) {
-        *reinterpret_cast<float4 *>(f.V + sg.s0) = make_float4(res[0], res[1], res[2], res[3]);
+        *reinterpret_cast<float4 *>(f.V + sg.s0) = make_float4(sg.cur[0], sg.cur[1], sg.cur[2], sg.cur[3]);
         *reinterpret_cast<unsigned *>(f.pi + sg.s0) = sg.act;
     } else {
         rres = 0.f;
     }
-    flow_finish(ctrl, rres, sp.timeout_ns, NW, gw == 0 && lane == 0, total, conv, backups, round, evals, q + 2);
+    // sweeps: greedy + evaluations + improvements; backups: |S||A| per greedy
+    // or improvement sweep, |S| per evaluation sweep
+    flow_finish(ctrl, rres, sp.timeout_ns, NW, gw == 0 && lane == 0, 1 + evals + round, conv,
+                (long long)(1 + round) * f.a.nstates * sp.nactions + (long long)evals * f.a.nstates, round, evals,
+                q + 2);
 }
 
-template <typename K>
-static cudaError_t flow_grid(K kern, const Factors &F, int &cache, int &grid) {
-    if (cache <= 0) {
-        int o = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 256, 0);
-        if (e != cudaSuccess) return e;
-        cache = o;
+// Launch shape: one block per SM (as far as the warps go), every block with
+// the same number of warps, one warp per 32 consecutive segments. Sweeps
+// move at the pace of the busiest SM, so the warps are spread evenly.
+static bool flow_shape(const Factors &F, int &block, int &grid) {
+    const long long nwarps = (F.nstates / 4 + 31) / 32;
+    const long long w = (nwarps + F.num_sms - 1) / F.num_sms;
+    if (w < 1 || w > kMaxWarps) return false;
+    block = 32 * (int)w;
+    grid = (int)((nwarps + w - 1) / w);
+    return true;
+}
+
+// Both kernels keep one block of up to kMaxThreads threads per SM resident.
+template <int D>
+static bool flow_resident() {
+    static int ok = -1;
+    if (ok < 0) {
+        int a = 0, b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, flow_vi_kernel<D>, kMaxThreads, 0) != cudaSuccess) a = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, flow_pi_kernel<D>, kMaxThreads, 0) != cudaSuccess) b = 0;
+        ok = (a >= 1 && b >= 1) ? 1 : 0;
     }
-    const long long nsegs = F.nstates / 4;
-    const long long cap = (long long)cache * F.num_sms;
-    grid = (int)((nsegs + 255) / 256);
-    if (grid < 1) grid = 1;
-    if (cap < 1 || grid > cap) return cudaErrorCooperativeLaunchTooLarge;
-    return cudaSuccess;
+    return ok == 1;
 }
 
 template <int D>
 static cudaError_t launch_flow(const Factors &F, bool pim, const FlowArgs &fa, const SolveParams &sp, Ctrl *ctrl,
                                cudaStream_t st) {
-    static int occ_vi = 0, occ_pi = 0;
-    int grid = 1;
+    int block = 0, grid = 0;
+    if (!flow_shape(F, block, grid) || !flow_resident<D>()) return cudaErrorCooperativeLaunchTooLarge;
     FlowArgs f = fa;
     SolveParams spc = sp;
     void *args[] = {(void *)&f, (void *)&spc, (void *)&ctrl};
-    if (pim) {
-        auto kern = flow_pi_kernel<D>;
-        cudaError_t e = flow_grid(kern, F, occ_pi, grid);
-        if (e != cudaSuccess) return e;
-        return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(256), args, 0, st);
-    }
-    auto kern = flow_vi_kernel<D>;
-    cudaError_t e = flow_grid(kern, F, occ_vi, grid);
-    if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(256), args, 0, st);
-}
-
-// Largest grid (blocks of 256 threads) either flow kernel can keep resident.
-template <int D>
-static int flow_capacity_blocks(const Factors &F) {
-    static int occ[2] = {0, 0};
-    if (occ[0] <= 0) {
-        int a = 0, b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, flow_vi_kernel<D>, 256, 0) != cudaSuccess) a = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, flow_pi_kernel<D>, 256, 0) != cudaSuccess) b = 0;
-        occ[0] = a;
-        occ[1] = b;
-    }
-    const int o = occ[0] < occ[1] ? occ[0] : occ[1];
-    return o * F.num_sms;
+    const void *kern = pim ? (const void *)flow_pi_kernel<D> : (const void *)flow_vi_kernel<D>;
+    return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(block), args, 0, st);
 }
 
 }  // namespace
@@ -701,22 +717,20 @@ bool flow_eligible(const Factors &F, bool policy_iteration, const void *V, const
     if (F.shape[F.ndim - 1] % 4 != 0 || F.nstates % 4 != 0 || F.nstates >= (1ll << 30)) return false;
     if (((uintptr_t)V & 15u) != 0) return false;
     if (policy_iteration && ((uintptr_t)pi & 3u) != 0) return false;
-    int cap = 0;
+    int block = 0, grid = 0;
+    if (!flow_shape(F, block, grid) || grid > F.num_sms) return false;
+    bool res = false;
     switch (F.ndim) {
-        case 1: cap = flow_capacity_blocks<1>(F); break;
-        case 2: cap = flow_capacity_blocks<2>(F); break;
-        default: cap = flow_capacity_blocks<3>(F); break;
+        case 1: res = flow_resident<1>(); break;
+        case 2: res = flow_resident<2>(); break;
+        default: res = flow_resident<3>(); break;
     }
-    const long long blocks = (F.nstates / 4 + 255) / 256;
-    if (blocks > cap) return false;
-    // cumulative arrival counts stay below 2^32: (sweeps / 8 + 1) * warps / 8
-    const long long warps = blocks * kWarps;
+    if (!res) return false;
+    // tags (base <= 2^30, plus the sweeps of one launch) stay below 2^32 - 1
     const long long sweeps = policy_iteration
                                  ? (long long)o.max_rounds * ((long long)o.max_eval_iter + 2) + 2
                                  : (long long)o.max_iter + 2;
-    if ((sweeps / kSlots + 1) * (warps / kNC + 1) >= (1ll << 31)) return false;
-    if (sweeps >= (1ll << 30)) return false;
-    return true;
+    return sweeps < (1ll << 31);
 }
 
 size_t flow_bytes(const Factors &F) {

@@ -72,6 +72,7 @@ def test_vi_equals_grid_barrier_solver(cp, shape):
     f = cp.build_factors(gw, device=0)
     Va, pa, ta, ra = _vi(cp, f, gw, 1)
     Vb, pb, tb, rb = _vi(cp, f, gw, 2)
+    assert ra["solver"] == cp.SOLVER_BARRIER_FREE and rb["solver"] == cp.SOLVER_GRID_BARRIER
     assert ra["status"] == cp.OK and rb["status"] == cp.OK
     assert ra["iterations"] == rb["iterations"]
     assert ra["residual"] == rb["residual"]
@@ -94,6 +95,7 @@ def test_k_sweeps_match_oracle(cp, oc, k):
     Va, _, ta, ra = _vi(cp, f, gw, 1, max_iter=k, tol=1e-30, certify=0)
     Vb, _, tb, rb = _vi(cp, f, gw, 2, max_iter=k, tol=1e-30, certify=0)
     assert ra["status"] == cp.ENOCONV and ra["iterations"] == k
+    assert ra["solver"] == cp.SOLVER_BARRIER_FREE and rb["solver"] == cp.SOLVER_GRID_BARRIER
     assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
     assert np.array_equal(ta, tb)
     Vo = np.zeros(gw.nstates)
@@ -117,6 +119,7 @@ def test_pi_equals_grid_barrier_solver(cp, shape):
         r = cp.policy_iteration(f, cp.F32, V, pi, opts=cp.default_opts(fused=fused))
         out[fused] = (V.cpu().numpy(), pi.cpu().numpy(), r)
     (Va, pa, ra), (Vb, pb, rb) = out[1], out[2]
+    assert ra["solver"] == cp.SOLVER_BARRIER_FREE and rb["solver"] == cp.SOLVER_GRID_BARRIER
     for key in ("status", "iterations", "rounds", "eval_sweeps", "residual", "backups", "certified_residual"):
         assert ra[key] == rb[key], (key, ra[key], rb[key])
     assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
@@ -140,6 +143,7 @@ def test_pi_round_and_eval_limits(cp):
                                     raise_on_noconv=False)
             out[fused] = (V.cpu().numpy(), pi.cpu().numpy(), r)
         (Va, pa, ra), (Vb, pb, rb) = out[1], out[2]
+        assert ra["solver"] == cp.SOLVER_BARRIER_FREE and rb["solver"] == cp.SOLVER_GRID_BARRIER
         for key in ("status", "iterations", "rounds", "eval_sweeps", "residual", "backups"):
             assert ra[key] == rb[key], (kw, key, ra[key], rb[key])
         assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32)), kw
@@ -191,3 +195,17 @@ def test_timeout_then_recovery(cp):
     assert ra["iterations"] == rb["iterations"]
     assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
     f.close()
+
+
+def test_ineligible_shapes_use_grid_barrier(cp):
+    """Rows that are not a multiple of 4 states, and 4-D grids, take the
+    grid-barrier solver; F64 never runs barrier-free."""
+    import torch
+    for shape, prec in (((10, 10), cp.F32), ((6, 5, 4, 4), cp.F32), ((16, 16), cp.F64)):
+        gw = ci.gridworld(shape, p=0.8, gamma=0.9, step_reward=-0.04, goal_rewards=[1.0, -1.0], seed=1)
+        f = cp.build_factors(gw, device=0)
+        dt = torch.float64 if prec == cp.F64 else torch.float32
+        V = torch.zeros(gw.nstates, dtype=dt, device="cuda")
+        r = cp.value_iteration(f, prec, V, None)
+        assert r["solver"] == cp.SOLVER_GRID_BARRIER, shape
+        f.close()
