@@ -146,33 +146,34 @@ def aggregate(pg, units, ms, device=None):
     return float(t.item()), float(m.item())
 
 
-BANDED_SOURCES = ["banded_common.cuh", "banded.cu", "banded_solve.cu", "flow_solve.cu", "flow.h", "internal.h"]
-
-
-def banded_sources_hash():
+def sources_hash(files):
     h = hashlib.sha256()
-    for f in BANDED_SOURCES:
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_2103_00331_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel_file):
+def traffic_from_profile(kernel_file, scale=None):
     """DRAM bytes per launch of a kernel from its committed ncu summary, if
-    that summary was taken on the current kernel sources (hash match)."""
-    h = banded_sources_hash()
+    that summary was taken on the current sources of that kernel (the
+    summary's `sources:` line lists them, `sources_sha256_16:` their hash).
+    With scale = a state count, the summary's bytes per state times that
+    count (for captures taken on a smaller case of the same kernel)."""
     path = os.path.join(ROOT, "profiles", kernel_file)
     if not os.path.exists(path):
         return None
     vals = {}
     for ln in open(path):
-        if ":" in ln:
+        if ":" in ln and not ln.startswith("#"):
             k, v = ln.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("banded_sources_sha256_16") != h:
-        return None
     try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+        if vals.get("sources_sha256_16") != sources_hash(vals["sources"].split()):
+            return None
+        if scale is not None:
+            return float(vals["dram_bytes_per_state"].split()[0]) * scale
+        return float(vals["dram_bytes_per_launch"].split()[0])
+    except (KeyError, ValueError, OSError):
         return None
 
 
@@ -534,22 +535,23 @@ def hbm_sweep(cp, dev, stream, peak):
     f.close()
     del Va, Vb
     torch.cuda.empty_cache()
-    return {"kernel": "sweep_kernel<float,float,3,4>", "states": S, "ms": ms,
+    return {"kernel": "march_kernel<float,false> (plane-marching fused backup)", "states": S, "ms": ms,
             "bytes_per_state": BYTES_VI, "achieved_gbs": ach, "peak_gbs": peak, "frac": ach / peak,
-            "note": "inputs 1.7 GB > L2; residual fused, policy not written"}
+            "traffic": traffic_from_profile("march_kernel_gridworld320.txt", scale=S),
+            "note": "inputs 1.7 GB > L2; residual fused, policy not written; traffic scaled from a 320^3 capture"}
 
 
 def kernel_case(name, reps=3):
     """Run one kernel workload a few times and exit (for ncu captures):
-    sweep512 = fused FP32 backup of a 512^3 GridWorld; solve64 / pi64 = fused
+    sweep512 / sweep320 = fused FP32 backup of a 512^3 / 320^3 GridWorld; solve64 / pi64 = fused
     FP32 value / policy iteration of the 64^3 instance (barrier-free solver);
     solve64b / pi64b = the same on the grid-barrier solver."""
     import torch
     import paper_2103_00331_gb300 as cp
     import cpmdp_inputs as ci
     dev = torch.device("cuda", 0)
-    if name == "sweep512":
-        n = 512
+    if name in ("sweep512", "sweep320"):
+        n = int(name[5:])
         gw = ci.gridworld((n, n, n), p=0.8, gamma=0.99, step_reward=-0.01,
                           goal_rewards=list(ci.uniform(0, 12, 8, 0.5, 1.0)), obstacle_rate=0.05, seed=2)
         f = cp.build_factors(gw, device=0)
@@ -621,7 +623,8 @@ def main():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-warmstart", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--kernel-case", choices=["sweep512", "solve64", "pi64", "solve64b", "pi64b", "dense64", "dense64tc"],
+    ap.add_argument("--kernel-case", choices=["sweep512", "sweep320", "solve64", "pi64", "solve64b", "pi64b", "dense64",
+                                              "dense64tc"],
                     default=None,
                     help="run one kernel workload a few times (profiling) and exit")
     args = ap.parse_args()

@@ -10,6 +10,7 @@
 #include <type_traits>
 
 #include "banded_common.cuh"
+#include "march.h"
 
 namespace cpmdp {
 
@@ -160,6 +161,9 @@ static cudaError_t launch_sweep(const Factors &F, const T *V, T *W, uint8_t *pi,
 template <typename T, typename TA>
 static cudaError_t sweep_any(const Factors &F, const T *V, T *W, uint8_t *pi, unsigned long long *res,
                              cudaStream_t st) {
+    // large 3-D float grids: the plane-marching sweep (same arithmetic)
+    if (std::is_same<T, float>::value && march_eligible(F, V, W, pi))
+        return march_sweep(F, (const float *)V, (float *)W, pi, res, std::is_same<TA, double>::value, st);
     const int vec = band_pick_vec(F, sizeof(T), V, W);
     constexpr int V2 = (int)(16 / sizeof(T));
     cudaError_t e = cudaErrorInvalidValue;
