@@ -40,6 +40,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "banded_common.cuh"
 #include "flow.h"
@@ -76,6 +77,8 @@ __device__ __forceinline__ bool has(u64 w, unsigned tag) { return (unsigned)(w >
 
 struct FlowArgs {
     BandArgs a;
+    unsigned tol_bits;         // bits of the smallest float >= tol (value iteration) ...
+    unsigned eval_tol_bits;    // ... and >= eval_tol (policy evaluation)
     u64 *buf0, *buf1, *buf2;   // tagged value ring
     u64 *ctr;                  // kSlots x kNC arrival counters, kLineWords apart
     float *V;                  // caller's values: start in, result out
@@ -345,6 +348,14 @@ struct FlowSeg {
     }
 };
 
+// Whether the warp's largest residual r is still >= the tolerance whose
+// float round-up has bits tb: for a float r >= 0, (double)r < tol exactly
+// when r < the smallest float >= tol, and non-negative floats (a NaN above
+// +inf) order like their bits, so no FP64 instruction is needed.
+__device__ __forceinline__ bool warp_open(float r, unsigned tb) {
+    return __reduce_max_sync(FULL, __float_as_uint(r)) >= tb;
+}
+
 __device__ __forceinline__ unsigned long long warp_res_bits(float r) {
     const unsigned u = __reduce_max_sync(FULL, __float_as_uint(r));
     return (unsigned long long)__double_as_longlong((double)__uint_as_float(u));
@@ -472,9 +483,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_vi_kernel(FlowArgs f, Sol
             }
         }
         sg.publish(f, q + 1, base, nxt);
-        const u64 mb = warp_res_bits(r);
-        arv.arrive(!below_tol(mb, sp.tol));
-        if (f.trace && lane == 0 && mb) atomicMax(reinterpret_cast<u64 *>(f.trace) + q, mb);
+        arv.arrive(warp_open(r, f.tol_bits));
+        if (f.trace) {
+            const u64 mb = warp_res_bits(r);
+            if (lane == 0 && mb) atomicMax(reinterpret_cast<u64 *>(f.trace) + q, mb);
+        }
 #pragma unroll
         for (int k = 0; k < 4; k++) { sg.prev[k] = sg.cur[k]; sg.cur[k] = nxt[k]; }
         r2 = r1;
@@ -594,7 +607,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, Sol
                 }
             }
             sg.publish(f, q + 1, base, nxt);
-            arv.arrive(!below_tol(warp_res_bits(r), sp.eval_tol));
+            arv.arrive(warp_open(r, f.eval_tol_bits));
 #pragma unroll
             for (int k = 0; k < 4; k++) { sg.prev[k] = sg.cur[k]; sg.cur[k] = nxt[k]; }
             r2 = r1;
@@ -709,6 +722,16 @@ static cudaError_t launch_flow(const Factors &F, bool pim, const FlowArgs &fa, c
     return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(block), args, 0, st);
 }
 
+// Bits of the smallest non-negative float >= t (t > 0; +inf above the
+// float range).
+unsigned float_ceil_bits(double t) {
+    float f = (float)t;
+    if ((double)f < t) f = nextafterf(f, INFINITY);
+    unsigned u;
+    memcpy(&u, &f, sizeof u);
+    return u;
+}
+
 }  // namespace
 
 bool flow_eligible(const Factors &F, bool policy_iteration, const void *V, const uint8_t *pi,
@@ -753,6 +776,8 @@ cpmdp_status flow_solve(const Factors &F, bool policy_iteration, float *V, uint8
     fa.pi = pi;
     fa.trace = policy_iteration ? nullptr : trace;
     fa.base = F.flow_base;
+    fa.tol_bits = float_ceil_bits(sp.tol);
+    fa.eval_tol_bits = float_ceil_bits(sp.eval_tol);
     fa.nsegs = (int)(F.nstates / 4);
     CPMDP_CUDA(cudaMemsetAsync(F.d_flow, 0, flow_counter_bytes(), st));
     if (fa.trace) CPMDP_CUDA(cudaMemsetAsync(fa.trace, 0, (size_t)sp.max_iter * sizeof(double), st));
