@@ -12,7 +12,7 @@ struct SolveParams;
 // and one thread per 4 states fits in one co-resident grid.
 bool flow_eligible(const Factors &F, bool policy_iteration, const void *V, const uint8_t *pi, const SolveOpts &o);
 // Device bytes the solver needs beside the factors' own buffers: arrival
-// counters and three rings of |S| tagged 64-bit words.
+// counters and four rings of |S| tagged 64-bit words.
 size_t flow_bytes(const Factors &F);
 size_t flow_counter_bytes();
 // One cooperative launch on `st` (F.d_flow allocated, tags above F.flow_base

@@ -12,29 +12,33 @@
 // * Each thread owns one segment of 4 consecutive states of a row of the
 //   last dimension for the whole launch and keeps their values, rewards,
 //   codes and actions in registers.
-// * Values travel through three ring buffers of 64-bit words, each holding
-//   (sweep tag << 32) | float bits. Sweep q reads buffer q mod 3 and writes
-//   buffer (q + 1) mod 3. A thread waits (bounded) until every neighbour
-//   word it needs carries the tag of sweep q; a 64-bit word is written and
-//   read whole, so a matching tag also means a matching value. Neighbours
-//   held by other lanes of the same warp (the left and right neighbours,
-//   and rows less than 32 segments away) come by shuffle.
+// * Values travel through kRing = 4 ring buffers of 64-bit words, each
+//   holding (sweep tag << 32) | float bits. Sweep q reads buffer q mod 4 and
+//   writes buffer (q + 1) mod 4. A thread waits (bounded) until every
+//   neighbour word it needs carries the tag of sweep q; a 64-bit word is
+//   written and read whole, so a matching tag also means a matching value.
+//   Neighbours held by other lanes of the same warp (the left and right
+//   neighbours, and rows less than 32 segments away) come by shuffle.
 // * Each warp reports every sweep on an arrival counter (+1 in the low
 //   half, +1 in the high half when its residual is still >= tol). Before it
-//   stores sweep q, a warp checks that every warp has reported sweep q - 2.
-//   So nobody still reads the buffer it is about to overwrite, and it learns
-//   whether sweep q - 2 met the stopping rule. If it did, the warp returns
-//   the values of sweep q - 2, still in its registers, and two speculative
-//   sweeps are dropped. Values, sweep counts and residuals are exactly those
-//   of the grid-barrier solver: same Jacobi iterates, same per-state
-//   arithmetic (vi_state / eval_state), same stopping sweep.
+//   stores sweep q, a warp checks that every warp has reported sweep
+//   q - kLag (kLag = 3): nobody still reads the buffer it is about to
+//   overwrite, and it learns whether sweep q - kLag met the stopping rule.
+//   If it did, the warp returns the values of that sweep (its own words,
+//   still in the ring) and kLag speculative sweeps are dropped. Values,
+//   sweep counts and residuals are exactly those of the grid-barrier solver:
+//   same Jacobi iterates, same per-state arithmetic (vi_state /
+//   eval_state), same stopping sweep. Warps far apart on the grid drift up
+//   to a couple of sweeps from each other, and the three-sweep slack keeps
+//   that drift from stalling the check.
 //
 // Counters are cumulative per slot (arrival i uses slot i mod 8), spread
 // over 8 counters of their own 128-byte lines to limit atomic contention.
-// No warp can report arrival i + 8 before every warp has reported i + 6,
-// which every warp checks before it stores sweep i + 8, so a check of
-// arrival i sees exactly the arrivals i, i - 8, ... of its slot; flags are
-// told apart with the high half each lane saw at the slot's previous check.
+// No warp can report arrival i + 8 before every warp has reported i + 5,
+// which every warp checks before it stores sweep i + 8, and arrival i is
+// checked at sweep i + 3: a check of arrival i sees exactly the arrivals i,
+// i - 8, ... of its slot; flags are told apart with the count each lane saw
+// at the slot's previous check.
 // Every wait gives up after timeout_ns (CPMDP_ETIMEOUT in the status word)
 // or when another warp has recorded a status.
 #include <cuda_runtime.h>
@@ -51,7 +55,9 @@ namespace {
 
 typedef unsigned long long u64;
 constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr int kSlots = 8;            // arrival slots (arrival i uses slot i % kSlots)
+constexpr int kLag = 3;              // the stopping rule of sweep q is settled at sweep q + kLag
+constexpr int kRing = kLag + 1;      // tagged value buffers
+constexpr int kSlots = 8;            // arrival slots (arrival i uses slot i % kSlots; > 2 kLag + 1)
 constexpr int kNC = 8;               // counters per slot (warp w adds to counter w % kNC)
 constexpr int kLineWords = 16;       // 64-bit words per 128-byte line
 constexpr int kMaxWarps = 14;        // warps per block at most (one block per SM, 448 threads)
@@ -79,7 +85,7 @@ struct FlowArgs {
     BandArgs a;
     unsigned tol_bits;         // bits of the smallest float >= tol (value iteration) ...
     unsigned eval_tol_bits;    // ... and >= eval_tol (policy evaluation)
-    u64 *buf0, *buf1, *buf2;   // tagged value ring
+    u64 *buf[kRing];           // tagged value ring
     u64 *ctr;                  // kSlots x kNC arrival counters, kLineWords apart
     float *V;                  // caller's values: start in, result out
     uint8_t *pi;               // caller's policy (policy iteration)
@@ -88,10 +94,7 @@ struct FlowArgs {
     int nsegs;                 // |S| / 4
 };
 
-__device__ __forceinline__ u64 *ring(const FlowArgs &f, unsigned q) {
-    const unsigned m = q % 3u;
-    return m == 0 ? f.buf0 : (m == 1 ? f.buf1 : f.buf2);
-}
+__device__ __forceinline__ u64 *ring(const FlowArgs &f, unsigned q) { return f.buf[q % (unsigned)kRing]; }
 
 // Warp-uniform: true when this warp must stop waiting (another warp
 // recorded a status, or this wait ran past timeout_ns: then it records
@@ -181,7 +184,7 @@ struct FlowSeg {
     unsigned inw;         // served by a shuffle in this warp: bits 2j, 2j+1 (row j), HM, HP
     unsigned need;        // needed from memory: bit 2j + h (row j, half h), HM, HP
     int own;              // first ring word of this segment (a lane without one: the last segment's)
-    float R[4], cur[4], prev[4];
+    float R[4], cur[4];
     unsigned act;         // policy iteration: 4 actions, state k in byte k
 
     __device__ __forceinline__ void init(const FlowArgs &f, int seg, int lane) {
@@ -206,7 +209,7 @@ struct FlowSeg {
         if (lane >= 1) inw |= 1u << HM;
         if (lane <= 30) inw |= 1u << HP;
 #pragma unroll
-        for (int k = 0; k < 4; k++) { R[k] = 0.f; cur[k] = 0.f; prev[k] = 0.f; }
+        for (int k = 0; k < 4; k++) { R[k] = 0.f; cur[k] = 0.f; }
         // A lane without a segment reads the last segment's words, which
         // its owner (the last valid lane of this warp) writes every sweep.
         own = valid ? s0 : a.nstates - 4;
@@ -239,6 +242,18 @@ struct FlowSeg {
     }
     __device__ __forceinline__ int wol() const { return own - (int)((need >> HM) & 1u); }
     __device__ __forceinline__ int wor() const { return own + (int)(((need >> HP) & 1u) << 2); }
+
+    // This segment's own values of sequence q, read back from the ring: its
+    // own words, written by this thread and still there while q is one of
+    // the kRing - 1 latest sequences written.
+    __device__ __forceinline__ void own_values(const FlowArgs &f, unsigned q, float (&v)[4]) const {
+        if (!valid) return;
+        const u64 *in = ring(f, q);
+        u64 a, b, c, d;
+        ld_rlx2(in + s0, a, b);
+        ld_rlx2(in + s0 + 2, c, d);
+        v[0] = val(a); v[1] = val(b); v[2] = val(c); v[3] = val(d);
+    }
 
     __device__ __forceinline__ void publish(const FlowArgs &f, unsigned q, unsigned base, const float (&v)[4]) const {
         if (!valid) return;
@@ -446,12 +461,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_vi_kernel(FlowArgs f, Sol
     constexpr unsigned OBST = FlowSeg<D>::OBST;
     const unsigned maxq = (unsigned)sp.max_iter;
     unsigned q = 0;
-    float r1 = 0.f, r2 = 0.f;              // thread residuals of sweeps q-1, q-2
+    float rh[kLag];                        // thread residuals of sweeps q-1, q-2, ...
+#pragma unroll
+    for (int i = 0; i < kLag; i++) rh[i] = 0.f;
     float res[4];
     float rres = 0.f;
     int iters = 0, conv = 0;
     for (;;) {
-        const u64 pk = q >= 2 ? arv.peek(arv.nchk) : 0ull;
+        const u64 pk = q >= kLag ? arv.peek(arv.nchk) : 0ull;
         float rows[NR][4], hl, hr;
         if (!sg.gather(f, q, base, sg.cur, rows, hl, hr, ctrl, sp.timeout_ns)) return;
         float nxt[4];
@@ -470,14 +487,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_vi_kernel(FlowArgs f, Sol
             }
         }
         if (!sg.valid) r = 0.f;
-        if (q >= 2) {
+        if (q >= kLag) {
             const int nf = arv.check(pk, ctrl, sp.timeout_ns);
             if (nf < 0) return;
-            if (nf == 0) {  // sweep q - 2 met the stopping rule: its result is V_{q-1}
-#pragma unroll
-                for (int k = 0; k < 4; k++) res[k] = sg.prev[k];
-                rres = r2;
-                iters = (int)q - 1;
+            if (nf == 0) {  // sweep q - kLag met the stopping rule: its result is V_{q-kLag+1}
+                sg.own_values(f, q - kLag + 1, res);
+                rres = rh[kLag - 1];
+                iters = (int)q - kLag + 1;
                 conv = 1;
                 break;
             }
@@ -489,15 +505,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_vi_kernel(FlowArgs f, Sol
             if (lane == 0 && mb) atomicMax(reinterpret_cast<u64 *>(f.trace) + q, mb);
         }
 #pragma unroll
-        for (int k = 0; k < 4; k++) { sg.prev[k] = sg.cur[k]; sg.cur[k] = nxt[k]; }
-        r2 = r1;
-        r1 = r;
+        for (int k = 0; k < 4; k++) sg.cur[k] = nxt[k];
+#pragma unroll
+        for (int i = kLag - 1; i > 0; i--) rh[i] = rh[i - 1];
+        rh[0] = r;
         q++;
         if (q == maxq) {
-            // the limit: settle the two unchecked sweeps in order
+            // the limit: settle the unchecked sweeps in order
 #pragma unroll
             for (int k = 0; k < 4; k++) res[k] = sg.cur[k];
-            rres = r1;
+            rres = rh[0];
             iters = (int)q;
             while (arv.nchk < arv.na) {
                 const unsigned sweep = arv.nchk;  // value iteration: arrival i is sweep i
@@ -506,10 +523,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_vi_kernel(FlowArgs f, Sol
                 if (nf == 0 && !conv) {
                     conv = 1;
                     iters = (int)sweep + 1;
-                    const bool older = sweep + 2 == q;
+                    if (sweep + 1 != q) sg.own_values(f, sweep + 1, res);
+                    const unsigned back = q - 1 - sweep;   // 0 .. kLag-1
 #pragma unroll
-                    for (int k = 0; k < 4; k++) res[k] = older ? sg.prev[k] : sg.cur[k];
-                    rres = older ? r2 : r1;
+                    for (int i = 0; i < kLag; i++)
+                        if ((unsigned)i == back) rres = rh[i];
                 }
             }
             break;
@@ -572,9 +590,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, Sol
         const unsigned q0 = q;
         unsigned rq = q;
         int e = 0, eval_ok = 0;
-        float r1 = 0.f, r2 = 0.f;
+        float rh[kLag];
+#pragma unroll
+        for (int i = 0; i < kLag; i++) rh[i] = 0.f;
         for (;;) {
-            const bool chk = q - q0 >= 2;
+            const bool chk = q - q0 >= (unsigned)kLag;
             const u64 pk = chk ? arv.peek(arv.nchk) : 0ull;
             float rows[NR][4], hl, hr;
             if (!sg.gather(f, q, base, sg.cur, rows, hl, hr, ctrl, sp.timeout_ns)) return;
@@ -597,11 +617,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, Sol
             if (chk) {
                 const int nf = arv.check(pk, ctrl, sp.timeout_ns);
                 if (nf < 0) return;
-                if (nf == 0) {  // sweep q - 2 met eval_tol: its result is V_{q-1}
-#pragma unroll
-                    for (int k = 0; k < 4; k++) sg.cur[k] = sg.prev[k];
-                    rres = r2;
-                    rq = q - 1;
+                if (nf == 0) {  // sweep q - kLag met eval_tol: its result is V_{q-kLag+1}
+                    sg.own_values(f, q - kLag + 1, sg.cur);
+                    rres = rh[kLag - 1];
+                    rq = q - kLag + 1;
                     eval_ok = 1;
                     break;
                 }
@@ -609,13 +628,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, Sol
             sg.publish(f, q + 1, base, nxt);
             arv.arrive(warp_open(r, f.eval_tol_bits));
 #pragma unroll
-            for (int k = 0; k < 4; k++) { sg.prev[k] = sg.cur[k]; sg.cur[k] = nxt[k]; }
-            r2 = r1;
-            r1 = r;
+            for (int k = 0; k < 4; k++) sg.cur[k] = nxt[k];
+#pragma unroll
+            for (int i = kLag - 1; i > 0; i--) rh[i] = rh[i - 1];
+            rh[0] = r;
             q++;
             e++;
             if (e == sp.max_eval_iter) {
-                rres = r1;
+                rres = rh[0];
                 rq = q;
                 // arrivals of this phase are its sweeps q0, q0 + 1, ... in order
                 const unsigned na0 = arv.na - (unsigned)e;
@@ -626,10 +646,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, Sol
                     if (nf == 0 && !eval_ok) {
                         eval_ok = 1;
                         rq = sweep + 1;
-                        const bool older = sweep + 2 == q;
+                        if (rq != q) sg.own_values(f, rq, sg.cur);
+                        const unsigned back = q - 1 - sweep;   // 0 .. kLag-1
 #pragma unroll
-                        for (int k = 0; k < 4; k++) sg.cur[k] = older ? sg.prev[k] : sg.cur[k];
-                        rres = older ? r2 : r1;
+                        for (int i2 = 0; i2 < kLag; i2++)
+                            if ((unsigned)i2 == back) rres = rh[i2];
                     }
                 }
                 break;
@@ -757,7 +778,7 @@ bool flow_eligible(const Factors &F, bool policy_iteration, const void *V, const
 }
 
 size_t flow_bytes(const Factors &F) {
-    return (size_t)kSlots * kNC * kLineWords * sizeof(u64) + 3 * (size_t)F.nstates * sizeof(u64);
+    return (size_t)kSlots * kNC * kLineWords * sizeof(u64) + (size_t)kRing * F.nstates * sizeof(u64);
 }
 
 size_t flow_counter_bytes() { return (size_t)kSlots * kNC * kLineWords * sizeof(u64); }
@@ -769,9 +790,7 @@ cpmdp_status flow_solve(const Factors &F, bool policy_iteration, float *V, uint8
     char *base = static_cast<char *>(F.d_flow);
     fa.ctr = reinterpret_cast<u64 *>(base);
     u64 *bufs = reinterpret_cast<u64 *>(base + flow_counter_bytes());
-    fa.buf0 = bufs;
-    fa.buf1 = bufs + F.nstates;
-    fa.buf2 = bufs + 2 * F.nstates;
+    for (int i = 0; i < kRing; i++) fa.buf[i] = bufs + (size_t)i * F.nstates;
     fa.V = V;
     fa.pi = pi;
     fa.trace = policy_iteration ? nullptr : trace;

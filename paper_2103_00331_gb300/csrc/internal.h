@@ -88,7 +88,7 @@ struct Factors {
     float *d_Vbase = nullptr;          // base value tensor of the defect correction
     int *d_tc_err = nullptr;           // error word of the tensor-core kernels
     // barrier-free FP32 solver (flow_solve.cu), allocated on first use
-    void *d_flow = nullptr;            // arrival counters + three rings of |S| tagged words
+    void *d_flow = nullptr;            // arrival counters + four rings of |S| tagged words
     unsigned flow_base = 0;            // first tag not written to the rings yet
     bool flow_pending = false;         // a launch whose tags are not accounted for yet
 };
