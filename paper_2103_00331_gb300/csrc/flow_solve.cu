@@ -11,7 +11,10 @@
 //
 // * Each thread owns one segment of 4 consecutive states of a row of the
 //   last dimension for the whole launch and keeps their values, rewards,
-//   codes and actions in registers.
+//   codes and actions in registers. Grids too large for that take columns
+//   of 2 or 4 segments stacked along dimension 0 in one thread (their
+//   dimension-0 neighbours inside the column come from registers): up to
+//   about 620,000 states stay in one co-resident grid.
 // * Values travel through kRing = 4 ring buffers of 64-bit words, each
 //   holding (sweep tag << 32) | float bits. Sweep q reads buffer q mod 4 and
 //   writes buffer (q + 1) mod 4. A thread waits (bounded) until every
@@ -61,7 +64,10 @@ constexpr int kSlots = 8;            // arrival slots (arrival i uses slot i % k
 constexpr int kNC = 8;               // counters per slot (warp w adds to counter w % kNC)
 constexpr int kLineWords = 16;       // 64-bit words per 128-byte line
 constexpr int kMaxWarps = 14;        // warps per block at most (one block per SM, 448 threads)
-constexpr int kMaxThreads = 32 * kMaxWarps;
+// Warps per block at most for a column of ZS segments: 14 single segments
+// fit 128 registers a thread (4 warps per scheduler); columns take more
+// registers and fewer, fuller warps.
+template <int ZS> struct ColWarps { static constexpr int value = ZS == 1 ? 14 : 8; };
 
 __device__ __forceinline__ u64 ld_rlx(const u64 *p) {
     u64 v;
@@ -92,6 +98,9 @@ struct FlowArgs {
     double *trace;             // optional per-sweep residual (value iteration)
     unsigned base;             // tag of sweep 0
     int nsegs;                 // |S| / 4
+    int slice;                 // segments per dimension-0 slice (all of them for one dimension)
+    int nz;                    // dimension-0 slices (1 for one dimension)
+    int ncols;                 // columns: slice * ceil(nz / ZS)
 };
 
 __device__ __forceinline__ u64 *ring(const FlowArgs &f, unsigned q) { return f.buf[q % (unsigned)kRing]; }
@@ -170,196 +179,256 @@ struct Arrivals {
     __device__ __forceinline__ int check_next(Ctrl *ctrl, u64 timeout_ns) { return check(peek(nchk), ctrl, timeout_ns); }
 };
 
-// One thread's segment: states s0 .. s0+3 of a row of the last dimension.
-template <int D>
-struct FlowSeg {
+// One thread's column: ZS segments of 4 consecutive states of a row of the
+// last dimension, at the same place of ZS consecutive slices of dimension 0
+// (ZS = 1 for one-dimensional grids). Columns are numbered slice group by
+// slice group, so consecutive lanes hold neighbouring segments of a slice;
+// the dimension-0 neighbours inside a column are in this thread's registers.
+template <int D, int ZS>
+struct FlowCol {
     static constexpr int NRR = 2 * (D - 1);          // row-neighbour directions (other dimensions)
     static constexpr int NR = NRR > 0 ? NRR : 1;
-    static constexpr int HM = 2 * NRR, HP = 2 * NRR + 1;  // need bits of the left / right halo words
+    static constexpr int HM = 2 * NRR, HP = 2 * NRR + 1;  // bits of the left / right halo words
     static constexpr unsigned OBST = 1u << (2 * D), TERM = 1u << (2 * D + 1);
 
-    int s0;
-    bool valid;
-    unsigned code;        // the 4 codes, state k in byte k
-    unsigned inw;         // served by a shuffle in this warp: bits 2j, 2j+1 (row j), HM, HP
-    unsigned need;        // needed from memory: bit 2j + h (row j, half h), HM, HP
-    int own;              // first ring word of this segment (a lane without one: the last segment's)
-    float R[4], cur[4];
-    unsigned act;         // policy iteration: 4 actions, state k in byte k
+    int s0[ZS];
+    bool valid[ZS];
+    unsigned code[ZS];    // the 4 codes of segment i, state k in byte k
+    unsigned inw[ZS];     // not from memory (shuffle, or a register inside the column):
+                          // bits 2j, 2j+1 (row j), HM, HP
+    unsigned need[ZS];    // needed from memory: bit 2j + h (row j, half h), HM, HP
+    int own[ZS];          // first ring word of segment i (a lane without one: the last segment's)
+    float R[ZS][4], cur[ZS][4];
+    unsigned act[ZS];     // policy iteration: 4 actions, state k in byte k
 
-    __device__ __forceinline__ void init(const FlowArgs &f, int seg, int lane) {
+    // Row j of segment i can come from memory: the other dimensions always,
+    // dimension 0 only at the column's ends.
+    static __device__ __forceinline__ constexpr bool memrow(int i, int j) {
+        return j >= 2 || (j == 0 && i == 0) || (j == 1 && i == ZS - 1);
+    }
+
+    __device__ __forceinline__ void init(const FlowArgs &f, int col, int lane) {
         const BandArgs &a = f.a;
-        valid = seg < f.nsegs;
-        s0 = seg * 4;
-        code = 0;
-        act = 0;
-        inw = 0;
-        int off[NR];
+        const int P = f.slice;                    // segments per dimension-0 slice
+        const int zc = col / P, ps = col - zc * P;
+        const bool colok = col < f.ncols;
 #pragma unroll
-        for (int j = 0; j < NR; j++) {
-            off[j] = 0;
-            if (j < NRR) {
-                const int st = a.stride[j / 2];
-                const int so = st / 4;
+        for (int i = 0; i < ZS; i++) {
+            const int z = zc * ZS + i;
+            valid[i] = colok && z < f.nz;
+            s0[i] = (D == 1) ? 4 * col : z * a.stride[0] + 4 * ps;
+            code[i] = 0;
+            act[i] = 0;
+            need[i] = 0;
+            own[i] = valid[i] ? s0[i] : a.nstates - 4;
+            unsigned m = 0;
+#pragma unroll
+            for (int j = 0; j < NRR; j++) {
                 const bool up = (j & 1) != 0;
-                off[j] = up ? st : -st;
-                if (so < 32 && (up ? lane + so < 32 : lane >= so)) inw |= 3u << (2 * j);
+                if (j < 2 && ((!up && i > 0) || (up && i < ZS - 1))) { m |= 3u << (2 * j); continue; }
+                const int so = a.stride[j / 2] / 4;
+                if (so < 32 && (up ? lane + so < 32 : lane >= so)) m |= 3u << (2 * j);
             }
+            if (lane >= 1) m |= 1u << HM;
+            if (lane <= 30) m |= 1u << HP;
+            inw[i] = m;
+#pragma unroll
+            for (int k = 0; k < 4; k++) { R[i][k] = 0.f; cur[i][k] = 0.f; }
+            if (!valid[i]) continue;
+            code[i] = *reinterpret_cast<const unsigned *>(static_cast<const uint8_t *>(a.code) + s0[i]);
+            const float4 r = *reinterpret_cast<const float4 *>(a.R32 + s0[i]);
+            const float4 v = *reinterpret_cast<const float4 *>(f.V + s0[i]);
+            R[i][0] = r.x; R[i][1] = r.y; R[i][2] = r.z; R[i][3] = r.w;
+            cur[i][0] = v.x; cur[i][1] = v.y; cur[i][2] = v.z; cur[i][3] = v.w;
+            unsigned nd = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const unsigned c = (code[i] >> (8 * k)) & 0xFFu;
+                if (c & (OBST | TERM)) continue;
+#pragma unroll
+                for (int j = 0; j < NRR; j++)
+                    if (!((c >> j) & 1u)) nd |= 1u << (2 * j + (k >> 1));
+                if (k == 0 && !((c >> NRR) & 1u)) nd |= 1u << HM;
+                if (k == 3 && !((c >> (NRR + 1)) & 1u)) nd |= 1u << HP;
+            }
+            need[i] = nd & ~m;
         }
-        if (lane >= 1) inw |= 1u << HM;
-        if (lane <= 30) inw |= 1u << HP;
-#pragma unroll
-        for (int k = 0; k < 4; k++) { R[k] = 0.f; cur[k] = 0.f; }
-        // A lane without a segment reads the last segment's words, which
-        // its owner (the last valid lane of this warp) writes every sweep.
-        own = valid ? s0 : a.nstates - 4;
-        need = 0;
-        if (!valid) return;
-        code = *reinterpret_cast<const unsigned *>(static_cast<const uint8_t *>(a.code) + s0);
-        const float4 r = *reinterpret_cast<const float4 *>(a.R32 + s0);
-        const float4 v = *reinterpret_cast<const float4 *>(f.V + s0);
-        R[0] = r.x; R[1] = r.y; R[2] = r.z; R[3] = r.w;
-        cur[0] = v.x; cur[1] = v.y; cur[2] = v.z; cur[3] = v.w;
-        unsigned nd = 0;
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const unsigned c = (code >> (8 * k)) & 0xFFu;
-            if (c & (OBST | TERM)) continue;
-#pragma unroll
-            for (int j = 0; j < NRR; j++)
-                if (!((c >> j) & 1u)) nd |= 1u << (2 * j + (k >> 1));
-            if (k == 0 && !((c >> NRR) & 1u)) nd |= 1u << HM;
-            if (k == 3 && !((c >> (NRR + 1)) & 1u)) nd |= 1u << HP;
-        }
-        need = nd & ~inw;
     }
 
-    // Ring word read for row j, half h: the neighbours' pair when it is
-    // needed from memory, else this segment's own pair (already written).
-    __device__ __forceinline__ int wo(const BandArgs &a, int j, int h) const {
+    // Ring word read for row j, half h of segment i: the neighbours' pair
+    // when it is needed from memory, else the segment's own pair (already
+    // written).
+    __device__ __forceinline__ int wo(const BandArgs &a, int i, int j, int h) const {
         const int st = a.stride[j / 2];
-        return own + 2 * h + (((need >> (2 * j + h)) & 1u) ? ((j & 1) ? st : -st) : 0);
+        return own[i] + 2 * h + (((need[i] >> (2 * j + h)) & 1u) ? ((j & 1) ? st : -st) : 0);
     }
-    __device__ __forceinline__ int wol() const { return own - (int)((need >> HM) & 1u); }
-    __device__ __forceinline__ int wor() const { return own + (int)(((need >> HP) & 1u) << 2); }
+    __device__ __forceinline__ int wol(int i) const { return own[i] - (int)((need[i] >> HM) & 1u); }
+    __device__ __forceinline__ int wor(int i) const { return own[i] + (int)(((need[i] >> HP) & 1u) << 2); }
 
-    // This segment's own values of sequence q, read back from the ring: its
-    // own words, written by this thread and still there while q is one of
-    // the kRing - 1 latest sequences written.
-    __device__ __forceinline__ void own_values(const FlowArgs &f, unsigned q, float (&v)[4]) const {
-        if (!valid) return;
+    // Segment i's own values of sequence q, read back from the ring: its own
+    // words, written by this thread and still there while q is one of the
+    // kRing - 1 latest sequences written.
+    __device__ __forceinline__ void own_values(const FlowArgs &f, unsigned q, int i, float (&v)[4]) const {
+        if (!valid[i]) return;
         const u64 *in = ring(f, q);
         u64 a, b, c, d;
-        ld_rlx2(in + s0, a, b);
-        ld_rlx2(in + s0 + 2, c, d);
+        ld_rlx2(in + s0[i], a, b);
+        ld_rlx2(in + s0[i] + 2, c, d);
         v[0] = val(a); v[1] = val(b); v[2] = val(c); v[3] = val(d);
     }
-
-    __device__ __forceinline__ void publish(const FlowArgs &f, unsigned q, unsigned base, const float (&v)[4]) const {
-        if (!valid) return;
-        u64 *out = ring(f, q);
-        const unsigned tg = base + q;
-        st_rlx2(out + s0, word(v[0], tg), word(v[1], tg));
-        st_rlx2(out + s0 + 2, word(v[2], tg), word(v[3], tg));
+    __device__ __forceinline__ void own_values_all(const FlowArgs &f, unsigned q, float (&v)[ZS][4]) const {
+#pragma unroll
+        for (int i = 0; i < ZS; i++) own_values(f, q, i, v[i]);
     }
 
-    // Neighbour values of sweep q (tag base + q, buffer q mod 3) for the
-    // values `self` (this segment's values of sweep q): rows[j][k] is the
-    // value one move in direction j from state k, hl / hr the states just
-    // left of state 0 and right of state 3 (for blocked moves: anything).
-    // Every lane reads all its ring words at once (words it does not need
-    // are its own, already written), checks all tags with one OR and
-    // re-reads only on a mismatch. Returns false when the warp must stop
+    __device__ __forceinline__ void publish(const FlowArgs &f, unsigned q, unsigned base,
+                                            const float (&v)[ZS][4]) const {
+        u64 *out = ring(f, q);
+        const unsigned tg = base + q;
+#pragma unroll
+        for (int i = 0; i < ZS; i++) {
+            if (!valid[i]) continue;
+            st_rlx2(out + s0[i], word(v[i][0], tg), word(v[i][1], tg));
+            st_rlx2(out + s0[i] + 2, word(v[i][2], tg), word(v[i][3], tg));
+        }
+    }
+
+    // Neighbour values of sweep q (tag base + q, buffer q mod kRing) for the
+    // column's values `self` of sweep q: rows[i][j][k] is the value one move
+    // in direction j from state k of segment i, hl[i] / hr[i] the states
+    // just left of state 0 and right of state 3 (for blocked moves:
+    // anything). Every lane reads all its ring words at once (words it does
+    // not need are its own, already written), checks all tags with one OR
+    // and re-reads only on a mismatch. Returns false when the warp must stop
     // (status recorded).
-    __device__ __forceinline__ bool gather(const FlowArgs &f, unsigned q, unsigned base, const float (&self)[4],
-                                           float (&rows)[NR][4], float &hl, float &hr, Ctrl *ctrl,
+    __device__ __forceinline__ bool gather(const FlowArgs &f, unsigned q, unsigned base, const float (&self)[ZS][4],
+                                           float (&rows)[ZS][NR][4], float (&hl)[ZS], float (&hr)[ZS], Ctrl *ctrl,
                                            u64 timeout_ns) const {
         const unsigned tg = base + q;
         const u64 *in = ring(f, q);
-        u64 w[NR][2][2];
-        u64 wl, wr;
+        u64 w[ZS][NR][2][2];
+        u64 wl[ZS], wr[ZS];
         // The neighbours' words of sweep q are usually stored just as this
         // warp finishes sweep q - 1; a read that reaches L2 before them costs
         // a second round trip. A short pause first lowers that share
         // (measured at 64^3 and 32^3: about 2 % and 4 % faster sweeps).
         __nanosleep(100);
 #pragma unroll
-        for (int j = 0; j < NRR; j++)
+        for (int i = 0; i < ZS; i++) {
 #pragma unroll
-            for (int h = 0; h < 2; h++) ld_rlx2(in + wo(f.a, j, h), w[j][h][0], w[j][h][1]);
-        wl = ld_rlx(in + wol());
-        wr = ld_rlx(in + wor());
-        // rows less than 32 segments away: the lanes holding them (the
-        // stride is the same for every thread, so this branch is uniform)
-        const int lane = threadIdx.x & 31;
-        float sh[NR][4];
+            for (int j = 0; j < NRR; j++)
+                if (memrow(i, j))
 #pragma unroll
-        for (int j = 0; j < NRR; j++) {
-            const int so = f.a.stride[j / 2] >> 2;
-            if (so < 32) {
-                const int src = ((j & 1) ? lane + so : lane - so) & 31;
-#pragma unroll
-                for (int k = 0; k < 4; k++) sh[j][k] = __shfl_sync(FULL, self[k], src);
-            }
+                    for (int h = 0; h < 2; h++) ld_rlx2(in + wo(f.a, i, j, h), w[i][j][h][0], w[i][j][h][1]);
+            wl[i] = ld_rlx(in + wol(i));
+            wr[i] = ld_rlx(in + wor(i));
         }
-        const float sl = __shfl_up_sync(FULL, self[3], 1);
-        const float sr = __shfl_down_sync(FULL, self[0], 1);
-        unsigned bad = ((unsigned)(wl >> 32) ^ tg) | ((unsigned)(wr >> 32) ^ tg);
+        // neighbours held by other lanes (the stride is the same for every
+        // thread, so these branches are uniform)
+        const int lane = threadIdx.x & 31;
+        float sh[ZS][NR][4];
 #pragma unroll
-        for (int j = 0; j < NRR; j++)
+        for (int i = 0; i < ZS; i++)
 #pragma unroll
-            for (int h = 0; h < 2; h++) bad |= ((unsigned)(w[j][h][0] >> 32) ^ tg) | ((unsigned)(w[j][h][1] >> 32) ^ tg);
+            for (int j = 0; j < NRR; j++) {
+                if (!memrow(i, j)) continue;
+                const int so = f.a.stride[j / 2] >> 2;
+                if (so < 32) {
+                    const int src = ((j & 1) ? lane + so : lane - so) & 31;
+                    // dimension 0 across columns: the other end of the neighbouring column
+                    const int si = j >= 2 ? i : ((j & 1) ? 0 : ZS - 1);
+#pragma unroll
+                    for (int k = 0; k < 4; k++) sh[i][j][k] = __shfl_sync(FULL, self[si][k], src);
+                }
+            }
+        float sl[ZS], sr[ZS];
+#pragma unroll
+        for (int i = 0; i < ZS; i++) {
+            sl[i] = __shfl_up_sync(FULL, self[i][3], 1);
+            sr[i] = __shfl_down_sync(FULL, self[i][0], 1);
+        }
+        unsigned bad = 0;
+#pragma unroll
+        for (int i = 0; i < ZS; i++) {
+            bad |= ((unsigned)(wl[i] >> 32) ^ tg) | ((unsigned)(wr[i] >> 32) ^ tg);
+#pragma unroll
+            for (int j = 0; j < NRR; j++)
+                if (memrow(i, j))
+#pragma unroll
+                    for (int h = 0; h < 2; h++)
+                        bad |= ((unsigned)(w[i][j][h][0] >> 32) ^ tg) | ((unsigned)(w[i][j][h][1] >> 32) ^ tg);
+        }
         if (__any_sync(FULL, bad != 0u)) {
             // slow path: re-read the words whose tag is not there yet
             u64 t0 = 0;
             unsigned spins = 0;
             for (;;) {
-                unsigned pend = 0;
+                unsigned pend[ZS];
+                unsigned any = 0;
 #pragma unroll
-                for (int j = 0; j < NRR; j++)
+                for (int i = 0; i < ZS; i++) {
+                    pend[i] = 0;
 #pragma unroll
-                    for (int h = 0; h < 2; h++)
-                        if (!has(w[j][h][0], tg) || !has(w[j][h][1], tg)) pend |= 1u << (2 * j + h);
-                if (!has(wl, tg)) pend |= 1u << HM;
-                if (!has(wr, tg)) pend |= 1u << HP;
-                if (!__any_sync(FULL, pend != 0u)) break;
+                    for (int j = 0; j < NRR; j++)
+                        if (memrow(i, j))
+#pragma unroll
+                            for (int h = 0; h < 2; h++)
+                                if (!has(w[i][j][h][0], tg) || !has(w[i][j][h][1], tg)) pend[i] |= 1u << (2 * j + h);
+                    if (!has(wl[i], tg)) pend[i] |= 1u << HM;
+                    if (!has(wr[i], tg)) pend[i] |= 1u << HP;
+                    any |= pend[i];
+                }
+                if (!__any_sync(FULL, any != 0u)) break;
                 if ((++spins & 15u) == 0 && give_up(ctrl, t0, timeout_ns)) return false;
 #pragma unroll
-                for (int j = 0; j < NRR; j++)
+                for (int i = 0; i < ZS; i++) {
 #pragma unroll
-                    for (int h = 0; h < 2; h++)
-                        if ((pend >> (2 * j + h)) & 1u) ld_rlx2(in + wo(f.a, j, h), w[j][h][0], w[j][h][1]);
-                if ((pend >> HM) & 1u) wl = ld_rlx(in + wol());
-                if ((pend >> HP) & 1u) wr = ld_rlx(in + wor());
+                    for (int j = 0; j < NRR; j++)
+                        if (memrow(i, j))
+#pragma unroll
+                            for (int h = 0; h < 2; h++)
+                                if ((pend[i] >> (2 * j + h)) & 1u)
+                                    ld_rlx2(in + wo(f.a, i, j, h), w[i][j][h][0], w[i][j][h][1]);
+                    if ((pend[i] >> HM) & 1u) wl[i] = ld_rlx(in + wol(i));
+                    if ((pend[i] >> HP) & 1u) wr[i] = ld_rlx(in + wor(i));
+                }
             }
         }
 #pragma unroll
-        for (int j = 0; j < NRR; j++)
+        for (int i = 0; i < ZS; i++) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const float m = val(w[j][k >> 1][k & 1]);
-                rows[j][k] = ((inw >> (2 * j)) & 1u) ? sh[j][k] : m;
+            for (int j = 0; j < NRR; j++)
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    if (!memrow(i, j)) {
+                        rows[i][j][k] = (j & 1) ? self[i < ZS - 1 ? i + 1 : i][k] : self[i > 0 ? i - 1 : 0][k];
+                    } else {
+                        const float m = val(w[i][j][k >> 1][k & 1]);
+                        rows[i][j][k] = ((inw[i] >> (2 * j)) & 1u) ? sh[i][j][k] : m;
+                    }
+                }
+            if (NRR == 0) {
+#pragma unroll
+                for (int k = 0; k < 4; k++) rows[i][0][k] = 0.f;
             }
-        if (NRR == 0) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) rows[0][k] = 0.f;
+            hl[i] = ((inw[i] >> HM) & 1u) ? sl[i] : val(wl[i]);
+            hr[i] = ((inw[i] >> HP) & 1u) ? sr[i] : val(wr[i]);
         }
-        hl = ((inw >> HM) & 1u) ? sl : val(wl);
-        hr = ((inw >> HP) & 1u) ? sr : val(wr);
         return true;
     }
 
-    // Neighbour values of state k with blocked moves replaced by V(s), in
-    // the order of the codes' move bits (as Segment::neighbours).
-    __device__ __forceinline__ void nbk(const float (&self)[4], const float (&rows)[NR][4], float hl, float hr, int k,
+    // Neighbour values of state k of segment i with blocked moves replaced
+    // by V(s), in the order of the codes' move bits (as Segment::neighbours).
+    __device__ __forceinline__ void nbk(const float (&self)[ZS][4], const float (&rows)[ZS][NR][4],
+                                        const float (&hl)[ZS], const float (&hr)[ZS], int i, int k,
                                         float (&nb)[2 * D]) const {
-        const unsigned c = (code >> (8 * k)) & 0xFFu;
+        const unsigned c = (code[i] >> (8 * k)) & 0xFFu;
 #pragma unroll
-        for (int j = 0; j < NRR; j++) nb[j] = ((c >> j) & 1u) ? self[k] : rows[j][k];
-        const float left = (k == 0) ? hl : self[k > 0 ? k - 1 : 0];
-        const float right = (k == 3) ? hr : self[k < 3 ? k + 1 : 0];
-        nb[NRR] = ((c >> NRR) & 1u) ? self[k] : left;
-        nb[NRR + 1] = ((c >> (NRR + 1)) & 1u) ? self[k] : right;
+        for (int j = 0; j < NRR; j++) nb[j] = ((c >> j) & 1u) ? self[i][k] : rows[i][j][k];
+        const float left = (k == 0) ? hl[i] : self[i][k > 0 ? k - 1 : 0];
+        const float right = (k == 3) ? hr[i] : self[i][k < 3 ? k + 1 : 0];
+        nb[NRR] = ((c >> NRR) & 1u) ? self[i][k] : left;
+        nb[NRR + 1] = ((c >> (NRR + 1)) & 1u) ? self[i][k] : right;
     }
 };
 
@@ -432,8 +501,8 @@ __device__ __forceinline__ void flow_finish(Ctrl *ctrl, float rres, u64 timeout_
     ctrl->last_residual = __longlong_as_double((long long)*(volatile u64 *)&ctrl->res_slot[0]);
 }
 
-template <int D>
-__global__ void __launch_bounds__(kMaxThreads, 1) flow_vi_kernel(FlowArgs f, SolveParams sp, Ctrl *ctrl) {
+template <int D, int ZS>
+__global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_vi_kernel(FlowArgs f, SolveParams sp, Ctrl *ctrl) {
     __shared__ unsigned prevhi_all[kMaxWarps][kSlots * kNC];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int NW = gridDim.x * (blockDim.x >> 5);
@@ -452,46 +521,48 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_vi_kernel(FlowArgs f, Sol
 
     float wm, wp, wst, g;
     weights<float>(f.a, wm, wp, wst, g);
-    FlowSeg<D> sg;
+    typedef FlowCol<D, ZS> Col;
+    Col sg;
     sg.init(f, blockIdx.x * blockDim.x + threadIdx.x, lane);
     const unsigned base = f.base;
     sg.publish(f, 0, base, sg.cur);
 
-    constexpr int NR = FlowSeg<D>::NR;
-    constexpr unsigned OBST = FlowSeg<D>::OBST;
+    constexpr int NR = Col::NR;
+    constexpr unsigned OBST = Col::OBST;
     const unsigned maxq = (unsigned)sp.max_iter;
     unsigned q = 0;
     float rh[kLag];                        // thread residuals of sweeps q-1, q-2, ...
 #pragma unroll
     for (int i = 0; i < kLag; i++) rh[i] = 0.f;
-    float res[4];
+    float res[ZS][4];
     float rres = 0.f;
     int iters = 0, conv = 0;
     for (;;) {
         const u64 pk = q >= kLag ? arv.peek(arv.nchk) : 0ull;
-        float rows[NR][4], hl, hr;
+        float rows[ZS][NR][4], hl[ZS], hr[ZS];
         if (!sg.gather(f, q, base, sg.cur, rows, hl, hr, ctrl, sp.timeout_ns)) return;
-        float nxt[4];
+        float nxt[ZS][4];
         float r = 0.f;
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            float nb[2 * D];
-            sg.nbk(sg.cur, rows, hl, hr, k, nb);
-            const unsigned c = (sg.code >> (8 * k)) & 0xFFu;
-            int arg;
-            const float v = vi_state<float, D>(sg.cur[k], nb, c, sg.R[k], wm, wp, wst, g, arg);
-            nxt[k] = v;
-            if (!(c & OBST)) {
-                const float dv = abs_diff(v, sg.cur[k]);
-                r = dv > r ? dv : r;
+        for (int i = 0; i < ZS; i++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                float nb[2 * D];
+                sg.nbk(sg.cur, rows, hl, hr, i, k, nb);
+                const unsigned c = (sg.code[i] >> (8 * k)) & 0xFFu;
+                int arg;
+                const float v = vi_state<float, D>(sg.cur[i][k], nb, c, sg.R[i][k], wm, wp, wst, g, arg);
+                nxt[i][k] = v;
+                if (sg.valid[i] && !(c & OBST)) {
+                    const float dv = abs_diff(v, sg.cur[i][k]);
+                    r = dv > r ? dv : r;
+                }
             }
-        }
-        if (!sg.valid) r = 0.f;
         if (q >= kLag) {
             const int nf = arv.check(pk, ctrl, sp.timeout_ns);
             if (nf < 0) return;
             if (nf == 0) {  // sweep q - kLag met the stopping rule: its result is V_{q-kLag+1}
-                sg.own_values(f, q - kLag + 1, res);
+                sg.own_values_all(f, q - kLag + 1, res);
                 rres = rh[kLag - 1];
                 iters = (int)q - kLag + 1;
                 conv = 1;
@@ -505,7 +576,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_vi_kernel(FlowArgs f, Sol
             if (lane == 0 && mb) atomicMax(reinterpret_cast<u64 *>(f.trace) + q, mb);
         }
 #pragma unroll
-        for (int k = 0; k < 4; k++) sg.cur[k] = nxt[k];
+        for (int i = 0; i < ZS; i++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) sg.cur[i][k] = nxt[i][k];
 #pragma unroll
         for (int i = kLag - 1; i > 0; i--) rh[i] = rh[i - 1];
         rh[0] = r;
@@ -513,7 +586,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_vi_kernel(FlowArgs f, Sol
         if (q == maxq) {
             // the limit: settle the unchecked sweeps in order
 #pragma unroll
-            for (int k = 0; k < 4; k++) res[k] = sg.cur[k];
+            for (int i = 0; i < ZS; i++)
+#pragma unroll
+                for (int k = 0; k < 4; k++) res[i][k] = sg.cur[i][k];
             rres = rh[0];
             iters = (int)q;
             while (arv.nchk < arv.na) {
@@ -523,7 +598,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_vi_kernel(FlowArgs f, Sol
                 if (nf == 0 && !conv) {
                     conv = 1;
                     iters = (int)sweep + 1;
-                    if (sweep + 1 != q) sg.own_values(f, sweep + 1, res);
+                    if (sweep + 1 != q) sg.own_values_all(f, sweep + 1, res);
                     const unsigned back = q - 1 - sweep;   // 0 .. kLag-1
 #pragma unroll
                     for (int i = 0; i < kLag; i++)
@@ -533,14 +608,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_vi_kernel(FlowArgs f, Sol
             break;
         }
     }
-    if (sg.valid) *reinterpret_cast<float4 *>(f.V + sg.s0) = make_float4(res[0], res[1], res[2], res[3]);
-    if (!sg.valid) rres = 0.f;
+#pragma unroll
+    for (int i = 0; i < ZS; i++)
+        if (sg.valid[i])
+            *reinterpret_cast<float4 *>(f.V + sg.s0[i]) = make_float4(res[i][0], res[i][1], res[i][2], res[i][3]);
     flow_finish(ctrl, rres, sp.timeout_ns, NW, gw == 0 && lane == 0, iters, conv,
                 (long long)iters * f.a.nstates * sp.nactions, 0, 0, q + 2);
 }
 
-template <int D>
-__global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, SolveParams sp, Ctrl *ctrl) {
+template <int D, int ZS>
+__global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(FlowArgs f, SolveParams sp, Ctrl *ctrl) {
     __shared__ unsigned prevhi_all[kMaxWarps][kSlots * kNC];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int NW = gridDim.x * (blockDim.x >> 5);
@@ -560,28 +637,33 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, Sol
     float wm, wp, wst, g;
     weights<float>(f.a, wm, wp, wst, g);
     const float margin = (float)sp.margin;
-    FlowSeg<D> sg;
+    typedef FlowCol<D, ZS> Col;
+    Col sg;
     sg.init(f, blockIdx.x * blockDim.x + threadIdx.x, lane);
     const unsigned base = f.base;
-    constexpr int NR = FlowSeg<D>::NR;
-    constexpr unsigned OBST = FlowSeg<D>::OBST;
+    constexpr int NR = Col::NR;
+    constexpr unsigned OBST = Col::OBST;
 
     // initial policy: greedy with respect to the input V
     unsigned q = 0;
     sg.publish(f, 0, base, sg.cur);
     {
-        float rows[NR][4], hl, hr;
+        float rows[ZS][NR][4], hl[ZS], hr[ZS];
         if (!sg.gather(f, 0, base, sg.cur, rows, hl, hr, ctrl, sp.timeout_ns)) return;
-        unsigned dummy = 0, act = 0;
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            float nb[2 * D];
-            sg.nbk(sg.cur, rows, hl, hr, k, nb);
-            const unsigned c = (sg.code >> (8 * k)) & 0xFFu;
-            const int a = improve_state<D>(nb, sg.cur[k], c, sg.R[k], 0, true, margin, wm, wp, wst, g, dummy);
-            act |= (unsigned)a << (8 * k);
+        for (int i = 0; i < ZS; i++) {
+            unsigned dummy = 0, act = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                float nb[2 * D];
+                sg.nbk(sg.cur, rows, hl, hr, i, k, nb);
+                const unsigned c = (sg.code[i] >> (8 * k)) & 0xFFu;
+                const int a = improve_state<D>(nb, sg.cur[i][k], c, sg.R[i][k], 0, true, margin, wm, wp, wst, g,
+                                               dummy);
+                act |= (unsigned)a << (8 * k);
+            }
+            sg.act[i] = act;
         }
-        sg.act = act;
     }
     int evals = 0, round = 0, conv = 0;
     float rres = 0.f;
@@ -596,29 +678,30 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, Sol
         for (;;) {
             const bool chk = q - q0 >= (unsigned)kLag;
             const u64 pk = chk ? arv.peek(arv.nchk) : 0ull;
-            float rows[NR][4], hl, hr;
+            float rows[ZS][NR][4], hl[ZS], hr[ZS];
             if (!sg.gather(f, q, base, sg.cur, rows, hl, hr, ctrl, sp.timeout_ns)) return;
-            float nxt[4];
+            float nxt[ZS][4];
             float r = 0.f;
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                float nb[2 * D];
-                sg.nbk(sg.cur, rows, hl, hr, k, nb);
-                const unsigned c = (sg.code >> (8 * k)) & 0xFFu;
-                const float v = eval_state<float, D>(sg.cur[k], nb, c, sg.R[k], (int)((sg.act >> (8 * k)) & 0xFFu),
-                                                     wm, wp, wst, g);
-                nxt[k] = v;
-                if (!(c & OBST)) {
-                    const float dv = abs_diff(v, sg.cur[k]);
-                    r = dv > r ? dv : r;
+            for (int i = 0; i < ZS; i++)
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    float nb[2 * D];
+                    sg.nbk(sg.cur, rows, hl, hr, i, k, nb);
+                    const unsigned c = (sg.code[i] >> (8 * k)) & 0xFFu;
+                    const float v = eval_state<float, D>(sg.cur[i][k], nb, c, sg.R[i][k],
+                                                         (int)((sg.act[i] >> (8 * k)) & 0xFFu), wm, wp, wst, g);
+                    nxt[i][k] = v;
+                    if (sg.valid[i] && !(c & OBST)) {
+                        const float dv = abs_diff(v, sg.cur[i][k]);
+                        r = dv > r ? dv : r;
+                    }
                 }
-            }
-            if (!sg.valid) r = 0.f;
             if (chk) {
                 const int nf = arv.check(pk, ctrl, sp.timeout_ns);
                 if (nf < 0) return;
                 if (nf == 0) {  // sweep q - kLag met eval_tol: its result is V_{q-kLag+1}
-                    sg.own_values(f, q - kLag + 1, sg.cur);
+                    sg.own_values_all(f, q - kLag + 1, sg.cur);
                     rres = rh[kLag - 1];
                     rq = q - kLag + 1;
                     eval_ok = 1;
@@ -628,7 +711,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, Sol
             sg.publish(f, q + 1, base, nxt);
             arv.arrive(warp_open(r, f.eval_tol_bits));
 #pragma unroll
-            for (int k = 0; k < 4; k++) sg.cur[k] = nxt[k];
+            for (int i = 0; i < ZS; i++)
+#pragma unroll
+                for (int k = 0; k < 4; k++) sg.cur[i][k] = nxt[i][k];
 #pragma unroll
             for (int i = kLag - 1; i > 0; i--) rh[i] = rh[i - 1];
             rh[0] = r;
@@ -646,7 +731,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, Sol
                     if (nf == 0 && !eval_ok) {
                         eval_ok = 1;
                         rq = sweep + 1;
-                        if (rq != q) sg.own_values(f, rq, sg.cur);
+                        if (rq != q) sg.own_values_all(f, rq, sg.cur);
                         const unsigned back = q - 1 - sweep;   // 0 .. kLag-1
 #pragma unroll
                         for (int i2 = 0; i2 < kLag; i2++)
@@ -662,24 +747,29 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, Sol
             if (arv.check_next(ctrl, sp.timeout_ns) < 0) return;
         const unsigned hq = q;  // highest tag sequence written so far
         // sg.cur now holds V_rq, the values of this evaluation
-        // improvement on V_rq (tag base + rq, buffer rq mod 3)
+        // improvement on V_rq (tag base + rq, buffer rq mod kRing)
         unsigned changed = 0;
         {
-            float rows[NR][4], hl, hr;
+            float rows[ZS][NR][4], hl[ZS], hr[ZS];
             if (!sg.gather(f, rq, base, sg.cur, rows, hl, hr, ctrl, sp.timeout_ns)) return;
-            unsigned act = 0;
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                float nb[2 * D];
-                sg.nbk(sg.cur, rows, hl, hr, k, nb);
-                const unsigned c = (sg.code >> (8 * k)) & 0xFFu;
-                const int old = (int)((sg.act >> (8 * k)) & 0xFFu);
-                const int a = improve_state<D>(nb, sg.cur[k], c, sg.R[k], old, false, margin, wm, wp, wst, g,
-                                               changed);
-                act |= (unsigned)a << (8 * k);
+            for (int i = 0; i < ZS; i++) {
+                unsigned act = 0, ch = 0;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    float nb[2 * D];
+                    sg.nbk(sg.cur, rows, hl, hr, i, k, nb);
+                    const unsigned c = (sg.code[i] >> (8 * k)) & 0xFFu;
+                    const int old = (int)((sg.act[i] >> (8 * k)) & 0xFFu);
+                    const int a = improve_state<D>(nb, sg.cur[i][k], c, sg.R[i][k], old, false, margin, wm, wp, wst,
+                                                   g, ch);
+                    act |= (unsigned)a << (8 * k);
+                }
+                if (sg.valid[i]) {
+                    sg.act[i] = act;
+                    changed += ch;
+                }
             }
-            if (sg.valid) sg.act = act;
-            else changed = 0;
         }
         // the next evaluation starts from V_rq republished as sequence hq + 1
         q = hq + 1;
@@ -693,12 +783,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, Sol
         if (moved == 0) { conv = eval_ok; break; }
         if (!eval_ok) break;
     }
-    if (sg.valid) {
-        *reinterpret_cast<float4 *>(f.V + sg.s0) = make_float4(sg.cur[0], sg.cur[1], sg.cur[2], sg.cur[3]);
-        *reinterpret_cast<unsigned *>(f.pi + sg.s0) = sg.act;
-    } else {
-        rres = 0.f;
-    }
+#pragma unroll
+    for (int i = 0; i < ZS; i++)
+        if (sg.valid[i]) {
+            *reinterpret_cast<float4 *>(f.V + sg.s0[i]) =
+                make_float4(sg.cur[i][0], sg.cur[i][1], sg.cur[i][2], sg.cur[i][3]);
+            *reinterpret_cast<unsigned *>(f.pi + sg.s0[i]) = sg.act[i];
+        }
     // sweeps: greedy + evaluations + improvements; backups: |S||A| per greedy
     // or improvement sweep, |S| per evaluation sweep
     flow_finish(ctrl, rres, sp.timeout_ns, NW, gw == 0 && lane == 0, 1 + evals + round, conv,
@@ -707,40 +798,76 @@ __global__ void __launch_bounds__(kMaxThreads, 1) flow_pi_kernel(FlowArgs f, Sol
 }
 
 // Launch shape: one block per SM (as far as the warps go), every block with
-// the same number of warps, one warp per 32 consecutive segments. Sweeps
+// the same number of warps, one warp per 32 consecutive columns. Sweeps
 // move at the pace of the busiest SM, so the warps are spread evenly.
-static bool flow_shape(const Factors &F, int &block, int &grid) {
-    const long long nwarps = (F.nstates / 4 + 31) / 32;
+struct FlowShape {
+    int zs, block, grid, slice, nz, ncols;
+};
+
+template <int D, int ZS>
+static bool shape_for(const Factors &F, FlowShape &s) {
+    s.zs = ZS;
+    s.slice = D == 1 ? (int)(F.nstates / 4) : (int)(F.stride[0] / 4);
+    s.nz = D == 1 ? 1 : (int)F.shape[0];
+    const long long ncols = (long long)s.slice * ((s.nz + ZS - 1) / ZS);
+    const long long nwarps = (ncols + 31) / 32;
     const long long w = (nwarps + F.num_sms - 1) / F.num_sms;
-    if (w < 1 || w > kMaxWarps) return false;
-    block = 32 * (int)w;
-    grid = (int)((nwarps + w - 1) / w);
-    return true;
+    if (w < 1 || w > ColWarps<ZS>::value || ncols > (1ll << 30)) return false;
+    s.ncols = (int)ncols;
+    s.block = 32 * (int)w;
+    s.grid = (int)((nwarps + w - 1) / w);
+    if (s.grid > F.num_sms) return false;
+    // both kernels keep one such block per SM resident
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, flow_vi_kernel<D, ZS>, s.block, 0) != cudaSuccess) a = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, flow_pi_kernel<D, ZS>, s.block, 0) != cudaSuccess) b = 0;
+    return a >= 1 && b >= 1;
 }
 
-// Both kernels keep one block of up to kMaxThreads threads per SM resident.
+#ifndef CPMDP_FLOW_ZS
+#define CPMDP_FLOW_ZS 1
+#endif
+
+// Column height: the preferred one if the grid fits, else the next that does.
 template <int D>
-static bool flow_resident() {
-    static int ok = -1;
-    if (ok < 0) {
-        int a = 0, b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, flow_vi_kernel<D>, kMaxThreads, 0) != cudaSuccess) a = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, flow_pi_kernel<D>, kMaxThreads, 0) != cudaSuccess) b = 0;
-        ok = (a >= 1 && b >= 1) ? 1 : 0;
+static bool flow_pick(const Factors &F, FlowShape &s) {
+    if (D == 1) return shape_for<D, 1>(F, s);
+    const int order[3] = {CPMDP_FLOW_ZS, CPMDP_FLOW_ZS == 1 ? 2 : 1, CPMDP_FLOW_ZS == 4 ? 2 : 4};
+    for (int zs : order) {
+        if (zs == 1 && shape_for<D, 1>(F, s)) return true;
+        if (zs == 2 && shape_for<D, D == 1 ? 1 : 2>(F, s)) return true;
+        if (zs == 4 && shape_for<D, D == 1 ? 1 : 4>(F, s)) return true;
     }
-    return ok == 1;
+    return false;
+}
+
+static bool flow_pick_any(const Factors &F, FlowShape &s) {
+    switch (F.ndim) {
+        case 1: return flow_pick<1>(F, s);
+        case 2: return flow_pick<2>(F, s);
+        case 3: return flow_pick<3>(F, s);
+        default: return false;
+    }
+}
+
+template <int D, int ZS>
+static cudaError_t launch_zs(const FlowShape &s, bool pim, FlowArgs &f, SolveParams &spc, Ctrl *ctrl, cudaStream_t st) {
+    void *args[] = {(void *)&f, (void *)&spc, (void *)&ctrl};
+    const void *kern = pim ? (const void *)flow_pi_kernel<D, ZS> : (const void *)flow_vi_kernel<D, ZS>;
+    return cudaLaunchCooperativeKernel(kern, dim3(s.grid), dim3(s.block), args, 0, st);
 }
 
 template <int D>
-static cudaError_t launch_flow(const Factors &F, bool pim, const FlowArgs &fa, const SolveParams &sp, Ctrl *ctrl,
+static cudaError_t launch_flow(const FlowShape &s, bool pim, const FlowArgs &fa, const SolveParams &sp, Ctrl *ctrl,
                                cudaStream_t st) {
-    int block = 0, grid = 0;
-    if (!flow_shape(F, block, grid) || !flow_resident<D>()) return cudaErrorCooperativeLaunchTooLarge;
     FlowArgs f = fa;
     SolveParams spc = sp;
-    void *args[] = {(void *)&f, (void *)&spc, (void *)&ctrl};
-    const void *kern = pim ? (const void *)flow_pi_kernel<D> : (const void *)flow_vi_kernel<D>;
-    return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(block), args, 0, st);
+    f.slice = s.slice;
+    f.nz = s.nz;
+    f.ncols = s.ncols;
+    if (s.zs == 1 || D == 1) return launch_zs<D, 1>(s, pim, f, spc, ctrl, st);
+    if (s.zs == 2) return launch_zs<D, D == 1 ? 1 : 2>(s, pim, f, spc, ctrl, st);
+    return launch_zs<D, D == 1 ? 1 : 4>(s, pim, f, spc, ctrl, st);
 }
 
 // Bits of the smallest non-negative float >= t (t > 0; +inf above the
@@ -761,15 +888,8 @@ bool flow_eligible(const Factors &F, bool policy_iteration, const void *V, const
     if (F.shape[F.ndim - 1] % 4 != 0 || F.nstates % 4 != 0 || F.nstates >= (1ll << 30)) return false;
     if (((uintptr_t)V & 15u) != 0) return false;
     if (policy_iteration && ((uintptr_t)pi & 3u) != 0) return false;
-    int block = 0, grid = 0;
-    if (!flow_shape(F, block, grid) || grid > F.num_sms) return false;
-    bool res = false;
-    switch (F.ndim) {
-        case 1: res = flow_resident<1>(); break;
-        case 2: res = flow_resident<2>(); break;
-        default: res = flow_resident<3>(); break;
-    }
-    if (!res) return false;
+    FlowShape s;
+    if (!flow_pick_any(F, s)) return false;
     // tags (base <= 2^30, plus the sweeps of one launch) stay below 2^32 - 1
     const long long sweeps = policy_iteration
                                  ? (long long)o.max_rounds * ((long long)o.max_eval_iter + 2) + 2
@@ -800,11 +920,13 @@ cpmdp_status flow_solve(const Factors &F, bool policy_iteration, float *V, uint8
     fa.nsegs = (int)(F.nstates / 4);
     CPMDP_CUDA(cudaMemsetAsync(F.d_flow, 0, flow_counter_bytes(), st));
     if (fa.trace) CPMDP_CUDA(cudaMemsetAsync(fa.trace, 0, (size_t)sp.max_iter * sizeof(double), st));
+    FlowShape shp;
+    if (!flow_pick_any(F, shp)) CPMDP_CUDA(cudaErrorCooperativeLaunchTooLarge);
     cudaError_t e;
     switch (F.ndim) {
-        case 1: e = launch_flow<1>(F, policy_iteration, fa, sp, F.d_ctrl, st); break;
-        case 2: e = launch_flow<2>(F, policy_iteration, fa, sp, F.d_ctrl, st); break;
-        default: e = launch_flow<3>(F, policy_iteration, fa, sp, F.d_ctrl, st); break;
+        case 1: e = launch_flow<1>(shp, policy_iteration, fa, sp, F.d_ctrl, st); break;
+        case 2: e = launch_flow<2>(shp, policy_iteration, fa, sp, F.d_ctrl, st); break;
+        default: e = launch_flow<3>(shp, policy_iteration, fa, sp, F.d_ctrl, st); break;
     }
     CPMDP_CUDA(e);
     return CPMDP_OK;

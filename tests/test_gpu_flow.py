@@ -6,9 +6,10 @@ Both solvers run the same Jacobi iterates with the same per-state
 arithmetic and stop at the same sweep, so their results must be equal bit
 for bit: values, policies, sweep counts, rounds, residuals and the
 per-sweep residual trace. fused=1 picks the barrier-free solver where it is
-eligible (1 to 3 dimensions, rows a multiple of 4 states, one thread per 4
-states in one co-resident grid); fused=2 always takes the grid-barrier
-solver. The oracle checks the k-sweep iterates directly.
+eligible (1 to 3 dimensions, rows a multiple of 4 states, one thread per
+column of 1, 2 or 4 segments of 4 states in one co-resident grid); fused=2
+always takes the grid-barrier solver. The oracle checks the k-sweep
+iterates directly.
 """
 import numpy as np
 import pytest
@@ -209,3 +210,72 @@ def test_ineligible_shapes_use_grid_barrier(cp):
         r = cp.value_iteration(f, prec, V, None)
         assert r["solver"] == cp.SOLVER_GRID_BARRIER, shape
         f.close()
+
+
+# Grids past what one 4-state segment per thread covers (152 SMs x 14 warps
+# x 32 lanes x 4 = 272,384 states) run with columns of 2 or 4 segments
+# stacked along dimension 0 in one thread:
+#   (71, 64, 64)  290,816 states: columns of 2, the last group one slice short
+#   (73, 72, 72)  378,432 states: columns of 4, the last group three slices short
+#   (600, 600)    360,000 states: 2-D, columns of 4 rows
+COLUMN_SHAPES = [(71, 64, 64), (73, 72, 72), (600, 600)]
+
+
+@pytest.mark.parametrize("shape", COLUMN_SHAPES)
+def test_columns_equal_grid_barrier_solver(cp, shape):
+    import torch
+    gw = _world(shape, seed=21 + shape[0])
+    f = cp.build_factors(gw, device=0)
+    Va, pa, ta, ra = _vi(cp, f, gw, 1)
+    Vb, pb, tb, rb = _vi(cp, f, gw, 2)
+    assert ra["solver"] == cp.SOLVER_BARRIER_FREE and rb["solver"] == cp.SOLVER_GRID_BARRIER
+    assert ra["iterations"] == rb["iterations"] and ra["residual"] == rb["residual"]
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+    assert np.array_equal(pa, pb)
+    k = ra["iterations"]
+    assert np.array_equal(ta[:k], tb[:k])
+    # (the large 2-D grid needs hundreds of improvement rounds: stop both after 5)
+    kw = dict(max_rounds=5) if len(shape) == 2 else {}
+    out = {}
+    for fused in (1, 2):
+        V = torch.zeros(gw.nstates, dtype=torch.float32, device="cuda")
+        pi = torch.zeros(gw.nstates, dtype=torch.uint8, device="cuda")
+        r = cp.policy_iteration(f, cp.F32, V, pi, opts=cp.default_opts(fused=fused, **kw), raise_on_noconv=False)
+        out[fused] = (V.cpu().numpy(), pi.cpu().numpy(), r)
+    (Va, pa, ra), (Vb, pb, rb) = out[1], out[2]
+    assert ra["solver"] == cp.SOLVER_BARRIER_FREE
+    for key in ("status", "iterations", "rounds", "eval_sweeps", "residual", "backups"):
+        assert ra[key] == rb[key], (key, ra[key], rb[key])
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+    assert np.array_equal(pa, pb)
+    f.close()
+
+
+def test_columns_k_sweeps_and_limits(cp, oc):
+    """Columns of 4 (73 x 72 x 72): k Jacobi sweeps equal the grid-barrier
+    solver's and the oracle's; a PI evaluation limit ends both the same way."""
+    import torch
+    gw = _world((73, 72, 72), seed=4)
+    f = cp.build_factors(gw, device=0)
+    for k in (1, 2, 3, 5):
+        Va, _, ta, ra = _vi(cp, f, gw, 1, max_iter=k, tol=1e-30, certify=0)
+        Vb, _, tb, rb = _vi(cp, f, gw, 2, max_iter=k, tol=1e-30, certify=0)
+        assert ra["solver"] == cp.SOLVER_BARRIER_FREE and ra["iterations"] == k
+        assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32)) and np.array_equal(ta, tb)
+    Vo = np.zeros(gw.nstates)
+    for _ in range(5):
+        Vo, _, _, _ = oc.backup(gw, Vo)
+    eps = 14 * U32 * (np.abs(gw.reward).max() + np.abs(Vo).max() + 1.0)
+    assert np.abs(Va.astype(np.float64) - Vo).max() <= eps * 5
+    out = {}
+    for fused in (1, 2):
+        V = torch.zeros(gw.nstates, dtype=torch.float32, device="cuda")
+        pi = torch.zeros(gw.nstates, dtype=torch.uint8, device="cuda")
+        r = cp.policy_iteration(f, cp.F32, V, pi, opts=cp.default_opts(fused=fused, max_eval_iter=4),
+                                raise_on_noconv=False)
+        out[fused] = (V.cpu().numpy(), pi.cpu().numpy(), r)
+    (Va, pa, ra), (Vb, pb, rb) = out[1], out[2]
+    for key in ("status", "iterations", "rounds", "eval_sweeps", "residual"):
+        assert ra[key] == rb[key], (key, ra[key], rb[key])
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32)) and np.array_equal(pa, pb)
+    f.close()
