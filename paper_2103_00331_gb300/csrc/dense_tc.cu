@@ -71,11 +71,14 @@ __device__ __forceinline__ void sync_for_async() {
     tc::fence_after();
 }
 
-// Intermediate layout: for chain c and pass-B slab q = (i3', i4'), a 16 KB
-// tile of 64 rows (i1) x 16 quads; quad j of row i1 (16 bytes at
-// (c * 4096 + q) * 16384 + (i1 * 16 + j) * 16) holds the bf16 hi parts of
+// Intermediate layout: for chain c and pass-B slab pair P (slabs q = 2P and
+// 2P + 1, q = (i3', i4')), a 32 KB tile of 64 rows (i1) x 16 quad pairs;
+// quad j of row i1 of slab q (16 bytes at (c * 4096 + 2P) * 16384 +
+// ((i1 * 16 + j) * 2 + (q & 1)) * 16) holds the bf16 hi parts of
 // k = i2 = 4j .. 4j+3 followed by their lo parts. Pass A writes whole quads,
-// pass B copies a slab pair (32 KB, contiguous) with one bulk copy.
+// the two slabs of a pair side by side, so two adjacent lanes fill one
+// 32-byte sector; pass B copies a slab pair (32 KB, contiguous) with one
+// bulk copy.
 constexpr int kQuadTileBytes = 16384;
 
 // Quads of one staged item (chain c, slab group starting at b0), those with
@@ -83,7 +86,7 @@ constexpr int kQuadTileBytes = 16384;
 // words) as 16-byte units of the intermediate layout.
 __device__ __forceinline__ void write_quads(uint8_t *T, const uint32_t *stage, int c, int b0, int q_lo, int q_hi,
                                             int tid, int nthreads) {
-    uint8_t *Tc = T + (size_t)c * kSlab * kQuadTileBytes + (size_t)((b0 >> 6) * 16 + ((b0 & 63) >> 2)) * 16;
+    uint8_t *Tc = T + (size_t)c * kSlab * kQuadTileBytes + (size_t)((b0 >> 6) * 16 + ((b0 & 63) >> 2)) * 32;
     for (int q = q_lo + tid; q < q_hi; q += nthreads) {
         const uint32_t w0 = stage[q], w1 = stage[kSlab + q], w2 = stage[2 * kSlab + q], w3 = stage[3 * kSlab + q];
         uint4 v;
@@ -91,7 +94,7 @@ __device__ __forceinline__ void write_quads(uint8_t *T, const uint32_t *stage, i
         v.y = (w2 & 0xFFFFu) | (w3 << 16);
         v.z = (w0 >> 16) | (w1 & 0xFFFF0000u);
         v.w = (w2 >> 16) | (w3 & 0xFFFF0000u);
-        *reinterpret_cast<uint4 *>(Tc + (size_t)q * kQuadTileBytes) = v;
+        *reinterpret_cast<uint4 *>(Tc + (size_t)(q >> 1) * (2 * kQuadTileBytes) + (q & 1) * 16) = v;
     }
 }
 
@@ -326,8 +329,8 @@ __global__ void __launch_bounds__(128, 2) dense_pass_b(const uint8_t *__restrict
 #pragma unroll 4
                     for (int idx = tid; idx < 2 * 1024; idx += 128) {
                         const uint4 w = raw[idx];
-                        const uint32_t s2 = idx >> 10, rem = idx & 1023;
-                        const uint32_t row = s2 * 64 + (rem >> 4), k = (rem & 15) * 4;
+                        const uint32_t s2 = idx & 1, i1 = idx >> 5, j = (idx >> 1) & 15;
+                        const uint32_t row = s2 * 64 + i1, k = j * 4;
                         const uint32_t off = tc::sw128_off(row, k);
                         *reinterpret_cast<uint2 *>(sZ + off) = make_uint2(w.x, w.y);
                         *reinterpret_cast<uint2 *>(sZ + kPairBytes + off) = make_uint2(w.z, w.w);
