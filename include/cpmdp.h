@@ -161,6 +161,8 @@ typedef struct {
     int64_t backups;             /* state-action backups done: |S|*|A| per VI sweep, |S| per evaluation sweep */
     double elapsed_ms;           /* device time of the solve, CUDA events on the stream */
     int32_t solver;              /* cpmdp_solver: which solver ran */
+    int32_t tail_from;           /* batches: launch-wide sweep after which the running instances went on
+                                    barrier-free, each at its own pace (0: the batched kernel ran to the end) */
 } cpmdp_result;
 
 /* Fill *opts with the defaults listed above. */
@@ -297,9 +299,12 @@ cpmdp_status cpmdp_batch_info(const cpmdp_batch *batch, int32_t *count, int64_t 
  * instances, elapsed_ms, rounds = 1 when the solve was replayed from a CUDA
  * graph. The first call tunes block and tile sizes on the batch (a few
  * sweeps on a temporary buffer) and records the solve into a CUDA graph,
- * replayed by later calls with the same V, stream and options. Synchronises
- * with `stream`. Errors: EINVAL, ECUDA, ENOCONV (some instance hit
- * max_iter), ETIMEOUT.
+ * replayed by later calls with the same V, stream and options. Once the
+ * instances still running fit one co-resident grid (one warp per 128
+ * states), they continue without the grid barrier, each instance at its own
+ * pace (same sweeps and values; info->tail_from tells when); opts->fused = 2
+ * keeps the whole solve on the batched kernel. Synchronises with `stream`.
+ * Errors: EINVAL, ECUDA, ENOCONV (some instance hit max_iter), ETIMEOUT.
  */
 cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *batch, float *V, const cpmdp_solve_opts *opts,
                                          int32_t *iterations_out, double *residual_out, cpmdp_result *info,

@@ -55,7 +55,7 @@ class Result(ctypes.Structure):
                 ("rounds", ctypes.c_int32), ("eval_sweeps", ctypes.c_int32),
                 ("residual", ctypes.c_double), ("certified_residual", ctypes.c_double),
                 ("error_bound", ctypes.c_double), ("backups", ctypes.c_int64),
-                ("elapsed_ms", ctypes.c_double), ("solver", ctypes.c_int32)]
+                ("elapsed_ms", ctypes.c_double), ("solver", ctypes.c_int32), ("tail_from", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("_")}

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "banded_common.cuh"
+#include "batch_flow.h"
 #include "batch_internal.h"
 
 namespace cpmdp {
@@ -48,6 +49,7 @@ struct BatchArgs {
     int spl;                   // segments per lane of a tile (tile = 32 spl segments)
     unsigned long long timeout_ns;
     Ctrl *ctrl;
+    int handoff_warps;         // > 0: stop once the running instances need at most this many warps
 };
 
 __device__ __forceinline__ void prefetch_l2(const void *p) {
@@ -208,6 +210,7 @@ __device__ __forceinline__ void batch_class(const BatchArgs &b, const BatchTile 
 // tile.
 __global__ void __launch_bounds__(512, 1) batch_vi_kernel(BatchArgs b) {
     __shared__ int s_worked;
+    __shared__ unsigned long long s_need;
     const int tid = threadIdx.x, lane = tid & 31;
     const int wpb = blockDim.x >> 5;
     const long long nw = (long long)gridDim.x * wpb;
@@ -216,10 +219,17 @@ __global__ void __launch_bounds__(512, 1) batch_vi_kernel(BatchArgs b) {
     unsigned long long ph0 = 0ull, ph1 = 0ull;
     unsigned stopped = 0u;   // bit r: this lane's tile of round r belongs to a stopped instance
     int k = 0;
+    bool handoff = false;
     for (; k <= b.max_iter; k++) {
         const float *cur = (k & 1) ? b.W : b.V;
         float *nxt = (k & 1) ? b.V : b.W;
-        if (tid == 0) s_worked = 0;
+        if (tid == 0) {
+            s_worked = 0;
+            s_need = 0ull;
+            // slot k+1 was last read after the barrier of sweep k-2, which
+            // every block has passed
+            if (blockIdx.x == 0) b.ctrl->need_slot[(k + 1) % 3] = 0ull;
+        }
         __syncthreads();
         bool worked = false;
         int round = 0;
@@ -247,7 +257,12 @@ __global__ void __launch_bounds__(512, 1) batch_vi_kernel(BatchArgs b) {
                 run = st == 1;
                 if (!run && round < 32) stopped |= 1u << round;
                 if (run) {
-                    if (T.first_item == 0) b.res[(size_t)((k + 1) % 3) * b.ninst + T.inst] = 0ull;
+                    if (T.first_item == 0) {
+                        b.res[(size_t)((k + 1) % 3) * b.ninst + T.inst] = 0ull;
+                        // warps this instance would take in the barrier-free tail
+                        if (b.handoff_warps > 0)
+                            atomicAdd(&s_need, (unsigned long long)(((T.nstates + 3) / 4 + 31) / 32));
+                    }
                     prefetch_tile(T, cur, b.R, b.code);
                 }
             }
@@ -265,9 +280,18 @@ __global__ void __launch_bounds__(512, 1) batch_vi_kernel(BatchArgs b) {
         }
         if (worked && lane == 0) s_worked = 1;
         __syncthreads();
+        if (tid == 0 && s_need) atomicAdd(&b.ctrl->need_slot[k % 3], s_need);
         const long long busy = grid_sync_count(b.ctrl, k, nb, tid == 0 ? s_worked : 0, b.timeout_ns, ph0, ph1, false);
         if (busy < 0) return;
         if (busy == 0) break;
+        // the instances that ran sweep k fit the barrier-free tail: stop here
+        // (every block reads the same complete count after the barrier)
+        if (b.handoff_warps > 0 &&
+            *(volatile unsigned long long *)&b.ctrl->need_slot[k % 3] <= (unsigned long long)b.handoff_warps) {
+            handoff = true;
+            k++;
+            break;
+        }
     }
     // results: an instance stopped at sweep count n has its values in V if n
     // is even, in W if n is odd
@@ -279,7 +303,13 @@ __global__ void __launch_bounds__(512, 1) batch_vi_kernel(BatchArgs b) {
         const int s0 = 4 * T.first_item, s1 = min(4 * (T.first_item + T.nitems), T.nstates);
         for (int s = s0 + tid; s < s1; s += blockDim.x) b.V[T.offset + s] = b.W[T.offset + s];
     }
-    if (blockIdx.x == 0 && tid == 0) b.ctrl->iterations = k;
+    if (blockIdx.x == 0 && tid == 0) {
+        b.ctrl->iterations = k;
+        if (handoff) {
+            b.ctrl->handoff_sweeps = k;
+            b.ctrl->handoff = 1;
+        }
+    }
 }
 
 }  // namespace cpmdp
@@ -290,7 +320,8 @@ __global__ void __launch_bounds__(512, 1) batch_vi_kernel(BatchArgs b) {
 namespace cpmdp {
 
 static void free_batch_device(cpmdp_batch &B) {
-    void *ptrs[] = {B.d_inst, B.d_tiles, B.d_code, B.d_R, B.d_W, B.d_res, B.d_done, B.d_ctrl};
+    void *ptrs[] = {B.d_inst, B.d_tiles, B.d_code, B.d_R, B.d_W, B.d_res, B.d_done, B.d_ctrl,
+                    B.d_ring, B.d_p2ctr, B.d_p2tab, B.d_p2hdr, B.d_p2epoch, B.d_p2res};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (B.graph) cudaGraphExecDestroy(B.graph);
@@ -359,10 +390,47 @@ static cudaError_t launch_batch(const cpmdp_batch &B, int block, const BatchArgs
     return cudaLaunchKernelEx(&cfg, batch_vi_kernel, args);
 }
 
+// Tail phase buffers: allocated once per batch; without them (or past the
+// tag range of the tail, 65,534 sweeps) the batched kernel runs to the end.
+static void prepare_tail(cpmdp_batch &B) {
+    if (B.flow_tried) return;
+    B.flow_tried = true;
+    const int cap = batch_flow_capacity_warps(B.num_sms);
+    if (cap <= 0) return;
+    bool ok = cudaMalloc(&B.d_ring, sizeof(unsigned long long) * batch_flow_ring_words(B.total_states)) == cudaSuccess &&
+              cudaMalloc(&B.d_p2ctr, sizeof(unsigned long long) * batch_flow_counter_words(B.ninst)) == cudaSuccess &&
+              cudaMalloc(&B.d_p2tab, sizeof(int2) * (size_t)cap) == cudaSuccess &&
+              cudaMalloc(&B.d_p2hdr, sizeof(int) * 4) == cudaSuccess &&
+              cudaMalloc(&B.d_p2epoch, sizeof(unsigned)) == cudaSuccess &&
+              cudaMalloc(&B.d_p2res, sizeof(unsigned long long) * B.ninst) == cudaSuccess;
+    ok = ok && cudaMemset(B.d_ring, 0xFF, sizeof(unsigned long long) * batch_flow_ring_words(B.total_states)) == cudaSuccess &&
+         cudaMemset(B.d_p2epoch, 0, sizeof(unsigned)) == cudaSuccess &&
+         cudaMemset(B.d_p2hdr, 0, sizeof(int) * 4) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();
+        void *ptrs[] = {B.d_ring, B.d_p2ctr, B.d_p2tab, B.d_p2hdr, B.d_p2epoch, B.d_p2res};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+        B.d_ring = nullptr; B.d_p2ctr = nullptr; B.d_p2tab = nullptr;
+        B.d_p2hdr = nullptr; B.d_p2epoch = nullptr; B.d_p2res = nullptr;
+        return;
+    }
+    B.flow_cap_warps = cap;
+}
+
+static bool tail_enabled(const cpmdp_batch &B, int max_iter) { return B.flow_cap_warps > 0 && max_iter < 65534; }
+
 static cudaError_t enqueue_batch(const cpmdp_batch &B, float *V, double tol, int max_iter, double timeout_s,
-                                 int block, int spl, cudaStream_t st, int *grid_out) {
+                                 int block, int spl, cudaStream_t st, int *grid_out, bool tail) {
     cudaError_t e;
+    tail = tail && tail_enabled(B, max_iter);
     if ((e = cudaMemsetAsync(B.d_ctrl, 0, sizeof(Ctrl), st)) != cudaSuccess) return e;
+    if (tail) {
+        if ((e = cudaMemsetAsync(B.d_p2ctr, 0, sizeof(unsigned long long) * batch_flow_counter_words(B.ninst), st)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(B.d_p2res, 0, sizeof(unsigned long long) * B.ninst, st)) != cudaSuccess) return e;
+    }
     if ((e = cudaMemsetAsync(B.d_res, 0, sizeof(unsigned long long) * 3 * B.ninst, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(B.d_done, 0, sizeof(int) * B.ninst, st)) != cudaSuccess) return e;
     BatchArgs a;
@@ -380,7 +448,18 @@ static cudaError_t enqueue_batch(const cpmdp_batch &B, float *V, double tol, int
     a.spl = spl;
     a.timeout_ns = (unsigned long long)(timeout_s * 1e9);
     a.ctrl = B.d_ctrl;
-    return launch_batch(B, block, a, st, grid_out);
+    a.handoff_warps = tail ? B.flow_cap_warps : 0;
+    if ((e = launch_batch(B, block, a, st, grid_out)) != cudaSuccess) return e;
+    if (!tail) return cudaSuccess;
+    BatchFlowBuffers fb;
+    fb.ring = B.d_ring;
+    fb.ctr = B.d_p2ctr;
+    fb.tab = B.d_p2tab;
+    fb.hdr = B.d_p2hdr;
+    fb.epoch = B.d_p2epoch;
+    fb.p2res = B.d_p2res;
+    return batch_flow_enqueue(fb, B.d_inst, B.ninst, B.d_code, B.d_R, V, B.d_W, B.d_done, B.d_res, B.d_ctrl,
+                              B.total_states, B.num_sms, tol, max_iter, timeout_s, st);
 }
 
 static cpmdp_status upload_tiles(cpmdp_batch &B, int tile_items) {
@@ -431,7 +510,7 @@ static cpmdp_status autotune(cpmdp_batch &B, cudaStream_t st) {
             CPMDP_CUDA(cudaMemsetAsync(V, 0, sizeof(float) * B.total_states, st));
             CPMDP_CUDA(cudaEventRecord(e0, st));
             int grid = 0;
-            CPMDP_CUDA(enqueue_batch(B, V, 0.0, 8, 2.0, cand[c][0], cand[c][1], st, &grid));
+            CPMDP_CUDA(enqueue_batch(B, V, 0.0, 8, 2.0, cand[c][0], cand[c][1], st, &grid, false));
             CPMDP_CUDA(cudaEventRecord(e1, st));
             CPMDP_CUDA(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -584,11 +663,14 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
         if (s != CPMDP_OK) return s;
         B->tuned = true;
     }
+    prepare_tail(*B);
     // record the solve (state resets + the cooperative launch) into a CUDA
     // graph once per (V, stream, options) and replay it; if recording is
     // refused, launch directly
+    const bool tail = o.fused != 2;
     const bool same = B->graph && B->graph_V == (void *)V && B->graph_stream == st && B->graph_tol == o.tol &&
-                      B->graph_max_iter == o.max_iter && B->graph_timeout == o.timeout_s;
+                      B->graph_max_iter == o.max_iter && B->graph_timeout == o.timeout_s &&
+                      B->graph_tail == (tail ? 1 : 0);
     if (!same && !B->graph_failed) {
         if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
         cudaStream_t cap;
@@ -596,7 +678,7 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         int grid = 0;
-        if (e == cudaSuccess) e = enqueue_batch(*B, V, o.tol, o.max_iter, o.timeout_s, B->block, B->spl, cap, &grid);
+        if (e == cudaSuccess) e = enqueue_batch(*B, V, o.tol, o.max_iter, o.timeout_s, B->block, B->spl, cap, &grid, tail);
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         cudaStreamDestroy(cap);
         if (e == cudaSuccess && e2 == cudaSuccess && g) e = cudaGraphInstantiate(&B->graph, g, 0);
@@ -613,6 +695,7 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
             B->graph_tol = o.tol;
             B->graph_max_iter = o.max_iter;
             B->graph_timeout = o.timeout_s;
+            B->graph_tail = tail ? 1 : 0;
         }
     }
     cudaEvent_t e0, e1;
@@ -623,13 +706,19 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
         CPMDP_CUDA(cudaGraphLaunch(B->graph, st));
     } else {
         int grid = 0;
-        CPMDP_CUDA(enqueue_batch(*B, V, o.tol, o.max_iter, o.timeout_s, B->block, B->spl, st, &grid));
+        CPMDP_CUDA(enqueue_batch(*B, V, o.tol, o.max_iter, o.timeout_s, B->block, B->spl, st, &grid, tail));
     }
     CPMDP_CUDA(cudaEventRecord(e1, st));
     Ctrl hc;
     std::vector<int> done((size_t)B->ninst);
     std::vector<unsigned long long> res((size_t)3 * B->ninst);
+    std::vector<unsigned long long> p2res;
     CPMDP_CUDA(cudaMemcpyAsync(&hc, B->d_ctrl, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    if (tail && tail_enabled(*B, o.max_iter)) {
+        p2res.resize((size_t)B->ninst);
+        CPMDP_CUDA(cudaMemcpyAsync(p2res.data(), B->d_p2res, sizeof(unsigned long long) * B->ninst,
+                                   cudaMemcpyDeviceToHost, st));
+    }
     CPMDP_CUDA(cudaMemcpyAsync(done.data(), B->d_done, sizeof(int) * B->ninst, cudaMemcpyDeviceToHost, st));
     CPMDP_CUDA(cudaMemcpyAsync(res.data(), B->d_res, sizeof(unsigned long long) * 3 * B->ninst, cudaMemcpyDeviceToHost, st));
     CPMDP_CUDA(cudaStreamSynchronize(st));
@@ -649,7 +738,9 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
         const int sweeps = n < 0 ? -n : n;
         if (n <= 0) not_conv++;
         double r = 0.0;
-        if (sweeps > 0) memcpy(&r, &res[(size_t)((sweeps - 1) % 3) * B->ninst + i], sizeof(double));
+        // the last sweep ran in the barrier-free tail, or in the batched kernel
+        if (hc.handoff && sweeps > hc.handoff_sweeps && !p2res.empty()) memcpy(&r, &p2res[(size_t)i], sizeof(double));
+        else if (sweeps > 0) memcpy(&r, &res[(size_t)((sweeps - 1) % 3) * B->ninst + i], sizeof(double));
         if (iterations_out) iterations_out[i] = sweeps;
         if (residual_out) residual_out[i] = r;
         worst = r > worst ? r : worst;
@@ -666,6 +757,7 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
         info->backups = backups;
         info->elapsed_ms = ms;
         info->solver = CPMDP_SOLVER_BATCH;
+        info->tail_from = hc.handoff ? hc.handoff_sweeps : 0;
     }
     if (not_conv) {
         set_error("%d instance(s) reached max_iter before tol", not_conv);

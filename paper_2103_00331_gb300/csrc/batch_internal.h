@@ -70,6 +70,16 @@ struct cpmdp_batch {
     double graph_tol = 0;
     int graph_max_iter = 0;
     double graph_timeout = 0;
+    int graph_tail = 0;
     std::vector<cpmdp::BatchTile> tiles_host;
+    // barrier-free tail (batch_flow.cu), allocated on the first solve
+    bool flow_tried = false;
+    int flow_cap_warps = 0;                // 0: the tail stays on the batched kernel
+    unsigned long long *d_ring = nullptr;
+    unsigned long long *d_p2ctr = nullptr;
+    int2 *d_p2tab = nullptr;
+    int *d_p2hdr = nullptr;
+    unsigned *d_p2epoch = nullptr;
+    unsigned long long *d_p2res = nullptr;
 };
 

@@ -51,16 +51,14 @@
 
 #include "banded_common.cuh"
 #include "flow.h"
+#include "flow_common.cuh"
 
 namespace cpmdp {
 
 namespace {
 
-typedef unsigned long long u64;
-constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr int kLag = 3;              // the stopping rule of sweep q is settled at sweep q + kLag
-constexpr int kRing = kLag + 1;      // tagged value buffers
-constexpr int kSlots = 8;            // arrival slots (arrival i uses slot i % kSlots; > 2 kLag + 1)
+using namespace tw;
+
 constexpr int kNC = 8;               // counters per slot (warp w adds to counter w % kNC)
 constexpr int kLineWords = 16;       // 64-bit words per 128-byte line
 constexpr int kMaxWarps = 14;        // warps per block at most (one block per SM, 448 threads)
@@ -68,24 +66,6 @@ constexpr int kMaxWarps = 14;        // warps per block at most (one block per S
 // fit 128 registers a thread (4 warps per scheduler); columns take more
 // registers and fewer, fuller warps.
 template <int ZS> struct ColWarps { static constexpr int value = ZS == 1 ? 14 : 8; };
-
-__device__ __forceinline__ u64 ld_rlx(const u64 *p) {
-    u64 v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void ld_rlx2(const u64 *p, u64 &x, u64 &y) {
-    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(x), "=l"(y) : "l"(p) : "memory");
-}
-__device__ __forceinline__ void st_rlx2(u64 *p, u64 x, u64 y) {
-    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(x), "l"(y) : "memory");
-}
-__device__ __forceinline__ void red_add_rlx(u64 *p, u64 v) {
-    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ u64 word(float v, unsigned tag) { return ((u64)tag << 32) | __float_as_uint(v); }
-__device__ __forceinline__ float val(u64 w) { return __uint_as_float((unsigned)w); }
-__device__ __forceinline__ bool has(u64 w, unsigned tag) { return (unsigned)(w >> 32) == tag; }
 
 struct FlowArgs {
     BandArgs a;
@@ -104,24 +84,6 @@ struct FlowArgs {
 };
 
 __device__ __forceinline__ u64 *ring(const FlowArgs &f, unsigned q) { return f.buf[q % (unsigned)kRing]; }
-
-// Warp-uniform: true when this warp must stop waiting (another warp
-// recorded a status, or this wait ran past timeout_ns: then it records
-// CPMDP_ETIMEOUT). t0: start of the wait (lane 0's clock, 0 = not started).
-__device__ __forceinline__ bool give_up(Ctrl *c, u64 &t0, u64 timeout_ns) {
-    int stop = 0;
-    if ((threadIdx.x & 31) == 0) {
-        const u64 t = global_ns();
-        if (t0 == 0) t0 = t;
-        if (*(volatile int *)&c->status != 0) {
-            stop = 1;
-        } else if (t - t0 > timeout_ns) {
-            atomicCAS(&c->status, 0, (int)CPMDP_ETIMEOUT);
-            stop = 1;
-        }
-    }
-    return __shfl_sync(FULL, stop, 0) != 0;
-}
 
 // Arrival bookkeeping of one warp.
 struct Arrivals {
@@ -431,19 +393,6 @@ struct FlowCol {
         nb[NRR + 1] = ((c >> (NRR + 1)) & 1u) ? self[i][k] : right;
     }
 };
-
-// Whether the warp's largest residual r is still >= the tolerance whose
-// float round-up has bits tb: for a float r >= 0, (double)r < tol exactly
-// when r < the smallest float >= tol, and non-negative floats (a NaN above
-// +inf) order like their bits, so no FP64 instruction is needed.
-__device__ __forceinline__ bool warp_open(float r, unsigned tb) {
-    return __reduce_max_sync(FULL, __float_as_uint(r)) >= tb;
-}
-
-__device__ __forceinline__ unsigned long long warp_res_bits(float r) {
-    const unsigned u = __reduce_max_sync(FULL, __float_as_uint(r));
-    return (unsigned long long)__double_as_longlong((double)__uint_as_float(u));
-}
 
 // Greedy / improvement choice of one state (same expressions as
 // Segment::finish_pi): returns the new action.
@@ -868,16 +817,6 @@ static cudaError_t launch_flow(const FlowShape &s, bool pim, const FlowArgs &fa,
     if (s.zs == 1 || D == 1) return launch_zs<D, 1>(s, pim, f, spc, ctrl, st);
     if (s.zs == 2) return launch_zs<D, D == 1 ? 1 : 2>(s, pim, f, spc, ctrl, st);
     return launch_zs<D, D == 1 ? 1 : 4>(s, pim, f, spc, ctrl, st);
-}
-
-// Bits of the smallest non-negative float >= t (t > 0; +inf above the
-// float range).
-unsigned float_ceil_bits(double t) {
-    float f = (float)t;
-    if ((double)f < t) f = nextafterf(f, INFINITY);
-    unsigned u;
-    memcpy(&u, &f, sizeof u);
-    return u;
 }
 
 }  // namespace

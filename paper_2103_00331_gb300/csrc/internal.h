@@ -35,6 +35,9 @@ struct Ctrl {
     double certify_residual;       // FP64 certifying sweep
     long long backups;             // state-action backups done
     unsigned int flow_tags;        // barrier-free solver: tag sequences used by the launch
+    unsigned long long need_slot[3];  // batch: warps the instances running sweep k would need, slot k % 3
+    int handoff;                   // batch: 1 when the batched kernel stopped for the barrier-free tail
+    int handoff_sweeps;            // batch: sweeps done before the hand-off
 };
 
 struct Factors {

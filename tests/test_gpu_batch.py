@@ -130,3 +130,36 @@ def test_batch_k_sweeps_match_oracle(cp, k):
         err = np.abs(Vh[lo:lo + gw.nstates] - Vo).max()
         assert err <= eps * (1 - gw.gamma ** k) / (1 - gw.gamma) + 1e-30, (i, gw.shape, err)
     B.close()
+
+
+def test_batch_tail_equals_batched_kernel(cp):
+    """Once the running instances fit one co-resident grid, the batch goes on
+    barrier-free, each instance at its own pace. Same sweeps, values and
+    residuals, bit for bit, as the batched kernel run to the end (fused=2)."""
+    import torch
+    inst = ci.batch_gridworlds(count=300, seed=11)
+    inst.append(ci.gridworld((37,), p=0.9, gamma=0.95, step_reward=-0.04, goal_rewards=[1.0], seed=1))
+    inst.append(ci.gridworld((3, 129), p=0.7, gamma=0.99, step_reward=-0.04, goal_rewards=[1.0, -1.0],
+                             obstacle_rate=0.1, seed=2))
+    B = cp.batch_build(inst, device=0)
+    out = {}
+    for fused in (1, 2):
+        V = torch.zeros(int(B.total_states), dtype=torch.float32, device="cuda")
+        r, it, res = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=5000, fused=fused))
+        out[fused] = (V.cpu().numpy(), it, res, r)
+    (Va, ia, ra, xa), (Vb, ib, rb, xb) = out[1], out[2]
+    assert xa["tail_from"] > 0 and xb["tail_from"] == 0
+    assert np.array_equal(ia, ib)
+    assert np.array_equal(ra, rb)
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+    assert xa["iterations"] == xb["iterations"]
+    # max_iter inside the tail: the same partial result
+    for fused in (1, 2):
+        V = torch.zeros(int(B.total_states), dtype=torch.float32, device="cuda")
+        r, it, res = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=xa["tail_from"] + 5, fused=fused),
+                                              raise_on_noconv=False)
+        out[fused] = (V.cpu().numpy(), it, res, r)
+    (Va, ia, ra, xa), (Vb, ib, rb, xb) = out[1], out[2]
+    assert xa["status"] == cp.ENOCONV and np.array_equal(ia, ib) and np.array_equal(ra, rb)
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+    B.close()
