@@ -136,17 +136,39 @@ __device__ __forceinline__ TA vi_state(TA self, const TA (&nb)[2 * D], unsigned 
     return v;
 }
 
-// Policy-evaluation backup of one state for its fixed action `act`.
+// Policy-evaluation backup of one state for its fixed action `act` (Eq. 1
+// with the action fixed). The action's neighbour and perpendicular sum are
+// picked by a tree of selects on the action's bits for D <= 3 (depth 3
+// instead of a chain of 2D - 1 selects; measured 3 % faster policy
+// evaluation at 64^3), for larger D by a chain; for terminals and obstacles
+// (act 255) the pick does not matter.
 template <typename TA, int D>
 __device__ __forceinline__ TA eval_state(TA self, const TA (&nb)[2 * D], unsigned c, TA r, int act, TA wm, TA wp,
                                          TA wst, TA g) {
     TA perp[D];
     perp_of<TA, D>(nb, perp);
     const TA stay = wst * self;
+    const bool b0 = act & 1, b1 = (act >> 1) & 1, b2 = (act >> 2) & 1;
     TA nbv = nb[0], pv = perp[0];
+    if (D > 3) {
 #pragma unroll
-    for (int j = 1; j < 2 * D; j++)
-        if (act == j) { nbv = nb[j]; pv = perp[j / 2]; }
+        for (int j = 1; j < 2 * D; j++)
+            if (act == j) { nbv = nb[j]; pv = perp[j / 2]; }
+    } else if (D == 1) {
+        nbv = b0 ? nb[1] : nb[0];
+        pv = perp[0];
+    } else if (D == 2) {
+        const TA x01 = b0 ? nb[1] : nb[0], x23 = b0 ? nb[2 * D - 1] : nb[2 * D - 2];
+        nbv = b1 ? x23 : x01;
+        pv = b1 ? perp[D - 1] : perp[0];
+    } else {
+        const TA x01 = b0 ? nb[1] : nb[0], x23 = b0 ? nb[3 % (2 * D)] : nb[2 % (2 * D)];
+        const TA x45 = b0 ? nb[5 % (2 * D)] : nb[4 % (2 * D)];
+        const TA y = b1 ? x23 : x01;
+        nbv = b2 ? x45 : y;
+        const TA p01 = b1 ? perp[1 % D] : perp[0];
+        pv = b2 ? perp[2 % D] : p01;
+    }
     TA v = r + g * (wm * nbv + wp * pv + stay);
     if (c & (1u << (2 * D + 1))) v = r;
     if (c & (1u << (2 * D))) v = 0;
