@@ -113,10 +113,12 @@ constexpr int kAOffStage = kAOffU + 2 * 4 * kTileBytes;  // 4 slabs x 4096 x 4 B
 constexpr int kAOffBar = kAOffStage + 4 * kSlab * 4;
 constexpr int kASmem = kAOffBar + 64 + 1024;
 
-// Two warpgroups: thread t reads accumulator row t % 128 (its warp's TMEM
-// lane quarter) and columns 32 (t / 128) .. +31, so every CUDA-core phase
-// between the GEMMs is split over 8 warps.
-constexpr int kAThreads = 256;
+// Four warpgroups: thread t reads accumulator row t % 128 (its warp's TMEM
+// lane quarter) and columns 16 (t / 128) .. +15, so every CUDA-core phase
+// between the GEMMs is split over 16 warps (4 per scheduler, to hide the
+// latencies of the conversions and stores).
+constexpr int kAThreads = 512;
+constexpr int kACols = 64 * 128 / kAThreads;   // accumulator columns per thread
 
 __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__restrict__ V, const float *__restrict__ Vbase,
                                                        const uint8_t *__restrict__ U, uint8_t *__restrict__ T,
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kAOffBar + 16);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kAOffBar + 24);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int row = tid & 127, cbase = 32 * (tid >> 7);   // accumulator row, first column
+    const int row = tid & 127, cbase = kACols * (tid >> 7);   // accumulator row, first column
     if (tid == 0) {
         tc::mbar_init(&full[0], 1);
         tc::mbar_init(&full[1], 1);
@@ -191,12 +193,12 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
                 if (p == 0 && pend_c >= 0) write_quads(T, stage, pend_c, pend_b0, 0, kSlab / 2, tid, kAThreads);
                 if (!wait_all(mbar, phase, err)) { alive = false; break; }
                 tc::fence_after();
-                float z[32];
-                tc::tmem_ld32(tmem + lane_off + cbase, z);   // row = (s2, i3), cols i4' = cbase ..
+                float z[kACols];
+                tc::tmem_ld16(tmem + lane_off + cbase, z);   // row = (s2, i3), cols i4' = cbase ..
                 {
                     const uint32_t s2 = row >> 6, i3 = row & 63;
 #pragma unroll
-                    for (int jj = 0; jj < 32; jj++) {
+                    for (int jj = 0; jj < kACols; jj++) {
                         const uint32_t j = cbase + jj;
                         __nv_bfloat16 h, l;
                         tc::split_bf16(z[jj], h, l);
@@ -217,12 +219,12 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
                 // stage buffer before it is overwritten below)
                 if (!wait_all(mbar, phase, err)) { alive = false; break; }
                 tc::fence_after();
-                float y[32];
-                tc::tmem_ld32(tmem + lane_off + 64 + cbase, y);   // row = (s2, i4'), cols i3' = cbase ..
+                float y[kACols];
+                tc::tmem_ld16(tmem + lane_off + 64 + cbase, y);   // row = (s2, i4'), cols i3' = cbase ..
                 {
                     const int s = 2 * p + (row >> 6), i4 = row & 63;
 #pragma unroll
-                    for (int jj = 0; jj < 32; jj++) stage[s * kSlab + (cbase + jj) * 64 + i4] = tc::pack_hilo(y[jj]);
+                    for (int jj = 0; jj < kACols; jj++) stage[s * kSlab + (cbase + jj) * 64 + i4] = tc::pack_hilo(y[jj]);
                 }
                 tc::fence_before();
                 __syncthreads();
@@ -264,7 +266,12 @@ constexpr int kBOffArg = kBOffZ + 2 * kPairBytes;        // 64 x 128 argmax byte
 constexpr int kBOffBar = kBOffArg + 64 * 128;
 constexpr int kBSmem = kBOffBar + 64 + 1024;
 
-__global__ void __launch_bounds__(128, 2) dense_pass_b(const uint8_t *__restrict__ T, const uint8_t *__restrict__ U,
+// Two warpgroups per CTA: thread t owns accumulator row t % 128 and
+// columns 32 (t / 128) .. +31 (16 warps per SM with two CTAs).
+constexpr int kBThreads = 256;
+constexpr int kBCols = 64 * 128 / kBThreads;
+
+__global__ void __launch_bounds__(kBThreads, 2) dense_pass_b(const uint8_t *__restrict__ T, const uint8_t *__restrict__ U,
                                                        const float *__restrict__ RB, const float *__restrict__ EB,
                                                        const float *__restrict__ Vin, float *__restrict__ Vout,
                                                        uint8_t *__restrict__ pi, int nact, int nrank, float gamma,
@@ -287,7 +294,8 @@ __global__ void __launch_bounds__(128, 2) dense_pass_b(const uint8_t *__restrict
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sync_for_async();
     const uint32_t tmem = *tslot;
-    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    const int row = tid & 127, cbase = kBCols * (tid >> 7);   // accumulator row, first column
     uint32_t mph = 0, rph = 0, uph = 0;
     // a copy issued and not yet waited for (its phase is flipped already
     // when its own wait ran out)
@@ -311,9 +319,9 @@ __global__ void __launch_bounds__(128, 2) dense_pass_b(const uint8_t *__restrict
     raw_pending = u_pending = blockIdx.x < npairs;
     for (int P = blockIdx.x; P < npairs && alive; P += gridDim.x) {
         const int q0 = 2 * P;
-        float best[64];
+        float best[kBCols];
 #pragma unroll
-        for (int j = 0; j < 64; j++) best[j] = 0.f;
+        for (int j = 0; j < kBCols; j++) best[j] = 0.f;
         for (int a = 0; a < nact && alive; a++) {
             for (int r = 0; r < nrank && alive; r++) {
                 const int c = a * nrank + r;
@@ -327,7 +335,7 @@ __global__ void __launch_bounds__(128, 2) dense_pass_b(const uint8_t *__restrict
                 {
                     const uint4 *raw = reinterpret_cast<const uint4 *>(sm + kBOffRaw);
 #pragma unroll 4
-                    for (int idx = tid; idx < 2 * 1024; idx += 128) {
+                    for (int idx = tid; idx < 2 * 1024; idx += kBThreads) {
                         const uint4 w = raw[idx];
                         const uint32_t s2 = idx & 1, i1 = idx >> 5, j = (idx >> 1) & 15;
                         const uint32_t row = s2 * 64 + i1, k = j * 4;
@@ -351,15 +359,16 @@ __global__ void __launch_bounds__(128, 2) dense_pass_b(const uint8_t *__restrict
                 }
                 if (!wait_all(mbar, mph, err)) { alive = false; break; }
                 tc::fence_after();
-                float w1[64];
-                tc::tmem_ld64(tmem + lane_off, w1);   // row tid = (s2, i1), cols i2'
+                float w1[kBCols];
+                tc::tmem_ld32(tmem + lane_off + cbase, w1);   // row = (s2, i1), cols i2' = cbase ..
                 {
                     // the second GEMM's A operand, into the operand buffer
-                    const uint32_t s2 = tid >> 6, i1 = tid & 63;
+                    const uint32_t s2 = row >> 6, i1 = row & 63;
 #pragma unroll
-                    for (int j = 0; j < 64; j++) {
+                    for (int jj = 0; jj < kBCols; jj++) {
+                        const uint32_t j = cbase + jj;
                         __nv_bfloat16 h, l;
-                        tc::split_bf16(w1[j], h, l);
+                        tc::split_bf16(w1[jj], h, l);
                         put_bf16(sZ, s2 * 64 + j, i1, __bfloat16_as_ushort(h));
                         put_bf16(sZ + kPairBytes, s2 * 64 + j, i1, __bfloat16_as_ushort(l));
                     }
@@ -378,19 +387,19 @@ __global__ void __launch_bounds__(128, 2) dense_pass_b(const uint8_t *__restrict
             }
             if (!alive) break;
             tc::fence_after();
-            float e[64];
-            tc::tmem_ld64(tmem + lane_off + 64, e);   // row tid = (s2, i2'), cols i1'
-            const int q = q0 + (tid >> 6), i2 = tid & 63;
+            float e[kBCols];
+            tc::tmem_ld32(tmem + lane_off + 64 + cbase, e);   // row = (s2, i2'), cols i1' = cbase ..
+            const int q = q0 + (row >> 6), i2 = row & 63;
             if (EB) {
                 const float *eb = EB + (size_t)a * kS + (size_t)q * kSlab + i2;
 #pragma unroll
-                for (int j = 0; j < 64; j++) e[j] += eb[j * 64];
+                for (int jj = 0; jj < kBCols; jj++) e[jj] += eb[(cbase + jj) * 64];
             }
 #pragma unroll
-            for (int j = 0; j < 64; j++) {
-                if (a == 0 || e[j] > best[j]) {
-                    best[j] = e[j];
-                    sArg[j * 128 + tid] = (uint8_t)a;
+            for (int jj = 0; jj < kBCols; jj++) {
+                if (a == 0 || e[jj] > best[jj]) {
+                    best[jj] = e[jj];
+                    sArg[(cbase + jj) * 128 + row] = (uint8_t)a;
                 }
             }
             tc::fence_before();
@@ -399,14 +408,15 @@ __global__ void __launch_bounds__(128, 2) dense_pass_b(const uint8_t *__restrict
         }
         if (!alive) break;
         // V'(s) = R(s) + gamma max_a E_a(s); state s = (i1' * 64 + i2') * 4096 + q
-        const int q = q0 + (tid >> 6), i2 = tid & 63;
+        const int q = q0 + (row >> 6), i2 = row & 63;
         const float *rb = RB + (size_t)q * kSlab + i2;
 #pragma unroll
-        for (int j = 0; j < 64; j++) {
+        for (int jj = 0; jj < kBCols; jj++) {
+            const int j = cbase + jj;
             const size_t s = (size_t)(j * 64 + i2) * kSlab + q;
-            const float v = rb[j * 64] + gamma * best[j];
+            const float v = rb[j * 64] + gamma * best[jj];
             if (Vout) Vout[s] = v;
-            if (pi) pi[s] = sArg[j * 128 + tid];
+            if (pi) pi[s] = sArg[j * 128 + row];
             if (res) local_res = fmax(local_res, fabs((double)v - (double)Vin[s]));
         }
         __syncthreads();
@@ -504,7 +514,7 @@ static cpmdp_status tc_sweep(const Factors &F, const float *Vin, float *Vout, ui
                                             (uint8_t *)F.d_T, C, err);
     CPMDP_CUDA(cudaGetLastError());
     // pass B: two CTAs per SM (about 106 KB of shared memory each)
-    dense_pass_b<<<2 * grid, 128, kBSmem, st>>>((const uint8_t *)F.d_T, (const uint8_t *)F.d_Ubf, F.d_RB,
+    dense_pass_b<<<2 * grid, kBThreads, kBSmem, st>>>((const uint8_t *)F.d_T, (const uint8_t *)F.d_Ubf, F.d_RB,
                                             use_base ? F.d_EB : nullptr, Vin, Vout, pi, F.nactions, F.rank,
                                             (float)F.gamma, res, err);
     CPMDP_CUDA(cudaGetLastError());
