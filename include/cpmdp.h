@@ -333,11 +333,14 @@ cpmdp_status cpmdp_ws_targets(const cpmdp_batch *batch, const float *V, int32_t 
                               float *mask, void *stream);
 cpmdp_status cpmdp_ws_upsample(const cpmdp_batch *batch, const float *coarse, int32_t first, int32_t count, float *V,
                                void *stream);
-/* y = conv(x, W) + b (ReLU if relu); wf = W as [27][in][out] bf16; y0 (nullable) gets channel 0 in FP32. */
+/* y = conv(x, W) + b (ReLU if relu); wf = the forward weight tiles written by cpmdp_ws_cast_weights;
+ * y0 (nullable) gets channel 0 in FP32. Runs on the tcgen05 tensor cores (bf16 operands, FP32
+ * accumulation): 128 voxels x 64 channels per CTA, 27 taps x K = 64. */
 cpmdp_status cpmdp_conv3d_forward(const uint16_t *x, const uint16_t *wf, const float *bias, uint16_t *y, float *y0,
                                   int32_t n, int32_t z, int32_t y_, int32_t x_, int32_t dilation, int32_t relu,
                                   void *stream);
-/* dx = conv^T(dy, W) times (act_in > 0) when act_in is given; wb = W as [27][out][in] bf16. */
+/* dx = conv^T(dy, W) times (act_in > 0) when act_in is given; wb = the data-gradient weight tiles
+ * written by cpmdp_ws_cast_weights. Tensor cores, as the forward call. */
 cpmdp_status cpmdp_conv3d_backward_data(const uint16_t *dy, const uint16_t *wb, const uint16_t *act_in, uint16_t *dx,
                                         int32_t n, int32_t z, int32_t y_, int32_t x_, int32_t dilation, void *stream);
 /* dw += dL/dW (FP32 [27][64][64]), db += dL/db (FP32 [64], nullable). */
@@ -349,8 +352,14 @@ cpmdp_status cpmdp_ws_loss_grad(const float *pred, const float *target, const fl
 /* One Adam step (bias-corrected, step >= 1) on n FP32 parameters. */
 cpmdp_status cpmdp_adam_step(float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1,
                              float beta2, float eps, int32_t step, void *stream);
-/* FP32 W[layers][27][64][64] -> bf16 wf (per tap [in][out]) and wb (per tap [out][in]). */
+/* FP32 W[layers][27][64][64] -> bf16 weight tiles, per layer and tap 64 x 64 bf16 (8 KB) in the
+ * tensor cores' shared-memory layout (128-byte rows, 16-byte chunk c of row r stored at chunk
+ * c ^ (r % 8)): wf row = out, column = in (forward); wb row = in, column = out (data gradient).
+ * wf and wb each hold layers * 27 * 4096 bf16. */
 cpmdp_status cpmdp_ws_cast_weights(const float *w, uint16_t *wf, uint16_t *wb, int32_t layers, void *stream);
+/* Waits for the work queued on `stream`; ETIMEOUT if a bounded tensor-core wait in a convolution
+ * ran out since the last call (the error is cleared; outputs of that call are not valid). */
+cpmdp_status cpmdp_ws_sync(void *stream);
 
 /* Message of the last failed call on this host thread ("" if none). */
 const char *cpmdp_last_error(void);

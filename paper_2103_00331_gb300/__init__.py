@@ -109,7 +109,8 @@ def _load():
             ("cpmdp_ws_loss_grad", [vp, vp, vp, i32, vp, vp, vp]),
             ("cpmdp_adam_step", [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                  ctypes.c_float, i32, vp]),
-            ("cpmdp_ws_cast_weights", [vp, vp, vp, i32, vp])]:
+            ("cpmdp_ws_cast_weights", [vp, vp, vp, i32, vp]),
+            ("cpmdp_ws_sync", [vp])]:
         getattr(lib, name).argtypes = args
         getattr(lib, name).restype = ctypes.c_int
     lib.cpmdp_last_error.argtypes = []
@@ -127,7 +128,7 @@ EXPORTED = ["cpmdp_default_opts", "cpmdp_build_factors", "cpmdp_free_factors", "
             "cpmdp_batch_free", "cpmdp_batch_info", "cpmdp_batch_value_iteration", "cpmdp_ws_features",
             "cpmdp_ws_targets", "cpmdp_ws_upsample", "cpmdp_conv3d_forward", "cpmdp_conv3d_backward_data",
             "cpmdp_conv3d_backward_weight", "cpmdp_ws_loss_grad", "cpmdp_adam_step", "cpmdp_ws_cast_weights",
-            "cpmdp_last_error", "cpmdp_version"]
+            "cpmdp_ws_sync", "cpmdp_last_error", "cpmdp_version"]
 
 
 def last_error() -> str:
@@ -402,3 +403,9 @@ def adam_step(p, g, m, v, n, lr, beta1, beta2, eps, step, stream=None):
 
 def ws_cast_weights(w, wf, wb, layers, stream=None):
     _check(lib.cpmdp_ws_cast_weights(_ptr(w), _ptr(wf), _ptr(wb), int(layers), _stream(stream)))
+
+
+def ws_sync(stream=None):
+    """``cpmdp_ws_sync``: wait for the queued warm-start work; raises on a
+    tensor-core wait that ran out."""
+    _check(lib.cpmdp_ws_sync(_stream(stream)))

@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include "batch_internal.h"
+#include "tc_common.cuh"
 
 namespace cpmdp {
 
@@ -35,71 +36,166 @@ struct Dims {
 __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
 
 // ---------------------------------------------------------------------------
-// convolution (forward and data gradient)
+// convolution (forward and data gradient) on the tcgen05 tensor cores
+//
+// Implicit GEMM per tap: D[v, n] += sum_k A_t[v, k] B_t[n, k] with
+// A_t[v, k] = x[v + s d off(t), k] (zero outside the grid) and B_t the tap's
+// 64 x 64 weight tile; 27 taps x 4 K-steps of 16 accumulate into one TMEM
+// tile of 128 voxels x 64 channels (FP32). One warpgroup per CTA, thread i
+// owns voxel row i: it gathers that voxel's 128 contiguous bytes of the tap
+// (channels-last) into the 128-byte-swizzled K-major A tile, and the tap's
+// B tile, pre-swizzled by the weight cast, arrives by one bulk copy. Two
+// buffers: the gather of tap t + 1 runs under the MMAs of tap t. Every
+// mbarrier wait is bounded; one that runs out records an error (read by
+// cpmdp_ws_sync) and the CTA stops.
 
-__global__ void __launch_bounds__(256) conv_kernel(const __nv_bfloat16 *__restrict__ x,
-                                                   const __nv_bfloat16 *__restrict__ wk,
-                                                   const float *__restrict__ bias,
-                                                   const __nv_bfloat16 *__restrict__ mask_act,
-                                                   __nv_bfloat16 *__restrict__ y, float *__restrict__ y0,
-                                                   Dims dm, int dil, int sign, int relu) {
-    __shared__ float sA[64][65];   // [voxel][k]
-    __shared__ float sB[64][65];   // [k][n]
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int v0 = blockIdx.x * 64;
+constexpr int kCvThreads = 128;
+constexpr int kCvATile = 128 * 128;                  // 128 voxels x 64 bf16
+constexpr int kCvBTile = 64 * 128;                   // 64 channels x 64 bf16
+constexpr int kCvOffA = 0;
+constexpr int kCvOffB = 2 * kCvATile;
+constexpr int kCvOffBar = kCvOffB + 2 * kCvBTile;
+constexpr int kCvSmem = kCvOffBar + 64 + 1024;
+constexpr long long kCvWaitCycles = 2000000000LL;    // about 1 s at 2 GHz
+
+__device__ int g_conv_err = 0;
+
+// Element offset of (row r, k) in a 64-wide bf16 tile with 128-byte rows
+// and the 128-byte swizzle (16-byte chunk k / 8 of row r at chunk
+// (k / 8) ^ (r % 8)).
+__host__ __device__ __forceinline__ int sw_elem(int r, int k) { return r * 64 + ((((k >> 3) ^ (r & 7)) & 7) << 3) + (k & 7); }
+
+__global__ void __launch_bounds__(kCvThreads, 4) conv_tc_kernel(const __nv_bfloat16 *__restrict__ x,
+                                                             const uint8_t *__restrict__ wimg,
+                                                             const float *__restrict__ bias,
+                                                             const __nv_bfloat16 *__restrict__ mask_act,
+                                                             __nv_bfloat16 *__restrict__ y, float *__restrict__ y0,
+                                                             Dims dm, int dil, int sign, int relu) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bfull = reinterpret_cast<uint64_t *>(sm + kCvOffBar);   // [2] weight tile in
+    uint64_t *mdone = bfull + 2;                                      // [2] MMAs of the buffer done
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bfull + 4);
+    volatile int *sflag = reinterpret_cast<volatile int *>(bfull + 5);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        for (int i = 0; i < 4; i++) tc::mbar_init(&bfull[i], 1);
+        *sflag = 0;
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 64);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t aA = tc::smem_u32(sm + kCvOffA), aB = tc::smem_u32(sm + kCvOffB);
     const int nvox = dm.nvox();
-    float acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = 0.f;
+    const int v = blockIdx.x * kCvThreads + tid;
+    const bool valid = v < nvox;
+    int xx = 0, yy = 0, zz = 0, nn = 0;
+    if (valid) {
+        int r = v;
+        xx = r % dm.x; r /= dm.x;
+        yy = r % dm.y; r /= dm.y;
+        zz = r % dm.z; nn = r / dm.z;
+    }
+    int last = -1;             // thread 0: last tap whose MMAs were committed
+    int ptap0 = -1, ptap1 = -1;   // thread 0: tap of a weight copy (buffer 0 / 1) not yet waited for
+    bool ok = true;
     for (int t = 0; t < 27; t++) {
+        const int b = t & 1;
+        // the MMAs of tap t - 2 read buffer b
+        if (t >= 2 && !tc::mbar_wait(&mdone[b], (uint32_t)(((t >> 1) - 1) & 1), kCvWaitCycles)) *sflag = 1;
+        if (tid == 0 && !*sflag) {
+            tc::mbar_expect_tx(&bfull[b], kCvBTile);
+            tc::bulk_g2s(aB + b * kCvBTile, wimg + (size_t)t * kCvBTile, kCvBTile, &bfull[b]);
+            if (b) ptap1 = t; else ptap0 = t;
+        }
         const int oz = sign * dil * (t / 9 - 1), oy = sign * dil * ((t / 3) % 3 - 1), ox = sign * dil * (t % 3 - 1);
-        for (int e = tid; e < 64 * 64; e += 256) {
-            const int vv = e >> 6, k = e & 63;
-            const int v = v0 + vv;
-            float val = 0.f;
-            if (v < nvox) {
-                int r = v;
-                const int xx = r % dm.x; r /= dm.x;
-                const int yy = r % dm.y; r /= dm.y;
-                const int zz = r % dm.z; const int nn = r / dm.z;
-                const int z2 = zz + oz, y2 = yy + oy, x2 = xx + ox;
-                if (z2 >= 0 && z2 < dm.z && y2 >= 0 && y2 < dm.y && x2 >= 0 && x2 < dm.x)
-                    val = bf(x[((size_t)((nn * dm.z + z2) * dm.y + y2) * dm.x + x2) * kC + k]);
+        const int z2 = zz + oz, y2 = yy + oy, x2 = xx + ox;
+        uint4 row[8];
+        if (valid && z2 >= 0 && z2 < dm.z && y2 >= 0 && y2 < dm.y && x2 >= 0 && x2 < dm.x) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(x + ((size_t)((nn * dm.z + z2) * dm.y + y2) * dm.x + x2) * kC);
+#pragma unroll
+            for (int j = 0; j < 8; j++) row[j] = src[j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; j++) row[j] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        uint8_t *arow = sm + kCvOffA + b * kCvATile + tid * 128;
+#pragma unroll
+        for (int j = 0; j < 8; j++) *reinterpret_cast<uint4 *>(arow + ((j ^ (tid & 7)) << 4)) = row[j];
+        tc::fence_proxy_async();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (*sflag) { ok = false; break; }
+        if (tid == 0) {
+            if (!tc::mbar_wait(&bfull[b], (uint32_t)((t >> 1) & 1), kCvWaitCycles)) {
+                *sflag = 1;
+            } else {
+                if (b) ptap1 = -1; else ptap0 = -1;
+#pragma unroll
+                for (int ks = 0; ks < 4; ks++)
+                    tc::mma(tmem, tc::sdesc(aA + b * kCvATile + ks * 32), tc::sdesc(aB + b * kCvBTile + ks * 32),
+                            tc::kIdescM128N64, (t > 0 || ks > 0) ? 1u : 0u);
+                tc::commit(&mdone[b]);
+                last = t;
             }
-            sA[vv][k] = val;
-            sB[vv][k] = bf(wk[(size_t)t * kC * kC + e]);   // e = k_row * 64 + n
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < 64; k++) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; i++) a[i] = sA[ty + 16 * i][k];
-#pragma unroll
-            for (int j = 0; j < 4; j++) b[j] = sB[k][tx + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 4; i++)
-#pragma unroll
-                for (int j = 0; j < 4; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const int v = v0 + ty + 16 * i;
-        if (v >= nvox) continue;
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int n = tx + 16 * j;
-            float val = acc[i][j] + (bias ? bias[n] : 0.f);
-            if (mask_act && !(bf(mask_act[(size_t)v * kC + n]) > 0.f)) val = 0.f;
-            if (relu) val = fmaxf(val, 0.f);
-            y[(size_t)v * kC + n] = __float2bfloat16_rn(val);
-            if (y0 && n == 0) y0[v] = val;
         }
     }
+    // tap 26 (buffer 0, its 14th use) completes after every earlier MMA
+    if (ok && !tc::mbar_wait(&mdone[0], 1u, kCvWaitCycles)) *sflag = 1;
+    __syncthreads();
+    if (*sflag) {
+        if (tid == 0) {
+            atomicExch(&g_conv_err, 1);
+            // let copies and MMAs still in flight finish before the CTA's shared memory goes
+            if (ptap0 >= 0) tc::mbar_wait(&bfull[0], (uint32_t)((ptap0 >> 1) & 1), kCvWaitCycles);
+            if (ptap1 >= 0) tc::mbar_wait(&bfull[1], (uint32_t)((ptap1 >> 1) & 1), kCvWaitCycles);
+            if (last >= 0) tc::mbar_wait(&mdone[last & 1], (uint32_t)((last >> 1) & 1), kCvWaitCycles);
+        }
+    } else {
+        tc::fence_after();
+        float acc[64];
+        tc::tmem_ld64(tmem + ((uint32_t)(32 * warp) << 16), acc);
+        if (valid) {
+#pragma unroll
+            for (int n = 0; n < 64; n++) acc[n] += bias ? bias[n] : 0.f;
+            if (mask_act) {
+                const uint4 *mrow = reinterpret_cast<const uint4 *>(mask_act + (size_t)v * kC);
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const uint4 m = mrow[j];
+                    const uint32_t w[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+                    for (int h = 0; h < 8; h++) {
+                        const uint16_t bits = (uint16_t)(w[h >> 1] >> (16 * (h & 1)));
+                        if (!(bf(__ushort_as_bfloat16(bits)) > 0.f)) acc[8 * j + h] = 0.f;
+                    }
+                }
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(y + (size_t)v * kC);
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                uint32_t w[4];
+#pragma unroll
+                for (int h = 0; h < 4; h++) {
+                    float a0 = acc[8 * j + 2 * h], a1 = acc[8 * j + 2 * h + 1];
+                    if (relu) { a0 = fmaxf(a0, 0.f); a1 = fmaxf(a1, 0.f); }
+                    if (j == 0 && h == 0 && y0) y0[v] = a0;
+                    w[h] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a0)) |
+                           ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(a1)) << 16);
+                }
+                dst[j] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
 // dW[t, co, ci] += sum over a chunk of voxels of dy[v, co] x[v + d off(t), ci]
@@ -202,14 +298,17 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
     }
 }
 
-// W [t][co][ci] (FP32) -> wf [t][ci][co] (forward operand) and wb [t][co][ci] (data gradient operand)
+// W [t][co][ci] (FP32) -> per tap the B tiles of the tensor-core convolution
+// (64 rows x 64 bf16, 128-byte swizzle): wf row co, column ci (forward) and
+// wb row ci, column co (data gradient).
 __global__ void cast_weights_kernel(const float *__restrict__ w, __nv_bfloat16 *__restrict__ wf,
                                     __nv_bfloat16 *__restrict__ wb, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const long long t = i / (kC * kC), r = i % (kC * kC), co = r / kC, ci = r % kC;
+        const long long t = i / (kC * kC), r = i % (kC * kC);
+        const int co = (int)(r / kC), ci = (int)(r % kC);
         const __nv_bfloat16 h = __float2bfloat16_rn(w[i]);
-        wb[i] = h;
-        wf[t * kC * kC + ci * kC + co] = h;
+        wf[t * kC * kC + sw_elem(co, ci)] = h;
+        wb[t * kC * kC + sw_elem(ci, co)] = h;
     }
 }
 
@@ -328,6 +427,16 @@ static cpmdp_status batch_range(const cpmdp_batch *B, int first, int count, int 
     return CPMDP_OK;
 }
 
+static cudaError_t launch_conv(const __nv_bfloat16 *x, const uint8_t *wimg, const float *bias,
+                               const __nv_bfloat16 *mask_act, __nv_bfloat16 *y, float *y0, Dims dm, int dil, int sign,
+                               int relu, cudaStream_t st) {
+    const cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCvSmem);
+    if (e != cudaSuccess) return e;
+    conv_tc_kernel<<<(dm.nvox() + kCvThreads - 1) / kCvThreads, kCvThreads, kCvSmem, st>>>(x, wimg, bias, mask_act, y,
+                                                                                         y0, dm, dil, sign, relu);
+    return cudaGetLastError();
+}
+
 static cpmdp_status dims_ok(int n, int z, int y, int x, int dil) {
     if (n < 1 || z < 1 || y < 1 || x < 1 || dil < 1 || (long long)n * z * y * x > (1LL << 31) - 64) {
         set_error("invalid convolution dimensions");
@@ -384,10 +493,8 @@ cpmdp_status cpmdp_conv3d_forward(const uint16_t *x, const uint16_t *wf, const f
     if (s != CPMDP_OK) return s;
     if (!x || !wf || !y) { set_error("x, w and y are required"); return CPMDP_EINVAL; }
     Dims dm{n, z, yy, xx};
-    conv_kernel<<<(dm.nvox() + 63) / 64, 256, 0, (cudaStream_t)stream>>>(
-        (const __nv_bfloat16 *)x, (const __nv_bfloat16 *)wf, bias, nullptr, (__nv_bfloat16 *)y, y0, dm, dilation, 1,
-        relu);
-    CPMDP_CUDA(cudaGetLastError());
+    CPMDP_CUDA(launch_conv((const __nv_bfloat16 *)x, (const uint8_t *)wf, bias, nullptr, (__nv_bfloat16 *)y, y0, dm,
+                           dilation, 1, relu, (cudaStream_t)stream));
     return CPMDP_OK;
 }
 
@@ -397,10 +504,8 @@ cpmdp_status cpmdp_conv3d_backward_data(const uint16_t *dy, const uint16_t *wb, 
     if (s != CPMDP_OK) return s;
     if (!dy || !wb || !dx) { set_error("dy, w and dx are required"); return CPMDP_EINVAL; }
     Dims dm{n, z, yy, xx};
-    conv_kernel<<<(dm.nvox() + 63) / 64, 256, 0, (cudaStream_t)stream>>>(
-        (const __nv_bfloat16 *)dy, (const __nv_bfloat16 *)wb, nullptr, (const __nv_bfloat16 *)act_in,
-        (__nv_bfloat16 *)dx, nullptr, dm, dilation, -1, 0);
-    CPMDP_CUDA(cudaGetLastError());
+    CPMDP_CUDA(launch_conv((const __nv_bfloat16 *)dy, (const uint8_t *)wb, nullptr, (const __nv_bfloat16 *)act_in,
+                           (__nv_bfloat16 *)dx, nullptr, dm, dilation, -1, 0, (cudaStream_t)stream));
     return CPMDP_OK;
 }
 
@@ -447,6 +552,19 @@ cpmdp_status cpmdp_ws_cast_weights(const float *w, uint16_t *wf, uint16_t *wb, i
     cast_weights_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(w, (__nv_bfloat16 *)wf,
                                                                             (__nv_bfloat16 *)wb, n);
     CPMDP_CUDA(cudaGetLastError());
+    return CPMDP_OK;
+}
+
+cpmdp_status cpmdp_ws_sync(void *stream) {
+    CPMDP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int e = 0;
+    CPMDP_CUDA(cudaMemcpyFromSymbol(&e, g_conv_err, sizeof(int)));
+    if (e) {
+        const int zero = 0;
+        CPMDP_CUDA(cudaMemcpyToSymbol(g_conv_err, &zero, sizeof(int)));
+        set_error("a tensor-core wait in a warm-start convolution ran out");
+        return CPMDP_ETIMEOUT;
+    }
     return CPMDP_OK;
 }
 

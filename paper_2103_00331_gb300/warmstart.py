@@ -24,7 +24,7 @@ import numpy as np
 
 from . import (BF16X3, adam_step, batch_build, batch_value_iteration, conv3d_backward_data,  # noqa: F401
                conv3d_backward_weight, conv3d_forward, default_opts, ws_cast_weights, ws_features,
-               ws_loss_grad, ws_targets, ws_upsample)
+               ws_loss_grad, ws_sync, ws_targets, ws_upsample)
 
 C = 64
 FACTOR = 4
@@ -166,6 +166,7 @@ def train(net, feat, target, mask, dims, epochs=10, batch=64, lr=1e-3, lr_final=
             net.train_step(feat[lo:hi], target[lo:hi], mask[lo:hi], (batch,) + tuple(dims[1:]), lr=rate,
                            loss_acc=acc)
             k += 1
+        ws_sync()
         losses.append(acc.item() / steps_per_epoch)
         if log:
             log(f"epoch {ep}: loss {losses[-1]:.3e}")
@@ -205,13 +206,13 @@ def evaluate(net, count=512, side=64, seed=424242, device=0, log=None):
     torch.cuda.synchronize()
     Vz = V.clone()
     warm_start_values(net, B, count, (side,) * 3, V)      # warm-up of the network kernels
-    torch.cuda.synchronize()
+    ws_sync()
     ev[2].record()
     warm_start_values(net, B, count, (side,) * 3, V)
     ev[3].record()
     r1, it1, res1 = batch_value_iteration(B, V, opts=opts)
     ev[4].record()
-    torch.cuda.synchronize()
+    ws_sync()
     zero_ms = ev[0].elapsed_time(ev[1])
     net_ms = ev[2].elapsed_time(ev[3])
     vi_ms = ev[3].elapsed_time(ev[4])

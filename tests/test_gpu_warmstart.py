@@ -40,10 +40,12 @@ def _bf16(a, torch):
     return t, t.to(torch.float64).numpy()
 
 
-def test_conv_kernels_match_oracle(env):
+@pytest.mark.parametrize("dims,dils", [((2, 3, 4, 5), (1, 2)), ((3, 7, 9, 11), (1, 4))])
+def test_conv_kernels_match_oracle(env, dims, dils):
+    """Tensor-core convolutions (128 voxels per CTA): one partial tile, and
+    17 tiles with a ragged last one and taps that leave the grid (dilation 4)."""
     cp, ws, torch = env
     from oracle import convnet as N
-    dims = (2, 3, 4, 5)
     shp = dims + (64,)
     xb, x = _bf16(ci.random_values(shp, seed=1), torch)
     dyb, dy = _bf16(ci.random_values(shp, seed=2), torch)
@@ -56,10 +58,11 @@ def test_conv_kernels_match_oracle(env):
     wb = torch.empty_like(wf)
     cp.ws_cast_weights(wt, wf, wb, 1)
     xg, dyg = xb.to(dev).reshape(-1, 64), dyb.to(dev).reshape(-1, 64)
-    for dil in (1, 2):
+    for dil in dils:
         y = torch.empty_like(xg)
         y0 = torch.empty(xg.shape[0], dtype=torch.float32, device=dev)
         cp.conv3d_forward(xg, wf, torch.as_tensor(b).to(dev), y, y0, dims, dil, relu=False)
+        cp.ws_sync()
         ref = N.conv_forward(x, wq, b.astype(np.float64), dil).reshape(-1, 64)
         mag = N.conv_forward(np.abs(x), np.abs(wq), np.zeros(64), dil).reshape(-1, 64)
         got = y.to(torch.float64).cpu().numpy()
@@ -70,6 +73,7 @@ def test_conv_kernels_match_oracle(env):
         act_mask = act.to(torch.float64).cpu().numpy().reshape(shp) > 0
         dx = torch.empty_like(dyg)
         cp.conv3d_backward_data(dyg, wb, act.reshape(-1, 64), dx, dims, dil)
+        cp.ws_sync()
         dref, dWref, dbref = N.conv_backward(x, wq, dy, dil)
         dref = (dref * act_mask).reshape(-1, 64)
         dmag = N.conv_backward(np.abs(x), np.abs(wq), np.abs(dy), dil)[0].reshape(-1, 64)
