@@ -86,26 +86,44 @@ static void build_gridworld(Factors &F) {
     const int64_t S = F.nstates;
     F.code.assign((size_t)S, 0u);
     const uint32_t all_dirs = (uint32_t)((1ull << (2 * D)) - 1);
-    for (int64_t s = 0; s < S; s++) {
-        const uint8_t k = F.cell[(size_t)s];
-        if (k == CPMDP_CELL_OBSTACLE) { F.code[(size_t)s] = all_dirs | (1u << (2 * D)); continue; }
-        if (k == CPMDP_CELL_TERMINAL) { F.code[(size_t)s] = all_dirs | (1u << (2 * D + 1)); continue; }
-        uint32_t c = 0;
-        int64_t rem = s;
-        for (int d = 0; d < D; d++) {
-            const int64_t x = rem / F.stride[d];
-            rem -= x * F.stride[d];
-            for (int sg = 0; sg < 2; sg++) {
-                const int64_t y = x + (sg ? 1 : -1);
-                bool blocked = y < 0 || y >= F.shape[d];
-                if (!blocked) {
-                    const int64_t t = s + (sg ? F.stride[d] : -F.stride[d]);
-                    blocked = F.cell[(size_t)t] == CPMDP_CELL_OBSTACLE;
+    // locals: stores through the code array may not alias the byte reads of
+    // the cells in the compiler's eyes, so nothing is reloaded per state
+    const uint8_t *cell = F.cell.data();
+    uint32_t *code = F.code.data();
+    int64_t shape[CPMDP_MAX_DIM], stride[CPMDP_MAX_DIM];
+    for (int d = 0; d < D; d++) { shape[d] = F.shape[d]; stride[d] = F.stride[d]; }
+    const int64_t n = shape[D - 1];          // rows of the last dimension
+    // coordinates of the row kept by an odometer (no divisions)
+    int64_t x[CPMDP_MAX_DIM] = {0};
+    for (int64_t row = 0; row < S; row += n) {
+        // blocked moves of the leading dimensions are the same test for every
+        // state of the row, against the neighbouring rows' cells
+        for (int64_t i = 0; i < n; i++) {
+            const int64_t s = row + i;
+            const uint8_t k = cell[s];
+            uint32_t c;
+            if (k == CPMDP_CELL_OBSTACLE) {
+                c = all_dirs | (1u << (2 * D));
+            } else if (k == CPMDP_CELL_TERMINAL) {
+                c = all_dirs | (1u << (2 * D + 1));
+            } else {
+                c = 0;
+                // branch-free: at a wall the cell read is the state's own
+                for (int d = 0; d < D - 1; d++) {
+                    const bool lo = x[d] == 0, hi = x[d] == shape[d] - 1;
+                    c |= (uint32_t)(lo | (cell[lo ? s : s - stride[d]] == CPMDP_CELL_OBSTACLE)) << (2 * d);
+                    c |= (uint32_t)(hi | (cell[hi ? s : s + stride[d]] == CPMDP_CELL_OBSTACLE)) << (2 * d + 1);
                 }
-                if (blocked) c |= 1u << (2 * d + sg);
+                const bool lo = i == 0, hi = i == n - 1;
+                c |= (uint32_t)(lo | (cell[lo ? s : s - 1] == CPMDP_CELL_OBSTACLE)) << (2 * (D - 1));
+                c |= (uint32_t)(hi | (cell[hi ? s : s + 1] == CPMDP_CELL_OBSTACLE)) << (2 * (D - 1) + 1);
             }
+            code[s] = c;
         }
-        F.code[(size_t)s] = c;
+        for (int d = D - 2; d >= 0; d--) {
+            if (++x[d] < shape[d]) break;
+            x[d] = 0;
+        }
     }
 }
 
@@ -120,14 +138,26 @@ static cpmdp_status validate(const cpmdp_problem *p) {
     if (S >= 2147483648.0) { set_error("|S| = %.0f exceeds 2^31 - 1", S); return CPMDP_EINVAL; }
     if (!(p->gamma >= 0.0 && p->gamma <= 1.0)) { set_error("gamma %g outside [0, 1]", p->gamma); return CPMDP_EINVAL; }
     if (!p->reward) { set_error("reward is NULL"); return CPMDP_EINVAL; }
-    for (int64_t s = 0; s < (int64_t)S; s++)
-        if (!isfinite(p->reward[s])) { set_error("reward[%lld] is not finite", (long long)s); return CPMDP_EINVAL; }
+    {
+        // a double is not finite exactly when its exponent bits are all ones:
+        // one branch-free integer pass, then a search only when it failed
+        const uint64_t *bits = reinterpret_cast<const uint64_t *>(p->reward);
+        uint64_t bad = 0;
+        for (int64_t s = 0; s < (int64_t)S; s++) bad |= ((bits[s] >> 52) & 0x7FFu) == 0x7FFu;
+        if (bad)
+            for (int64_t s = 0; s < (int64_t)S; s++)
+                if (!isfinite(p->reward[s])) { set_error("reward[%lld] is not finite", (long long)s); return CPMDP_EINVAL; }
+    }
     if (p->kind == CPMDP_GRIDWORLD) {
         if (p->nactions != 2 * p->ndim) { set_error("GridWorld needs nactions = 2*ndim = %d (got %d)", 2 * p->ndim, p->nactions); return CPMDP_EINVAL; }
         if (!(p->p_success >= 0.0 && p->p_success <= 1.0)) { set_error("p_success %g outside [0, 1]", p->p_success); return CPMDP_EINVAL; }
-        if (p->cell)
-            for (int64_t s = 0; s < (int64_t)S; s++)
-                if (p->cell[s] > CPMDP_CELL_TERMINAL) { set_error("cell[%lld] = %d is not 0, 1 or 2", (long long)s, p->cell[s]); return CPMDP_EINVAL; }
+        if (p->cell) {
+            uint8_t top = 0;
+            for (int64_t s = 0; s < (int64_t)S; s++) top = p->cell[s] > top ? p->cell[s] : top;
+            if (top > CPMDP_CELL_TERMINAL)
+                for (int64_t s = 0; s < (int64_t)S; s++)
+                    if (p->cell[s] > CPMDP_CELL_TERMINAL) { set_error("cell[%lld] = %d is not 0, 1 or 2", (long long)s, p->cell[s]); return CPMDP_EINVAL; }
+        }
     } else if (p->kind == CPMDP_DENSE_CP) {
         if (p->nactions < 1 || p->nactions > 64) { set_error("dense nactions %d outside [1, 64]", p->nactions); return CPMDP_EINVAL; }
         if (p->rank < 1 || p->rank > 64) { set_error("dense rank %d outside [1, 64]", p->rank); return CPMDP_EINVAL; }
