@@ -583,7 +583,8 @@ def kernel_case(name, reps=3):
     """Run one kernel workload a few times and exit (for ncu captures):
     sweep512 / sweep320 = fused FP32 backup of a 512^3 / 320^3 GridWorld; solve64 / pi64 = fused
     FP32 value / policy iteration of the 64^3 instance (barrier-free solver);
-    solve64b / pi64b = the same on the grid-barrier solver."""
+    solve64b / pi64b = the same on the grid-barrier solver; ws512 = the warm-start network on
+    512 x 16^3 coarse cells (six tensor-core convolutions)."""
     import torch
     import paper_2103_00331_gb300 as cp
     import cpmdp_inputs as ci
@@ -630,6 +631,23 @@ def kernel_case(name, reps=3):
             torch.cuda.synchronize()
             print(f"dense 64^4 FP32 SIMT sweep: {e0.elapsed_time(e1):.3f} ms")
             Va, Vb = Vb, Va
+    elif name == "ws512":
+        from paper_2103_00331_gb300 import warmstart as ws
+        path = os.path.join(ROOT, "paper_2103_00331_gb300", "data", "warmstart_weights.npz")
+        net = ws.WarmStartNet.load(path, device=0)
+        dims = (512, 16, 16, 16)
+        nv = int(np.prod(dims))
+        feat = torch.zeros((nv, 64), dtype=torch.bfloat16, device=dev)
+        feat[:, :4] = torch.as_tensor(ci.random_values((nv, 4), seed=5).astype(np.float32)).to(dev)
+        for i in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            net.predict(feat, dims)
+            e1.record()
+            ws.ws_sync()
+            flops = 2.0 * nv * 27 * 64 * 64 * ws.LAYERS
+            print(f"warm-start network, 512 x 16^3 coarse cells: {e0.elapsed_time(e1):.3f} ms, "
+                  f"{flops / e0.elapsed_time(e1) / 1e9:.1f} TFLOP/s bf16 (tcgen05 convolutions)")
     elif name in ("solve64", "pi64", "solve64b", "pi64b"):
         gw = workload(0)
         fused = 2 if name.endswith("b") else 1
@@ -662,7 +680,7 @@ def main():
     ap.add_argument("--skip-warmstart", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--kernel-case", choices=["sweep512", "sweep320", "solve64", "pi64", "solve64b", "pi64b", "dense64",
-                                              "dense64tc"],
+                                              "dense64tc", "ws512"],
                     default=None,
                     help="run one kernel workload a few times (profiling) and exit")
     args = ap.parse_args()
