@@ -83,6 +83,9 @@ static void build_gridworld(Factors &F) {
     F.w_perp = D >= 2 ? (1.0 - F.p) / (2.0 * (D - 1)) : 0.0;
     F.w_stay = D == 1 ? 1.0 - F.p : 0.0;
     F.code_bytes = code_bytes_for(D);
+    // factors on a device get their codes from codes_kernel (upload); the
+    // host keeps its own copy only for host-only factors
+    if (F.device >= 0) return;
     const int64_t S = F.nstates;
     F.code.assign((size_t)S, 0u);
     const uint32_t all_dirs = (uint32_t)((1ull << (2 * D)) - 1);
@@ -172,17 +175,74 @@ static cpmdp_status validate(const cpmdp_problem *p) {
     return CPMDP_OK;
 }
 
+// Code of blocked moves of one state (the same rule as build_gridworld), for
+// host queries on factors whose codes live on the device only.
+static uint32_t code_of(const Factors &F, int64_t s) {
+    const int D = F.ndim;
+    const uint32_t all_dirs = (uint32_t)((1ull << (2 * D)) - 1);
+    const uint8_t k = F.cell[(size_t)s];
+    if (k == CPMDP_CELL_OBSTACLE) return all_dirs | (1u << (2 * D));
+    if (k == CPMDP_CELL_TERMINAL) return all_dirs | (1u << (2 * D + 1));
+    uint32_t c = 0;
+    int64_t rem = s;
+    for (int d = 0; d < D; d++) {
+        const int64_t x = rem / F.stride[d];
+        rem -= x * F.stride[d];
+        if (x == 0 || F.cell[(size_t)(s - F.stride[d])] == CPMDP_CELL_OBSTACLE) c |= 1u << (2 * d);
+        if (x == F.shape[d] - 1 || F.cell[(size_t)(s + F.stride[d])] == CPMDP_CELL_OBSTACLE) c |= 1u << (2 * d + 1);
+    }
+    return c;
+}
+
+struct CodeGeom {
+    int ndim;
+    int64_t shape[kMaxDim], stride[kMaxDim];
+};
+
+// Per-state codes of blocked moves from the cell kinds (device copy of the
+// rule in build_gridworld), stored in `cb` bytes per state.
+__global__ void codes_kernel(const uint8_t *__restrict__ cell, CodeGeom g, int64_t S, int cb, uint8_t *__restrict__ out) {
+    const int D = g.ndim;
+    const uint32_t all_dirs = (uint32_t)((1ull << (2 * D)) - 1);
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t k = cell[s];
+        uint32_t c;
+        if (k == CPMDP_CELL_OBSTACLE) {
+            c = all_dirs | (1u << (2 * D));
+        } else if (k == CPMDP_CELL_TERMINAL) {
+            c = all_dirs | (1u << (2 * D + 1));
+        } else {
+            c = 0;
+            int64_t rem = s;
+            for (int d = 0; d < D; d++) {
+                const int64_t x = rem / g.stride[d];
+                rem -= x * g.stride[d];
+                if (x == 0 || cell[s - g.stride[d]] == CPMDP_CELL_OBSTACLE) c |= 1u << (2 * d);
+                if (x == g.shape[d] - 1 || cell[s + g.stride[d]] == CPMDP_CELL_OBSTACLE) c |= 1u << (2 * d + 1);
+            }
+        }
+        if (cb == 1) out[s] = (uint8_t)c;
+        else if (cb == 2) reinterpret_cast<uint16_t *>(out)[s] = (uint16_t)c;
+        else reinterpret_cast<uint32_t *>(out)[s] = c;
+    }
+}
+
+__global__ void to_f32_kernel(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
 static cpmdp_status upload(Factors &F) {
     DeviceGuard g(F.device);
     if (!g.ok) { set_error("cannot select CUDA device %d", F.device); return CPMDP_ECUDA; }
     CPMDP_CUDA(cudaDeviceGetAttribute(&F.num_sms, cudaDevAttrMultiProcessorCount, F.device));
     const size_t S = (size_t)F.nstates;
-    std::vector<float> r32(S);
-    for (size_t s = 0; s < S; s++) r32[s] = (float)F.reward[s];
+    const int blocks = (int)std::min<int64_t>((F.nstates + 255) / 256, (int64_t)F.num_sms * 16);
     CPMDP_CUDA(cudaMalloc(&F.d_R32, S * sizeof(float)));
     CPMDP_CUDA(cudaMalloc(&F.d_R64, S * sizeof(double)));
-    CPMDP_CUDA(cudaMemcpy(F.d_R32, r32.data(), S * sizeof(float), cudaMemcpyHostToDevice));
     CPMDP_CUDA(cudaMemcpy(F.d_R64, F.reward.data(), S * sizeof(double), cudaMemcpyHostToDevice));
+    to_f32_kernel<<<blocks, 256>>>(F.d_R64, F.d_R32, F.nstates);
+    CPMDP_CUDA(cudaGetLastError());
     CPMDP_CUDA(cudaMalloc(&F.d_cell, S));
     CPMDP_CUDA(cudaMemcpy(F.d_cell, F.cell.data(), S, cudaMemcpyHostToDevice));
     F.scratch_bytes = S * sizeof(double);
@@ -191,19 +251,18 @@ static cpmdp_status upload(Factors &F) {
     CPMDP_CUDA(cudaMemset(F.d_ctrl, 0, sizeof(Ctrl)));
     if (F.kind == CPMDP_GRIDWORLD) {
         const size_t cb = (size_t)F.code_bytes;
-        std::vector<uint8_t> packed(S * cb);
-        for (size_t s = 0; s < S; s++) {
-            const uint32_t c = F.code[s];
-            if (cb == 1) packed[s] = (uint8_t)c;
-            else if (cb == 2) { uint16_t v = (uint16_t)c; memcpy(&packed[2 * s], &v, 2); }
-            else memcpy(&packed[4 * s], &c, 4);
-        }
         CPMDP_CUDA(cudaMalloc(&F.d_code, S * cb));
-        CPMDP_CUDA(cudaMemcpy(F.d_code, packed.data(), S * cb, cudaMemcpyHostToDevice));
+        CodeGeom geo{};
+        geo.ndim = F.ndim;
+        for (int d = 0; d < F.ndim; d++) { geo.shape[d] = F.shape[d]; geo.stride[d] = F.stride[d]; }
+        codes_kernel<<<blocks, 256>>>(F.d_cell, geo, F.nstates, (int)cb, static_cast<uint8_t *>(F.d_code));
+        CPMDP_CUDA(cudaGetLastError());
     } else {
         cpmdp_status st = dense_prepare(F);
         if (st != CPMDP_OK) return st;
     }
+    // building is synchronous: the codes and FP32 rewards are complete on return
+    CPMDP_CUDA(cudaStreamSynchronize(0));
     return CPMDP_OK;
 }
 
@@ -339,7 +398,7 @@ cpmdp_status cpmdp_components(const cpmdp_factors *h, int64_t s, int32_t a, int6
     *count = 0;
     if (F.cell[(size_t)s] != CPMDP_CELL_FREE) return CPMDP_OK;
     const int D = F.ndim;
-    const uint32_t code = F.code[(size_t)s];
+    const uint32_t code = F.code.empty() ? code_of(F, s) : F.code[(size_t)s];
     std::map<int64_t, double> acc;
     auto move = [&](int d, int sg, double w) {
         const int j = 2 * d + sg;

@@ -322,3 +322,20 @@ def test_large_512_sampled(cp, oc):
     del V, out, pi
     f.close()
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("shape", [(7,), (5, 6), (4, 5, 3), (3, 2, 3, 2)])
+def test_device_factors_components_match_host(cp, shape):
+    """Factors on a device keep no host codes (the codes are built on the GPU);
+    their Definition-3 components, derived per state on the host, equal those
+    of host-only factors built by the other routine, for every state and
+    action (walls, obstacles and terminals included)."""
+    gw = ci.gridworld(shape, p=0.7, gamma=0.9, step_reward=-0.04, goal_rewards=[1.0, -1.0],
+                      obstacle_rate=0.2, seed=5)
+    fd = cp.build_factors(gw, device=0)
+    fh = cp.build_factors(gw, device=-1)
+    for s in range(gw.nstates):
+        for a in range(2 * len(shape)):
+            assert cp.components(fd, s, a) == cp.components(fh, s, a)
+    fd.close()
+    fh.close()
