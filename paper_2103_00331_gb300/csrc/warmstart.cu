@@ -8,11 +8,12 @@
 // Kernels (BF16 storage, FP32 accumulation, channels-last activations with
 // 64 channels, "same" dilated 3 x 3 x 3 convolutions, tap t = (dz+1) * 9 +
 // (dy+1) * 3 + (dx+1)):
-//   conv_kernel      y[v, n] = sum_t sum_k x[v + s d off(t), k] w[t, k, n] (+ b, ReLU, mask)
-//                    forward (s = +1, w = W^T per tap) and data gradient
-//                    (s = -1, w = W per tap, times the ReLU mask of the
-//                    layer input), a 64-voxel x 64-channel tile per block
-//   conv_dw_kernel   dW[t, co, ci] = sum_v dy[v, co] x[v + d off(t), ci]
+//   conv_tc_kernel   y[v, n] = sum_t sum_k x[v + s d off(t), k] B_t[n, k] (+ b, ReLU, mask)
+//                    on the tcgen05 tensor cores: forward (s = +1, B_t[co, ci] =
+//                    W[t, co, ci]) and data gradient (s = -1, B_t[ci, co] =
+//                    W[t, co, ci], times the ReLU mask of the layer input),
+//                    a 128-voxel x 64-channel tile per CTA
+//   conv_dw_kernel   dW[t, co, ci] = sum_v dy[v, co] x[v + d off(t), ci] (SIMT)
 //   plus features / targets / upsampling from a packed batch, the loss
 //   gradient, Adam and the FP32 -> BF16 weight casts.
 #include <cuda_bf16.h>
