@@ -192,9 +192,27 @@ def cpu_oracle_sample(gw, budget_s=12.0, max_reps=50):
         el = time.perf_counter() - t0
         if el >= budget_s or reps >= max_reps:
             break
-    return {"value": backups / el, "unit": UNIT, "cores": oc.threads(), "kind": "oracle",
-            "sample": f"{reps} full FP64 VI solves to 1e-6 of the 64^3 instance ({k} sweeps each), "
-                      f"{el:.1f} s on {oc.threads()} OpenMP threads"}
+    out = {"value": backups / el, "unit": UNIT, "cores": oc.threads(), "kind": "oracle",
+           "sample": f"{reps} full FP64 VI solves to 1e-6 of the 64^3 instance ({k} sweeps each), "
+                     f"{el:.1f} s on {oc.threads()} OpenMP threads"}
+    # the same oracle on one core (a bounded sample: whole solves until ~budget_s / 3)
+    nthreads = oc.threads()
+    oc.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        b1, r1 = 0, 0
+        while True:
+            _, _, k1, _ = oc.value_iteration(gw, tol=TOL, max_iter=5000)
+            b1 += k1 * S * A
+            r1 += 1
+            el1 = time.perf_counter() - t0
+            if el1 >= budget_s / 3 or r1 >= max_reps:
+                break
+    finally:
+        oc.set_threads(nthreads)
+    out["one_core"] = {"value": b1 / el1, "unit": UNIT, "cores": 1,
+                       "sample": f"{r1} full FP64 VI solves of the same instance, {el1:.1f} s on 1 thread"}
+    return out
 
 
 def run_reference(args, rank, world):
