@@ -196,15 +196,18 @@ static uint32_t code_of(const Factors &F, int64_t s) {
 
 struct CodeGeom {
     int ndim;
-    int64_t shape[kMaxDim], stride[kMaxDim];
+    int shape[kMaxDim], stride[kMaxDim];
 };
 
 // Per-state codes of blocked moves from the cell kinds (device copy of the
-// rule in build_gridworld), stored in `cb` bytes per state.
-__global__ void codes_kernel(const uint8_t *__restrict__ cell, CodeGeom g, int64_t S, int cb, uint8_t *__restrict__ out) {
+// rule in build_gridworld), stored in `cb` bytes per state. |S| < 2^31 is
+// validated, so 32-bit coordinates suffice (64-bit division is emulated).
+__global__ void codes_kernel(const uint8_t *__restrict__ cell, CodeGeom g, int S, int cb, uint8_t *__restrict__ out) {
     const int D = g.ndim;
     const uint32_t all_dirs = (uint32_t)((1ull << (2 * D)) - 1);
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+    // the loop index is 64-bit so the stride step cannot overflow near |S| = 2^31
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S; i += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)i;
         const uint8_t k = cell[s];
         uint32_t c;
         if (k == CPMDP_CELL_OBSTACLE) {
@@ -213,9 +216,9 @@ __global__ void codes_kernel(const uint8_t *__restrict__ cell, CodeGeom g, int64
             c = all_dirs | (1u << (2 * D + 1));
         } else {
             c = 0;
-            int64_t rem = s;
+            int rem = s;
             for (int d = 0; d < D; d++) {
-                const int64_t x = rem / g.stride[d];
+                const int x = rem / g.stride[d];
                 rem -= x * g.stride[d];
                 if (x == 0 || cell[s - g.stride[d]] == CPMDP_CELL_OBSTACLE) c |= 1u << (2 * d);
                 if (x == g.shape[d] - 1 || cell[s + g.stride[d]] == CPMDP_CELL_OBSTACLE) c |= 1u << (2 * d + 1);
@@ -254,8 +257,8 @@ static cpmdp_status upload(Factors &F) {
         CPMDP_CUDA(cudaMalloc(&F.d_code, S * cb));
         CodeGeom geo{};
         geo.ndim = F.ndim;
-        for (int d = 0; d < F.ndim; d++) { geo.shape[d] = F.shape[d]; geo.stride[d] = F.stride[d]; }
-        codes_kernel<<<blocks, 256>>>(F.d_cell, geo, F.nstates, (int)cb, static_cast<uint8_t *>(F.d_code));
+        for (int d = 0; d < F.ndim; d++) { geo.shape[d] = (int)F.shape[d]; geo.stride[d] = (int)F.stride[d]; }
+        codes_kernel<<<blocks, 256>>>(F.d_cell, geo, (int)F.nstates, (int)cb, static_cast<uint8_t *>(F.d_code));
         CPMDP_CUDA(cudaGetLastError());
     } else {
         cpmdp_status st = dense_prepare(F);
