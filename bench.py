@@ -372,6 +372,7 @@ def run_ours(args, rank, world, local, pg):
     if not args.skip_large:
         large = hbm_sweep(cp, dev, stream, hbm or 6800.0)
         p0 = paper_shaped_solve(cp, dev, stream)
+    small = small_10x10(cp, dev, stream)
 
     batch = None
     if not args.skip_batch:
@@ -402,13 +403,14 @@ def run_ours(args, rank, world, local, pg):
             e2e_units += r1["backups"] + r2["backups"]
     e2e_total, e2e_max = aggregate(pg, e2e_units, sum(e2e_ms), device=dev)
     e2e = {"value": e2e_total / (e2e_max / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": S * (4 + 8 + 1 + 1),   # R32, R64, cell, code uploaded by build_factors
+           "h2d_bytes_per_step": S * (8 + 1),           # R64 and the cell kinds uploaded by build_factors
            "d2h_bytes_per_step": 2 * S * (4 + 1),       # V and policy after VI and after PI
            "ms_per_step": statistics.median(e2e_ms)}
 
     cpu = None
     if rank == 0 and world >= 1 and not args.skip_cpu:
         cpu = cpu_oracle_sample(gw, budget_s=args.cpu_seconds)
+        small["cpu_oracles"] = small_10x10_cpu()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -421,7 +423,7 @@ def run_ours(args, rank, world, local, pg):
                 "vi_sweeps": statistics.median(vi_iters), "plain_vi_sweeps": rpl["iterations"],
                 "pi_sweeps": statistics.median(pi_iters), "pi_ms": statistics.median(pi_ms),
                 "certified_residual": rv["certified_residual"], "error_bound": rv["error_bound"],
-                "grid_barrier_solver": grid_barrier, "paper_shaped_1000x1000": p0,
+                "grid_barrier_solver": grid_barrier, "paper_shaped_1000x1000": p0, "small_10x10": small,
                 "hbm_sweep_512": large, "roofline_vi": roof_vi, "batch_4096": batch,
                 "warmstart_512x64": warm}
         print(json.dumps(line), flush=True)
@@ -561,6 +563,73 @@ def paper_shaped_solve(cp, dev, stream):
             "precision": "f64", "sweeps": r["iterations"], "converged": r["status"] == cp.OK,
             "ms": statistics.median(times), "solver": r["solver"],
             "paper_context": "2,140.34 s for CP-MDP VI on this shape, CPU, Python (paper's runtime table)"}
+
+
+def small_10x10(cp, dev, stream):
+    """The 10 x 10 GridWorld (4 actions, p = 0.8 with 0.1 slips, step -0.04,
+    +1 / -1 terminals, gamma = 0.9): FP64 value iteration to 1e-6 and FP64
+    policy iteration from zeros on the GPU, one persistent launch each
+    (100 states: latency bound), CUDA events, median of 10 after warm-up."""
+    import torch
+    import cpmdp_inputs as ci
+    gw = ci.config_small_2d(0)
+    f = cp.build_factors(gw, device=dev.index)
+    V = torch.zeros(gw.nstates, dtype=torch.float64, device=dev)
+    pi = torch.zeros(gw.nstates, dtype=torch.uint8, device=dev)
+    opts = cp.default_opts(tol=TOL, max_iter=1000)
+    out = {"states": gw.nstates, "actions": 4, "precision": "f64"}
+    for mode in ("vi", "pi"):
+        times, r = [], None
+        for i in range(11):
+            V.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if mode == "vi":
+                r = cp.value_iteration(f, cp.F64, V, pi, opts=opts, stream=stream)
+            else:
+                r = cp.policy_iteration(f, cp.F64, V, pi, opts=opts, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        out[mode] = {"ms": ms, "sweeps": r["iterations"], "backups_per_s": r["backups"] / (ms / 1e3)}
+    f.close()
+    return out
+
+
+def small_10x10_cpu(reps=20):
+    """The same 10 x 10 solves by the oracles as they stand: the tabular FP64
+    oracle (numpy, P expanded from the GridWorld rules; VI and PI with exact
+    evaluation) and the CP-factor C oracle (FP64 VI) on all host cores and on
+    one core."""
+    import cpmdp_inputs as ci
+    from oracle import cpfactor as oc
+    from oracle import tabular as tb
+    gw = ci.config_small_2d(0)
+    P = tb.transition_tabular(gw.shape, gw.cell, gw.p)
+    R = gw.reward.reshape(-1)
+
+    def timed(fn):
+        fn()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        return (time.perf_counter() - t0) * 1e3 / reps
+
+    oc.build()
+    out = {"tabular_vi_ms": timed(lambda: tb.value_iteration(P, R, gw.gamma, gw.cell, tol=TOL)),
+           "tabular_pi_ms": timed(lambda: tb.policy_iteration(P, R, gw.gamma, gw.cell)),
+           "cp_factor_vi_ms": timed(lambda: oc.value_iteration(gw, tol=TOL, max_iter=1000)),
+           "cp_factor_threads": oc.threads()}
+    nthreads = oc.threads()
+    oc.set_threads(1)
+    try:
+        out["cp_factor_vi_ms_one_core"] = timed(lambda: oc.value_iteration(gw, tol=TOL, max_iter=1000))
+    finally:
+        oc.set_threads(nthreads)
+    return out
 
 
 def hbm_sweep(cp, dev, stream, peak):
