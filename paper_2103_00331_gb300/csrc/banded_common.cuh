@@ -491,6 +491,11 @@ __device__ __forceinline__ long long grid_sync_count(Ctrl *c, int n, unsigned nb
         if (stall) {
             if (nblocks == 1) atomicCAS(&c->status, 0, (int)CPMDP_ETIMEOUT);
             result = -1;
+        } else if (nblocks == 1) {
+            // a single block: the block barriers around this call already
+            // order every thread's global accesses, so no arrival through L2
+            // (small grids: the fence and round trip were most of a sweep)
+            result = flag != 0 ? 1 : 0;
         } else {
             unsigned long long *ctr = &c->bar[n & 1];
             red_add_release(ctr, 1ull | ((unsigned long long)(flag != 0) << 32));
