@@ -49,3 +49,17 @@ def test_reference_arm_other_ranks_do_nothing():
     import bench
     args = argparse.Namespace(steps=1, warmup=0)
     assert bench.run_reference(args, rank=1, world=2) == 0
+
+
+def test_small_case_cpu_oracles_report():
+    """The 10 x 10 CPU-oracle timings bench.py reports beside the GPU solve:
+    every field present and positive, the one-core run restores the
+    oracle's thread count."""
+    import bench
+    from oracle import cpfactor as oc
+    oc.build()
+    before = oc.threads()
+    out = bench.small_10x10_cpu(reps=1)
+    for k in ("tabular_vi_ms", "tabular_pi_ms", "cp_factor_vi_ms", "cp_factor_vi_ms_one_core"):
+        assert out[k] > 0
+    assert out["cp_factor_threads"] == before == oc.threads()
