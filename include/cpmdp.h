@@ -129,9 +129,10 @@ typedef struct {
                                 certified residual and the policy (FP64 argmax) */
     int32_t fused;           /* 1 (default): fused device-resident solver; FP32 GridWorld solves of
                                 1 to 3 dimensions whose rows are a multiple of 4 states and that fit
-                                one co-resident grid at one thread per 4 states run barrier-free
-                                (sweeps synchronised through sweep-tagged values, the stopping rule
-                                checked two sweeps late; same values and sweep counts), the rest with
+                                one co-resident grid at one thread per column of 1, 2 or 4 segments of
+                                4 states run barrier-free (sweeps synchronised through sweep-tagged
+                                values, the stopping rule checked three sweeps late; same values and
+                                sweep counts), the rest with
                                 a grid barrier per sweep; 2: always the grid-barrier solver; 0: the
                                 plain unfused FP32/FP64 baseline (one kernel per action, separate max
                                 and residual kernels, residual checked on the host every sweep) */

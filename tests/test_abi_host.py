@@ -129,3 +129,25 @@ def test_solvers_refuse_host_only_factors(cp):
         with pytest.raises(cp.CpmdpError) as ei:
             call()
         assert ei.value.status == cp.EINVAL and "host-only" in cp.last_error()
+
+
+def _c_struct_fields(hdr, name):
+    """(field, C type) of `typedef struct { ... } name;` in declaration order."""
+    body = re.search(r"typedef struct \{((?:(?!typedef struct).)*?)\}\s*" + name + r";", hdr, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return [(n, t + p) for t, p, n in re.findall(r"\b(double|int32_t|int64_t)\s*(\*?)\s*(\w+)\s*;", body)]
+
+
+def test_ctypes_structs_match_header(cp):
+    """The binding's SolveOpts / Result mirror cpmdp_solve_opts / cpmdp_result
+    field for field (names, order, types), so results are not misread when
+    the header grows a field."""
+    hdr = open(os.path.join(ROOT, "include", "cpmdp.h")).read()
+    ctype = {"double": ctypes.c_double, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64,
+             "double*": ctypes.c_void_p}
+    for cname, pycls in (("cpmdp_solve_opts", cp.SolveOpts), ("cpmdp_result", cp.Result)):
+        c = _c_struct_fields(hdr, cname)
+        py = list(pycls._fields_)
+        assert [n for n, _ in c] == [n for n, _ in py], cname
+        for (n, ct), (_, pt) in zip(c, py):
+            assert ctype[ct] is pt, (cname, n)
