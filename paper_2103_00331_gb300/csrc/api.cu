@@ -61,11 +61,12 @@ SolveOpts resolve_opts(const cpmdp_solve_opts *o, cpmdp_precision prec) {
 }
 
 static void free_device(Factors &F) {
-    void *ptrs[] = {F.d_code, F.d_R32, F.d_R64, F.d_cell, F.d_scratch, F.d_q, F.d_ctrl,
-                    F.d_U32, F.d_U64, F.d_Ubf, F.d_lam32, F.d_lam64, F.d_dense_work, F.d_Vd,
-                    F.d_RB, F.d_T, F.d_EB, F.d_Vbase, F.d_tc_err, F.d_flow};
+    // the arena holds d_code, d_R32, d_R64, d_cell, d_scratch and d_ctrl
+    void *ptrs[] = {F.d_arena, F.d_q, F.d_U32, F.d_U64, F.d_Ubf, F.d_lam32, F.d_lam64, F.d_dense_work,
+                    F.d_Vd, F.d_RB, F.d_T, F.d_EB, F.d_Vbase, F.d_tc_err, F.d_flow};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    F.d_arena = nullptr;
     F.d_code = nullptr; F.d_R32 = nullptr; F.d_R64 = nullptr; F.d_cell = nullptr;
     F.d_scratch = nullptr; F.d_q = nullptr; F.d_ctrl = nullptr; F.d_U32 = nullptr;
     F.d_U64 = nullptr; F.d_Ubf = nullptr; F.d_lam32 = nullptr; F.d_lam64 = nullptr;
@@ -241,20 +242,28 @@ static cpmdp_status upload(Factors &F) {
     CPMDP_CUDA(cudaDeviceGetAttribute(&F.num_sms, cudaDevAttrMultiProcessorCount, F.device));
     const size_t S = (size_t)F.nstates;
     const int blocks = (int)std::min<int64_t>((F.nstates + 255) / 256, (int64_t)F.num_sms * 16);
-    CPMDP_CUDA(cudaMalloc(&F.d_R32, S * sizeof(float)));
-    CPMDP_CUDA(cudaMalloc(&F.d_R64, S * sizeof(double)));
+    // one allocation for the per-state arrays, the scratch and the control
+    // block, each part 256-byte aligned
+    const size_t cb = F.kind == CPMDP_GRIDWORLD ? (size_t)F.code_bytes : 0;
+    auto up = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    F.scratch_bytes = S * sizeof(double);
+    const size_t o_R64 = 0, o_scratch = o_R64 + up(S * sizeof(double)), o_R32 = o_scratch + up(F.scratch_bytes);
+    const size_t o_cell = o_R32 + up(S * sizeof(float)), o_ctrl = o_cell + up(S), o_code = o_ctrl + up(sizeof(Ctrl));
+    const size_t total = o_code + up(S * cb);
+    CPMDP_CUDA(cudaMalloc(&F.d_arena, total));
+    char *arena = static_cast<char *>(F.d_arena);
+    F.d_R64 = reinterpret_cast<double *>(arena + o_R64);
+    F.d_scratch = arena + o_scratch;
+    F.d_R32 = reinterpret_cast<float *>(arena + o_R32);
+    F.d_cell = reinterpret_cast<uint8_t *>(arena + o_cell);
+    F.d_ctrl = reinterpret_cast<Ctrl *>(arena + o_ctrl);
+    F.d_code = cb ? arena + o_code : nullptr;
     CPMDP_CUDA(cudaMemcpy(F.d_R64, F.reward.data(), S * sizeof(double), cudaMemcpyHostToDevice));
     to_f32_kernel<<<blocks, 256>>>(F.d_R64, F.d_R32, F.nstates);
     CPMDP_CUDA(cudaGetLastError());
-    CPMDP_CUDA(cudaMalloc(&F.d_cell, S));
     CPMDP_CUDA(cudaMemcpy(F.d_cell, F.cell.data(), S, cudaMemcpyHostToDevice));
-    F.scratch_bytes = S * sizeof(double);
-    CPMDP_CUDA(cudaMalloc(&F.d_scratch, F.scratch_bytes));
-    CPMDP_CUDA(cudaMalloc(&F.d_ctrl, sizeof(Ctrl)));
     CPMDP_CUDA(cudaMemset(F.d_ctrl, 0, sizeof(Ctrl)));
     if (F.kind == CPMDP_GRIDWORLD) {
-        const size_t cb = (size_t)F.code_bytes;
-        CPMDP_CUDA(cudaMalloc(&F.d_code, S * cb));
         CodeGeom geo{};
         geo.ndim = F.ndim;
         for (int d = 0; d < F.ndim; d++) { geo.shape[d] = (int)F.shape[d]; geo.stride[d] = (int)F.stride[d]; }

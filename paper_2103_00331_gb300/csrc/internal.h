@@ -63,7 +63,9 @@ struct Factors {
     std::vector<double> lambda;        // [a][r]
     std::vector<int64_t> factor_off;   // offset of block (a, r, d) in dense_factors
 
-    // device copies
+    // device copies (rewards, cells, scratch, control block and codes share
+    // one allocation, d_arena; free only that)
+    void *d_arena = nullptr;
     void *d_code = nullptr;
     float *d_R32 = nullptr;
     double *d_R64 = nullptr;
