@@ -253,45 +253,52 @@ def run_ours(args, rank, world, local, pg):
     S, A = gw.nstates, 2 * len(gw.shape)
     f = cp.build_factors(gw, device=local)
     V = torch.zeros(S, dtype=torch.float32, device=dev)
+    Vp = torch.zeros(S, dtype=torch.float32, device=dev)
     pi = torch.zeros(S, dtype=torch.uint8, device=dev)
+    pip = torch.zeros(S, dtype=torch.uint8, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     vi_opts = cp.default_opts(tol=TOL, max_iter=5000)
     pi_opts = cp.default_opts(tol=TOL, max_iter=5000)
 
-    def step(timers=None):
-        V.zero_()
-        if timers:
-            timers[0].record(stream)
+    # One step: value iteration from V = 0 and policy iteration from V = 0
+    # (two zeroed buffers, prepared before the step), each with its FP64
+    # certifying sweep. The device time of a step is the sum of the two
+    # calls' elapsed_ms: CUDA events the library records on the stream
+    # around its own launches, so a host-side stall between a Python event
+    # and the library's first launch (GIL, other threads of the process)
+    # cannot enter it. The Python-side event bracket is reported beside it.
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
         rv = cp.value_iteration(f, cp.F32, V, pi, opts=vi_opts, stream=stream)
-        if timers:
-            timers[1].record(stream)
-        V.zero_()
-        if timers:
-            timers[2].record(stream)
-        rp = cp.policy_iteration(f, cp.F32, V, pi, opts=pi_opts, stream=stream)
-        if timers:
-            timers[3].record(stream)
+        rp = cp.policy_iteration(f, cp.F32, Vp, pip, opts=pi_opts, stream=stream)
+        if ev:
+            ev[1].record(stream)
         return rv, rp
 
     for _ in range(max(args.warmup, 0)):
+        V.zero_()
+        Vp.zero_()
         step()
     torch.cuda.synchronize()
     if pg is not None:
         pg.barrier()
     sampler = ClockSampler(local)
     sampler.start()
-    total_ms, vi_ms, pi_ms, backups, launches = 0.0, [], [], 0, 0
+    total_ms, py_ms, vi_ms, pi_ms, backups, launches = 0.0, [], [], [], 0, 0
     vi_bytes, pi_bytes, vi_iters, pi_iters = 0, 0, [], []
     for _ in range(args.steps):
+        V.zero_()
+        Vp.zero_()
         flush.zero_()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         torch.cuda.synchronize()
         rv, rp = step(ev)
         torch.cuda.synchronize()
-        a, b = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
-        vi_ms.append(a)
-        pi_ms.append(b)
-        total_ms += ev[0].elapsed_time(ev[3])
+        vi_ms.append(rv["elapsed_ms"])
+        pi_ms.append(rp["elapsed_ms"])
+        py_ms.append(ev[0].elapsed_time(ev[1]))
+        total_ms += rv["elapsed_ms"] + rp["elapsed_ms"]
         backups += rv["backups"] + rp["backups"]
         launches += 4   # persistent VI solve + certify sweep, persistent PI solve + certify sweep
         vi_iters.append(rv["iterations"])
@@ -304,6 +311,14 @@ def run_ours(args, rank, world, local, pg):
         pg.barrier()
     units, ms_max = aggregate(pg, backups, total_ms, device=dev)
     value = units / (ms_max / 1e3)
+    per_step = {"timing": "device time of each step = elapsed_ms of its VI and PI calls (CUDA events the "
+                          "library records on the stream around its launches)",
+                "vi_ms": step_stats(vi_ms), "pi_ms": step_stats(pi_ms),
+                "python_event_bracket_ms": step_stats(py_ms),
+                "host_stall_ms_total": sum(py_ms) - total_ms,
+                "pi_ms_each": [round(x, 4) for x in pi_ms], "vi_ms_each": [round(x, 4) for x in vi_ms],
+                "python_bracket_ms_each": [round(x, 4) for x in py_ms],
+                "pi_sweeps_each": pi_iters}
 
     # plain unfused FP32 VI on the same instance (the comparator of the metric)
     plain_opts = cp.default_opts(tol=TOL, max_iter=5000, fused=0, certify=0)
@@ -328,20 +343,15 @@ def run_ours(args, rank, world, local, pg):
     gb_vi, gb_pi = [], []
     for i in range(max(3, min(args.steps, 10)) + 1):
         flush.zero_()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        V.zero_()
+        Vp.zero_()
         torch.cuda.synchronize()
-        V.zero_()
-        ev[0].record(stream)
         gv = cp.value_iteration(f, cp.F32, V, pi, opts=gb_opts_vi, stream=stream)
-        ev[1].record(stream)
-        V.zero_()
-        ev[2].record(stream)
-        gp = cp.policy_iteration(f, cp.F32, V, pi, opts=gb_opts_pi, stream=stream)
-        ev[3].record(stream)
+        gp = cp.policy_iteration(f, cp.F32, Vp, pip, opts=gb_opts_pi, stream=stream)
         torch.cuda.synchronize()
         if i > 0:
-            gb_vi.append(ev[0].elapsed_time(ev[1]))
-            gb_pi.append(ev[2].elapsed_time(ev[3]))
+            gb_vi.append(gv["elapsed_ms"])
+            gb_pi.append(gp["elapsed_ms"])
     grid_barrier = {"kernels": "solve_vi_kernel<float,3,4> / solve_pi_kernel<float,3,4> (fused=2)",
                     "vi_ms": statistics.median(gb_vi), "pi_ms": statistics.median(gb_pi),
                     "vi_sweeps": gv["iterations"], "pi_sweeps": gp["iterations"],
@@ -373,6 +383,10 @@ def run_ours(args, rank, world, local, pg):
         large = hbm_sweep(cp, dev, stream, hbm or 6800.0)
         p0 = paper_shaped_solve(cp, dev, stream)
     small = small_10x10(cp, dev, stream)
+
+    dense = None
+    if not args.skip_dense:
+        dense = dense_measure(cp, dev, stream)
 
     batch = None
     if not args.skip_batch:
@@ -423,8 +437,8 @@ def run_ours(args, rank, world, local, pg):
                 "vi_sweeps": statistics.median(vi_iters), "plain_vi_sweeps": rpl["iterations"],
                 "pi_sweeps": statistics.median(pi_iters), "pi_ms": statistics.median(pi_ms),
                 "certified_residual": rv["certified_residual"], "error_bound": rv["error_bound"],
-                "grid_barrier_solver": grid_barrier, "paper_shaped_1000x1000": p0, "small_10x10": small,
-                "hbm_sweep_512": large, "roofline_vi": roof_vi, "batch_4096": batch,
+                "per_step": per_step, "grid_barrier_solver": grid_barrier, "paper_shaped_1000x1000": p0, "small_10x10": small,
+                "hbm_sweep_512": large, "roofline_vi": roof_vi, "dense_64x4": dense, "batch_4096": batch,
                 "warmstart_512x64": warm}
         print(json.dumps(line), flush=True)
     f.close()
@@ -508,6 +522,97 @@ def batch_measure(cp, dev, stream, seed=0, count=4096, reps=3):
                     f"and scaled by {scale:.0f}"}
 
 
+def dense_measure(cp, dev, stream, reps=2):
+    """Config 3: the 4-D dense CP model 64^4 (16.8M states, 8 actions, rank
+    8, factor rows U(0,1) normalised, R ~ N(0,1), gamma = 0.95). Value
+    iteration from V = 0 with BF16x3 tensor-core sweeps (defect correction
+    against FP32 base expectations) until the FP64 residual max |T(V) - V| is
+    below 1e-6, FP64 certifying sweeps and the FP64 argmax policy included;
+    one BF16x3 sweep alone (tcgen05 passes) for the tensor roofline; one FP64
+    sweep; the FP32 SIMT mode-product value iteration (residual read by the
+    host each sweep) as the plain comparator; and the error against the FP64
+    oracle's own value iteration at its 4096 stored sample states."""
+    import torch
+    import cpmdp_inputs as ci
+    dc = ci.config_dense_4d(side=64, seed=0)
+    f = cp.build_factors(dc, device=dev.index)
+    S, A, Rk = dc.nstates, dc.nactions, dc.rank
+    V = torch.zeros(S, dtype=torch.float32, device=dev)
+    pi = torch.zeros(S, dtype=torch.uint8, device=dev)
+    opts = cp.default_opts(tol=TOL, max_iter=1000)
+    r = cp.value_iteration(f, cp.BF16X3, V, pi, opts=opts, stream=stream)   # warm-up: tiles, buffers
+    times = []
+    for _ in range(reps):
+        V.zero_()
+        torch.cuda.synchronize()
+        r = cp.value_iteration(f, cp.BF16X3, V, pi, opts=opts, stream=stream)
+        times.append(r["elapsed_ms"])
+    solve_ms = statistics.median(times)
+
+    def timed(fn, n=4):
+        ts = []
+        for i in range(n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i:
+                ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    Vb = torch.empty_like(V)
+    sweep_ms = timed(lambda: cp.bellman_backup(f, cp.BF16X3, V, Vb, None, None, stream=stream))
+    Vd = V.double()
+    Wd = torch.empty_like(Vd)
+    fp64_ms = timed(lambda: cp.bellman_backup(f, cp.F64, Vd, Wd, None, None, stream=stream), n=2)
+    del Vd, Wd
+    flops = 2.0 * 64 * 4 * S * A * Rk            # method flops per sweep (4 mode products per chain)
+    pk = measured_peaks()
+    bf16 = pk.get("bf16_tflops")
+    peak = bf16 or 1900.0
+    ach = flops / (sweep_ms * 1e9)
+    roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)" if bf16 else "fallback 1.9 PFLOP/s",
+            "kernel": "dense_pass_a + dense_pass_b (BF16x3 tcgen05 sweep)",
+            "flops_per_sweep": flops, "issued_bf16_tflops": 3 * ach, "issued_frac": 3 * ach / peak,
+            "note": "achieved counts the method's FP32-equivalent flops (2 R D N per state-action); "
+                    "BF16x3 issues three bf16 products for each"}
+    # plain comparator: FP32 SIMT mode products, residual read back each sweep
+    Vp = torch.zeros_like(V)
+    torch.cuda.synchronize()
+    rp = cp.value_iteration(f, cp.F32, Vp, None, opts=cp.default_opts(tol=TOL, max_iter=1000, certify=0),
+                            stream=stream)
+    out = {"workload": "dense-cp-64^4-A8-R8-gamma0.95 (config 3)", "states": S, "actions": A, "rank": Rk,
+           "time_to_tol_ms": solve_ms, "sweeps": r["iterations"], "rebases": r["rounds"],
+           "fp64_certify_sweeps": r["eval_sweeps"], "residual": r["residual"],
+           "certified_residual": r["certified_residual"], "error_bound": r["error_bound"],
+           "backups_per_s": r["backups"] / (solve_ms / 1e3), "bf16x3_sweep_ms": sweep_ms,
+           "fp64_sweep_ms": fp64_ms, "fp64_tflops": flops / (fp64_ms * 1e9),
+           "fp64_frac_of_nominal_1.25": flops / (fp64_ms * 1e9) / 1.25, "roofline": roof,
+           "plain_fp32_simt_vi_ms": rp["elapsed_ms"], "plain_fp32_simt_vi_sweeps": rp["iterations"],
+           "speedup_vs_plain_fp32_vi": rp["elapsed_ms"] / solve_ms}
+    del Vp
+    gold = os.path.join(ROOT, "tests", "golden", "dense64_vi_samples.npz")
+    if os.path.exists(gold):
+        g = np.load(gold)
+        idx = torch.as_tensor(g["state"], device=dev)
+        got = V[idx].double().cpu().numpy()
+        gp = pi[idx].cpu().numpy()
+        err = float(np.abs(got - g["value"]).max())
+        bound = r["error_bound"] + float(g["certified_residual"]) / (1 - dc.gamma)
+        sure = g["gap"] > 2 * dc.gamma * bound
+        out["vs_fp64_oracle_vi"] = {"samples": int(len(idx)), "max_abs_diff": err,
+                                    "max_rel_diff": err / float(g["max_abs_value"]),
+                                    "oracle_sweeps": int(g["sweeps"]),
+                                    "policy_equal_where_gap_exceeds_bound": int((gp[sure] == g["policy"][sure]).sum()),
+                                    "policy_compared": int(sure.sum())}
+    f.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def warmstart_measure(device_index):
     """Config 5: the committed network (trained on 20,000 solved 32^3
     instances) warm-starts batched value iteration on 512 held-out 64^3
@@ -518,6 +623,11 @@ def warmstart_measure(device_index):
         return None
     net = ws.WarmStartNet.load(path, device=device_index)
     return ws.evaluate(net, count=512, side=64)
+
+
+def step_stats(xs):
+    """min / median / mean / max of per-step times (ms)."""
+    return {"min": min(xs), "median": statistics.median(xs), "mean": statistics.mean(xs), "max": max(xs)}
 
 
 def measured_peaks():
@@ -775,6 +885,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-dense", action="store_true")
     ap.add_argument("--skip-warmstart", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--kernel-case", choices=["sweep512", "sweep320", "solve64", "pi64", "solve64b", "pi64b", "dense64",

@@ -155,7 +155,8 @@ typedef struct {
     int32_t status;              /* cpmdp_status of the solve */
     int32_t iterations;          /* sweeps: VI backups, or PI evaluation + improvement sweeps */
     int32_t rounds;              /* policy iteration improvement rounds (0 for VI) */
-    int32_t eval_sweeps;         /* policy iteration evaluation sweeps (0 for VI) */
+    int32_t eval_sweeps;         /* policy iteration evaluation sweeps (0 for VI); BF16X3 value
+                                    iteration: the FP64 certifying sweeps it took */
     double residual;             /* last max |V' - V| in working precision */
     double certified_residual;   /* FP64 max |T(V) - V| of the returned V (-1 if not computed) */
     double error_bound;          /* certified_residual / (1 - gamma): bound on max |V - V*| (-1 if n/a) */
@@ -222,6 +223,12 @@ cpmdp_status cpmdp_bellman_backup(const cpmdp_factors *factors, cpmdp_precision 
  * policy_out (device, |S|, may be NULL) receives the greedy policy of the
  * returned V (FP64 argmax when certify is on). opts may be NULL (defaults);
  * info may be NULL. Synchronises with `stream` before returning.
+ * BF16X3 (dense models) with certify on: the working FP32 residual of float
+ * iterates cannot resolve differences below a few units in the last place
+ * of the largest |V|, so once it is below tol the solve runs
+ * ceil(ln 2 / ln(1/gamma)) more sweeps and then an FP64 backup; it repeats
+ * that until the FP64 residual max |T(V) - V| is below tol, so the returned
+ * V meets the stopping rule in FP64 (info->eval_sweeps = FP64 sweeps taken).
  * Errors: EINVAL, ECUDA, ENOCONV (max_iter reached), ETIMEOUT.
  */
 cpmdp_status cpmdp_value_iteration(const cpmdp_factors *factors, cpmdp_precision precision,
@@ -310,6 +317,23 @@ cpmdp_status cpmdp_batch_info(const cpmdp_batch *batch, int32_t *count, int64_t 
 cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *batch, float *V, const cpmdp_solve_opts *opts,
                                          int32_t *iterations_out, double *residual_out, cpmdp_result *info,
                                          void *stream);
+
+/*
+ * One FP64 backup (Eq. 1 in double arithmetic, FP64 rewards and weights) of
+ * every instance of a packed float value array V (device, 16-byte aligned),
+ * for instance the result of cpmdp_batch_value_iteration: the greedy policy
+ * of the returned values (background section: value iteration ends with
+ * the greedy policy) and per instance the certified residual
+ * max |T(V) - V| over its non-obstacle states, which bounds the distance
+ * to V* by certified / (1 - gamma_i).
+ *   policy_out     device, packed like V (uint8, FP64 argmax, lowest action
+ *                  on exact ties, 255 on obstacles and terminals), or NULL;
+ *                  the padding between instances is not written.
+ *   certified_out  host array of `count` doubles, or NULL.
+ * Synchronises with `stream`. Errors: EINVAL, ECUDA.
+ */
+cpmdp_status cpmdp_batch_certify(const cpmdp_batch *batch, const float *V, uint8_t *policy_out,
+                                 double *certified_out, void *stream);
 
 /*
  * Learned warm start (no counterpart in the paper's method; it only changes

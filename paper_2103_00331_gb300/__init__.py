@@ -99,6 +99,8 @@ def _load():
     lib.cpmdp_batch_value_iteration.argtypes = [vp, vp, ctypes.POINTER(SolveOpts), vp, vp,
                                                 ctypes.POINTER(Result), vp]
     lib.cpmdp_batch_value_iteration.restype = ctypes.c_int
+    lib.cpmdp_batch_certify.argtypes = [vp, vp, vp, vp, vp]
+    lib.cpmdp_batch_certify.restype = ctypes.c_int
     for name, args in [
             ("cpmdp_ws_features", [vp, i32, i32, vp, vp]),
             ("cpmdp_ws_targets", [vp, vp, i32, i32, vp, vp, vp]),
@@ -125,7 +127,8 @@ lib = _load()
 EXPORTED = ["cpmdp_default_opts", "cpmdp_build_factors", "cpmdp_free_factors", "cpmdp_factors_info",
             "cpmdp_components", "cpmdp_bellman_backup", "cpmdp_value_iteration",
             "cpmdp_policy_iteration", "cpmdp_value_iteration_static", "cpmdp_batch_build",
-            "cpmdp_batch_free", "cpmdp_batch_info", "cpmdp_batch_value_iteration", "cpmdp_ws_features",
+            "cpmdp_batch_free", "cpmdp_batch_info", "cpmdp_batch_value_iteration", "cpmdp_batch_certify",
+            "cpmdp_ws_features",
             "cpmdp_ws_targets", "cpmdp_ws_upsample", "cpmdp_conv3d_forward", "cpmdp_conv3d_backward_data",
             "cpmdp_conv3d_backward_weight", "cpmdp_ws_loss_grad", "cpmdp_adam_step", "cpmdp_ws_cast_weights",
             "cpmdp_ws_sync", "cpmdp_last_error", "cpmdp_version"]
@@ -358,6 +361,16 @@ def batch_value_iteration(batch: Batch, V, opts=None, stream=None, raise_on_noco
     if st != OK and not (st == ENOCONV and not raise_on_noconv):
         _check(st)
     return res.as_dict(), it, rs
+
+
+def batch_certify(batch: Batch, V, policy_out=None, stream=None):
+    """``cpmdp_batch_certify``: one FP64 backup of every instance of the
+    packed values V; writes the FP64 argmax policy to ``policy_out`` (packed
+    uint8 device tensor, optional) and returns the certified residual
+    max |T(V) - V| per instance (numpy float64)."""
+    cert = np.zeros(batch.count, dtype=np.float64)
+    _check(lib.cpmdp_batch_certify(batch.handle, _ptr(V), _ptr(policy_out), cert.ctypes.data, _stream(stream)))
+    return cert
 
 
 def ws_features(batch, first, count, feat, stream=None):

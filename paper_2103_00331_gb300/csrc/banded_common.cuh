@@ -470,15 +470,23 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
     return v;
 }
 
+// Whether a barrier counter v (arrivals in the low half, raised flags in
+// the high half, one 64-bit sum) still misses arrivals of a barrier that is
+// complete at A arrivals; valid while at most 2^31 arrivals are missing.
+__device__ __forceinline__ bool arrivals_short(unsigned long long v, unsigned long long A) {
+    return (int)((unsigned)v - (unsigned)A) < 0;
+}
+
 // Grid-wide barrier of a co-resident (cooperative) grid that also counts
 // how many blocks raised `flag` (thread 0's value) in the step it closes.
-// Barrier number n uses counter bar[n % 2]: the low 32 bits count arrivals
-// ((n/2 + 1) * nblocks once everyone has arrived), the high 32 bits count
-// raised flags. A block cannot reach barrier n+2 before every block has left
-// barrier n+1, so the value read when barrier n completes holds exactly the
-// arrivals up to barrier n; the flags of step n are its high part minus the
-// high part seen at barrier n-2 (prev0 / prev1 for even / odd n, kept by
-// thread 0). Every wait gives up after timeout_ns or when another block has
+// Barrier number n uses counter bar[n % 2]: every arrival adds 1, and 2^32
+// more when it raises its flag, so the counter is A + F * 2^32 with A =
+// (n/2 + 1) * nblocks arrivals once everyone has arrived and F the flags
+// raised on that counter so far. A block cannot reach barrier n+2 before
+// every block has left barrier n+1, so the value read when barrier n
+// completes holds exactly the arrivals up to barrier n; the flags of step n
+// are (v - A) >> 32 minus the same count at barrier n-2 (prev0 / prev1 for
+// even / odd n, kept by thread 0). Every wait gives up after timeout_ns or when another block has
 // recorded a status: returns -1 (CPMDP_ETIMEOUT stored in the status word).
 // stall: testing aid, this block leaves without arriving.
 __device__ __forceinline__ long long grid_sync_count(Ctrl *c, int n, unsigned nblocks, int flag,
@@ -499,15 +507,20 @@ __device__ __forceinline__ long long grid_sync_count(Ctrl *c, int n, unsigned nb
         } else {
             unsigned long long *ctr = &c->bar[n & 1];
             red_add_release(ctr, 1ull | ((unsigned long long)(flag != 0) << 32));
-            const unsigned long long target = (unsigned long long)(n / 2 + 1) * nblocks;
+            // After this barrier completes, the counter holds A arrivals plus
+            // F raised flags times 2^32 as one 64-bit sum (carries of the low
+            // half included). While blocks still arrive, its low half lies in
+            // [A - nblocks, A) modulo 2^32, so completion is tested on the
+            // low halves' signed difference: no wrap, however many sweeps.
+            const unsigned long long A = (unsigned long long)(n / 2 + 1) * nblocks;
             unsigned long long v = ld_acquire(ctr);
-            if ((v & 0xFFFFFFFFull) < target) {
+            if (arrivals_short(v, A)) {
                 const unsigned long long t0 = global_ns();
                 unsigned spins = 0;
                 do {
                     __nanosleep(32);
                     v = ld_acquire(ctr);
-                    if ((++spins & 15u) == 0 && (v & 0xFFFFFFFFull) < target) {
+                    if ((++spins & 15u) == 0 && arrivals_short(v, A)) {
                         if (*(volatile int *)&c->status != 0) { result = -1; break; }
                         if (global_ns() - t0 > timeout_ns) {
                             atomicCAS(&c->status, 0, (int)CPMDP_ETIMEOUT);
@@ -515,14 +528,14 @@ __device__ __forceinline__ long long grid_sync_count(Ctrl *c, int n, unsigned nb
                             break;
                         }
                     }
-                } while ((v & 0xFFFFFFFFull) < target);
+                } while (arrivals_short(v, A));
             }
             if (result == 0) {
-                const unsigned long long hi = v >> 32;
+                const unsigned long long F = (v - A) >> 32;   // flags raised so far on this counter
                 const unsigned long long prev = (n & 1) ? prev1 : prev0;
-                result = (long long)((hi - prev) & 0xFFFFFFFFull);
-                if (n & 1) prev1 = hi;
-                else prev0 = hi;
+                result = (long long)(F - prev);
+                if (n & 1) prev1 = F;
+                else prev0 = F;
             }
         }
     }

@@ -26,6 +26,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "banded_common.cuh"
@@ -100,8 +101,8 @@ __device__ __forceinline__ void prefetch_tile(const BatchTile &T, const float *V
 // neighbour where that neighbour does not exist, and there the move is
 // blocked in the code (a wall at the end of a row included), so the backup
 // uses V(s) instead. Padding states are obstacles: value 0, no residual.
-template <int D>
-__device__ __forceinline__ void load_rows_any(Segment<float, float, D, 4> &sg, const BandArgs &a, const float *V,
+template <typename TA, int D>
+__device__ __forceinline__ void load_rows_any(Segment<float, TA, D, 4> &sg, const BandArgs &a, const float *V,
                                               int s0, int npad) {
     load_pack<uint8_t, 4>(static_cast<const uint8_t *>(a.code) + s0, sg.code);
     load_pack<float, 4>(V + s0, sg.vs);
@@ -116,7 +117,12 @@ __device__ __forceinline__ void load_rows_any(Segment<float, float, D, 4> &sg, c
     }
     sg.halo_m = V[s0 > 0 ? s0 - 1 : 0];
     sg.halo_p = V[s0 + 4 < npad ? s0 + 4 : npad - 1];
-    load_pack<float, 4>(a.R32 + s0, sg.r);
+    if constexpr (std::is_same<TA, float>::value) {
+        load_pack<float, 4>(a.R32 + s0, sg.r);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) sg.r[k] = a.R64[s0 + k];
+    }
 }
 
 // One 4-state segment of a tile per lane (segment first + lane of the
@@ -147,7 +153,7 @@ __device__ __forceinline__ float batch_tile(const BatchTile &T, const uint8_t *c
     if (lane >= nitems) return 0.f;
     Segment<float, float, D, VEC> sg;
     if (ROWS4) sg.template load<M_VI>(a, Vi, nullptr, (first + lane) * VEC);
-    else load_rows_any<D>(sg, a, Vi, (first + lane) * VEC, (T.nstates + 3) & ~3);
+    else load_rows_any<float, D>(sg, a, Vi, (first + lane) * VEC, (T.nstates + 3) & ~3);
     return sg.template finish_vi<false>(a, Wi, nullptr, (first + lane) * VEC);
 }
 
@@ -312,6 +318,98 @@ __global__ void __launch_bounds__(512, 1) batch_vi_kernel(BatchArgs b) {
     }
 }
 
+// One FP64 backup of every instance of the packed values (Eq. 1 in double
+// arithmetic on the float iterate, FP64 rewards and weights): per instance
+// the certified residual max |T(V) - V| over its non-obstacle states, and
+// the FP64 argmax policy (lowest action on exact ties; 255 on obstacles and
+// terminals). One warp per tile, lane l taking segments l, l + 32, ... of
+// the tile; the padding states between instances are neither read as
+// states nor written.
+struct BatchCertArgs {
+    const BatchTile *tiles;
+    int ntiles;
+    const uint8_t *code;
+    const double *R64;
+    const double *instw;       // per instance: w_move, w_perp, w_stay, gamma
+    const float *V;
+    uint8_t *pi;               // packed policy (nullable)
+    unsigned long long *cert;  // per instance: bits of the certified residual
+};
+
+template <int D, bool ROWS4>
+__device__ __forceinline__ double certify_segment(const BatchCertArgs &c, const BatchTile &T, int item) {
+    BandArgs a;
+    a.nstates = T.nstates;
+    a.nlast = T.nlast;
+#pragma unroll
+    for (int d = 0; d < kMaxDim; d++) a.stride[d] = 0;
+    if (D >= 2) a.stride[0] = T.stride0;
+    if (D >= 3) a.stride[1] = T.stride1;
+    const double *w = c.instw + 4 * (size_t)T.inst;
+    a.w_move = w[0];
+    a.w_perp = w[1];
+    a.w_stay = w[2];
+    a.gamma = w[3];
+    a.code = c.code + T.offset;
+    a.R32 = nullptr;
+    a.R64 = c.R64 + T.offset;
+    const float *Vi = c.V + T.offset;
+    const int s0 = item * 4;
+    Segment<float, double, D, 4> sg;
+    if (ROWS4) sg.template load<M_VI>(a, Vi, nullptr, s0);
+    else load_rows_any<double, D>(sg, a, Vi, s0, (T.nstates + 3) & ~3);
+    double self[4], nb[2 * D][4];
+    sg.neighbours(self, nb);
+    double wm, wp, wst, g;
+    weights<double>(a, wm, wp, wst, g);
+    constexpr unsigned OBST = 1u << (2 * D), TERM = 1u << (2 * D + 1);
+    double res = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (s0 + k >= T.nstates) break;
+        const unsigned code = sg.code[k];
+        double nbk[2 * D];
+#pragma unroll
+        for (int j = 0; j < 2 * D; j++) nbk[j] = nb[j][k];
+        int arg;
+        const double v = vi_state<double, D>(self[k], nbk, code, sg.r[k], wm, wp, wst, g, arg);
+        if (c.pi) c.pi[T.offset + s0 + k] = (code & (OBST | TERM)) ? (uint8_t)255 : (uint8_t)arg;
+        if (!(code & OBST)) res = fmax(res, fabs(v - self[k]));
+    }
+    return res;
+}
+
+__global__ void __launch_bounds__(256) batch_certify_kernel(BatchCertArgs c) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < c.ntiles; t += nw) {
+        const BatchTile T = c.tiles[t];
+        double r = 0.0;
+        for (int i = lane; i < T.nitems; i += 32) {
+            const int item = T.first_item + i;
+            double x = 0.0;
+            switch (T.cls) {
+                case 2: x = certify_segment<1, false>(c, T, item); break;
+                case 3: x = certify_segment<1, true>(c, T, item); break;
+                case 4: x = certify_segment<2, false>(c, T, item); break;
+                case 5: x = certify_segment<2, true>(c, T, item); break;
+                case 6: x = certify_segment<3, false>(c, T, item); break;
+                default: x = certify_segment<3, true>(c, T, item); break;
+            }
+            r = fmax(r, x);
+        }
+        // non-negative doubles order like their bit patterns
+        const unsigned long long b = (unsigned long long)__double_as_longlong(r);
+        unsigned long long m = b;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, m, o);
+            m = y > m ? y : m;
+        }
+        if (lane == 0 && m) atomicMax(&c.cert[T.inst], m);
+    }
+}
+
 }  // namespace cpmdp
 
 // ---------------------------------------------------------------------------
@@ -321,7 +419,8 @@ namespace cpmdp {
 
 static void free_batch_device(cpmdp_batch &B) {
     void *ptrs[] = {B.d_inst, B.d_tiles, B.d_code, B.d_R, B.d_W, B.d_res, B.d_done, B.d_ctrl,
-                    B.d_ring, B.d_p2ctr, B.d_p2tab, B.d_p2hdr, B.d_p2epoch, B.d_p2res};
+                    B.d_ring, B.d_p2ctr, B.d_p2tab, B.d_p2hdr, B.d_p2epoch, B.d_p2res,
+                    B.d_R64, B.d_instw, B.d_cert};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (B.graph) cudaGraphExecDestroy(B.graph);
@@ -546,6 +645,7 @@ cpmdp_status cpmdp_batch_build(const cpmdp_problem *problems, int32_t count, int
     B->ninst = count;
     std::vector<uint8_t> codes;
     std::vector<float> rew;
+    std::vector<double> rew64, instw;
     long long off = 0;
     for (int i = 0; i < count; i++) {
         const cpmdp_problem &p = problems[i];
@@ -584,16 +684,21 @@ cpmdp_status cpmdp_batch_build(const cpmdp_problem *problems, int32_t count, int
         I.w_perp = (float)F.w_perp;
         I.w_stay = (float)F.w_stay;
         I.gamma = (float)F.gamma;
+        instw.push_back(F.w_move);
+        instw.push_back(F.w_perp);
+        instw.push_back(F.w_stay);
+        instw.push_back(F.gamma);
         B->inst.push_back(I);
         B->inst_actions.push_back(F.nactions);
         B->offsets.push_back(off);
         for (int64_t s = 0; s < F.nstates; s++) {
             codes.push_back((uint8_t)F.code[(size_t)s]);
             rew.push_back((float)F.reward[(size_t)s]);
+            rew64.push_back(F.reward[(size_t)s]);
         }
         // pad each instance to a multiple of 4 states so every instance starts 16-byte aligned
         off += F.nstates;
-        while (off % 4) { codes.push_back(0xFF); rew.push_back(0.f); off++; }
+        while (off % 4) { codes.push_back(0xFF); rew.push_back(0.f); rew64.push_back(0.0); off++; }
         cpmdp_free_factors(f);
     }
     B->offsets.push_back(off);
@@ -619,6 +724,12 @@ cpmdp_status cpmdp_batch_build(const cpmdp_problem *problems, int32_t count, int
     if ((e = cudaMalloc(&B->d_inst, sizeof(BatchInst) * count)) != cudaSuccess) return fail(e, "cudaMalloc inst");
     if ((e = cudaMemcpy(B->d_code, codes.data(), (size_t)off, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "copy code");
     if ((e = cudaMemcpy(B->d_R, rew.data(), (size_t)off * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "copy R");
+    // FP64 rewards and weights of the certifying sweep (cpmdp_batch_certify)
+    if ((e = cudaMalloc(&B->d_R64, (size_t)off * sizeof(double))) != cudaSuccess) return fail(e, "cudaMalloc R64");
+    if ((e = cudaMalloc(&B->d_instw, sizeof(double) * 4 * count)) != cudaSuccess) return fail(e, "cudaMalloc instw");
+    if ((e = cudaMalloc(&B->d_cert, sizeof(unsigned long long) * count)) != cudaSuccess) return fail(e, "cudaMalloc cert");
+    if ((e = cudaMemcpy(B->d_R64, rew64.data(), (size_t)off * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "copy R64");
+    if ((e = cudaMemcpy(B->d_instw, instw.data(), sizeof(double) * 4 * count, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e, "copy instw");
     B->block = 256;
     B->spl = 1;
     if (upload_tiles(*B, 32) != CPMDP_OK) { free_batch_device(*B); delete B; if (prev >= 0) cudaSetDevice(prev); return CPMDP_ECUDA; }
@@ -762,6 +873,40 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
     if (not_conv) {
         set_error("%d instance(s) reached max_iter before tol", not_conv);
         return CPMDP_ENOCONV;
+    }
+    return CPMDP_OK;
+}
+
+cpmdp_status cpmdp_batch_certify(const cpmdp_batch *B, const float *V, uint8_t *policy_out, double *certified_out,
+                                 void *stream) {
+    if (!B || !V) { set_error("batch and V are required"); return CPMDP_EINVAL; }
+    if (((uintptr_t)V & 15u) != 0) { set_error("V must be 16-byte aligned"); return CPMDP_EINVAL; }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(B->device) != cudaSuccess) { set_error("cannot select CUDA device %d", B->device); return CPMDP_ECUDA; }
+    struct Restore { int p; ~Restore() { if (p >= 0) cudaSetDevice(p); } } restore{prev};
+    cudaStream_t st = (cudaStream_t)stream;
+    CPMDP_CUDA(cudaMemsetAsync(B->d_cert, 0, sizeof(unsigned long long) * B->ninst, st));
+    BatchCertArgs c;
+    c.tiles = B->d_tiles;
+    c.ntiles = B->ntiles;
+    c.code = B->d_code;
+    c.R64 = B->d_R64;
+    c.instw = B->d_instw;
+    c.V = V;
+    c.pi = policy_out;
+    c.cert = B->d_cert;
+    const int grid = B->num_sms * 8;
+    batch_certify_kernel<<<grid, 256, 0, st>>>(c);
+    CPMDP_CUDA(cudaGetLastError());
+    if (certified_out) {
+        std::vector<unsigned long long> bits((size_t)B->ninst);
+        CPMDP_CUDA(cudaMemcpyAsync(bits.data(), B->d_cert, sizeof(unsigned long long) * B->ninst,
+                                   cudaMemcpyDeviceToHost, st));
+        CPMDP_CUDA(cudaStreamSynchronize(st));
+        memcpy(certified_out, bits.data(), sizeof(double) * B->ninst);
+    } else {
+        CPMDP_CUDA(cudaStreamSynchronize(st));
     }
     return CPMDP_OK;
 }

@@ -81,5 +81,9 @@ struct cpmdp_batch {
     int *d_p2hdr = nullptr;
     unsigned *d_p2epoch = nullptr;
     unsigned long long *d_p2res = nullptr;
+    // FP64 certifying sweep (cpmdp_batch_certify)
+    double *d_R64 = nullptr;
+    double *d_instw = nullptr;
+    unsigned long long *d_cert = nullptr;
 };
 

@@ -554,7 +554,19 @@ cpmdp_status dense_store_expectation(const Factors &F, const float *V, float *EB
 cpmdp_status dense_certify(const Factors &F, const float *V, uint8_t *pi, double *res, cudaStream_t st);
 
 // Value iteration with BF16x3 sweeps and defect correction against an FP32
-// base expectation; FP64 certifying sweep at the end.
+// base expectation, stopped by an FP64 residual.
+//
+// The working residual max |V' - V| of float iterates bottoms out at one to
+// three units in the last place of the largest |V| (rounding of V' flips
+// from sweep to sweep), so once it is below tol it no longer shows the
+// geometric part of the error, which still shrinks by gamma per sweep. With
+// certify on, the solve therefore runs ceil(ln 2 / ln(1 / gamma)) more
+// sweeps (halving that part), then one FP64 backup of V gives the certified
+// residual max |T(V) - V| and the FP64 argmax policy; if the certified
+// residual is not below tol either, it runs as many sweeps again and
+// certifies again (within max_iter). The returned V then meets the value
+// iteration stopping rule evaluated in FP64. eval_sweeps in the result
+// counts the FP64 certifying sweeps.
 cpmdp_status dense_tc_solve(const Factors &F, float *V, uint8_t *pi, const SolveOpts &o, Ctrl *hc, cudaStream_t st) {
     if (!dense_tc_supported(F)) {
         set_error("BF16X3 needs a dense model with 4 dimensions of size 64 and at most 16 actions");
@@ -565,9 +577,12 @@ cpmdp_status dense_tc_solve(const Factors &F, float *V, uint8_t *pi, const Solve
     CPMDP_CUDA(cudaMemsetAsync(F.d_tc_err, 0, sizeof(int), st));
     float *W = (float *)F.d_scratch;
     unsigned long long *rb = &F.d_ctrl->res_slot[0];
+    double *cert = (double *)((char *)F.d_ctrl + offsetof(Ctrl, certify_residual));
     float *cur = V, *nxt = W;
     std::vector<double> hist;
-    int k = 0, conv = 0, last_rebase = 0, rebases = 0;
+    int k = 0, conv = 0, last_rebase = 0, rebases = 0, certs = 0;
+    int extra = -1;   // sweeps left before the next FP64 check (-1: working residual not below tol yet)
+    const int halve = F.gamma > 0.0 && F.gamma < 1.0 ? (int)ceil(log(2.0) / log(1.0 / F.gamma)) : 1;
     bool base = false;
     double res = INFINITY;
     while (k < o.max_iter) {
@@ -583,7 +598,23 @@ cpmdp_status dense_tc_solve(const Factors &F, float *V, uint8_t *pi, const Solve
         hist.push_back(res);
         float *t = cur; cur = nxt; nxt = t;
         k++;
-        if (res < o.tol) { conv = 1; break; }
+        if (extra < 0 && res < o.tol) {
+            if (!o.certify) { conv = 1; break; }
+            extra = halve;
+        }
+        if (extra > 0) {
+            if (--extra > 0) continue;
+            // FP64 backup of the current iterate: certified residual and policy
+            s = dense_certify(F, cur, pi, cert, st);
+            if (s != CPMDP_OK) return s;
+            certs++;
+            double c = INFINITY;
+            CPMDP_CUDA(cudaMemcpyAsync(&c, cert, sizeof(c), cudaMemcpyDeviceToHost, st));
+            CPMDP_CUDA(cudaStreamSynchronize(st));
+            if (c < o.tol) { conv = 1; break; }
+            extra = halve;
+            continue;
+        }
         // the residual stopped falling: the BF16x3 error of the correction
         // dominates; refresh the FP32 base at the current iterate
         if (k - last_rebase >= 6 && res > 0.9 * hist[k - 6] && rebases < 64) {
@@ -596,16 +627,18 @@ cpmdp_status dense_tc_solve(const Factors &F, float *V, uint8_t *pi, const Solve
         }
     }
     if (cur != V) CPMDP_CUDA(cudaMemcpyAsync(V, cur, (size_t)kS * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    double *cert = (double *)((char *)F.d_ctrl + offsetof(Ctrl, certify_residual));
-    if (o.certify) {
+    if (o.certify && !conv) {
+        // max_iter ran out: still certify what is returned
         s = dense_certify(F, V, pi, cert, st);
         if (s != CPMDP_OK) return s;
-    } else if (pi) {
+        certs++;
+    } else if (!o.certify && pi) {
         s = tc_sweep(F, V, W, pi, base, nullptr, st);
         if (s != CPMDP_OK) return s;
     }
     hc->iterations = k;
     hc->rounds = rebases;
+    hc->eval_sweeps = certs;
     hc->converged = conv;
     hc->last_residual = res;
     hc->backups = (long long)k * kS * F.nactions;

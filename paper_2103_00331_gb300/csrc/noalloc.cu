@@ -70,6 +70,11 @@ __global__ void static_codes_kernel(StaticArgs a, const uint8_t *__restrict__ ce
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.nstates; s += gridDim.x * blockDim.x) {
         const uint8_t k = cell ? cell[s] : (uint8_t)CPMDP_CELL_FREE;
         const unsigned all = (1u << (2 * D)) - 1u;
+        if (k > CPMDP_CELL_TERMINAL) {   // not a cell code: the solve is refused
+            atomicCAS(&reinterpret_cast<StaticCtrl *>(scratch)->status, 0, (int)CPMDP_EINVAL);
+            code[s] = (uint8_t)(all | (1u << (2 * D)));
+            continue;
+        }
         if (k == CPMDP_CELL_OBSTACLE) { code[s] = (uint8_t)(all | (1u << (2 * D))); continue; }
         if (k == CPMDP_CELL_TERMINAL) { code[s] = (uint8_t)(all | (1u << (2 * D + 1))); continue; }
         unsigned c = 0;
@@ -102,15 +107,19 @@ __device__ __forceinline__ long long static_grid_sync(StaticCtrl *c, int n, unsi
         unsigned long long *ctr = &c->bar[n & 1];
         const unsigned long long add = 1ull | ((unsigned long long)(flag != 0) << 32);
         asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(ctr), "l"(add) : "memory");
-        const unsigned long long target = (unsigned long long)(n / 2 + 1) * nblocks;
+        // complete at A arrivals; the counter is then A + F * 2^32 (F raised
+        // flags so far on it, carries of the low half included), and while
+        // blocks still arrive its low half trails A's by at most nblocks, so
+        // the test on the low halves' signed difference never wraps
+        const unsigned long long A = (unsigned long long)(n / 2 + 1) * nblocks;
         unsigned long long v;
         asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
         const unsigned long long t0 = static_ns();
         unsigned spins = 0;
-        while ((v & 0xFFFFFFFFull) < target) {
+        while ((int)((unsigned)v - (unsigned)A) < 0) {
             __nanosleep(32);
             asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
-            if ((++spins & 15u) == 0 && (v & 0xFFFFFFFFull) < target) {
+            if ((++spins & 15u) == 0 && (int)((unsigned)v - (unsigned)A) < 0) {
                 if (*(volatile int *)&c->status != 0) { result = -1; break; }
                 if (static_ns() - t0 > timeout_ns) {
                     atomicCAS(&c->status, 0, (int)CPMDP_ETIMEOUT);
@@ -120,10 +129,10 @@ __device__ __forceinline__ long long static_grid_sync(StaticCtrl *c, int n, unsi
             }
         }
         if (result == 0) {
-            const unsigned long long hi = v >> 32;
-            result = (long long)(hi - ((n & 1) ? p1 : p0));
-            if (n & 1) p1 = hi;
-            else p0 = hi;
+            const unsigned long long F = (v - A) >> 32;
+            result = (long long)(F - ((n & 1) ? p1 : p0));
+            if (n & 1) p1 = F;
+            else p0 = F;
         }
     }
     __syncthreads();
@@ -138,6 +147,9 @@ __global__ void __launch_bounds__(kBlock) static_vi_kernel(StaticArgs a, const f
     const uint8_t *code = scratch + kCtrlBytes;
     float *W = reinterpret_cast<float *>(scratch + kCtrlBytes + kMaxStates);
     __shared__ unsigned shm[kBlock / 32];
+    // the codes kernel (earlier on the stream) refused a cell code: every
+    // block sees the same word and leaves before the first barrier
+    if (*(volatile int *)&c->status != 0) return;
     const int D = a.ndim;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     float *cur = V, *nxt = W;
@@ -289,6 +301,10 @@ extern "C" cpmdp_status cpmdp_value_iteration_static(int32_t ndim, const int64_t
     StaticCtrl h;
     CPMDP_CUDA(cudaMemcpyAsync(&h, scratch, sizeof(h), cudaMemcpyDeviceToHost, s));
     CPMDP_CUDA(cudaStreamSynchronize(s));
+    if (h.status == CPMDP_EINVAL) {
+        set_error("cell codes must be 0 (free), 1 (obstacle) or 2 (terminal); V is unchanged");
+        return CPMDP_EINVAL;
+    }
     if (h.status != 0) {
         set_error("a device-side wait exceeded 2 s; V is undefined");
         return (cpmdp_status)h.status;

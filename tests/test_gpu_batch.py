@@ -163,3 +163,57 @@ def test_batch_tail_equals_batched_kernel(cp):
     assert xa["status"] == cp.ENOCONV and np.array_equal(ia, ib) and np.array_equal(ra, rb)
     assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
     B.close()
+
+
+def test_batch_certify_policy_matches_oracle(cp):
+    """cpmdp_batch_certify after a batched solve: per instance the certified
+    residual equals the oracle's own FP64 backup of the returned values
+    (max |T(V) - V| over non-obstacle states), the policy equals the oracle's
+    argmax of that backup wherever its best and second-best Q differ by
+    more than FP64 rounding, and it equals the policy of the oracle's own
+    value iteration wherever that gap exceeds twice gamma times the distance
+    bound between the two results (both within residual / (1 - gamma) of
+    V*). Obstacles and terminals get 255; the padding between instances is
+    not written."""
+    import torch
+    from oracle import cpfactor as oc
+    inst = _instances()
+    B = cp.batch_build(inst, device=0)
+    V = torch.zeros(int(B.total_states), dtype=torch.float32, device="cuda")
+    r, iters, res = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=5000))
+    pi = torch.full((int(B.total_states),), 77, dtype=torch.uint8, device="cuda")
+    cert = cp.batch_certify(B, V, pi)
+    Vh = V.double().cpu().numpy()
+    ph = pi.cpu().numpy()
+    for i in range(len(inst) - 1):   # padding after instance i, before instance i + 1
+        lo, hi = int(B.offsets[i]) + inst[i].nstates, int(B.offsets[i + 1])
+        assert np.all(ph[lo:hi] == 77)
+    picks = list(range(0, 192, 6)) + list(range(192, len(inst)))
+    compared = 0
+    for i in picks:
+        gw = inst[i]
+        lo, n = int(B.offsets[i]), gw.nstates
+        got, gp = Vh[lo:lo + n], ph[lo:lo + n]
+        TV, opi, ores, Q = oc.backup(gw, got, want_q=True)
+        free = gw.cell.reshape(-1) != ci.OBSTACLE
+        want = float(np.abs(TV - got)[free].max()) if free.any() else 0.0
+        assert abs(cert[i] - want) <= 1e-13 * (1 + np.abs(got).max()), (i, cert[i], want)
+        inner = gw.cell.reshape(-1) == ci.FREE
+        assert np.all(gp[~inner] == 255)
+        if not inner.any():
+            continue
+        Qs = np.sort(Q[:, inner], axis=0)
+        gap = Qs[-1] - Qs[-2] if Q.shape[0] > 1 else np.full(inner.sum(), np.inf)
+        sure = gap > 1e-12 * (1 + np.abs(Qs[-1]))
+        assert np.array_equal(gp[inner][sure], opi[inner][sure]), i
+        # against the oracle's own value iteration
+        Vo, po, ko, ro = oc.value_iteration(gw, tol=1e-6, max_iter=5000)
+        bound = (cert[i] + gw.gamma * ro) / (1 - gw.gamma)
+        _, _, _, Qo = oc.backup(gw, Vo, want_q=True)
+        Qos = np.sort(Qo[:, inner], axis=0)
+        gapo = Qos[-1] - Qos[-2] if Qo.shape[0] > 1 else np.full(inner.sum(), np.inf)
+        sure_o = gapo > max(1e-6, 2 * gw.gamma * bound)
+        assert np.array_equal(gp[inner][sure_o], po[inner][sure_o]), i
+        compared += int(sure_o.sum())
+    assert compared > 1000
+    B.close()
