@@ -335,6 +335,22 @@ def run_ours(args, rank, world, local, pg):
             plain_ms.append((time.perf_counter() - t0) * 1e3)
     fused_vi_ms = statistics.median(vi_ms)
     plain_vi_ms = statistics.median(plain_ms) if plain_ms else None
+    # the same plain kernels with the stopping rule on the device (fused = 3:
+    # a recorded 32-sweep graph replayed until the device flag is up), so the
+    # gain from fusion is separated from the gain from not syncing every sweep
+    plain3_opts = cp.default_opts(tol=TOL, max_iter=5000, fused=3, certify=0)
+    plain3_ms = []
+    rp3 = {"iterations": None}
+    for i in range(0 if args.skip_plain else max(3, min(args.steps, 10)) + 1):
+        V.zero_()
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rp3 = cp.value_iteration(f, cp.F32, V, None, opts=plain3_opts, stream=stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            plain3_ms.append((time.perf_counter() - t0) * 1e3)
+    plain3_vi_ms = statistics.median(plain3_ms) if plain3_ms else None
 
     # the same step on the grid-barrier solver (one grid barrier per sweep),
     # for comparison with the barrier-free solver timed above
@@ -434,7 +450,12 @@ def run_ours(args, rank, world, local, pg):
                 "gpu_launches": launches, "clocks": clocks,
                 "time_to_tol_ms": fused_vi_ms, "plain_fp32_vi_ms": plain_vi_ms,
                 "speedup_vs_plain_fp32_vi": plain_vi_ms / fused_vi_ms if plain_vi_ms else None,
+                "plain_fp32_vi_device_stop_ms": plain3_vi_ms,
+                "speedup_vs_plain_fp32_vi_device_stop": plain3_vi_ms / fused_vi_ms if plain3_vi_ms else None,
+                "plain_timing": "host wall clock around the call (host-checked: one residual read per sweep; "
+                                "device stop: one flag read per 32 sweeps)",
                 "vi_sweeps": statistics.median(vi_iters), "plain_vi_sweeps": rpl["iterations"],
+                "plain_device_stop_sweeps": rp3["iterations"],
                 "pi_sweeps": statistics.median(pi_iters), "pi_ms": statistics.median(pi_ms),
                 "certified_residual": rv["certified_residual"], "error_bound": rv["error_bound"],
                 "per_step": per_step, "grid_barrier_solver": grid_barrier, "paper_shaped_1000x1000": p0, "small_10x10": small,
@@ -470,16 +491,34 @@ def batch_measure(cp, dev, stream, seed=0, count=4096, reps=3):
         times.append(e0.elapsed_time(e1))
         backups = r["backups"]
     batched_ms = statistics.median(times)
-    # one instance at a time: fused persistent solver and plain FP32 VI, sampled
+    # FP64 certifying sweep of every instance: certified residuals and the
+    # FP64 argmax policy (packed like V)
+    pol = torch.empty(int(B.total_states), dtype=torch.uint8, device=dev)
+    cert_times = []
+    cert = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cert = cp.batch_certify(B, V, pol, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cert_times.append(e0.elapsed_time(e1))
+    certify_ms = statistics.median(cert_times)
+    gam = np.array([g.gamma for g in inst])
+    # one instance at a time, all instances: the fused single-instance solver
+    # and the plain kernels with the device-side stop (fused = 3); the plain
+    # host-checked baseline (fused = 0) on every 16th instance, scaled
     step = 16
-    sample = list(range(0, count, step))
-    fused_ms, plain_ms = 0.0, 0.0
+    fused_ms, plain3_ms, plain_ms = 0.0, 0.0, 0.0
     popts = cp.default_opts(max_iter=5000, fused=0, certify=0)
+    p3opts = cp.default_opts(max_iter=5000, fused=3, certify=0)
     fopts = cp.default_opts(max_iter=5000, certify=0)
-    for i in sample:
+    for i in range(count):
         f = cp.build_factors(inst[i], device=dev.index)
         Vi = torch.zeros(inst[i].nstates, dtype=torch.float32, device=dev)
-        for mode, o in (("fused", fopts), ("plain", popts)):
+        modes = (("fused", fopts), ("plain3", p3opts)) + ((("plain", popts),) if i % step == 0 else ())
+        for mode, o in modes:
             Vi.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -488,11 +527,13 @@ def batch_measure(cp, dev, stream, seed=0, count=4096, reps=3):
             dt = (time.perf_counter() - t0) * 1e3
             if mode == "fused":
                 fused_ms += dt
+            elif mode == "plain3":
+                plain3_ms += dt
             else:
                 plain_ms += dt
         f.close()
     B.close()
-    scale = count / len(sample)
+    scale = step
     # algorithmic bytes: every sweep of every instance reads V, R, code and
     # writes V' (13 B per state); the floor takes each global sweep at the
     # larger of its bytes at the measured HBM peak and the single-instance
@@ -516,10 +557,15 @@ def batch_measure(cp, dev, stream, seed=0, count=4096, reps=3):
             "batched_ms": batched_ms, "batched_backups_per_s": backups / (batched_ms / 1e3),
             "launch_sweeps": r["iterations"], "max_instance_sweeps": int(iters.max()),
             "graph_replay": bool(r["rounds"] == 1),
-            "one_at_a_time_fused_ms_est": fused_ms * scale, "plain_fp32_vi_ms_est": plain_ms * scale,
+            "certify_ms": certify_ms, "batched_with_certify_ms": batched_ms + certify_ms,
+            "max_certified_residual": float(cert.max()),
+            "max_error_bound": float((cert / (1 - gam)).max()),
+            "one_at_a_time_fused_ms": fused_ms, "plain_fp32_vi_device_stop_ms": plain3_ms,
+            "plain_fp32_vi_ms_est": plain_ms * scale,
+            "speedup_vs_plain_fp32_vi_device_stop": plain3_ms / batched_ms,
             "speedup_vs_plain_fp32_vi": plain_ms * scale / batched_ms,
-            "note": f"one-at-a-time times measured on every {step}th instance ({len(sample)} of {count}) "
-                    f"and scaled by {scale:.0f}"}
+            "note": f"one-at-a-time fused and device-stop plain measured on all {count} instances (host wall "
+                    f"clock per call); host-checked plain on every {step}th instance, scaled by {step}"}
 
 
 def dense_measure(cp, dev, stream, reps=2):
@@ -767,13 +813,31 @@ def hbm_sweep(cp, dev, stream, peak):
         Va, Vb = Vb, Va
     ms = statistics.median(times)
     ach = S * BYTES_VI / (ms / 1e3) / 1e9
+    # value iteration of the same instance from zeros to max|dV| < 1e-6:
+    # marching sweeps from a replayed CUDA graph with the stop decided on the
+    # device (fused = 1), and the grid-barrier persistent solver (fused = 2);
+    # library-recorded CUDA events, second of two runs (the first records the graph)
+    solves = {}
+    for fused in (1, 2):
+        r = None
+        for _ in range(2):
+            Va.zero_()
+            torch.cuda.synchronize()
+            r = cp.value_iteration(f, cp.F32, Va, None, opts=cp.default_opts(tol=TOL, max_iter=5000, fused=fused,
+                                                                               certify=0), stream=stream)
+        gbs = r["iterations"] * S * BYTES_VI / (r["elapsed_ms"] / 1e3) / 1e9
+        solves["march_graph" if fused == 1 else "grid_barrier"] = {
+            "time_to_tol_ms": r["elapsed_ms"], "sweeps": r["iterations"], "achieved_gbs": gbs, "frac": gbs / peak,
+            "solver": r["solver"], "backups_per_s": r["backups"] / (r["elapsed_ms"] / 1e3)}
     f.close()
     del Va, Vb
     torch.cuda.empty_cache()
     return {"kernel": "march_kernel<float,false> (plane-marching fused backup)", "states": S, "ms": ms,
             "bytes_per_state": BYTES_VI, "achieved_gbs": ach, "peak_gbs": peak, "frac": ach / peak,
             "traffic": traffic_from_profile("march_kernel_gridworld320.txt", scale=S),
-            "note": "inputs 1.7 GB > L2; residual fused, policy not written; traffic scaled from a 320^3 capture"}
+            "solve_to_1e-6": solves,
+            "note": "inputs 1.7 GB > L2; residual fused, policy not written; traffic scaled from a 320^3 capture; "
+                    "solve frac = algorithmic bytes (13 per state and sweep) over the solve's time"}
 
 
 def kernel_case(name, reps=3):

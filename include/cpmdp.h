@@ -81,7 +81,9 @@ typedef enum {
     CPMDP_SOLVER_GRID_BARRIER = 1,  /* fused GridWorld solver, one grid barrier per sweep */
     CPMDP_SOLVER_BARRIER_FREE = 2,  /* fused FP32 GridWorld solver without a barrier in its sweep loop */
     CPMDP_SOLVER_DENSE = 3,         /* dense CP solver */
-    CPMDP_SOLVER_BATCH = 4          /* batched value iteration */
+    CPMDP_SOLVER_BATCH = 4,         /* batched value iteration */
+    CPMDP_SOLVER_MARCH_GRAPH = 5    /* FP32 value iteration of a 3-D grid of 2^23+ states: plane-marching
+                                       sweeps replayed from a CUDA graph, stopping rule taken on the device */
 } cpmdp_solver;
 
 /*
@@ -132,10 +134,17 @@ typedef struct {
                                 one co-resident grid at one thread per column of 1, 2 or 4 segments of
                                 4 states run barrier-free (sweeps synchronised through sweep-tagged
                                 values, the stopping rule checked three sweeps late; same values and
-                                sweep counts), the rest with
-                                a grid barrier per sweep; 2: always the grid-barrier solver; 0: the
+                                sweep counts); FP32 value iteration of 3-D grids of 2^23 states or
+                                more runs plane-marching sweeps from a replayed CUDA graph with the
+                                stopping rule on the device (same values and sweep counts); the rest
+                                with a grid barrier per sweep; 2: always the grid-barrier solver; 0: the
                                 plain unfused FP32/FP64 baseline (one kernel per action, separate max
-                                and residual kernels, residual checked on the host every sweep) */
+                                and residual kernels, residual checked on the host every sweep); 3: the
+                                same plain kernels with the stopping rule taken on the device (a
+                                one-thread check kernel after each sweep raises a flag on which every
+                                later kernel returns at once), 32 sweeps recorded once into a CUDA
+                                graph that is replayed until the flag is up (the host reads it once
+                                per 32 sweeps); 0 and 3 run value iteration only */
     double eval_tol;         /* policy iteration: evaluation stops below this residual
                                 (default: tol for F32, 1e-10 for F64) */
     int32_t max_eval_iter;   /* policy iteration: evaluation sweep limit per round (default 100000) */
@@ -144,6 +153,12 @@ typedef struct {
     double *trace;           /* optional device buffer of max_iter doubles: residual of each sweep
                                 (value iteration, fused path only; the barrier-free solver zeroes it
                                 first and also fills the entries of its two dropped sweeps) */
+    int32_t partial_eval;    /* policy iteration (default 32): while the policy keeps changing, each
+                                round's evaluation stops after at most this many sweeps (modified
+                                policy iteration); once an improvement changes no action, every
+                                later round evaluates to eval_tol, and the solve stops only when
+                                an improvement after such a full evaluation changes no action.
+                                0: every round evaluates to eval_tol */
     int32_t inject_stall;    /* testing aid (default 0): 1 makes one block of the fused GridWorld
                                 solver leave at once (without arriving at its first grid barrier, or,
                                 barrier-free, without publishing its values), so the other blocks'
@@ -348,16 +363,29 @@ cpmdp_status cpmdp_batch_certify(const cpmdp_batch *batch, const float *V, uint8
  *   (3-D, one shape, contiguous): per 4x4x4 cell the mean reward of its
  *   non-obstacle states, its obstacle fraction, its largest terminal reward
  *   (0 if none), -log(1 - gamma) / 5; channels 4..63 zero.
+ * cpmdp_ws_coarse_vi: value iteration of a coarsened copy of every instance
+ *   (the same Eq. 1 backup on the coarse grid; one CTA per instance, in
+ *   shared memory, at most 8192 coarse cells): a coarse cell is an obstacle
+ *   when at least half of its states are, else a terminal of value max R(t)
+ *   when it holds terminals, else free with reward (mean fine reward of its
+ *   free states) x (1 + gamma + gamma^2 + gamma^3); discount gamma^4, the
+ *   instance's slip model. Jacobi sweeps from zero until max |dV| < tol or
+ *   max_sweeps. Writes coarse_v (float [count][cells]) and, when feat is not
+ *   NULL, its bf16 copy into feature channel 4.
  * cpmdp_ws_targets: per coarse cell the mean of V over its non-obstacle
- *   states (float [count][cells]) and a mask (1 if it has any).
- * cpmdp_ws_upsample: V (packed batch layout) = coarse estimate on free
- *   states, R(t) on terminals, 0 on obstacles.
+ *   states minus base (float [count][cells], NULL = 0), and a mask (1 if the
+ *   cell has any non-obstacle state).
+ * cpmdp_ws_upsample: V (packed batch layout) = coarse + base (base NULL = 0)
+ *   at the cell centres, interpolated trilinearly to every free state
+ *   (clamped to the outermost centres); R(t) on terminals, 0 on obstacles.
  */
 cpmdp_status cpmdp_ws_features(const cpmdp_batch *batch, int32_t first, int32_t count, uint16_t *feat, void *stream);
-cpmdp_status cpmdp_ws_targets(const cpmdp_batch *batch, const float *V, int32_t first, int32_t count, float *target,
-                              float *mask, void *stream);
-cpmdp_status cpmdp_ws_upsample(const cpmdp_batch *batch, const float *coarse, int32_t first, int32_t count, float *V,
-                               void *stream);
+cpmdp_status cpmdp_ws_coarse_vi(const cpmdp_batch *batch, int32_t first, int32_t count, float tol, int32_t max_sweeps,
+                                float *coarse_v, uint16_t *feat, void *stream);
+cpmdp_status cpmdp_ws_targets(const cpmdp_batch *batch, const float *V, int32_t first, int32_t count, const float *base,
+                              float *target, float *mask, void *stream);
+cpmdp_status cpmdp_ws_upsample(const cpmdp_batch *batch, const float *coarse, const float *base, int32_t first,
+                               int32_t count, float *V, void *stream);
 /* y = conv(x, W) + b (ReLU if relu); wf = the forward weight tiles written by cpmdp_ws_cast_weights;
  * y0 (nullable) gets channel 0 in FP32. Runs on the tcgen05 tensor cores (bf16 operands, FP32
  * accumulation): 128 voxels x 64 channels per CTA, 27 taps x K = 64. */

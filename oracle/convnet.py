@@ -175,11 +175,65 @@ def coarse_target(gw, V):
 
 
 def upsample(gw, coarse):
-    """Warm start on the full grid: every free state takes its coarse cell's
-    value, terminals R(t), obstacles 0."""
+    """Warm start on the full grid: the coarse values sit at the cell
+    centres; a free state at fine coordinate x is at (x + 0.5) / FACTOR - 0.5
+    in cell units (clamped to the outermost centres) and takes the trilinear
+    interpolation of the eight surrounding centres; terminals R(t),
+    obstacles 0."""
     shape = gw.shape
-    idx = np.meshgrid(*[np.arange(n) // FACTOR for n in shape], indexing="ij")
-    V0 = np.asarray(coarse)[tuple(idx)]
+    C = np.asarray(coarse, dtype=np.float64)
+    V0 = np.zeros(shape)
+    for z in range(shape[0]):
+        for y in range(shape[1]):
+            for x in range(shape[2]):
+                lo, hi, t = [], [], []
+                for p, n in zip((z, y, x), C.shape):
+                    u = min(max((p + 0.5) / FACTOR - 0.5, 0.0), n - 1.0)
+                    a = int(np.floor(u))
+                    lo.append(a)
+                    hi.append(min(a + 1, n - 1))
+                    t.append(u - a)
+                v = 0.0
+                for k in range(8):
+                    pick = [(hi if (k >> (2 - d)) & 1 else lo)[d] for d in range(3)]
+                    w = np.prod([t[d] if (k >> (2 - d)) & 1 else 1.0 - t[d] for d in range(3)])
+                    v += w * C[tuple(pick)]
+                V0[z, y, x] = v
     cell = np.asarray(gw.cell)
     V0 = np.where(cell == 2, np.asarray(gw.reward), V0)
     return np.where(cell == 1, 0.0, V0)
+
+
+def coarse_gridworld(gw):
+    """The coarsened copy of a 3-D GridWorld on which the warm start's coarse
+    value iteration runs, written out as an ordinary GridWorld: cells of
+    FACTOR^3 states; a cell is an obstacle when at least half of its states
+    are, else a terminal of reward max R(t) when it holds terminals, else a
+    free cell whose reward is the mean reward of its free states times
+    1 + gamma + ... + gamma^(FACTOR-1) (FACTOR fine steps); discount
+    gamma^FACTOR and the same slip probability. Returns (GridWorld, kind)
+    with kind 0 free, 1 obstacle, 2 terminal."""
+    import cpmdp_inputs as ci
+    shape = gw.shape
+    cs = tuple((n + FACTOR - 1) // FACTOR for n in shape)
+    R = np.asarray(gw.reward, dtype=np.float64)
+    cell = np.asarray(gw.cell)
+    kind = np.zeros(cs, dtype=np.uint8)
+    rew = np.zeros(cs)
+    steps = sum(gw.gamma ** j for j in range(FACTOR))
+    for cz in range(cs[0]):
+        for cy in range(cs[1]):
+            for cx in range(cs[2]):
+                blk = (slice(cz * FACTOR, min((cz + 1) * FACTOR, shape[0])),
+                       slice(cy * FACTOR, min((cy + 1) * FACTOR, shape[1])),
+                       slice(cx * FACTOR, min((cx + 1) * FACTOR, shape[2])))
+                c, r = cell[blk], R[blk]
+                if 2 * (c == 1).sum() >= c.size:
+                    kind[cz, cy, cx] = 1
+                elif (c == 2).any():
+                    kind[cz, cy, cx] = 2
+                    rew[cz, cy, cx] = r[c == 2].max()
+                else:
+                    free = c == 0
+                    rew[cz, cy, cx] = r[free].mean() * steps if free.any() else 0.0
+    return ci.GridWorld(shape=cs, p=gw.p, gamma=gw.gamma ** FACTOR, cell=kind, reward=rew), kind

@@ -23,7 +23,7 @@ MAX_DIM = 9
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT = 0, 1, 2, 3, 4, 5
 F32, F64, BF16X3 = 0, 1, 2
 GRIDWORLD, DENSE_CP = 0, 1
-SOLVER_PLAIN, SOLVER_GRID_BARRIER, SOLVER_BARRIER_FREE, SOLVER_DENSE, SOLVER_BATCH = 0, 1, 2, 3, 4
+SOLVER_PLAIN, SOLVER_GRID_BARRIER, SOLVER_BARRIER_FREE, SOLVER_DENSE, SOLVER_BATCH, SOLVER_MARCH_GRAPH = 0, 1, 2, 3, 4, 5
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT"}
 
 
@@ -47,7 +47,7 @@ class SolveOpts(ctypes.Structure):
                 ("fused", ctypes.c_int32), ("eval_tol", ctypes.c_double),
                 ("max_eval_iter", ctypes.c_int32), ("max_rounds", ctypes.c_int32),
                 ("timeout_s", ctypes.c_double), ("trace", ctypes.c_void_p),
-                ("inject_stall", ctypes.c_int32)]
+                ("partial_eval", ctypes.c_int32), ("inject_stall", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -103,8 +103,9 @@ def _load():
     lib.cpmdp_batch_certify.restype = ctypes.c_int
     for name, args in [
             ("cpmdp_ws_features", [vp, i32, i32, vp, vp]),
-            ("cpmdp_ws_targets", [vp, vp, i32, i32, vp, vp, vp]),
-            ("cpmdp_ws_upsample", [vp, vp, i32, i32, vp, vp]),
+            ("cpmdp_ws_coarse_vi", [vp, i32, i32, ctypes.c_float, i32, vp, vp, vp]),
+            ("cpmdp_ws_targets", [vp, vp, i32, i32, vp, vp, vp, vp]),
+            ("cpmdp_ws_upsample", [vp, vp, vp, i32, i32, vp, vp]),
             ("cpmdp_conv3d_forward", [vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, i32, vp]),
             ("cpmdp_conv3d_backward_data", [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]),
             ("cpmdp_conv3d_backward_weight", [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]),
@@ -128,7 +129,7 @@ EXPORTED = ["cpmdp_default_opts", "cpmdp_build_factors", "cpmdp_free_factors", "
             "cpmdp_components", "cpmdp_bellman_backup", "cpmdp_value_iteration",
             "cpmdp_policy_iteration", "cpmdp_value_iteration_static", "cpmdp_batch_build",
             "cpmdp_batch_free", "cpmdp_batch_info", "cpmdp_batch_value_iteration", "cpmdp_batch_certify",
-            "cpmdp_ws_features",
+            "cpmdp_ws_features", "cpmdp_ws_coarse_vi",
             "cpmdp_ws_targets", "cpmdp_ws_upsample", "cpmdp_conv3d_forward", "cpmdp_conv3d_backward_data",
             "cpmdp_conv3d_backward_weight", "cpmdp_ws_loss_grad", "cpmdp_adam_step", "cpmdp_ws_cast_weights",
             "cpmdp_ws_sync", "cpmdp_last_error", "cpmdp_version"]
@@ -377,13 +378,19 @@ def ws_features(batch, first, count, feat, stream=None):
     _check(lib.cpmdp_ws_features(batch.handle, int(first), int(count), _ptr(feat), _stream(stream)))
 
 
-def ws_targets(batch, V, first, count, target, mask, stream=None):
-    _check(lib.cpmdp_ws_targets(batch.handle, _ptr(V), int(first), int(count), _ptr(target), _ptr(mask),
-                                _stream(stream)))
+def ws_coarse_vi(batch, first, count, coarse_v, feat=None, tol=1e-4, max_sweeps=4000, stream=None):
+    _check(lib.cpmdp_ws_coarse_vi(batch.handle, int(first), int(count), float(tol), int(max_sweeps), _ptr(coarse_v),
+                                  _ptr(feat), _stream(stream)))
 
 
-def ws_upsample(batch, coarse, first, count, V, stream=None):
-    _check(lib.cpmdp_ws_upsample(batch.handle, _ptr(coarse), int(first), int(count), _ptr(V), _stream(stream)))
+def ws_targets(batch, V, first, count, target, mask, base=None, stream=None):
+    _check(lib.cpmdp_ws_targets(batch.handle, _ptr(V), int(first), int(count), _ptr(base), _ptr(target),
+                                _ptr(mask), _stream(stream)))
+
+
+def ws_upsample(batch, coarse, first, count, V, base=None, stream=None):
+    _check(lib.cpmdp_ws_upsample(batch.handle, _ptr(coarse), _ptr(base), int(first), int(count), _ptr(V),
+                                 _stream(stream)))
 
 
 def conv3d_forward(x, wf, bias, y, y0, dims, dilation, relu, stream=None):

@@ -56,6 +56,7 @@ SolveOpts resolve_opts(const cpmdp_solve_opts *o, cpmdp_precision prec) {
     r.max_rounds = o->max_rounds;
     r.timeout_s = o->timeout_s;
     r.trace = o->trace;
+    r.partial_eval = o->partial_eval;
     r.inject_stall = o->inject_stall;
     return r;
 }
@@ -66,6 +67,10 @@ static void free_device(Factors &F) {
                     F.d_Vd, F.d_RB, F.d_T, F.d_EB, F.d_Vbase, F.d_tc_err, F.d_flow};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (F.plain_graph) cudaGraphExecDestroy(F.plain_graph);
+    F.plain_graph = nullptr;
+    if (F.march_graph) cudaGraphExecDestroy(F.march_graph);
+    F.march_graph = nullptr;
     F.d_arena = nullptr;
     F.d_code = nullptr; F.d_R32 = nullptr; F.d_R64 = nullptr; F.d_cell = nullptr;
     F.d_scratch = nullptr; F.d_q = nullptr; F.d_ctrl = nullptr; F.d_U32 = nullptr;
@@ -296,6 +301,7 @@ void cpmdp_default_opts(cpmdp_solve_opts *o) {
     o->max_rounds = 1000;
     o->timeout_s = 2.0;
     o->trace = nullptr;
+    o->partial_eval = 32;
 }
 
 const char *cpmdp_last_error(void) { return g_err; }
@@ -464,12 +470,14 @@ static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, boo
     if (pi_mode && !pi) { set_error("policy iteration needs a policy buffer"); return CPMDP_EINVAL; }
     const Factors &F = h->f;
     SolveOpts o = resolve_opts(opts, prec);
-    if (!(o.tol > 0) || o.max_iter < 1 || o.max_eval_iter < 1 || o.max_rounds < 1 || !(o.timeout_s > 0)) {
-        set_error("invalid solve options (tol > 0, max_iter >= 1, timeout_s > 0 required)");
+    if (!(o.tol > 0) || o.max_iter < 1 || o.max_eval_iter < 1 || o.max_rounds < 1 || !(o.timeout_s > 0) ||
+        o.partial_eval < 0) {
+        set_error("invalid solve options (tol > 0, max_iter >= 1, timeout_s > 0, partial_eval >= 0 required)");
         return CPMDP_EINVAL;
     }
-    if (o.fused < 0 || o.fused > 2) { set_error("fused must be 0, 1 or 2"); return CPMDP_EINVAL; }
-    if (pi_mode && !o.fused) { set_error("the plain baseline implements value iteration only"); return CPMDP_EINVAL; }
+    if (o.fused < 0 || o.fused > 3) { set_error("fused must be 0, 1, 2 or 3"); return CPMDP_EINVAL; }
+    const bool plain = o.fused == 0 || o.fused == 3;
+    if (pi_mode && plain) { set_error("the plain baseline implements value iteration only"); return CPMDP_EINVAL; }
     DeviceGuard g(F.device);
     if (!g.ok) { set_error("cannot select CUDA device %d", F.device); return CPMDP_ECUDA; }
     cudaStream_t s = (cudaStream_t)stream;
@@ -481,7 +489,7 @@ static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, boo
     memset(&hc, 0, sizeof(hc));
     bool have_ctrl = false;
     if (F.kind == CPMDP_GRIDWORLD) {
-        if (o.fused) {
+        if (!plain) {
             st = banded_solve(F, prec, pi_mode, V, pi, o, s);
         } else {
             if (!F.d_q) {
@@ -511,7 +519,7 @@ static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, boo
             st = banded_certify(F, (const float *)V, pi_mode ? nullptr : pi, cert, s);
         }
         if (st != CPMDP_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
-    } else if (!pi_mode && pi && F.kind == CPMDP_GRIDWORLD && o.fused) {
+    } else if (!pi_mode && pi && F.kind == CPMDP_GRIDWORLD && !plain) {
         st = banded_backup(F, prec, V, F.d_scratch, pi, nullptr, s);
         if (st != CPMDP_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
     }
@@ -524,9 +532,10 @@ static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, boo
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     const int solver = F.kind != CPMDP_GRIDWORLD ? CPMDP_SOLVER_DENSE
-                       : !o.fused ? CPMDP_SOLVER_PLAIN
-                       : F.flow_pending ? CPMDP_SOLVER_BARRIER_FREE : CPMDP_SOLVER_GRID_BARRIER;
-    if (F.kind == CPMDP_GRIDWORLD && o.fused) {
+                       : plain ? CPMDP_SOLVER_PLAIN
+                       : F.flow_pending ? CPMDP_SOLVER_BARRIER_FREE
+                       : F.march_pending ? CPMDP_SOLVER_MARCH_GRAPH : CPMDP_SOLVER_GRID_BARRIER;
+    if (F.kind == CPMDP_GRIDWORLD && !plain) {
         st = banded_solve_finished(F, dc, s);
         if (st != CPMDP_OK) return st;
     }

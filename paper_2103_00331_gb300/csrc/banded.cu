@@ -43,7 +43,8 @@ struct PlainArgs {
 
 template <typename T>
 __global__ void plain_q_kernel(PlainArgs a, const T *__restrict__ V, const T *__restrict__ R,
-                               T *__restrict__ Q, int act) {
+                               T *__restrict__ Q, int act, const int *stop) {
+    if (stop && *(volatile const int *)stop) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.nstates || a.cell[s] != CPMDP_CELL_FREE) return;
     int c[kMaxDim], rem = s;
@@ -70,7 +71,8 @@ __global__ void plain_q_kernel(PlainArgs a, const T *__restrict__ V, const T *__
 
 template <typename T>
 __global__ void plain_max_kernel(PlainArgs a, const T *__restrict__ Q, const T *__restrict__ R,
-                                 T *__restrict__ W, uint8_t *pi, int nact) {
+                                 T *__restrict__ W, uint8_t *pi, int nact, const int *stop) {
+    if (stop && *(volatile const int *)stop) return;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.nstates) return;
     const uint8_t k = a.cell[s];
@@ -91,13 +93,34 @@ __global__ void plain_max_kernel(PlainArgs a, const T *__restrict__ Q, const T *
 
 template <typename T>
 __global__ void plain_residual_kernel(int n, const uint8_t *__restrict__ cell, const T *__restrict__ V,
-                                      const T *__restrict__ W, unsigned long long *res) {
+                                      const T *__restrict__ W, unsigned long long *res, const int *stop) {
     __shared__ double shd[32];
+    if (stop && *(volatile const int *)stop) return;
     double m = 0.0;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
         if (cell[s] != CPMDP_CELL_OBSTACLE) m = fmax(m, fabs((double)W[s] - (double)V[s]));
     m = block_max(m, shd);
     if (threadIdx.x == 0 && m > 0.0) atomicMax(res, (unsigned long long)__double_as_longlong(m));
+}
+
+// Device-side stopping rule of the plain baseline's graph variant: after
+// each sweep one thread reads the sweep's residual, clears its slot for the
+// next sweep, counts the sweep and raises stop when the residual is below
+// tol or max_iter sweeps are done; every kernel of a later sweep then
+// returns at once.
+__global__ void plain_check_kernel(Ctrl *c, double tol, int max_iter) {
+    if (c->plain_stop) return;
+    double r;
+    memcpy(&r, &c->res_slot[0], sizeof(r));
+    c->res_slot[0] = 0ull;
+    c->iterations += 1;
+    c->last_residual = r;
+    if (r < tol) {
+        c->converged = 1;
+        c->plain_stop = 1;
+    } else if (c->iterations >= max_iter) {
+        c->plain_stop = 1;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -198,9 +221,80 @@ cpmdp_status banded_certify(const Factors &F, const float *V, uint8_t *pi, doubl
     return CPMDP_OK;
 }
 
+// Plain baseline, second variant (fused = 3): the same unfused kernels,
+// but the stopping rule is taken on the device (plain_check_kernel) and the
+// host looks at it once per chunk of kPlainChunk sweeps. A chunk (an even
+// number of sweeps, so it starts and ends in V) is recorded once into a
+// CUDA graph and replayed until the stop flag is up; the sweeps of a chunk
+// after the stopping sweep launch and return at once. The result is in V
+// after an even number of sweeps and in the scratch buffer after an odd
+// number.
+constexpr int kPlainChunk = 32;
+
+template <typename T>
+static cpmdp_status plain_vi_graph(const Factors &F, const PlainArgs &a, T *V, const SolveOpts &o, Ctrl *hc,
+                                   cudaStream_t st) {
+    Factors &M = const_cast<Factors &>(F);
+    const T *R = std::is_same<T, double>::value ? (const T *)F.d_R64 : (const T *)F.d_R32;
+    T *Q = (T *)F.d_q;
+    T *W = (T *)F.d_scratch;
+    const int n = (int)F.nstates;
+    const int grid = (n + 255) / 256;
+    int rgrid = grid > F.num_sms * 8 ? F.num_sms * 8 : grid;
+    if (rgrid < 1) rgrid = 1;
+    unsigned long long *rb = &F.d_ctrl->res_slot[0];
+    const int *stop = &F.d_ctrl->plain_stop;
+    const int prec = std::is_same<T, double>::value ? 1 : 0;
+    const bool same = M.plain_graph && M.plain_graph_V == (void *)V && M.plain_graph_tol == o.tol &&
+                      M.plain_graph_max_iter == o.max_iter && M.plain_graph_prec == prec;
+    if (!same) {
+        if (M.plain_graph) { cudaGraphExecDestroy(M.plain_graph); M.plain_graph = nullptr; }
+        cudaStream_t cap;
+        CPMDP_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        for (int k = 0; k < kPlainChunk && e == cudaSuccess; k++) {
+            const T *cur = (k & 1) ? W : V;
+            T *nxt = (k & 1) ? V : W;
+            for (int act = 0; act < F.nactions; act++) plain_q_kernel<T><<<grid, 256, 0, cap>>>(a, cur, R, Q, act, stop);
+            plain_max_kernel<T><<<grid, 256, 0, cap>>>(a, Q, R, nxt, nullptr, F.nactions, stop);
+            plain_residual_kernel<T><<<rgrid, 256, 0, cap>>>(n, F.d_cell, cur, nxt, rb, stop);
+            plain_check_kernel<<<1, 1, 0, cap>>>(F.d_ctrl, o.tol, o.max_iter);
+            e = cudaGetLastError();
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&M.plain_graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) { M.plain_graph = nullptr; CPMDP_CUDA(e); }
+        M.plain_graph_V = (void *)V;
+        M.plain_graph_tol = o.tol;
+        M.plain_graph_max_iter = o.max_iter;
+        M.plain_graph_prec = prec;
+    }
+    // stop = 0, iterations = 0, residual slot 0
+    CPMDP_CUDA(cudaMemsetAsync(F.d_ctrl, 0, sizeof(Ctrl), st));
+    Ctrl h;
+    for (;;) {
+        CPMDP_CUDA(cudaGraphLaunch(M.plain_graph, st));
+        CPMDP_CUDA(cudaMemcpyAsync(&h, F.d_ctrl, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CPMDP_CUDA(cudaStreamSynchronize(st));
+        if (h.plain_stop || h.status) break;
+    }
+    if (h.iterations & 1) CPMDP_CUDA(cudaMemcpyAsync(V, W, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+    hc->iterations = h.iterations;
+    hc->converged = h.converged;
+    hc->last_residual = h.last_residual;
+    hc->backups = (long long)h.iterations * F.nstates * F.nactions;
+    return CPMDP_OK;
+}
+
 // Plain baseline value iteration: per sweep |A| Q kernels, a max kernel, a
 // residual kernel and a device-to-host copy of the residual checked on the
-// host. Fills host_ctrl (iterations, converged, residual, backups).
+// host (fused = 0), or the same kernels with the stopping rule taken on the
+// device and checked by the host once per chunk of sweeps (fused = 3).
+// Fills host_ctrl (iterations, converged, residual, backups).
 template <typename T>
 static cpmdp_status plain_vi_impl(const Factors &F, T *V, uint8_t *pi, const SolveOpts &o, Ctrl *hc,
                                   cudaStream_t st) {
@@ -222,13 +316,22 @@ static cpmdp_status plain_vi_impl(const Factors &F, T *V, uint8_t *pi, const Sol
     const int grid = (n + 255) / 256;
     int rgrid = grid > F.num_sms * 8 ? F.num_sms * 8 : grid;
     if (rgrid < 1) rgrid = 1;
+    if (o.fused == 3) {
+        cpmdp_status s3 = plain_vi_graph<T>(F, a, V, o, hc, st);
+        if (s3 != CPMDP_OK || !pi) return s3;
+        T *spare = (T *)F.d_scratch;
+        for (int act = 0; act < F.nactions; act++) plain_q_kernel<T><<<grid, 256, 0, st>>>(a, V, R, Q, act, nullptr);
+        plain_max_kernel<T><<<grid, 256, 0, st>>>(a, Q, R, spare, pi, F.nactions, nullptr);
+        CPMDP_CUDA(cudaGetLastError());
+        return CPMDP_OK;
+    }
     int k = 0, conv = 0;
     double res = INFINITY;
     while (k < o.max_iter) {
         CPMDP_CUDA(cudaMemsetAsync(rb, 0, sizeof(unsigned long long), st));
-        for (int act = 0; act < F.nactions; act++) plain_q_kernel<T><<<grid, 256, 0, st>>>(a, cur, R, Q, act);
-        plain_max_kernel<T><<<grid, 256, 0, st>>>(a, Q, R, nxt, nullptr, F.nactions);
-        plain_residual_kernel<T><<<rgrid, 256, 0, st>>>(n, F.d_cell, cur, nxt, rb);
+        for (int act = 0; act < F.nactions; act++) plain_q_kernel<T><<<grid, 256, 0, st>>>(a, cur, R, Q, act, nullptr);
+        plain_max_kernel<T><<<grid, 256, 0, st>>>(a, Q, R, nxt, nullptr, F.nactions, nullptr);
+        plain_residual_kernel<T><<<rgrid, 256, 0, st>>>(n, F.d_cell, cur, nxt, rb, nullptr);
         CPMDP_CUDA(cudaGetLastError());
         CPMDP_CUDA(cudaMemcpyAsync(&hres_bits, rb, sizeof(hres_bits), cudaMemcpyDeviceToHost, st));
         CPMDP_CUDA(cudaStreamSynchronize(st));
@@ -241,8 +344,8 @@ static cpmdp_status plain_vi_impl(const Factors &F, T *V, uint8_t *pi, const Sol
     if (pi) {
         // policy of the returned V; the max goes to the scratch buffer (V is the result)
         T *spare = (T *)F.d_scratch;
-        for (int act = 0; act < F.nactions; act++) plain_q_kernel<T><<<grid, 256, 0, st>>>(a, V, R, Q, act);
-        plain_max_kernel<T><<<grid, 256, 0, st>>>(a, Q, R, spare, pi, F.nactions);
+        for (int act = 0; act < F.nactions; act++) plain_q_kernel<T><<<grid, 256, 0, st>>>(a, V, R, Q, act, nullptr);
+        plain_max_kernel<T><<<grid, 256, 0, st>>>(a, Q, R, spare, pi, F.nactions, nullptr);
         CPMDP_CUDA(cudaGetLastError());
     }
     hc->iterations = k;

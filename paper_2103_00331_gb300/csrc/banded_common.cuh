@@ -553,6 +553,7 @@ struct SolveParams {
     unsigned long long timeout_ns;
     int nactions;
     int inject_stall;
+    int partial_eval;   // policy iteration: evaluation sweep cap while the policy changes (0: none)
 };
 
 BandArgs make_band_args(const Factors &F);

@@ -19,6 +19,7 @@
 // so the result equals the grid-stride sweep's bit for bit.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "banded_common.cuh"
 #include "march.h"
@@ -63,8 +64,10 @@ template <> struct Rew4<double> {
 
 template <typename TA, bool WITH_PI>
 __global__ void __launch_bounds__(256) march_kernel(MarchArgs m, const float *__restrict__ V, float *__restrict__ W,
-                                                    uint8_t *__restrict__ pi, unsigned long long *res_out) {
+                                                    uint8_t *__restrict__ pi, unsigned long long *res_out,
+                                                    const int *stop) {
     __shared__ unsigned shm[64];
+    if (stop && *(volatile const int *)stop) return;   // value iteration: a sweep after the stopping one
     constexpr int D = 3;
     constexpr unsigned OBST = 1u << (2 * D), TERM = 1u << (2 * D + 1);
     const BandArgs &a = m.a;
@@ -166,6 +169,38 @@ __global__ void __launch_bounds__(256) march_kernel(MarchArgs m, const float *__
     }
 }
 
+static MarchArgs march_args(const Factors &F) {
+    MarchArgs m;
+    m.a = make_band_args(F);
+    m.nz = (int)F.shape[0];
+    m.ny = (int)F.shape[1];
+    m.nx = (int)F.shape[2];
+    m.xtiles = (m.nx + kTileX - 1) / kTileX;
+    m.ytiles = (m.ny + kTileY - 1) / kTileY;
+    return m;
+}
+
+// Stopping rule of the graph-driven value iteration: one thread reads the
+// sweep's residual, clears its slot, counts the sweep (and its backups),
+// writes the trace entry and raises stop once the residual is below tol or
+// max_iter sweeps are done; later sweeps of the graph then return at once.
+__global__ void march_check_kernel(Ctrl *c, double tol, int max_iter, long long backups_per_sweep, double *trace) {
+    if (c->plain_stop) return;
+    double r;
+    memcpy(&r, &c->res_slot[0], sizeof(r));
+    c->res_slot[0] = 0ull;
+    if (trace) trace[c->iterations] = r;
+    c->iterations += 1;
+    c->backups += backups_per_sweep;
+    c->last_residual = r;
+    if (r < tol) {
+        c->converged = 1;
+        c->plain_stop = 1;
+    } else if (c->iterations >= max_iter) {
+        c->plain_stop = 1;
+    }
+}
+
 template <typename TA, bool WITH_PI>
 cudaError_t launch_march(const Factors &F, const float *V, float *W, uint8_t *pi, unsigned long long *res,
                          cudaStream_t st) {
@@ -178,9 +213,11 @@ cudaError_t launch_march(const Factors &F, const float *V, float *W, uint8_t *pi
     m.ytiles = (m.ny + kTileY - 1) / kTileY;
     const long long blocks = (long long)m.xtiles * m.ytiles * ((m.nz + kChunk - 1) / kChunk);
     if (blocks < 1 || blocks > 0x7FFFFFFFll) return cudaErrorInvalidValue;
-    march_kernel<TA, WITH_PI><<<(unsigned)blocks, 256, 0, st>>>(m, V, W, pi, res);
+    march_kernel<TA, WITH_PI><<<(unsigned)blocks, 256, 0, st>>>(m, V, W, pi, res, nullptr);
     return cudaGetLastError();
 }
+
+constexpr int kMarchChunkSweeps = 16;   // sweeps per recorded graph (even: it starts and ends in V)
 
 }  // namespace
 
@@ -189,6 +226,63 @@ bool march_eligible(const Factors &F, const void *V, const void *W, const void *
     // that the sweep is bound by DRAM rather than by L2 or its launch
     return F.ndim == 3 && F.shape[2] % 4 == 0 && F.nstates >= kMarchMinStates && F.shape[1] * F.shape[2] < (1ll << 31) &&
            ((uintptr_t)V & 15u) == 0 && ((uintptr_t)W & 15u) == 0 && ((uintptr_t)pi & 3u) == 0;
+}
+
+// FP32 value iteration of a large 3-D grid: kMarchChunkSweeps sweeps of
+// march_kernel (V -> scratch -> V ...), each followed by march_check_kernel,
+// recorded once into a CUDA graph (per V, tol, max_iter, trace) and replayed
+// until the device raised stop; the host reads the control block once per
+// graph. The result is in V after an even number of sweeps, in the scratch
+// buffer (copied to V) after an odd number. Same per-state arithmetic and
+// stopping sweep as the grid-barrier solver.
+cudaError_t march_solve(const Factors &F, float *V, double tol, int max_iter, double *trace, cudaStream_t st) {
+    Factors &M = const_cast<Factors &>(F);
+    float *W = (float *)F.d_scratch;
+    const MarchArgs m = march_args(F);
+    const long long blocks = (long long)m.xtiles * m.ytiles * ((m.nz + kChunk - 1) / kChunk);
+    if (blocks < 1 || blocks > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+    unsigned long long *rb = &F.d_ctrl->res_slot[0];
+    const int *stop = &F.d_ctrl->plain_stop;
+    const long long bps = (long long)F.nstates * F.nactions;
+    const bool same = M.march_graph && M.march_graph_V == (void *)V && M.march_graph_tol == tol &&
+                      M.march_graph_max_iter == max_iter && M.march_graph_trace == (void *)trace;
+    cudaError_t e = cudaSuccess;
+    if (!same) {
+        if (M.march_graph) { cudaGraphExecDestroy(M.march_graph); M.march_graph = nullptr; }
+        cudaStream_t cap;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        for (int k = 0; k < kMarchChunkSweeps && e == cudaSuccess; k++) {
+            const float *cur = (k & 1) ? W : V;
+            float *nxt = (k & 1) ? V : W;
+            march_kernel<float, false><<<(unsigned)blocks, 256, 0, cap>>>(m, cur, nxt, nullptr, rb, stop);
+            march_check_kernel<<<1, 1, 0, cap>>>(F.d_ctrl, tol, max_iter, bps, trace);
+            e = cudaGetLastError();
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&M.march_graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) { M.march_graph = nullptr; return e; }
+        M.march_graph_V = (void *)V;
+        M.march_graph_tol = tol;
+        M.march_graph_max_iter = max_iter;
+        M.march_graph_trace = (void *)trace;
+    }
+    // the control block was cleared by the caller
+    if (trace && (e = cudaMemsetAsync(trace, 0, (size_t)max_iter * sizeof(double), st)) != cudaSuccess) return e;
+    Ctrl h;
+    for (;;) {
+        if ((e = cudaGraphLaunch(M.march_graph, st)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(&h, F.d_ctrl, sizeof(h), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+        if (h.plain_stop) break;
+    }
+    if (h.iterations & 1) return cudaMemcpyAsync(V, W, sizeof(float) * F.nstates, cudaMemcpyDeviceToDevice, st);
+    return cudaSuccess;
 }
 
 cudaError_t march_sweep(const Factors &F, const float *V, float *W, uint8_t *pi, unsigned long long *res, bool fp64,

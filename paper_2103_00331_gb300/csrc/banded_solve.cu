@@ -17,6 +17,7 @@
 
 #include "banded_common.cuh"
 #include "flow.h"
+#include "march.h"
 
 namespace cpmdp {
 
@@ -81,9 +82,13 @@ __global__ void __launch_bounds__(256) solve_pi_kernel(BandArgs a, T *V, T *Wbuf
     if (grid_sync_count(ctrl, nbar++, nb, 0, sp.timeout_ns, ph0, ph1, stall) < 0) return;
     total++;
     backups += (long long)a.nstates * sp.nactions;
+    // modified policy iteration: evaluations capped at partial_eval sweeps
+    // until an improvement changes no action, full evaluations after that
+    bool full = sp.partial_eval <= 0;
     while (round < sp.max_rounds) {
+        const int cap = full ? sp.max_eval_iter : min(sp.partial_eval, sp.max_eval_iter);
         int e = 0, eval_ok = 0;
-        while (e < sp.max_eval_iter) {
+        while (e < cap) {
             const TA r = sweep_all<T, TA, D, VEC, M_EVAL, true>(a, cur, nxt, pi, (TA)0, dummy);
             const unsigned long long mb = block_max_bits(r, shm);
             int flag = 0;
@@ -110,8 +115,13 @@ __global__ void __launch_bounds__(256) solve_pi_kernel(BandArgs a, T *V, T *Wbuf
         total++;
         round++;
         backups += (long long)a.nstates * sp.nactions;
-        if (moved == 0) { converged = eval_ok; break; }
-        if (!eval_ok) break;
+        if (moved == 0) {
+            if (eval_ok) { converged = 1; break; }
+            if (full) break;   // the evaluation limit ran out
+            full = true;       // evaluate this policy to eval_tol before deciding
+            continue;
+        }
+        if (!eval_ok && full) break;
     }
     if (cur != V) {
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.nstates; i += gridDim.x * blockDim.x) V[i] = cur[i];
@@ -207,6 +217,7 @@ cpmdp_status banded_solve(const Factors &F, cpmdp_precision prec, bool policy_it
     sp.timeout_ns = (unsigned long long)(o.timeout_s * 1e9);
     sp.nactions = F.nactions;
     sp.inject_stall = o.inject_stall;
+    sp.partial_eval = o.partial_eval;
     CPMDP_CUDA(cudaMemsetAsync(F.d_ctrl, 0, sizeof(Ctrl), st));
     // FP32 solves that fit one co-resident grid at one thread per 4 states
     // run on the barrier-free solver (fused = 2 asks for this file's
@@ -221,6 +232,16 @@ cpmdp_status banded_solve(const Factors &F, cpmdp_precision prec, bool policy_it
         }
         M.flow_pending = true;
         return flow_solve(F, policy_iteration, (float *)V, pi, sp, o.trace, st);
+    }
+    // FP32 value iteration of large 3-D grids: recorded graphs of the
+    // plane-marching sweep (DRAM read about once per sweep)
+    Factors &M2 = const_cast<Factors &>(F);
+    M2.march_pending = false;
+    if (prec == CPMDP_F32 && o.fused == 1 && !policy_iteration && !o.inject_stall &&
+        march_eligible(F, V, F.d_scratch, nullptr)) {
+        M2.march_pending = true;
+        CPMDP_CUDA(march_solve(F, (float *)V, o.tol, o.max_iter, o.trace, st));
+        return CPMDP_OK;
     }
     cudaError_t e;
     if (prec == CPMDP_F64) e = solve_t<double>(F, policy_iteration, (double *)V, pi, sp, o.trace, st);

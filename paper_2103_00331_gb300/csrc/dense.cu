@@ -15,6 +15,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <type_traits>
 #include <vector>
 
@@ -315,9 +316,12 @@ static cpmdp_status dense_solve_t(const Factors &F, bool pim, T *V, uint8_t *pi,
         if ((s2 = dense_sweep<T>(F, cur, nullptr, pi, DM_GREEDY, margin, nullptr, nullptr, st)) != CPMDP_OK) return s2;
         total++;
         backups += SA;
+        // modified policy iteration, as the GridWorld solvers
+        bool full = o.partial_eval <= 0;
         while (rounds < o.max_rounds) {
+            const int cap = full ? o.max_eval_iter : std::min(o.partial_eval, o.max_eval_iter);
             int e = 0, ok = 0;
-            while (e < o.max_eval_iter) {
+            while (e < cap) {
                 if ((s2 = sweep_res(DM_EVAL)) != CPMDP_OK) return s2;
                 e++;
                 if (res < o.eval_tol) { ok = 1; break; }
@@ -331,8 +335,13 @@ static cpmdp_status dense_solve_t(const Factors &F, bool pim, T *V, uint8_t *pi,
             total++;
             rounds++;
             backups += SA;
-            if (nchg == 0) { conv = ok; break; }
-            if (!ok) break;
+            if (nchg == 0) {
+                if (ok) { conv = 1; break; }
+                if (full) break;
+                full = true;
+                continue;
+            }
+            if (!ok && full) break;
         }
     }
     if (cur != V) CPMDP_CUDA(cudaMemcpyAsync(V, cur, sizeof(T) * F.nstates, cudaMemcpyDeviceToDevice, st));

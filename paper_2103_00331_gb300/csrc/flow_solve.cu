@@ -623,7 +623,12 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
     }
     int evals = 0, round = 0, conv = 0;
     float rres = 0.f;
+    // modified policy iteration: evaluations capped at partial_eval sweeps
+    // until an improvement changes no action, full evaluations after that
+    // (the same rule as the grid-barrier solver, so the same rounds)
+    bool full = sp.partial_eval <= 0;
     while (round < sp.max_rounds) {
+        const int cap = full ? sp.max_eval_iter : min(sp.partial_eval, sp.max_eval_iter);
         // evaluation of the current policy from V_q (tag base + q)
         const unsigned q0 = q;
         unsigned rq = q;
@@ -675,7 +680,7 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
             rh[0] = r;
             q++;
             e++;
-            if (e == sp.max_eval_iter) {
+            if (e == cap) {
                 rres = rh[0];
                 rq = q;
                 // arrivals of this phase are its sweeps q0, q0 + 1, ... in order
@@ -736,8 +741,13 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
         const int moved = arv.check_next(ctrl, sp.timeout_ns);
         if (moved < 0) return;
         round++;
-        if (moved == 0) { conv = eval_ok; break; }
-        if (!eval_ok) break;
+        if (moved == 0) {
+            if (eval_ok) { conv = 1; break; }
+            if (full) break;   // the evaluation limit ran out
+            full = true;       // evaluate this policy to eval_tol before deciding
+            continue;
+        }
+        if (!eval_ok && full) break;
     }
 #pragma unroll
     for (int i = 0; i < ZS; i++)

@@ -38,6 +38,7 @@ struct Ctrl {
     unsigned long long need_slot[3];  // batch: warps the instances running sweep k would need, slot k % 3
     int handoff;                   // batch: 1 when the batched kernel stopped for the barrier-free tail
     int handoff_sweeps;            // batch: sweeps done before the hand-off
+    int plain_stop;                // plain baseline, device-checked variant: stop every later kernel
 };
 
 struct Factors {
@@ -74,6 +75,17 @@ struct Factors {
     size_t scratch_bytes = 0;
     void *d_q = nullptr;               // plain baseline: |A| x |S| Q values (lazily allocated)
     size_t q_bytes = 0;
+    cudaGraphExec_t plain_graph = nullptr;   // plain baseline, fused = 3: one recorded chunk of sweeps
+    void *plain_graph_V = nullptr;
+    double plain_graph_tol = 0;
+    int plain_graph_max_iter = 0;
+    int plain_graph_prec = -1;
+    cudaGraphExec_t march_graph = nullptr;   // large 3-D value iteration: one recorded chunk of marching sweeps
+    void *march_graph_V = nullptr;
+    void *march_graph_trace = nullptr;
+    double march_graph_tol = 0;
+    int march_graph_max_iter = 0;
+    bool march_pending = false;              // the last solve ran march_solve
     Ctrl *d_ctrl = nullptr;
     int num_sms = 0;
 
@@ -118,6 +130,7 @@ struct SolveOpts {
     int max_rounds;
     double timeout_s;
     double *trace;
+    int partial_eval;
     int inject_stall;
 };
 SolveOpts resolve_opts(const cpmdp_solve_opts *o, cpmdp_precision prec);

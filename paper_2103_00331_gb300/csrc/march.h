@@ -18,5 +18,10 @@ bool march_eligible(const Factors &F, const void *V, const void *W, const void *
 // double, may be null): FP32 arithmetic, or FP64 when fp64 is set.
 cudaError_t march_sweep(const Factors &F, const float *V, float *W, uint8_t *pi, unsigned long long *res, bool fp64,
                         cudaStream_t st);
+// FP32 value iteration (V in place, the factors' scratch as the second
+// buffer) by recorded graphs of marching sweeps with the stopping rule taken
+// on the device; fills the control block (iterations, converged, residual,
+// backups). The control block must be cleared before the call.
+cudaError_t march_solve(const Factors &F, float *V, double tol, int max_iter, double *trace, cudaStream_t st);
 
 }  // namespace cpmdp

@@ -360,7 +360,7 @@ __global__ void features_kernel(const BatchInst *__restrict__ inst, const uint8_
 
 __global__ void targets_kernel(const BatchInst *__restrict__ inst, const uint8_t *__restrict__ code,
                                const float *__restrict__ V, int first, int count, int cells,
-                               float *__restrict__ target, float *__restrict__ mask) {
+                               const float *__restrict__ base, float *__restrict__ target, float *__restrict__ mask) {
     const long long total = (long long)count * cells;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total; g += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(g / cells), cell = (int)(g % cells);
@@ -378,14 +378,19 @@ __global__ void targets_kernel(const BatchInst *__restrict__ inst, const uint8_t
                     live++;
                     s += V[st];
                 }
-        target[g] = live ? s / live : 0.f;
+        target[g] = (live ? s / live : 0.f) - (base ? base[g] : 0.f);
         mask[g] = live ? 1.f : 0.f;
     }
 }
 
+// Coarse estimate (plus base, if given) at the cell centres, interpolated
+// trilinearly to every fine state: a fine coordinate x sits at
+// (x + 0.5) / 4 - 0.5 in cell units, clamped to the outermost centres.
+// Terminals take R(t), obstacles 0.
 __global__ void upsample_kernel(const BatchInst *__restrict__ inst, const uint8_t *__restrict__ code,
                                 const float *__restrict__ R, int first, int count, int cells,
-                                const float *__restrict__ coarse, float *__restrict__ V) {
+                                const float *__restrict__ coarse, const float *__restrict__ base,
+                                float *__restrict__ V) {
     const BatchInst I0 = inst[first];
     const long long per = I0.nstates;
     const long long total = (long long)count * per;
@@ -394,13 +399,158 @@ __global__ void upsample_kernel(const BatchInst *__restrict__ inst, const uint8_
         const int s = (int)(g % per);
         const BatchInst I = inst[first + i];
         const int z = s / I.stride[0], y = (s / I.stride[1]) % I.shape[1], x = s % I.shape[2];
-        const int xc = (I.shape[2] + kF - 1) / kF, yc = (I.shape[1] + kF - 1) / kF;
-        const int cell = ((z / kF) * yc + y / kF) * xc + x / kF;
+        const int zc = (I.shape[0] + kF - 1) / kF, yc = (I.shape[1] + kF - 1) / kF, xc = (I.shape[2] + kF - 1) / kF;
         const unsigned c = code[I.offset + s];
-        float v = coarse[(long long)i * cells + cell];
-        if (c & (1u << (2 * I.ndim + 1))) v = R[I.offset + s];
-        if (c & (1u << (2 * I.ndim))) v = 0.f;
+        float v;
+        if (c & (1u << (2 * I.ndim))) {
+            v = 0.f;
+        } else if (c & (1u << (2 * I.ndim + 1))) {
+            v = R[I.offset + s];
+        } else {
+            int lo[3], hi[3];
+            float t[3];
+            const int pos[3] = {z, y, x}, nc[3] = {zc, yc, xc};
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                float u = ((float)pos[d] + 0.5f) / (float)kF - 0.5f;
+                u = fminf(fmaxf(u, 0.f), (float)(nc[d] - 1));
+                lo[d] = (int)floorf(u);
+                hi[d] = min(lo[d] + 1, nc[d] - 1);
+                t[d] = u - (float)lo[d];
+            }
+            const float *cv = coarse + (long long)i * cells;
+            const float *bv = base ? base + (long long)i * cells : nullptr;
+            v = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int cz = (k & 4) ? hi[0] : lo[0], cy = (k & 2) ? hi[1] : lo[1], cx = (k & 1) ? hi[2] : lo[2];
+                const float w = ((k & 4) ? t[0] : 1.f - t[0]) * ((k & 2) ? t[1] : 1.f - t[1]) *
+                                ((k & 1) ? t[2] : 1.f - t[2]);
+                const int cell = (cz * yc + cy) * xc + cx;
+                v += w * (cv[cell] + (bv ? bv[cell] : 0.f));
+            }
+        }
         V[I.offset + s] = v;
+    }
+}
+
+// Value iteration of a coarsened copy of each instance, one CTA per
+// instance, entirely in shared memory (the input feature that gives the
+// network a view of the whole grid). Coarse cell = 4 x 4 x 4 fine states:
+// an obstacle when at least half of its states are obstacles, else a
+// terminal of value max R(t) when it holds terminals, else a free cell whose
+// reward per coarse step is the mean fine reward of its free states times
+// 1 + gamma + gamma^2 + gamma^3 (four fine steps); discount gamma^4, the
+// instance's slip model, walls and obstacle cells block moves. Jacobi sweeps
+// from zero until max |dV| < tol or max_sweeps.
+constexpr int kCoarseThreads = 512;
+constexpr int kMaxCoarseCells = 8192;
+
+__device__ __forceinline__ unsigned float_key(float f) {
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+__global__ void __launch_bounds__(kCoarseThreads) coarse_vi_kernel(const BatchInst *__restrict__ inst,
+                                                                   const uint8_t *__restrict__ code,
+                                                                   const float *__restrict__ R, int first, int cells,
+                                                                   float tol, int max_sweeps,
+                                                                   float *__restrict__ coarse_v,
+                                                                   __nv_bfloat16 *__restrict__ feat) {
+    extern __shared__ uint8_t smem_raw[];
+    int *n_obst = reinterpret_cast<int *>(smem_raw);                 // later: V (even sweeps)
+    int *n_free = n_obst + cells;                                    // later: V (odd sweeps)
+    float *rsum = reinterpret_cast<float *>(n_free + cells);         // later: coarse reward
+    unsigned *tkey = reinterpret_cast<unsigned *>(rsum + cells);     // largest terminal reward (0: none)
+    uint8_t *kind = reinterpret_cast<uint8_t *>(tkey + cells);      // bits 0-5 blocked moves, 6 obstacle, 7 terminal
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x;
+    const BatchInst I = inst[first + i];
+    const int zc = (I.shape[0] + kF - 1) / kF, yc = (I.shape[1] + kF - 1) / kF, xc = (I.shape[2] + kF - 1) / kF;
+    for (int c = tid; c < cells; c += kCoarseThreads) {
+        n_obst[c] = 0;
+        n_free[c] = 0;
+        rsum[c] = 0.f;
+        tkey[c] = 0u;
+    }
+    __syncthreads();
+    const unsigned ob = 1u << (2 * I.ndim), tb = 1u << (2 * I.ndim + 1);
+    for (int s = tid; s < I.nstates; s += kCoarseThreads) {   // coalesced over the fine states
+        const int z = s / I.stride[0], y = (s / I.stride[1]) % I.shape[1], x = s % I.shape[2];
+        const int c = ((z / kF) * yc + y / kF) * xc + x / kF;
+        const unsigned cs = code[I.offset + s];
+        if (cs & ob) { atomicAdd(&n_obst[c], 1); continue; }
+        const float r = R[I.offset + s];
+        if (cs & tb) { atomicMax(&tkey[c], float_key(r)); continue; }
+        atomicAdd(&n_free[c], 1);
+        atomicAdd(&rsum[c], r);
+    }
+    __syncthreads();
+    const float g = I.gamma;
+    const float gc = g * g * g * g, steps = 1.f + g + g * g + g * g * g;
+    for (int c = tid; c < cells; c += kCoarseThreads) {
+        const int cz = c / (yc * xc), cy = (c / xc) % yc, cx = c % xc;
+        const int n = (min((cz + 1) * kF, I.shape[0]) - cz * kF) * (min((cy + 1) * kF, I.shape[1]) - cy * kF) *
+                      (min((cx + 1) * kF, I.shape[2]) - cx * kF);
+        uint8_t k = 0;
+        float r = 0.f;
+        if (2 * n_obst[c] >= n) k = 0x40;
+        else if (tkey[c]) { k = 0x80; r = key_float(tkey[c]); }
+        else r = n_free[c] ? rsum[c] / (float)n_free[c] * steps : 0.f;
+        kind[c] = k;
+        rsum[c] = r;
+    }
+    __syncthreads();
+    float *va = reinterpret_cast<float *>(n_obst), *vb = reinterpret_cast<float *>(n_free);
+    for (int c = tid; c < cells; c += kCoarseThreads) {
+        const int cz = c / (yc * xc), cy = (c / xc) % yc, cx = c % xc;
+        uint8_t k = kind[c];
+        const int nbr[6] = {cz > 0 ? c - yc * xc : -1, cz < zc - 1 ? c + yc * xc : -1, cy > 0 ? c - xc : -1,
+                            cy < yc - 1 ? c + xc : -1, cx > 0 ? c - 1 : -1, cx < xc - 1 ? c + 1 : -1};
+#pragma unroll
+        for (int j = 0; j < 6; j++)
+            if (nbr[j] < 0 || (kind[nbr[j]] & 0x40)) k |= (uint8_t)(1u << j);
+        kind[c] = k;
+        const float v0 = (k & 0x80) ? rsum[c] : 0.f;
+        va[c] = v0;
+        vb[c] = v0;
+    }
+    __syncthreads();
+    const float wm = I.w_move, wp = I.w_perp, wst = I.w_stay;
+    float *src = va, *dst = vb;
+    for (int sweep = 0; sweep < max_sweeps; sweep++) {
+        int open = 0;
+        for (int c = tid; c < cells; c += kCoarseThreads) {
+            const uint8_t k = kind[c];
+            if (k & 0xC0) continue;   // obstacles (0) and terminals (their value) never change
+            const float self = src[c];
+            float nb[6];
+            const int step[3] = {yc * xc, xc, 1};
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                nb[2 * d] = ((k >> (2 * d)) & 1u) ? self : src[c - step[d]];
+                nb[2 * d + 1] = ((k >> (2 * d + 1)) & 1u) ? self : src[c + step[d]];
+            }
+            const float P0 = nb[0] + nb[1], P1 = nb[2] + nb[3], P2 = nb[4] + nb[5];
+            const float perp[3] = {P1 + P2, P0 + P2, P0 + P1};
+            float best = -INFINITY;
+#pragma unroll
+            for (int j = 0; j < 6; j++) best = fmaxf(best, wm * nb[j] + wp * perp[j / 2] + wst * self);
+            const float v = rsum[c] + gc * best;
+            dst[c] = v;
+            open |= fabsf(v - self) >= tol;
+        }
+        float *t = src; src = dst; dst = t;
+        if (!__syncthreads_or(open)) break;
+    }
+    for (int c = tid; c < cells; c += kCoarseThreads) {
+        const uint8_t k = kind[c];
+        const float v = (k & 0x40) ? 0.f : src[c];
+        coarse_v[(long long)i * cells + c] = v;
+        if (feat) feat[((long long)i * cells + c) * kC + 4] = __float2bfloat16_rn(v);
     }
 }
 
@@ -463,26 +613,45 @@ cpmdp_status cpmdp_ws_features(const cpmdp_batch *B, int32_t first, int32_t coun
     return CPMDP_OK;
 }
 
-cpmdp_status cpmdp_ws_targets(const cpmdp_batch *B, const float *V, int32_t first, int32_t count, float *target,
-                              float *mask, void *stream) {
+cpmdp_status cpmdp_ws_targets(const cpmdp_batch *B, const float *V, int32_t first, int32_t count, const float *base,
+                              float *target, float *mask, void *stream) {
     int cells = 0;
     cpmdp_status s = batch_range(B, first, count, &cells);
     if (s != CPMDP_OK) return s;
     const long long n = (long long)count * cells;
     targets_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(B->d_inst, B->d_code, V, first, count, cells,
-                                                                       target, mask);
+                                                                       base, target, mask);
     CPMDP_CUDA(cudaGetLastError());
     return CPMDP_OK;
 }
 
-cpmdp_status cpmdp_ws_upsample(const cpmdp_batch *B, const float *coarse, int32_t first, int32_t count, float *V,
-                               void *stream) {
+cpmdp_status cpmdp_ws_upsample(const cpmdp_batch *B, const float *coarse, const float *base, int32_t first,
+                               int32_t count, float *V, void *stream) {
     int cells = 0;
     cpmdp_status s = batch_range(B, first, count, &cells);
     if (s != CPMDP_OK) return s;
     const long long n = (long long)count * B->inst[(size_t)first].nstates;
     upsample_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(B->d_inst, B->d_code, B->d_R, first, count,
-                                                                        cells, coarse, V);
+                                                                        cells, coarse, base, V);
+    CPMDP_CUDA(cudaGetLastError());
+    return CPMDP_OK;
+}
+
+cpmdp_status cpmdp_ws_coarse_vi(const cpmdp_batch *B, int32_t first, int32_t count, float tol, int32_t max_sweeps,
+                                float *coarse_v, uint16_t *feat, void *stream) {
+    int cells = 0;
+    cpmdp_status s = batch_range(B, first, count, &cells);
+    if (s != CPMDP_OK) return s;
+    if (cells > kMaxCoarseCells) {
+        set_error("coarse value iteration holds at most %d coarse cells per instance", kMaxCoarseCells);
+        return CPMDP_EINVAL;
+    }
+    if (!coarse_v || !(tol > 0.f) || max_sweeps < 1) { set_error("coarse_v, tol > 0 and max_sweeps >= 1 required"); return CPMDP_EINVAL; }
+    const size_t smem = (size_t)cells * 17;
+    CPMDP_CUDA(cudaFuncSetAttribute(coarse_vi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    coarse_vi_kernel<<<count, kCoarseThreads, smem, (cudaStream_t)stream>>>(B->d_inst, B->d_code, B->d_R, first, cells,
+                                                                          tol, max_sweeps, coarse_v,
+                                                                          (__nv_bfloat16 *)feat);
     CPMDP_CUDA(cudaGetLastError());
     return CPMDP_OK;
 }

@@ -86,9 +86,60 @@ def test_features_target_upsample():
     assert t[0, 0, 0] == pytest.approx(V[0:4, 0:4, 0:4][live].mean())
     V0 = N.upsample(gw, t)
     assert V0.shape == gw.shape
-    free = gw.cell == 0
     assert np.all(V0[(gw.cell == 1)] == 0) and np.all(V0[gw.cell == 2] == gw.reward[gw.cell == 2])
-    assert V0[5, 6, 3] == (t[1, 1, 0] if free[5, 6, 3] else V0[5, 6, 3])
+
+
+def test_trilinear_upsample_closed_forms():
+    """Trilinear interpolation between cell centres: a constant coarse array
+    gives that constant everywhere; a coarse array linear in the cell index
+    (a z_c + b y_c + c x_c + d) gives, between the outermost centres, the
+    same linear function of the fine coordinate in cell units
+    (x + 0.5) / 4 - 0.5, and is clamped to the edge centres outside them."""
+    shape = (13, 9, 10)
+    gw = ci.GridWorld(shape=shape, p=0.8, gamma=0.9, cell=np.zeros(shape, np.uint8), reward=np.zeros(shape))
+    cs = (4, 3, 3)
+    assert np.allclose(N.upsample(gw, np.full(cs, 0.37)), 0.37)
+    a, b, c, d = 0.5, -1.25, 2.0, 0.1
+    C = np.fromfunction(lambda z, y, x: a * z + b * y + c * x + d, cs)
+    V0 = N.upsample(gw, C)
+
+    def u(p, n):
+        return min(max((p + 0.5) / 4 - 0.5, 0.0), n - 1.0)
+    for z, y, x in [(0, 0, 0), (5, 4, 7), (12, 8, 9), (7, 1, 3), (2, 6, 8)]:
+        want = a * u(z, 4) + b * u(y, 3) + c * u(x, 3) + d
+        assert V0[z, y, x] == pytest.approx(want, abs=1e-12)
+
+
+def test_coarse_gridworld_rules_and_closed_form():
+    """The coarse copy: cells with at least half obstacles are obstacles,
+    cells holding terminals are terminals with the largest terminal reward;
+    and with a constant reward r, no obstacles and no terminals, the coarse
+    value r (1 + ... + gamma^3) / (1 - gamma^4) equals the fine closed form
+    r / (1 - gamma) exactly (geometric series)."""
+    from oracle import cpfactor as oc
+    shape = (8, 8, 6)
+    cell = np.zeros(shape, np.uint8)
+    cell[0:4, 0:4, 0:2] = 1                      # 32 of 64: an obstacle cell
+    cell[4:8, 0:4, 0:1] = 1                      # 16 of 64: stays free
+    cell[5, 6, 5] = 2
+    cell[6, 7, 4] = 2
+    R = np.full(shape, -0.02)
+    R[cell == 1] = 0.0
+    R[5, 6, 5], R[6, 7, 4] = 0.4, 0.9
+    gw = ci.GridWorld(shape=shape, p=0.8, gamma=0.95, cell=cell, reward=R)
+    cg, kind = N.coarse_gridworld(gw)
+    assert cg.shape == (2, 2, 2) and kind[0, 0, 0] == 1 and kind[1, 0, 0] == 0
+    assert kind[1, 1, 1] == 2 and cg.reward[1, 1, 1] == 0.9
+    assert cg.gamma == pytest.approx(0.95 ** 4)
+    free = (cell[4:8, 0:4, 0:4] == 0)
+    assert cg.reward[1, 0, 0] == pytest.approx(-0.02 * sum(0.95 ** j for j in range(4)))
+    assert free.sum() == 48
+    r, g = -0.03, 0.97
+    flat = ci.GridWorld(shape=(12, 8, 8), p=0.8, gamma=g, cell=np.zeros((12, 8, 8), np.uint8),
+                        reward=np.full((12, 8, 8), r))
+    cf, _ = N.coarse_gridworld(flat)
+    Vc, _, _, _ = oc.value_iteration(cf, tol=1e-13, max_iter=100000)
+    assert np.allclose(Vc, r / (1 - g), atol=1e-10)
 
 
 def test_bf16_round_against_torch():

@@ -267,6 +267,44 @@ def test_plain_baseline_matches_fused(cp):
     assert np.mean(out[0][1] == out[1][1]) > 0.999
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_plain_device_stop_equals_host_stop(cp, prec):
+    """fused = 3 runs the plain kernels of fused = 0 with the stopping rule
+    taken on the device and a recorded 32-sweep graph: same sweep count,
+    same values bit for bit, same residual and policy, called twice (graph
+    replay); and max_iter inside a chunk (45: odd, the result sits in the
+    scratch buffer; 44: even) stops with ENOCONV at exactly max_iter sweeps
+    with the values of the host-checked run."""
+    import torch
+    dt = torch.float32 if prec == "f32" else torch.float64
+    P = cp.F32 if prec == "f32" else cp.F64
+    for side, seed in ((32, 5), (24, 6)):
+        gw = ci.config_3d(side=side, seed=seed)
+        f = cp.build_factors(gw, device=0)
+        out = {}
+        for fused in (0, 3, 3):
+            V = torch.zeros(gw.nstates, dtype=dt, device="cuda")
+            pi = torch.zeros(gw.nstates, dtype=torch.uint8, device="cuda")
+            r = cp.value_iteration(f, P, V, pi, opts=cp.default_opts(fused=fused, max_iter=5000, certify=0))
+            assert r["solver"] == cp.SOLVER_PLAIN
+            if fused in out:
+                assert r["iterations"] == out[fused][2]["iterations"]
+            out[fused] = (V.cpu().numpy(), pi.cpu().numpy(), r)
+        (V0, p0, r0), (V3, p3, r3) = out[0], out[3]
+        assert r0["iterations"] == r3["iterations"] and r0["residual"] == r3["residual"]
+        assert np.array_equal(V0, V3) and np.array_equal(p0, p3)
+        for mi in (45, 44):
+            got = {}
+            for fused in (0, 3):
+                V = torch.zeros(gw.nstates, dtype=dt, device="cuda")
+                r = cp.value_iteration(f, P, V, None, opts=cp.default_opts(fused=fused, max_iter=mi, certify=0),
+                                       raise_on_noconv=False)
+                assert r["status"] == cp.ENOCONV and r["iterations"] == mi
+                got[fused] = V.cpu().numpy()
+            assert np.array_equal(got[0], got[3])
+        f.close()
+
+
 def test_wait_timeout_returns_status(cp):
     """A block that never arrives at the grid barrier (inject_stall) makes the
     other blocks' bounded waits run out: the call returns CPMDP_ETIMEOUT

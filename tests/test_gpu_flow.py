@@ -128,6 +128,48 @@ def test_pi_equals_grid_barrier_solver(cp, shape):
     f.close()
 
 
+@pytest.mark.parametrize("partial", [0, 3, 8])
+def test_pi_partial_evaluation_same_in_both_solvers(cp, partial):
+    """Modified policy iteration (evaluations capped at partial_eval sweeps
+    until an improvement changes no action; 0 = every evaluation to
+    eval_tol): both solvers take the same rounds and sweeps, bit for bit;
+    the final policy is the same as with full evaluations wherever the
+    values leave no near-tie, and the values agree within the evaluation
+    bound 2 eval_tol / (1 - gamma) plus FP32 rounding."""
+    import torch
+    gw = _world((40, 36, 16), seed=21)
+    f = cp.build_factors(gw, device=0)
+    out = {}
+    for fused in (1, 2):
+        V = torch.zeros(gw.nstates, dtype=torch.float32, device="cuda")
+        pi = torch.zeros(gw.nstates, dtype=torch.uint8, device="cuda")
+        r = cp.policy_iteration(f, cp.F32, V, pi, opts=cp.default_opts(fused=fused, partial_eval=partial))
+        out[fused] = (V.cpu().numpy(), pi.cpu().numpy(), r)
+    (Va, pa, ra), (Vb, pb, rb) = out[1], out[2]
+    for key in ("status", "iterations", "rounds", "eval_sweeps", "residual", "backups"):
+        assert ra[key] == rb[key], (key, ra[key], rb[key])
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32)) and np.array_equal(pa, pb)
+    V = torch.zeros(gw.nstates, dtype=torch.float32, device="cuda")
+    pi = torch.zeros(gw.nstates, dtype=torch.uint8, device="cuda")
+    rf = cp.policy_iteration(f, cp.F32, V, pi, opts=cp.default_opts(partial_eval=0))
+    Vf, pf = V.cpu().numpy().astype(np.float64), pi.cpu().numpy()
+    eps = 14 * U32 * (np.abs(gw.reward).max() + np.abs(Vf).max())
+    bound = (2 * 1e-6 + eps) / (1 - gw.gamma)
+    assert np.abs(Va - Vf).max() <= bound
+    # the policies agree wherever the oracle's Q at the full-evaluation values
+    # leaves a gap above twice gamma times that bound plus the keep margin
+    from oracle import cpfactor as oc
+    _, _, _, Q = oc.backup(gw, Vf, want_q=True)
+    free = gw.cell.reshape(-1) == ci.FREE
+    Qs = np.sort(Q[:, free], axis=0)
+    sure = (Qs[-1] - Qs[-2]) > 2 * gw.gamma * bound + 2e-6 * (1 + np.abs(Qs[-1]))
+    assert sure.mean() > 0.9
+    assert np.array_equal(pa[free][sure], pf[free][sure])
+    if partial:
+        assert ra["eval_sweeps"] < rf["eval_sweeps"]
+    f.close()
+
+
 def test_pi_round_and_eval_limits(cp):
     """Evaluation and round limits end the solve the same way in both
     solvers (ENOCONV, same partial results)."""
@@ -135,7 +177,7 @@ def test_pi_round_and_eval_limits(cp):
     gw = _world((20, 36, 8), seed=5)
     f = cp.build_factors(gw, device=0)
     for kw in (dict(max_eval_iter=1), dict(max_eval_iter=2), dict(max_eval_iter=3),
-               dict(max_rounds=1), dict(max_rounds=2, max_eval_iter=5)):
+               dict(max_rounds=1), dict(max_rounds=2, max_eval_iter=5), dict(max_eval_iter=40, partial_eval=6)):
         out = {}
         for fused in (1, 2):
             V = torch.zeros(gw.nstates, dtype=torch.float32, device="cuda")

@@ -83,3 +83,45 @@ def test_march_sweep_equals_solver_sweep(cp, oc, shape):
     del V0, out, pi, V1, V2, pi2
     f.close()
     torch.cuda.empty_cache()
+
+
+def test_march_value_iteration_equals_grid_barrier(cp):
+    """Value iteration of a 3-D grid past 2^23 states runs the marching
+    sweep from a replayed CUDA graph with the stopping rule on the device:
+    the same sweeps, residual trace and values, bit for bit, as the
+    grid-barrier solver (fused = 2), its FP64 certificate and policy
+    included; a max_iter inside a graph chunk (odd: the result sits in the
+    scratch buffer) stops with ENOCONV at exactly max_iter sweeps with the
+    grid-barrier solver's values."""
+    import torch
+    gw = ci.gridworld((130, 256, 256), p=0.8, gamma=0.95, step_reward=-0.01,
+                      goal_rewards=list(ci.uniform(3, 12, 8, 0.5, 1.0)), obstacle_rate=0.05, seed=3)
+    assert gw.nstates >= 1 << 23
+    f = cp.build_factors(gw, device=0)
+    out = {}
+    for fused in (1, 2, 1):
+        V = torch.zeros(gw.nstates, dtype=torch.float32, device="cuda")
+        pi = torch.zeros(gw.nstates, dtype=torch.uint8, device="cuda")
+        tr = torch.zeros(5000, dtype=torch.float64, device="cuda")
+        o = cp.default_opts(max_iter=5000, fused=fused)
+        o.trace = tr.data_ptr()
+        r = cp.value_iteration(f, cp.F32, V, pi, opts=o)
+        assert r["solver"] == (cp.SOLVER_MARCH_GRAPH if fused == 1 else cp.SOLVER_GRID_BARRIER)
+        res = (V.cpu().numpy(), pi.cpu().numpy(), r, tr[:r["iterations"]].cpu().numpy())
+        if fused in out:   # the second march solve replays the recorded graph
+            assert np.array_equal(res[0].view(np.uint32), out[fused][0].view(np.uint32))
+        out[fused] = res
+    (Va, pa, ra, ta), (Vb, pb, rb, tb) = out[1], out[2]
+    assert ra["iterations"] == rb["iterations"] and ra["residual"] == rb["residual"]
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+    assert np.array_equal(ta, tb) and np.array_equal(pa, pb)
+    assert ra["certified_residual"] == rb["certified_residual"] and ra["backups"] == rb["backups"]
+    got = {}
+    for fused in (1, 2):
+        V = torch.zeros(gw.nstates, dtype=torch.float32, device="cuda")
+        r = cp.value_iteration(f, cp.F32, V, None, opts=cp.default_opts(max_iter=21, fused=fused, certify=0),
+                               raise_on_noconv=False)
+        assert r["status"] == cp.ENOCONV and r["iterations"] == 21
+        got[fused] = V.cpu().numpy()
+    assert np.array_equal(got[1].view(np.uint32), got[2].view(np.uint32))
+    f.close()
