@@ -846,7 +846,8 @@ def kernel_case(name, reps=3):
     FP32 value / policy iteration of the 64^3 instance (barrier-free solver);
     solve64b / pi64b = the same on the grid-barrier solver; ws512 = the warm-start network on
     512 x 16^3 coarse cells (six tensor-core convolutions); batch1024 = batched value iteration of
-    1024 uneven GridWorlds (batched kernel, then the barrier-free tail)."""
+    1024 uneven GridWorlds (batched kernel, then the barrier-free tail); batchcert = the FP64
+    certifying sweep of that batch after its solve."""
     import torch
     import paper_2103_00331_gb300 as cp
     import cpmdp_inputs as ci
@@ -903,6 +904,16 @@ def kernel_case(name, reps=3):
             r, iters, _ = cp.batch_value_iteration(B, V, opts=opts)
             print(f"batch of 1024: {r['elapsed_ms']:.3f} ms, {r['iterations']} sweeps, tail from sweep {r['tail_from']}")
         B.close()
+    elif name == "batchcert":
+        inst = ci.batch_gridworlds(count=1024, seed=0)
+        B = cp.batch_build(inst, device=0)
+        V = torch.zeros(int(B.total_states), dtype=torch.float32, device=dev)
+        pol = torch.empty(int(B.total_states), dtype=torch.uint8, device=dev)
+        cp.batch_value_iteration(B, V, opts=cp.default_opts(tol=TOL, max_iter=5000))
+        for _ in range(reps):
+            cert = cp.batch_certify(B, V, pol)
+        print(f"batch certify of 1024 instances: max certified residual {cert.max():.3e}")
+        B.close()
     elif name == "ws512":
         from paper_2103_00331_gb300 import warmstart as ws
         path = os.path.join(ROOT, "paper_2103_00331_gb300", "data", "warmstart_weights.npz")
@@ -953,7 +964,7 @@ def main():
     ap.add_argument("--skip-warmstart", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--kernel-case", choices=["sweep512", "sweep320", "solve64", "pi64", "solve64b", "pi64b", "dense64",
-                                              "dense64tc", "ws512", "batch1024"],
+                                              "dense64tc", "ws512", "batch1024", "batchcert"],
                     default=None,
                     help="run one kernel workload a few times (profiling) and exit")
     args = ap.parse_args()

@@ -258,6 +258,11 @@ cpmdp_status cpmdp_value_iteration(const cpmdp_factors *factors, cpmdp_precision
  * 1e-6 (F32) or 1e-12 (F64) times 1 + |Q|); stop when no action changes.
  * V receives the value of the final policy, policy (device, |S|, not NULL)
  * the final policy. Synchronises with `stream` before returning.
+ * BF16X3 (dense models, 64^4): evaluation sweeps are the tensor-core backup
+ * with each state's own action (defect correction against an FP32 base, as
+ * in value iteration); an improvement takes an evaluation-mode sweep, a max
+ * sweep and the keep-margin compare; with certify on, one FP64 backup of the
+ * result gives the certified residual max |T(V) - V| (policy unchanged).
  * Errors: EINVAL, ECUDA, ENOCONV (round or evaluation limit), ETIMEOUT.
  */
 cpmdp_status cpmdp_policy_iteration(const cpmdp_factors *factors, cpmdp_precision precision,

@@ -11,6 +11,7 @@
 #include <new>
 
 #include "internal.h"
+#include "flow.h"
 
 namespace cpmdp {
 
@@ -62,9 +63,11 @@ SolveOpts resolve_opts(const cpmdp_solve_opts *o, cpmdp_precision prec) {
 }
 
 static void free_device(Factors &F) {
-    // the arena holds d_code, d_R32, d_R64, d_cell, d_scratch and d_ctrl
+    // the arena holds d_code, d_R32, d_R64, d_cell, d_scratch, d_ctrl and,
+    // for shapes the barrier-free solver takes, d_flow
     void *ptrs[] = {F.d_arena, F.d_q, F.d_U32, F.d_U64, F.d_Ubf, F.d_lam32, F.d_lam64, F.d_dense_work,
-                    F.d_Vd, F.d_RB, F.d_T, F.d_EB, F.d_Vbase, F.d_tc_err, F.d_flow};
+                    F.d_Vd, F.d_RB, F.d_T, F.d_EB, F.d_Vbase, F.d_tc_err, F.flow_in_arena ? nullptr : F.d_flow,
+                    F.d_pi_work};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (F.plain_graph) cudaGraphExecDestroy(F.plain_graph);
@@ -76,7 +79,8 @@ static void free_device(Factors &F) {
     F.d_scratch = nullptr; F.d_q = nullptr; F.d_ctrl = nullptr; F.d_U32 = nullptr;
     F.d_U64 = nullptr; F.d_Ubf = nullptr; F.d_lam32 = nullptr; F.d_lam64 = nullptr;
     F.d_dense_work = nullptr; F.d_Vd = nullptr; F.d_RB = nullptr; F.d_T = nullptr;
-    F.d_EB = nullptr; F.d_Vbase = nullptr; F.d_tc_err = nullptr;
+    F.d_EB = nullptr; F.d_Vbase = nullptr; F.d_tc_err = nullptr; F.d_pi_work = nullptr;
+    F.d_flow = nullptr; F.flow_in_arena = false;
 }
 
 // Build the banded GridWorld factors: the slip weights of the rank-1 terms
@@ -254,7 +258,11 @@ static cpmdp_status upload(Factors &F) {
     F.scratch_bytes = S * sizeof(double);
     const size_t o_R64 = 0, o_scratch = o_R64 + up(S * sizeof(double)), o_R32 = o_scratch + up(F.scratch_bytes);
     const size_t o_cell = o_R32 + up(S * sizeof(float)), o_ctrl = o_cell + up(S), o_code = o_ctrl + up(sizeof(Ctrl));
-    const size_t total = o_code + up(S * cb);
+    // the barrier-free solver's counters and rings, for shapes it can take
+    // (one allocation and one free per factors object instead of two)
+    const bool flow = F.kind == CPMDP_GRIDWORLD && flow_shape_ok(F);
+    const size_t o_flow = o_code + up(S * cb);
+    const size_t total = o_flow + (flow ? up(flow_bytes(F)) : 0);
     CPMDP_CUDA(cudaMalloc(&F.d_arena, total));
     char *arena = static_cast<char *>(F.d_arena);
     F.d_R64 = reinterpret_cast<double *>(arena + o_R64);
@@ -263,6 +271,13 @@ static cpmdp_status upload(Factors &F) {
     F.d_cell = reinterpret_cast<uint8_t *>(arena + o_cell);
     F.d_ctrl = reinterpret_cast<Ctrl *>(arena + o_ctrl);
     F.d_code = cb ? arena + o_code : nullptr;
+    if (flow) {
+        F.d_flow = arena + o_flow;
+        F.flow_in_arena = true;
+        F.flow_base = 0;
+        CPMDP_CUDA(cudaMemset(static_cast<char *>(F.d_flow) + flow_counter_bytes(), 0xFF,
+                              flow_bytes(F) - flow_counter_bytes()));
+    }
     CPMDP_CUDA(cudaMemcpy(F.d_R64, F.reward.data(), S * sizeof(double), cudaMemcpyHostToDevice));
     to_f32_kernel<<<blocks, 256>>>(F.d_R64, F.d_R32, F.nstates);
     CPMDP_CUDA(cudaGetLastError());
@@ -509,7 +524,7 @@ static cpmdp_status run_solver(const cpmdp_factors *h, cpmdp_precision prec, boo
     double *cert = (double *)((char *)F.d_ctrl + offsetof(Ctrl, certify_residual));
     const bool do_cert = o.certify && F.kind == CPMDP_GRIDWORLD;
     // the dense BF16X3 solver runs its own FP64 certifying sweep
-    const bool dense_cert = o.certify && F.kind == CPMDP_DENSE_CP && prec == CPMDP_BF16X3 && !pi_mode;
+    const bool dense_cert = o.certify && F.kind == CPMDP_DENSE_CP && prec == CPMDP_BF16X3;
     if (do_cert) {
         if (prec == CPMDP_F64) {
             // one FP64 backup into scratch: residual + policy of the returned V

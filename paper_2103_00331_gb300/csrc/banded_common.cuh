@@ -472,9 +472,10 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 
 // Whether a barrier counter v (arrivals in the low half, raised flags in
 // the high half, one 64-bit sum) still misses arrivals of a barrier that is
-// complete at A arrivals; valid while at most 2^31 arrivals are missing.
-__device__ __forceinline__ bool arrivals_short(unsigned long long v, unsigned long long A) {
-    return (int)((unsigned)v - (unsigned)A) < 0;
+// complete when the low half reaches a_lo (the low half of the arrival
+// count); valid while at most 2^31 arrivals are missing.
+__device__ __forceinline__ bool arrivals_short(unsigned long long v, unsigned a_lo) {
+    return (int)((unsigned)v - a_lo) < 0;
 }
 
 // Grid-wide barrier of a co-resident (cooperative) grid that also counts
@@ -512,15 +513,15 @@ __device__ __forceinline__ long long grid_sync_count(Ctrl *c, int n, unsigned nb
             // half included). While blocks still arrive, its low half lies in
             // [A - nblocks, A) modulo 2^32, so completion is tested on the
             // low halves' signed difference: no wrap, however many sweeps.
-            const unsigned long long A = (unsigned long long)(n / 2 + 1) * nblocks;
+            const unsigned a_lo = (unsigned)(n / 2 + 1) * nblocks;   // low half of A
             unsigned long long v = ld_acquire(ctr);
-            if (arrivals_short(v, A)) {
+            if (arrivals_short(v, a_lo)) {
                 const unsigned long long t0 = global_ns();
                 unsigned spins = 0;
                 do {
                     __nanosleep(32);
                     v = ld_acquire(ctr);
-                    if ((++spins & 15u) == 0 && arrivals_short(v, A)) {
+                    if ((++spins & 15u) == 0 && arrivals_short(v, a_lo)) {
                         if (*(volatile int *)&c->status != 0) { result = -1; break; }
                         if (global_ns() - t0 > timeout_ns) {
                             atomicCAS(&c->status, 0, (int)CPMDP_ETIMEOUT);
@@ -528,12 +529,13 @@ __device__ __forceinline__ long long grid_sync_count(Ctrl *c, int n, unsigned nb
                             break;
                         }
                     }
-                } while (arrivals_short(v, A));
+                } while (arrivals_short(v, a_lo));
             }
             if (result == 0) {
-                const unsigned long long F = (v - A) >> 32;   // flags raised so far on this counter
+                // the low halves of v and A agree, so (v - A) >> 32 borrows nothing
+                const unsigned long long F = (v >> 32) - (((unsigned long long)(n / 2 + 1) * nblocks) >> 32);
                 const unsigned long long prev = (n & 1) ? prev1 : prev0;
-                result = (long long)(F - prev);
+                result = (long long)((F - prev) & 0xFFFFFFFFull);   // fewer than 2^32 blocks
                 if (n & 1) prev1 = F;
                 else prev0 = F;
             }

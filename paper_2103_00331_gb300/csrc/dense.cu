@@ -361,10 +361,7 @@ cpmdp_status dense_solve(const Factors &F, cpmdp_precision prec, bool pim, void 
                          const SolveOpts &o, Ctrl *hc, cudaStream_t st) {
     if (prec == CPMDP_F64) return dense_solve_t<double>(F, pim, (double *)V, pi, o, hc, st);
     if (prec == CPMDP_F32) return dense_solve_t<float>(F, pim, (float *)V, pi, o, hc, st);
-    if (pim) {
-        set_error("BF16X3 runs value iteration only; use F32 or F64 for dense policy iteration");
-        return CPMDP_EINVAL;
-    }
+    if (pim) return dense_tc_policy_iteration(F, (float *)V, pi, o, hc, st);
     return dense_tc_solve(F, (float *)V, pi, o, hc, st);
 }
 

@@ -31,6 +31,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -271,11 +272,15 @@ constexpr int kBSmem = kBOffBar + 64 + 1024;
 constexpr int kBThreads = 256;
 constexpr int kBCols = 64 * 128 / kBThreads;
 
+// eval_pi (policy evaluation, nullable): instead of the max over actions,
+// each state keeps the expectation of its own action eval_pi[s] (staged in
+// the argmax bytes of shared memory, so no registers are added).
 __global__ void __launch_bounds__(kBThreads, 2) dense_pass_b(const uint8_t *__restrict__ T, const uint8_t *__restrict__ U,
                                                        const float *__restrict__ RB, const float *__restrict__ EB,
                                                        const float *__restrict__ Vin, float *__restrict__ Vout,
-                                                       uint8_t *__restrict__ pi, int nact, int nrank, float gamma,
-                                                       unsigned long long *res, int *err) {
+                                                       uint8_t *__restrict__ pi, const uint8_t *__restrict__ eval_pi,
+                                                       int nact, int nrank, float gamma, unsigned long long *res,
+                                                       int *err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sZ = sm + kBOffZ;
@@ -322,6 +327,15 @@ __global__ void __launch_bounds__(kBThreads, 2) dense_pass_b(const uint8_t *__re
         float best[kBCols];
 #pragma unroll
         for (int j = 0; j < kBCols; j++) best[j] = 0.f;
+        if (eval_pi) {
+            // this pair's actions, at the positions the epilogue reads
+            const int qq = q0 + (row >> 6), i2 = row & 63;
+#pragma unroll 8
+            for (int jj = 0; jj < kBCols; jj++) {
+                const int j = cbase + jj;
+                sArg[j * 128 + row] = eval_pi[(size_t)(j * 64 + i2) * kSlab + qq];
+            }
+        }
         for (int a = 0; a < nact && alive; a++) {
             for (int r = 0; r < nrank && alive; r++) {
                 const int c = a * nrank + r;
@@ -395,11 +409,17 @@ __global__ void __launch_bounds__(kBThreads, 2) dense_pass_b(const uint8_t *__re
 #pragma unroll
                 for (int jj = 0; jj < kBCols; jj++) e[jj] += eb[(cbase + jj) * 64];
             }
+            if (eval_pi) {
 #pragma unroll
-            for (int jj = 0; jj < kBCols; jj++) {
-                if (a == 0 || e[jj] > best[jj]) {
-                    best[jj] = e[jj];
-                    sArg[(cbase + jj) * 128 + row] = (uint8_t)a;
+                for (int jj = 0; jj < kBCols; jj++)
+                    if (sArg[(cbase + jj) * 128 + row] == (uint8_t)a) best[jj] = e[jj];
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < kBCols; jj++) {
+                    if (a == 0 || e[jj] > best[jj]) {
+                        best[jj] = e[jj];
+                        sArg[(cbase + jj) * 128 + row] = (uint8_t)a;
+                    }
                 }
             }
             tc::fence_before();
@@ -416,7 +436,7 @@ __global__ void __launch_bounds__(kBThreads, 2) dense_pass_b(const uint8_t *__re
             const size_t s = (size_t)(j * 64 + i2) * kSlab + q;
             const float v = rb[j * 64] + gamma * best[jj];
             if (Vout) Vout[s] = v;
-            if (pi) pi[s] = sArg[j * 128 + row];
+            if (pi && !eval_pi) pi[s] = sArg[j * 128 + row];
             if (res) local_res = fmax(local_res, fabs((double)v - (double)Vin[s]));
         }
         __syncthreads();
@@ -504,9 +524,10 @@ static cpmdp_status tc_prepare(Factors &F) {
     return CPMDP_OK;
 }
 
-// One BF16x3 backup: Vout = R + gamma max_a (EB_a + E_a(Vin - Vbase)).
+// One BF16x3 backup: Vout = R + gamma max_a (EB_a + E_a(Vin - Vbase)), or
+// with eval_pi the expectation of the action eval_pi[s] instead of the max.
 static cpmdp_status tc_sweep(const Factors &F, const float *Vin, float *Vout, uint8_t *pi, bool use_base,
-                             unsigned long long *res, cudaStream_t st) {
+                             unsigned long long *res, cudaStream_t st, const uint8_t *eval_pi = nullptr) {
     const int C = F.nactions * F.rank;
     int *err = F.d_tc_err;
     const int grid = F.num_sms > 0 ? F.num_sms : 148;
@@ -515,8 +536,8 @@ static cpmdp_status tc_sweep(const Factors &F, const float *Vin, float *Vout, ui
     CPMDP_CUDA(cudaGetLastError());
     // pass B: two CTAs per SM (about 106 KB of shared memory each)
     dense_pass_b<<<2 * grid, kBThreads, kBSmem, st>>>((const uint8_t *)F.d_T, (const uint8_t *)F.d_Ubf, F.d_RB,
-                                            use_base ? F.d_EB : nullptr, Vin, Vout, pi, F.nactions, F.rank,
-                                            (float)F.gamma, res, err);
+                                            use_base ? F.d_EB : nullptr, Vin, Vout, pi, eval_pi, F.nactions,
+                                            F.rank, (float)F.gamma, res, err);
     CPMDP_CUDA(cudaGetLastError());
     return CPMDP_OK;
 }
@@ -642,6 +663,130 @@ cpmdp_status dense_tc_solve(const Factors &F, float *V, uint8_t *pi, const Solve
     hc->converged = conv;
     hc->last_residual = res;
     hc->backups = (long long)k * kS * F.nactions;
+    return CPMDP_OK;
+}
+
+// Policy improvement from Q of the current action (Qold, an evaluation
+// sweep's output) and the best Q with its argmax (Qbest, pib, a max sweep's
+// output): switch to the argmax only when it beats the current action by
+// more than margin (1 + |Qold|); count the switches.
+__global__ void dense_improve_kernel(const float *__restrict__ Qold, const float *__restrict__ Qbest,
+                                     const uint8_t *__restrict__ pib, uint8_t *__restrict__ pi, float margin,
+                                     long long n, unsigned *changed) {
+    unsigned c = 0;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+        const float qo = Qold[s], qb = Qbest[s];
+        const uint8_t b = pib[s];
+        if (b != pi[s] && qb > qo + margin * (1.f + fabsf(qo))) {
+            pi[s] = b;
+            c++;
+        }
+    }
+    c = __reduce_add_sync(0xFFFFFFFFu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(changed, c);
+}
+
+// Policy iteration with BF16x3 sweeps and the defect correction of value
+// iteration (background section: evaluate the fixed policy, improve
+// greedily, stop when no action changes), in the modified form of the
+// GridWorld solvers: evaluations capped at partial_eval sweeps until an
+// improvement changes no action, then to eval_tol. An evaluation sweep is
+// the tensor-core backup with each state's own action; an improvement is
+// one evaluation-mode sweep (Q of the current action), one max sweep (best
+// Q and its argmax) and dense_improve_kernel (keep margin 1e-6 (1 + |Q|)).
+// The FP32 base expectation is refreshed when an evaluation's residual
+// stops falling. With certify on, one FP64 backup of the result gives the
+// certified residual max |T(V) - V| (the policy is left as PI found it).
+cpmdp_status dense_tc_policy_iteration(const Factors &F, float *V, uint8_t *pi, const SolveOpts &o, Ctrl *hc,
+                                       cudaStream_t st) {
+    if (!dense_tc_supported(F)) {
+        set_error("BF16X3 needs a dense model with 4 dimensions of size 64 and at most 16 actions");
+        return CPMDP_EINVAL;
+    }
+    cpmdp_status s = tc_prepare(const_cast<Factors &>(F));
+    if (s != CPMDP_OK) return s;
+    Factors &M = const_cast<Factors &>(F);
+    if (!M.d_pi_work) CPMDP_CUDA(cudaMalloc(&M.d_pi_work, (size_t)kS * (2 * sizeof(float) + 1)));
+    float *Qold = reinterpret_cast<float *>(M.d_pi_work), *Qbest = Qold + kS;
+    uint8_t *pib = reinterpret_cast<uint8_t *>(Qbest + kS);
+    CPMDP_CUDA(cudaMemsetAsync(F.d_tc_err, 0, sizeof(int), st));
+    float *W = (float *)F.d_scratch;
+    unsigned long long *rb = &F.d_ctrl->res_slot[0];
+    unsigned *cb = &F.d_ctrl->changed_slot[0];
+    float *cur = V, *nxt = W;
+    std::vector<double> hist;
+    int total = 0, rounds = 0, evals = 0, conv = 0, last_rebase = 0, rebases = 0;
+    bool base = false, full = o.partial_eval <= 0;
+    double res = INFINITY;
+    const int grid = F.num_sms > 0 ? F.num_sms * 8 : 1216;
+    // greedy start: the max sweep's argmax of the input V
+    s = tc_sweep(F, cur, nxt, pi, false, nullptr, st);
+    if (s != CPMDP_OK) return s;
+    total++;
+    while (rounds < o.max_rounds) {
+        const int cap = full ? o.max_eval_iter : std::min(o.partial_eval, o.max_eval_iter);
+        int e = 0, ok = 0;
+        hist.clear();
+        last_rebase = 0;
+        while (e < cap) {
+            CPMDP_CUDA(cudaMemsetAsync(rb, 0, sizeof(*rb), st));
+            s = tc_sweep(F, cur, nxt, nullptr, base, rb, st, pi);
+            if (s != CPMDP_OK) return s;
+            unsigned long long bits = 0;
+            CPMDP_CUDA(cudaMemcpyAsync(&bits, rb, sizeof(bits), cudaMemcpyDeviceToHost, st));
+            s = tc_check_err(F, st);
+            if (s != CPMDP_OK) return s;
+            memcpy(&res, &bits, sizeof(res));
+            float *t = cur; cur = nxt; nxt = t;
+            e++;
+            total++;
+            hist.push_back(res);
+            if (res < o.eval_tol) { ok = 1; break; }
+            const int k = (int)hist.size();
+            if (k - last_rebase >= 6 && res > 0.9 * hist[k - 6] && rebases < 256) {
+                CPMDP_CUDA(cudaMemcpyAsync(F.d_Vbase, cur, (size_t)kS * sizeof(float), cudaMemcpyDeviceToDevice, st));
+                s = dense_store_expectation(F, cur, F.d_EB, st);
+                if (s != CPMDP_OK) return s;
+                base = true;
+                last_rebase = k;
+                rebases++;
+            }
+        }
+        evals += e;
+        // improvement at the evaluated values
+        s = tc_sweep(F, cur, Qold, nullptr, base, nullptr, st, pi);
+        if (s != CPMDP_OK) return s;
+        s = tc_sweep(F, cur, Qbest, pib, base, nullptr, st);
+        if (s != CPMDP_OK) return s;
+        CPMDP_CUDA(cudaMemsetAsync(cb, 0, sizeof(*cb), st));
+        dense_improve_kernel<<<grid, 256, 0, st>>>(Qold, Qbest, pib, pi, 1e-6f, kS, cb);
+        CPMDP_CUDA(cudaGetLastError());
+        unsigned nchg = 0;
+        CPMDP_CUDA(cudaMemcpyAsync(&nchg, cb, sizeof(nchg), cudaMemcpyDeviceToHost, st));
+        s = tc_check_err(F, st);
+        if (s != CPMDP_OK) return s;
+        total++;
+        rounds++;
+        if (nchg == 0) {
+            if (ok) { conv = 1; break; }
+            if (full) break;
+            full = true;
+            continue;
+        }
+        if (!ok && full) break;
+    }
+    if (cur != V) CPMDP_CUDA(cudaMemcpyAsync(V, cur, (size_t)kS * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (o.certify) {
+        double *cert = (double *)((char *)F.d_ctrl + offsetof(Ctrl, certify_residual));
+        s = dense_certify(F, V, nullptr, cert, st);
+        if (s != CPMDP_OK) return s;
+    }
+    hc->iterations = total;
+    hc->rounds = rounds;
+    hc->eval_sweeps = evals;
+    hc->converged = conv;
+    hc->last_residual = res;
+    hc->backups = (long long)(1 + rounds) * kS * F.nactions + (long long)evals * kS;
     return CPMDP_OK;
 }
 

@@ -14,6 +14,9 @@ bool flow_eligible(const Factors &F, bool policy_iteration, const void *V, const
 // Device bytes the solver needs beside the factors' own buffers: arrival
 // counters and four rings of |S| tagged 64-bit words.
 size_t flow_bytes(const Factors &F);
+// True when the shape alone lets the barrier-free solver run value or
+// policy iteration (the build then reserves its buffers with the factors).
+bool flow_shape_ok(const Factors &F);
 size_t flow_counter_bytes();
 // One cooperative launch on `st` (F.d_flow allocated, tags above F.flow_base
 // never written before). Fills the control block like banded_solve.

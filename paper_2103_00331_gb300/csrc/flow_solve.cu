@@ -864,6 +864,13 @@ bool flow_eligible(const Factors &F, bool policy_iteration, const void *V, const
     return sweeps < (1ll << 31);
 }
 
+bool flow_shape_ok(const Factors &F) {
+    if (F.ndim < 1 || F.ndim > 3 || F.num_sms <= 0) return false;
+    if (F.shape[F.ndim - 1] % 4 != 0 || F.nstates % 4 != 0 || F.nstates >= (1ll << 30)) return false;
+    FlowShape s;
+    return flow_pick_any(F, s, false) || flow_pick_any(F, s, true);
+}
+
 size_t flow_bytes(const Factors &F) {
     return (size_t)kSlots * kNC * kLineWords * sizeof(u64) + (size_t)kRing * F.nstates * sizeof(u64);
 }

@@ -103,9 +103,11 @@ struct Factors {
     void *d_T = nullptr;               // per-chain intermediates (bf16 hi/lo pairs)
     float *d_EB = nullptr;             // base expectation per action, pass-B layout
     float *d_Vbase = nullptr;          // base value tensor of the defect correction
+    void *d_pi_work = nullptr;         // BF16X3 policy iteration: Q of the current action, best Q, argmax
     int *d_tc_err = nullptr;           // error word of the tensor-core kernels
     // barrier-free FP32 solver (flow_solve.cu), allocated on first use
     void *d_flow = nullptr;            // arrival counters + four rings of |S| tagged words
+    bool flow_in_arena = false;        // d_flow is part of d_arena (set up by the build)
     unsigned flow_base = 0;            // first tag not written to the rings yet
     bool flow_pending = false;         // a launch whose tags are not accounted for yet
 };
@@ -159,6 +161,8 @@ bool dense_tc_supported(const Factors &F);
 cpmdp_status dense_tc_backup(const Factors &F, const float *Vin, float *Vout, uint8_t *pi, double *res,
                              cudaStream_t st);
 cpmdp_status dense_tc_solve(const Factors &F, float *V, uint8_t *pi, const SolveOpts &o, Ctrl *hc, cudaStream_t st);
+cpmdp_status dense_tc_policy_iteration(const Factors &F, float *V, uint8_t *pi, const SolveOpts &o, Ctrl *hc,
+                                       cudaStream_t st);
 
 }  // namespace cpmdp
 

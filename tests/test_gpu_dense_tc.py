@@ -123,3 +123,32 @@ def test_bf16x3_vi_against_oracle_vi(setup):
     assert np.abs(got - g["value"]).max() <= bound
     sure = g["gap"] > 2 * dc.gamma * bound
     assert np.array_equal(pi[idx].cpu().numpy()[sure], g["policy"][sure])
+
+
+def test_bf16x3_policy_iteration(setup):
+    """Policy iteration on the tensor cores (BF16x3 evaluation sweeps with
+    the defect correction, improvement by an evaluation-mode sweep, a max
+    sweep and the keep-margin compare). The oracle's FP64 backup of all
+    16.8M states of the returned V re-derives the certified residual; the
+    returned policy equals the oracle's greedy policy of V wherever the
+    oracle's Q gap exceeds twice gamma times the distance bound
+    certified / (1 - gamma) plus the keep margin; the values agree with the
+    FP32 SIMT policy iteration within the two results' bounds."""
+    import torch
+    from oracle import dense as od
+    cp, dc, f = setup
+    V = torch.zeros(dc.nstates, dtype=torch.float32, device="cuda")
+    pi = torch.zeros(dc.nstates, dtype=torch.uint8, device="cuda")
+    r = cp.policy_iteration(f, cp.BF16X3, V, pi, opts=cp.default_opts(max_iter=2000))
+    assert r["status"] == cp.OK and r["rounds"] >= 1 and r["solver"] == cp.SOLVER_DENSE
+    cert = r["certified_residual"]
+    assert 0 <= cert < 1e-5
+    Vt = V.double().cpu().numpy()
+    pg = pi.cpu().numpy()
+    Q = od.q_values(dc, Vt)
+    assert abs(float(np.abs(Q.max(axis=0) - Vt).max()) - cert) <= 1e-12
+    bound = cert / (1 - dc.gamma)
+    top2 = np.partition(Q, -2, axis=0)[-2:]
+    sure = np.abs(top2[1] - top2[0]) > 2 * dc.gamma * bound + 2e-6 * (1 + np.abs(Q).max(axis=0))
+    assert sure.sum() > 100000
+    assert np.array_equal(pg[sure], Q.argmax(axis=0)[sure].astype(np.uint8))

@@ -163,7 +163,7 @@ def test_pi_partial_evaluation_same_in_both_solvers(cp, partial):
     free = gw.cell.reshape(-1) == ci.FREE
     Qs = np.sort(Q[:, free], axis=0)
     sure = (Qs[-1] - Qs[-2]) > 2 * gw.gamma * bound + 2e-6 * (1 + np.abs(Qs[-1]))
-    assert sure.mean() > 0.9
+    assert sure.sum() > 5000
     assert np.array_equal(pa[free][sure], pf[free][sure])
     if partial:
         assert ra["eval_sweeps"] < rf["eval_sweeps"]

@@ -227,3 +227,27 @@ def test_trained_network_saves_sweeps(env):
     g = max(x.gamma for x in test_inst)
     assert (V - Vz).abs().max().item() <= (2 * g * 1e-6 + 4e-6) / (1 - g)
     B.close()
+
+
+@pytest.mark.xfail(reason="at 64^3 the committed network's per-cell estimate starts value iteration "
+                          "farther from V* than zero does in sweeps (a per-cell estimate, even the exact "
+                          "cell means of V*, saves at most about 5 % of the sweeps there)", strict=False)
+def test_committed_network_saves_sweeps_at_64(env):
+    """The committed weights (trained on 32^3 instances) on 8 held-out 64^3
+    instances of the config-5 recipe: the warm start should need fewer
+    sweeps in total than zero initialisation (both converge)."""
+    import os
+    cp, ws, torch = env
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2103_00331_gb300",
+                        "data", "warmstart_weights.npz")
+    net = ws.WarmStartNet.load(path, device=0)
+    test_inst = ws.training_instances(8, 64, seed=424243)
+    B = cp.batch_build(test_inst, device=0)
+    V = torch.zeros(int(B.total_states), dtype=torch.float32, device=net.dev)
+    _, it_zero, res0 = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=5000))
+    V.zero_()
+    ws.warm_start_values(net, B, 8, (64, 64, 64), V)
+    _, it_warm, res1 = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=5000))
+    B.close()
+    assert np.all(res0 < 1e-6) and np.all(res1 < 1e-6)
+    assert it_warm.sum() < it_zero.sum(), (it_warm.sum(), it_zero.sum())
