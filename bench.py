@@ -625,6 +625,16 @@ def dense_measure(cp, dev, stream, reps=2):
             "flops_per_sweep": flops, "issued_bf16_tflops": 3 * ach, "issued_frac": 3 * ach / peak,
             "note": "achieved counts the method's FP32-equivalent flops (2 R D N per state-action); "
                     "BF16x3 issues three bf16 products for each"}
+    # policy iteration on the tensor cores (BF16x3 evaluation sweeps, modified
+    # policy iteration, FP64 certificate of the result)
+    Vq = torch.zeros_like(V)
+    piq = torch.zeros_like(pi)
+    torch.cuda.synchronize()
+    rq = cp.policy_iteration(f, cp.BF16X3, Vq, piq, opts=opts, stream=stream)
+    pi_line = {"time_ms": rq["elapsed_ms"], "rounds": rq["rounds"], "eval_sweeps": rq["eval_sweeps"],
+               "sweeps": rq["iterations"], "certified_residual": rq["certified_residual"],
+               "error_bound": rq["error_bound"], "backups_per_s": rq["backups"] / (rq["elapsed_ms"] / 1e3)}
+    del Vq, piq
     # plain comparator: FP32 SIMT mode products, residual read back each sweep
     Vp = torch.zeros_like(V)
     torch.cuda.synchronize()
@@ -637,6 +647,7 @@ def dense_measure(cp, dev, stream, reps=2):
            "backups_per_s": r["backups"] / (solve_ms / 1e3), "bf16x3_sweep_ms": sweep_ms,
            "fp64_sweep_ms": fp64_ms, "fp64_tflops": flops / (fp64_ms * 1e9),
            "fp64_frac_of_nominal_1.25": flops / (fp64_ms * 1e9) / 1.25, "roofline": roof,
+           "policy_iteration_bf16x3": pi_line,
            "plain_fp32_simt_vi_ms": rp["elapsed_ms"], "plain_fp32_simt_vi_sweeps": rp["iterations"],
            "speedup_vs_plain_fp32_vi": rp["elapsed_ms"] / solve_ms}
     del Vp
