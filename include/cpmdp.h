@@ -153,7 +153,7 @@ typedef struct {
     double *trace;           /* optional device buffer of max_iter doubles: residual of each sweep
                                 (value iteration, fused path only; the barrier-free solver zeroes it
                                 first and also fills the entries of its two dropped sweeps) */
-    int32_t partial_eval;    /* policy iteration (default 32): while the policy keeps changing, each
+    int32_t partial_eval;    /* policy iteration (default 8): while the policy keeps changing, each
                                 round's evaluation stops after at most this many sweeps (modified
                                 policy iteration); once an improvement changes no action, every
                                 later round evaluates to eval_tol, and the solve stops only when

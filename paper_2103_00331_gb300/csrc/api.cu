@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <new>
 
 #include "internal.h"
@@ -62,6 +63,35 @@ SolveOpts resolve_opts(const cpmdp_solve_opts *o, cpmdp_precision prec) {
     return r;
 }
 
+// One stream-ordered memory pool per device for the factors' allocation:
+// memory freed by one factors object is reused by the next build without a
+// cudaMalloc, and a free does not synchronise the device (the pool keeps
+// what it holds: release threshold at its maximum). Created on first use.
+static std::mutex g_pool_mutex;
+static cudaMemPool_t g_pools[64];
+
+static cudaError_t arena_pool(int device, cudaMemPool_t *out) {
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pools[device]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        unsigned long long keep = ~0ull;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) { cudaMemPoolDestroy(pool); return e; }
+        g_pools[device] = pool;
+    }
+    *out = g_pools[device];
+    return cudaSuccess;
+}
+
 static void free_device(Factors &F) {
     // the arena holds d_code, d_R32, d_R64, d_cell, d_scratch, d_ctrl and,
     // for shapes the barrier-free solver takes, d_flow
@@ -69,7 +99,10 @@ static void free_device(Factors &F) {
                     F.d_Vd, F.d_RB, F.d_T, F.d_EB, F.d_Vbase, F.d_tc_err, F.flow_in_arena ? nullptr : F.d_flow,
                     F.d_pi_work};
     for (void *p : ptrs)
-        if (p) cudaFree(p);
+        if (p && p != F.d_arena) cudaFree(p);
+    // the arena came from the pool: returned in stream order (every call on
+    // this object has synchronised with its stream before returning)
+    if (F.d_arena) cudaFreeAsync(F.d_arena, 0);
     if (F.plain_graph) cudaGraphExecDestroy(F.plain_graph);
     F.plain_graph = nullptr;
     if (F.march_graph) cudaGraphExecDestroy(F.march_graph);
@@ -245,7 +278,9 @@ __global__ void to_f32_kernel(const double *__restrict__ a, float *__restrict__ 
         b[i] = (float)a[i];
 }
 
-static cpmdp_status upload(Factors &F) {
+// reward: the caller's rewards (device GridWorld builds keep no host copy),
+// or F.reward.
+static cpmdp_status upload(Factors &F, const double *reward) {
     DeviceGuard g(F.device);
     if (!g.ok) { set_error("cannot select CUDA device %d", F.device); return CPMDP_ECUDA; }
     CPMDP_CUDA(cudaDeviceGetAttribute(&F.num_sms, cudaDevAttrMultiProcessorCount, F.device));
@@ -263,7 +298,9 @@ static cpmdp_status upload(Factors &F) {
     const bool flow = F.kind == CPMDP_GRIDWORLD && flow_shape_ok(F);
     const size_t o_flow = o_code + up(S * cb);
     const size_t total = o_flow + (flow ? up(flow_bytes(F)) : 0);
-    CPMDP_CUDA(cudaMalloc(&F.d_arena, total));
+    cudaMemPool_t pool;
+    CPMDP_CUDA(arena_pool(F.device, &pool));
+    CPMDP_CUDA(cudaMallocFromPoolAsync(&F.d_arena, total, pool, 0));
     char *arena = static_cast<char *>(F.d_arena);
     F.d_R64 = reinterpret_cast<double *>(arena + o_R64);
     F.d_scratch = arena + o_scratch;
@@ -278,7 +315,7 @@ static cpmdp_status upload(Factors &F) {
         CPMDP_CUDA(cudaMemset(static_cast<char *>(F.d_flow) + flow_counter_bytes(), 0xFF,
                               flow_bytes(F) - flow_counter_bytes()));
     }
-    CPMDP_CUDA(cudaMemcpy(F.d_R64, F.reward.data(), S * sizeof(double), cudaMemcpyHostToDevice));
+    CPMDP_CUDA(cudaMemcpy(F.d_R64, reward, S * sizeof(double), cudaMemcpyHostToDevice));
     to_f32_kernel<<<blocks, 256>>>(F.d_R64, F.d_R32, F.nstates);
     CPMDP_CUDA(cudaGetLastError());
     CPMDP_CUDA(cudaMemcpy(F.d_cell, F.cell.data(), S, cudaMemcpyHostToDevice));
@@ -316,7 +353,7 @@ void cpmdp_default_opts(cpmdp_solve_opts *o) {
     o->max_rounds = 1000;
     o->timeout_s = 2.0;
     o->trace = nullptr;
-    o->partial_eval = 32;
+    o->partial_eval = 8;
 }
 
 const char *cpmdp_last_error(void) { return g_err; }
@@ -343,7 +380,9 @@ cpmdp_status cpmdp_build_factors(const cpmdp_problem *p, int device, cpmdp_facto
         F.nactions = p->nactions;
         F.p = p->p_success;
         F.gamma = p->gamma;
-        F.reward.assign(p->reward, p->reward + S);
+        // device GridWorld builds upload the caller's rewards directly; host-only
+        // factors (batches) and dense models keep a host copy
+        if (device < 0 || p->kind != CPMDP_GRIDWORLD) F.reward.assign(p->reward, p->reward + S);
         if (p->cell) F.cell.assign(p->cell, p->cell + S);
         else F.cell.assign((size_t)S, (uint8_t)CPMDP_CELL_FREE);
         if (F.kind == CPMDP_GRIDWORLD) {
@@ -391,8 +430,9 @@ cpmdp_status cpmdp_build_factors(const cpmdp_problem *p, int device, cpmdp_facto
         return CPMDP_ENOMEM;
     }
     if (device >= 0) {
-        st = upload(F);
+        st = upload(F, F.reward.empty() ? p->reward : F.reward.data());
         if (st != CPMDP_OK) {
+            DeviceGuard g(device);
             free_device(F);
             delete h;
             return st;
