@@ -97,7 +97,7 @@ static void free_device(Factors &F) {
     // for shapes the barrier-free solver takes, d_flow
     void *ptrs[] = {F.d_arena, F.d_q, F.d_U32, F.d_U64, F.d_Ubf, F.d_lam32, F.d_lam64, F.d_dense_work,
                     F.d_Vd, F.d_RB, F.d_T, F.d_EB, F.d_Vbase, F.d_tc_err, F.flow_in_arena ? nullptr : F.d_flow,
-                    F.d_pi_work};
+                    F.d_pi_work, F.d_dense_loop};
     for (void *p : ptrs)
         if (p && p != F.d_arena) cudaFree(p);
     // the arena came from the pool: returned in stream order (every call on
@@ -107,6 +107,9 @@ static void free_device(Factors &F) {
     F.plain_graph = nullptr;
     if (F.march_graph) cudaGraphExecDestroy(F.march_graph);
     F.march_graph = nullptr;
+    if (F.dense_graph) cudaGraphExecDestroy(F.dense_graph);
+    F.dense_graph = nullptr;
+    F.d_dense_loop = nullptr;
     F.d_arena = nullptr;
     F.d_code = nullptr; F.d_R32 = nullptr; F.d_R64 = nullptr; F.d_cell = nullptr;
     F.d_scratch = nullptr; F.d_q = nullptr; F.d_ctrl = nullptr; F.d_U32 = nullptr;

@@ -575,7 +575,7 @@ cpmdp_status dense_store_expectation(const Factors &F, const float *V, float *EB
 cpmdp_status dense_certify(const Factors &F, const float *V, uint8_t *pi, double *res, cudaStream_t st);
 
 // Value iteration with BF16x3 sweeps and defect correction against an FP32
-// base expectation, stopped by an FP64 residual.
+// base expectation, stopped by an FP64 residual, as one CUDA graph launch.
 //
 // The working residual max |V' - V| of float iterates bottoms out at one to
 // three units in the last place of the largest |V| (rounding of V' flips
@@ -588,6 +588,219 @@ cpmdp_status dense_certify(const Factors &F, const float *V, uint8_t *pi, double
 // certifies again (within max_iter). The returned V then meets the value
 // iteration stopping rule evaluated in FP64. eval_sweeps in the result
 // counts the FP64 certifying sweeps.
+//
+// The whole loop stays on the device: a conditional WHILE node repeats a
+// body of two sweeps (V -> scratch, scratch -> V); after each sweep a
+// one-thread control kernel reads the residual, keeps the last eight, and
+// sets the conditions of the nodes that follow it: refresh the FP32 base
+// (the residual stopped falling: no lower than 0.9 of its value five sweeps
+// earlier, six sweeps or more after the last refresh), take the FP64 check,
+// run the second sweep, repeat. Every sweep uses the base (zero until the
+// first refresh, which subtracts and adds exact zeros). The host reads the
+// control block once, after the graph. The graph is recorded once per
+// (V, policy, tol, max_iter, certify, trace) and replayed.
+struct DenseLoopCtl {
+    int k;              // sweeps done
+    int last_rebase;    // sweep of the last base refresh
+    int rebases;
+    int extra;          // -1: working residual not below tol yet; else sweeps left before the FP64 check
+    int certs;          // FP64 checks taken
+    int conv;           // FP64 residual below tol
+    int stop;
+    int which;          // buffer of the current iterate: 0 = V, 1 = scratch
+    double res;         // last working residual
+    double hist[8];     // last eight working residuals (sweep k - 1 at k - 1 mod 8)
+};
+
+__global__ void dense_loop_ctl_kernel(DenseLoopCtl *c, unsigned long long *res_slot, const int *err, double tol,
+                                      int max_iter, int certify, int halve, double *trace, int step,
+                                      cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_rebase,
+                                      cudaGraphConditionalHandle h_cert, cudaGraphConditionalHandle h_second) {
+    if (c->stop || *(volatile const int *)err) {
+        c->stop = 1;
+        cudaGraphSetConditional(h_rebase, 0u);
+        cudaGraphSetConditional(h_cert, 0u);
+        if (step == 0) cudaGraphSetConditional(h_second, 0u);
+        cudaGraphSetConditional(h_loop, 0u);
+        return;
+    }
+    double r;
+    memcpy(&r, res_slot, sizeof(r));
+    *res_slot = 0ull;
+    if (trace) trace[c->k] = r;
+    c->hist[c->k & 7] = r;
+    c->k++;
+    c->res = r;
+    c->which = step == 0 ? 1 : 0;
+    unsigned rebase = 0, cert = 0;
+    if (c->extra < 0 && r < tol) {
+        if (!certify) { c->conv = 1; c->stop = 1; }
+        else c->extra = halve;
+    }
+    if (!c->stop) {
+        if (c->extra > 0) {
+            if (--c->extra == 0) cert = 1;
+        } else if (c->k - c->last_rebase >= 6 && r > 0.9 * c->hist[(c->k - 6) & 7] && c->rebases < 64) {
+            rebase = 1;
+            c->last_rebase = c->k;
+            c->rebases++;
+        }
+        if (!cert && c->k >= max_iter) c->stop = 1;
+    }
+    cudaGraphSetConditional(h_rebase, rebase);
+    cudaGraphSetConditional(h_cert, cert);
+    if (step == 0) cudaGraphSetConditional(h_second, (!c->stop && !cert) ? 1u : 0u);
+    cudaGraphSetConditional(h_loop, c->stop ? 0u : 1u);
+}
+
+// After an FP64 check: stop below tol, else go on for `halve` more sweeps.
+__global__ void dense_cert_check_kernel(DenseLoopCtl *c, const double *cert, double tol, int max_iter, int halve,
+                                        int step, cudaGraphConditionalHandle h_loop,
+                                        cudaGraphConditionalHandle h_second) {
+    double v;
+    memcpy(&v, cert, sizeof(v));
+    c->certs++;
+    if (v < tol) {
+        c->conv = 1;
+        c->stop = 1;
+    } else {
+        c->extra = halve;
+        if (c->k >= max_iter) c->stop = 1;
+    }
+    if (step == 0) cudaGraphSetConditional(h_second, c->stop ? 0u : 1u);
+    cudaGraphSetConditional(h_loop, c->stop ? 0u : 1u);
+}
+
+// Nodes of g that no other node depends on.
+static cudaError_t graph_leaves(cudaGraph_t g, std::vector<cudaGraphNode_t> &out) {
+    size_t n = 0;
+    cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
+    if (e != cudaSuccess) return e;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n && (e = cudaGraphGetNodes(g, nodes.data(), &n)) != cudaSuccess) return e;
+    out.clear();
+    for (cudaGraphNode_t nd : nodes) {
+        size_t m = 0;
+        if ((e = cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &m)) != cudaSuccess) return e;
+        if (m == 0) out.push_back(nd);
+    }
+    return cudaSuccess;
+}
+
+// Add a conditional node (IF or WHILE) after `deps` in g; returns its body.
+static cudaError_t add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
+                                   cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                   cudaGraphNode_t *node, cudaGraph_t *body) {
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    cudaError_t e = cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p);
+    if (e != cudaSuccess) return e;
+    *body = p.conditional.phGraph_out[0];
+    return cudaSuccess;
+}
+
+cpmdp_status dense_certify(const Factors &F, const float *V, uint8_t *pi, double *res, cudaStream_t st);
+cpmdp_status dense_store_expectation(const Factors &F, const float *V, float *EB, cudaStream_t st);
+
+// Record the loop into a new graph (see above).
+static cpmdp_status record_dense_vi(Factors &F, float *V, uint8_t *pi, const SolveOpts &o, int halve,
+                                    cudaGraph_t *out) {
+    float *W = (float *)F.d_scratch;
+    unsigned long long *rb = &F.d_ctrl->res_slot[0];
+    double *cert = (double *)((char *)F.d_ctrl + offsetof(Ctrl, certify_residual));
+    DenseLoopCtl *c = reinterpret_cast<DenseLoopCtl *>(F.d_dense_loop);
+    cudaGraph_t G = nullptr;
+    cudaStream_t cap = nullptr;
+    cpmdp_status s = CPMDP_OK;
+    cudaError_t e = cudaGraphCreate(&G, 0);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    cudaGraphConditionalHandle h_loop = 0, h_reb0 = 0, h_cert0 = 0, h_second = 0, h_reb1 = 0, h_cert1 = 0;
+    cudaGraph_t body = nullptr, sbody = nullptr;
+    cudaGraphNode_t node;
+    std::vector<cudaGraphNode_t> leaves;
+    auto capture = [&](cudaGraph_t g, auto &&fn) -> cpmdp_status {
+        cudaError_t ce = cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) return cuda_fail(ce, "begin capture");
+        cpmdp_status cs = fn();
+        cudaGraph_t gg = g;
+        ce = cudaStreamEndCapture(cap, &gg);
+        if (cs != CPMDP_OK) return cs;
+        if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
+        return CPMDP_OK;
+    };
+    // one sweep from `in` to `out`, then the control kernel of that step
+    auto sweep_ctl = [&](const float *in, float *out, int step, cudaGraphConditionalHandle hr,
+                         cudaGraphConditionalHandle hc) -> cpmdp_status {
+        cudaError_t ce = cudaMemsetAsync(rb, 0, sizeof(*rb), cap);
+        if (ce != cudaSuccess) return cuda_fail(ce, "memset");
+        cpmdp_status cs = tc_sweep(F, in, out, nullptr, true, rb, cap);
+        if (cs != CPMDP_OK) return cs;
+        dense_loop_ctl_kernel<<<1, 1, 0, cap>>>(c, rb, F.d_tc_err, o.tol, o.max_iter, o.certify, halve, o.trace, step,
+                                                h_loop, hr, hc, h_second);
+        ce = cudaGetLastError();
+        return ce == cudaSuccess ? CPMDP_OK : cuda_fail(ce, "control kernel");
+    };
+    auto rebase_body = [&](const float *cur) -> cpmdp_status {
+        cudaError_t ce = cudaMemcpyAsync(F.d_Vbase, cur, (size_t)kS * sizeof(float), cudaMemcpyDeviceToDevice, cap);
+        if (ce != cudaSuccess) return cuda_fail(ce, "base copy");
+        return dense_store_expectation(F, cur, F.d_EB, cap);
+    };
+    auto cert_body = [&](const float *cur, int step) -> cpmdp_status {
+        cpmdp_status cs = dense_certify(F, cur, pi, cert, cap);
+        if (cs != CPMDP_OK) return cs;
+        dense_cert_check_kernel<<<1, 1, 0, cap>>>(c, cert, o.tol, o.max_iter, halve, step, h_loop, h_second);
+        cudaError_t ce = cudaGetLastError();
+        return ce == cudaSuccess ? CPMDP_OK : cuda_fail(ce, "check kernel");
+    };
+    if (e != cudaSuccess) { s = cuda_fail(e, "graph setup"); goto done; }
+    // root: WHILE(loop)
+    if ((e = cudaGraphConditionalHandleCreate(&h_loop, G, 1u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    if ((e = add_conditional(G, {}, h_loop, cudaGraphCondTypeWhile, &node, &body)) != cudaSuccess) goto fail;
+    // body: sweep V -> W, control, IF(refresh), IF(check), IF(second sweep)
+    if ((e = cudaGraphConditionalHandleCreate(&h_reb0, body, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    if ((e = cudaGraphConditionalHandleCreate(&h_cert0, body, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    if ((e = cudaGraphConditionalHandleCreate(&h_second, body, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    if ((s = capture(body, [&] { return sweep_ctl(V, W, 0, h_reb0, h_cert0); })) != CPMDP_OK) goto done;
+    {
+        cudaGraph_t b1, b2, b3;
+        cudaGraphNode_t n1, n2, n3;
+        if ((e = graph_leaves(body, leaves)) != cudaSuccess) goto fail;
+        if ((e = add_conditional(body, leaves, h_reb0, cudaGraphCondTypeIf, &n1, &b1)) != cudaSuccess) goto fail;
+        if ((e = add_conditional(body, {n1}, h_cert0, cudaGraphCondTypeIf, &n2, &b2)) != cudaSuccess) goto fail;
+        if ((e = add_conditional(body, {n2}, h_second, cudaGraphCondTypeIf, &n3, &b3)) != cudaSuccess) goto fail;
+        if ((s = capture(b1, [&] { return rebase_body(W); })) != CPMDP_OK) goto done;
+        if ((s = capture(b2, [&] { return cert_body(W, 0); })) != CPMDP_OK) goto done;
+        sbody = b3;
+    }
+    // second sweep W -> V, control, IF(refresh), IF(check)
+    if ((e = cudaGraphConditionalHandleCreate(&h_reb1, sbody, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    if ((e = cudaGraphConditionalHandleCreate(&h_cert1, sbody, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    if ((s = capture(sbody, [&] { return sweep_ctl(W, V, 1, h_reb1, h_cert1); })) != CPMDP_OK) goto done;
+    {
+        cudaGraph_t b1, b2;
+        cudaGraphNode_t n1, n2;
+        if ((e = graph_leaves(sbody, leaves)) != cudaSuccess) goto fail;
+        if ((e = add_conditional(sbody, leaves, h_reb1, cudaGraphCondTypeIf, &n1, &b1)) != cudaSuccess) goto fail;
+        if ((e = add_conditional(sbody, {n1}, h_cert1, cudaGraphCondTypeIf, &n2, &b2)) != cudaSuccess) goto fail;
+        if ((s = capture(b1, [&] { return rebase_body(V); })) != CPMDP_OK) goto done;
+        if ((s = capture(b2, [&] { return cert_body(V, 1); })) != CPMDP_OK) goto done;
+    }
+    goto done;
+fail:
+    s = cuda_fail(e, "recording the dense value iteration graph");
+done:
+    if (cap) cudaStreamDestroy(cap);
+    if (s != CPMDP_OK) {
+        if (G) cudaGraphDestroy(G);
+        return s;
+    }
+    *out = G;
+    return CPMDP_OK;
+}
+
 cpmdp_status dense_tc_solve(const Factors &F, float *V, uint8_t *pi, const SolveOpts &o, Ctrl *hc, cudaStream_t st) {
     if (!dense_tc_supported(F)) {
         set_error("BF16X3 needs a dense model with 4 dimensions of size 64 and at most 16 actions");
@@ -595,74 +808,63 @@ cpmdp_status dense_tc_solve(const Factors &F, float *V, uint8_t *pi, const Solve
     }
     cpmdp_status s = tc_prepare(const_cast<Factors &>(F));
     if (s != CPMDP_OK) return s;
-    CPMDP_CUDA(cudaMemsetAsync(F.d_tc_err, 0, sizeof(int), st));
-    float *W = (float *)F.d_scratch;
-    unsigned long long *rb = &F.d_ctrl->res_slot[0];
-    double *cert = (double *)((char *)F.d_ctrl + offsetof(Ctrl, certify_residual));
-    float *cur = V, *nxt = W;
-    std::vector<double> hist;
-    int k = 0, conv = 0, last_rebase = 0, rebases = 0, certs = 0;
-    int extra = -1;   // sweeps left before the next FP64 check (-1: working residual not below tol yet)
+    Factors &M = const_cast<Factors &>(F);
+    // buffers the recorded graph uses must exist before the recording
+    if (!M.d_dense_loop) CPMDP_CUDA(cudaMalloc(&M.d_dense_loop, sizeof(DenseLoopCtl)));
+    if (!M.d_Vd) CPMDP_CUDA(cudaMalloc(&M.d_Vd, (size_t)F.nstates * sizeof(double)));
     const int halve = F.gamma > 0.0 && F.gamma < 1.0 ? (int)ceil(log(2.0) / log(1.0 / F.gamma)) : 1;
-    bool base = false;
-    double res = INFINITY;
-    while (k < o.max_iter) {
-        CPMDP_CUDA(cudaMemsetAsync(rb, 0, sizeof(*rb), st));
-        s = tc_sweep(F, cur, nxt, nullptr, base, rb, st);
+    const bool same = M.dense_graph && M.dense_graph_V == (void *)V && M.dense_graph_pi == (void *)pi &&
+                      M.dense_graph_tol == o.tol && M.dense_graph_max_iter == o.max_iter &&
+                      M.dense_graph_certify == o.certify && M.dense_graph_trace == (void *)o.trace;
+    if (!same) {
+        if (M.dense_graph) { cudaGraphExecDestroy(M.dense_graph); M.dense_graph = nullptr; }
+        cudaGraph_t g = nullptr;
+        s = record_dense_vi(M, V, pi, o, halve, &g);
         if (s != CPMDP_OK) return s;
-        unsigned long long bits = 0;
-        CPMDP_CUDA(cudaMemcpyAsync(&bits, rb, sizeof(bits), cudaMemcpyDeviceToHost, st));
-        s = tc_check_err(F, st);
-        if (s != CPMDP_OK) return s;
-        memcpy(&res, &bits, sizeof(res));
-        if (o.trace) CPMDP_CUDA(cudaMemcpyAsync(o.trace + k, &res, sizeof(double), cudaMemcpyHostToDevice, st));
-        hist.push_back(res);
-        float *t = cur; cur = nxt; nxt = t;
-        k++;
-        if (extra < 0 && res < o.tol) {
-            if (!o.certify) { conv = 1; break; }
-            extra = halve;
-        }
-        if (extra > 0) {
-            if (--extra > 0) continue;
-            // FP64 backup of the current iterate: certified residual and policy
-            s = dense_certify(F, cur, pi, cert, st);
-            if (s != CPMDP_OK) return s;
-            certs++;
-            double c = INFINITY;
-            CPMDP_CUDA(cudaMemcpyAsync(&c, cert, sizeof(c), cudaMemcpyDeviceToHost, st));
-            CPMDP_CUDA(cudaStreamSynchronize(st));
-            if (c < o.tol) { conv = 1; break; }
-            extra = halve;
-            continue;
-        }
-        // the residual stopped falling: the BF16x3 error of the correction
-        // dominates; refresh the FP32 base at the current iterate
-        if (k - last_rebase >= 6 && res > 0.9 * hist[k - 6] && rebases < 64) {
-            CPMDP_CUDA(cudaMemcpyAsync(F.d_Vbase, cur, (size_t)kS * sizeof(float), cudaMemcpyDeviceToDevice, st));
-            s = dense_store_expectation(F, cur, F.d_EB, st);
-            if (s != CPMDP_OK) return s;
-            base = true;
-            last_rebase = k;
-            rebases++;
-        }
+        cudaError_t e = cudaGraphInstantiate(&M.dense_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { M.dense_graph = nullptr; CPMDP_CUDA(e); }
+        M.dense_graph_V = (void *)V;
+        M.dense_graph_pi = (void *)pi;
+        M.dense_graph_tol = o.tol;
+        M.dense_graph_max_iter = o.max_iter;
+        M.dense_graph_certify = o.certify;
+        M.dense_graph_trace = (void *)o.trace;
     }
-    if (cur != V) CPMDP_CUDA(cudaMemcpyAsync(V, cur, (size_t)kS * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    if (o.certify && !conv) {
-        // max_iter ran out: still certify what is returned
+    // start: zero base (E of a zero base is zero), control block, residual slot
+    DenseLoopCtl c0;
+    memset(&c0, 0, sizeof(c0));
+    c0.extra = -1;
+    CPMDP_CUDA(cudaMemcpyAsync(M.d_dense_loop, &c0, sizeof(c0), cudaMemcpyHostToDevice, st));
+    CPMDP_CUDA(cudaMemsetAsync(F.d_Vbase, 0, (size_t)kS * sizeof(float), st));
+    CPMDP_CUDA(cudaMemsetAsync(F.d_EB, 0, (size_t)F.nactions * kS * sizeof(float), st));
+    CPMDP_CUDA(cudaMemsetAsync(&F.d_ctrl->res_slot[0], 0, sizeof(unsigned long long), st));
+    CPMDP_CUDA(cudaMemsetAsync(F.d_tc_err, 0, sizeof(int), st));
+    if (o.trace) CPMDP_CUDA(cudaMemsetAsync(o.trace, 0, (size_t)o.max_iter * sizeof(double), st));
+    CPMDP_CUDA(cudaGraphLaunch(M.dense_graph, st));
+    DenseLoopCtl c;
+    CPMDP_CUDA(cudaMemcpyAsync(&c, M.d_dense_loop, sizeof(c), cudaMemcpyDeviceToHost, st));
+    s = tc_check_err(F, st);
+    if (s != CPMDP_OK) return s;
+    float *W = (float *)F.d_scratch;
+    if (c.which == 1) CPMDP_CUDA(cudaMemcpyAsync(V, W, (size_t)kS * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    int certs = c.certs;
+    double *cert = (double *)((char *)F.d_ctrl + offsetof(Ctrl, certify_residual));
+    if (o.certify && !c.conv) {
+        // max_iter ran out: certify what is returned
         s = dense_certify(F, V, pi, cert, st);
         if (s != CPMDP_OK) return s;
         certs++;
     } else if (!o.certify && pi) {
-        s = tc_sweep(F, V, W, pi, base, nullptr, st);
+        s = tc_sweep(F, V, W, pi, true, nullptr, st);
         if (s != CPMDP_OK) return s;
     }
-    hc->iterations = k;
-    hc->rounds = rebases;
+    hc->iterations = c.k;
+    hc->rounds = c.rebases;
     hc->eval_sweeps = certs;
-    hc->converged = conv;
-    hc->last_residual = res;
-    hc->backups = (long long)k * kS * F.nactions;
+    hc->converged = c.conv;
+    hc->last_residual = c.res;
+    hc->backups = (long long)c.k * kS * F.nactions;
     return CPMDP_OK;
 }
 

@@ -104,6 +104,14 @@ struct Factors {
     float *d_EB = nullptr;             // base expectation per action, pass-B layout
     float *d_Vbase = nullptr;          // base value tensor of the defect correction
     void *d_pi_work = nullptr;         // BF16X3 policy iteration: Q of the current action, best Q, argmax
+    void *d_dense_loop = nullptr;      // BF16X3 value iteration: the device-side loop control block
+    cudaGraphExec_t dense_graph = nullptr;   // BF16X3 value iteration, recorded once per (V, pi, options)
+    void *dense_graph_V = nullptr;
+    void *dense_graph_pi = nullptr;
+    void *dense_graph_trace = nullptr;
+    double dense_graph_tol = 0;
+    int dense_graph_max_iter = 0;
+    int dense_graph_certify = -1;
     int *d_tc_err = nullptr;           // error word of the tensor-core kernels
     // barrier-free FP32 solver (flow_solve.cu), allocated on first use
     void *d_flow = nullptr;            // arrival counters + four rings of |S| tagged words
