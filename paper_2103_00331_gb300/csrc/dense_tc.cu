@@ -102,24 +102,66 @@ __device__ __forceinline__ void write_quads(uint8_t *T, const uint32_t *stage, i
 // ---------------------------------------------------------------------------
 // pass A: slabs of V (minus V_base when given) -> T_c for every chain c
 //
-// The scattered 16-byte stores of an item's intermediates are issued during
-// the next item's first two GEMMs (half after each is started), so the
-// tensor core works while the threads store; the stage buffer is only
-// overwritten after both halves.
+// Warp-specialised: one control thread issues the GEMMs and the factor
+// copies; 16 converter warps move data between TMEM, shared memory and
+// global memory. An item is (slab group g, chain c); per item and pair p of
+// the group's two slab pairs:
+//   GEMM 1 (D1[p]) = X_p U_4^T           rows (s2, i3), cols i4'
+//   CONV: D1[p] -> A2 (bf16 hi/lo, MN-major: each thread writes its own
+//         accumulator row as 16-byte chunks, no transpose)
+//   GEMM 2 (D2[p]) = A2 U_3^T            rows (s2, i4'), cols i3'
+//   EPI: D2[p] -> stage (hi/lo words), then the item's quads -> T.
+// The accumulators are double-buffered in TMEM (D1[0..1], D2[0..1]) and the
+// factor tiles in shared memory, so the tensor core runs the GEMMs of one
+// pair or item while the converters work on another: per item the
+// converters run CONV(p0), EPI(previous item, p1) + its quads, CONV(p1),
+// EPI(p0). Every wait is bounded; a wait that runs out sets the error word
+// and every role leaves its loop (the converters decide together, so the
+// named barriers stay matched).
 
-constexpr int kAOffX = 0;                            // 2 pairs x {hi, lo} x 16 KB
-constexpr int kAOffA2 = 4 * kPairBytes;              // {hi, lo} x 16 KB
-constexpr int kAOffU = kAOffA2 + 2 * kPairBytes;     // 2 buffers x (U3 hi, lo, U4 hi, lo)
+constexpr int kAConv = 512;                          // converter threads
+constexpr int kAThreads = kAConv + 32;               // + the control warp
+constexpr int kACols = 64 * 128 / kAConv;            // accumulator columns per converter thread
+constexpr int kAOffX = 0;                            // 2 pairs x {hi, lo} x 16 KB, K-major
+constexpr int kAOffA2 = 4 * kPairBytes;              // {hi, lo} x 16 KB, MN-major
+constexpr int kAOffU = kAOffA2 + 2 * kPairBytes;     // U3 slots 0, 1 then U4 slots 0, 1 ({hi, lo} each)
 constexpr int kAOffStage = kAOffU + 2 * 4 * kTileBytes;  // 4 slabs x 4096 x 4 B
 constexpr int kAOffBar = kAOffStage + 4 * kSlab * 4;
-constexpr int kASmem = kAOffBar + 64 + 1024;
+constexpr int kASmem = kAOffBar + 160 + 1024;
+constexpr uint32_t kConvBar = 1;                     // named barrier of the converter warps
 
-// Four warpgroups: thread t reads accumulator row t % 128 (its warp's TMEM
-// lane quarter) and columns 16 (t / 128) .. +15, so every CUDA-core phase
-// between the GEMMs is split over 16 warps (4 per scheduler, to hide the
-// latencies of the conversions and stores).
-constexpr int kAThreads = 512;
-constexpr int kACols = 64 * 128 / kAThreads;   // accumulator columns per thread
+// Converter-side wait: lane 0 of every converter warp polls the mbarrier
+// (bounded); the converters then agree on the outcome (named AND barrier),
+// so they all continue or all stop.
+__device__ __forceinline__ bool conv_wait(uint64_t *mbar, uint32_t parity, int lane) {
+    bool ok = true;
+    if (lane == 0) ok = tc::mbar_wait(mbar, parity, kWaitCycles);
+    ok = __shfl_sync(0xFFFFFFFFu, ok ? 1 : 0, 0) != 0;
+    return tc::named_and(kConvBar, kAConv, ok);
+}
+
+// Stage the group's 4 slabs (b0 .. b0+3) of V (- V_base) as two K-major
+// pair tiles, bf16 hi / lo: row = (s % 2) * 64 + i3, k = i4.
+__device__ __forceinline__ void stage_x(uint8_t *sX, const float *V, const float *Vbase, int b0, int tid) {
+    for (int e4 = tid; e4 < kSlab; e4 += kAConv) {   // 4 consecutive elements per step
+        const int s = e4 >> 10, rem = (e4 & 1023) * 4;
+        const size_t gi = (size_t)(b0 + s) * kSlab + rem;
+        float4 x = *reinterpret_cast<const float4 *>(V + gi);
+        if (Vbase) {
+            const float4 y = *reinterpret_cast<const float4 *>(Vbase + gi);
+            x.x -= y.x; x.y -= y.y; x.z -= y.z; x.w -= y.w;
+        }
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn(x.x, x.y), h1 = __floats2bfloat162_rn(x.z, x.w);
+        const __nv_bfloat162 l0 = __floats2bfloat162_rn(x.x - __low2float(h0), x.y - __high2float(h0));
+        const __nv_bfloat162 l1 = __floats2bfloat162_rn(x.z - __low2float(h1), x.w - __high2float(h1));
+        uint8_t *tile = sX + (s >> 1) * 2 * kPairBytes;
+        const uint32_t off = tc::sw128_off((uint32_t)((s & 1) * 64 + (rem >> 6)), (uint32_t)(rem & 63));
+        *reinterpret_cast<uint2 *>(tile + off) =
+            make_uint2(*reinterpret_cast<const uint32_t *>(&h0), *reinterpret_cast<const uint32_t *>(&h1));
+        *reinterpret_cast<uint2 *>(tile + kPairBytes + off) =
+            make_uint2(*reinterpret_cast<const uint32_t *>(&l0), *reinterpret_cast<const uint32_t *>(&l1));
+    }
+}
 
 __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__restrict__ V, const float *__restrict__ Vbase,
                                                        const uint8_t *__restrict__ U, uint8_t *__restrict__ T,
@@ -129,125 +171,204 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
     uint8_t *sX = sm + kAOffX;
     uint8_t *sA2 = sm + kAOffA2;
     uint32_t *stage = reinterpret_cast<uint32_t *>(sm + kAOffStage);
-    uint64_t *full = reinterpret_cast<uint64_t *>(sm + kAOffBar);       // [2]
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + kAOffBar + 16);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kAOffBar + 24);
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int row = tid & 127, cbase = kACols * (tid >> 7);   // accumulator row, first column
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kAOffBar);
+    uint64_t *d1_full = bars + 0, *d1_empty = bars + 2, *d2_full = bars + 4, *a2_full = bars + 6;
+    uint64_t *u3_full = bars + 8, *u3_free = bars + 10, *u4_full = bars + 12, *u4_free = bars + 14;
+    uint64_t *x_full = bars + 16, *fin = bars + 17;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kAOffBar + 144);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        tc::mbar_init(&full[0], 1);
-        tc::mbar_init(&full[1], 1);
-        tc::mbar_init(mbar, 1);
+        for (int i = 0; i < 18; i++) tc::mbar_init(&bars[i], 1);
     }
-    if (warp == 0) tc::tmem_alloc(tslot, 128);
+    if (warp == 0) tc::tmem_alloc(tslot, 256);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    sync_for_async();
-    const uint32_t tmem = *tslot;
-    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
-    uint32_t phase = 0, fph0 = 0, fph1 = 0;
-    bool alive = true;
-    const uint32_t aX = tc::smem_u32(sX), aA2 = tc::smem_u32(sA2), aU = tc::smem_u32(sm + kAOffU);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;   // D1[p] at column 64 p, D2[p] at 128 + 64 p
     const int ngroups = kSlab / 4;
-    // items in order (group g, chain c); U tiles of item it go to buffer it % 2
-    int it = 0;
-    if (tid == 0 && blockIdx.x < ngroups) {
-        tc::mbar_expect_tx(&full[0], 4 * kTileBytes);
-        tc::bulk_g2s(aU, utile(U, 0, 2, 0), 4 * kTileBytes, &full[0]);
-    }
-    int pend_c = -1, pend_b0 = 0;   // staged item whose quads are not yet stored
-    for (int g = blockIdx.x; g < ngroups && alive; g += gridDim.x) {
-        const int b0 = 4 * g;
-        // stage the 4 slabs as 2 pair tiles: row = (s % 2) * 64 + i3, k = i4
-        for (int e = tid; e < 4 * kSlab; e += kAThreads) {
-            const int s = e >> 12, rem = e & (kSlab - 1);
-            const size_t gi = (size_t)(b0 + s) * kSlab + rem;
-            const float x = Vbase ? V[gi] - Vbase[gi] : V[gi];
-            __nv_bfloat16 h, l;
-            tc::split_bf16(x, h, l);
-            uint8_t *tile = sX + (s >> 1) * 2 * kPairBytes;
-            const uint32_t row = (uint32_t)((s & 1) * 64 + (rem >> 6)), k = (uint32_t)(rem & 63);
-            put_bf16(tile, row, k, __bfloat16_as_ushort(h));
-            put_bf16(tile + kPairBytes, row, k, __bfloat16_as_ushort(l));
+    const int my_groups = blockIdx.x < ngroups ? (ngroups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int nitems = my_groups * nchains;
+
+    if (warp == kAConv / 32) {
+        // ---------------- control thread ----------------
+        // Issue order: GEMM 1 of item 0, then per item it: GEMM 2 (it, p0),
+        // GEMM 1 (it+1, p0), GEMM 2 (it, p1), GEMM 1 (it+1, p1), so the next
+        // item's first GEMMs run while the converters work on this item.
+        // Factor rings: U4 of item j in slot j % 2 (free once GEMM 1 of item
+        // j completed), U3 of item j in slot j % 2 (free once GEMM 2 of j did).
+        if (lane == 0 && nitems > 0) {
+            const uint32_t aX = tc::smem_u32(sX), aA2 = tc::smem_u32(sA2), aU = tc::smem_u32(sm + kAOffU);
+            int issued3 = 0, landed3 = 0, issued4 = 0, landed4 = 0;   // factor copies issued / waited for
+            auto issue_u3 = [&]() {
+                const int j = issued3++, sl = j & 1;
+                tc::mbar_expect_tx(&u3_full[sl], 2 * kTileBytes);
+                tc::bulk_g2s(aU + sl * 2 * kTileBytes, utile(U, j % nchains, 2, 0), 2 * kTileBytes, &u3_full[sl]);
+            };
+            auto issue_u4 = [&]() {
+                const int j = issued4++, sl = j & 1;
+                tc::mbar_expect_tx(&u4_full[sl], 2 * kTileBytes);
+                tc::bulk_g2s(aU + (2 + sl) * 2 * kTileBytes, utile(U, j % nchains, 3, 0), 2 * kTileBytes,
+                             &u4_full[sl]);
+            };
+            // GEMM 1 (j, p) once D1[p] was read by CONV (j-1, p); for p = 0 also
+            // wait for X (first chain of a group) and for U4 of item j
+            auto gemm1 = [&](int j, int p) -> bool {
+                const int sl = j & 1;
+                if (p == 0) {
+                    if (j % nchains == 0 && !tc::mbar_wait(x_full, (uint32_t)((j / nchains) & 1), kWaitCycles))
+                        return false;
+                    if (!tc::mbar_wait(&u4_full[sl], (uint32_t)((j >> 1) & 1), kWaitCycles)) return false;
+                    landed4++;
+                }
+                if (!tc::mbar_wait(&d1_empty[p], (uint32_t)((j & 1) ^ 1), kWaitCycles)) return false;
+                tc::fence_after();
+                const uint32_t xa = aX + p * 2 * kPairBytes, u4 = aU + (2 + sl) * 2 * kTileBytes;
+                tc::mma_bf16x3(tmem + 64 * p, xa, xa + kPairBytes, u4, u4 + kTileBytes, 0);
+                tc::commit(&d1_full[p]);
+                if (p == 1) tc::commit(&u4_free[sl]);
+                return true;
+            };
+            auto gemm2 = [&](int it, int p) -> bool {
+                const int sl = it & 1;
+                if (!tc::mbar_wait(&a2_full[p], (uint32_t)(it & 1), kWaitCycles)) return false;
+                tc::fence_after();
+                const uint32_t u3 = aU + sl * 2 * kTileBytes;
+                tc::mma_bf16x3_amn(tmem + 128 + 64 * p, aA2, aA2 + kPairBytes, u3, u3 + kTileBytes, 0);
+                tc::commit(&d2_full[p]);
+                if (p == 1) tc::commit(&u3_free[sl]);
+                return true;
+            };
+            issue_u4();
+            issue_u3();
+            if (nitems > 1) {
+                issue_u4();
+                issue_u3();
+            }
+            bool ok = gemm1(0, 0) && gemm1(0, 1);
+            for (int it = 0; it < nitems && ok; it++) {
+                const int sl = it & 1;
+                // U4 of item it+2 into the slot GEMM 1 (it) has finished with
+                if (it + 2 < nitems) {
+                    ok = tc::mbar_wait(&u4_free[sl], (uint32_t)((it >> 1) & 1), kWaitCycles);
+                    if (!ok) break;
+                    issue_u4();
+                }
+                ok = tc::mbar_wait(&u3_full[sl], (uint32_t)((it >> 1) & 1), kWaitCycles);
+                if (!ok) break;
+                landed3++;
+                ok = gemm2(it, 0);
+                // U3 of item it+1 into the slot GEMM 2 (it-1) has finished with
+                if (ok && it >= 1 && it + 1 < nitems) {
+                    ok = tc::mbar_wait(&u3_free[sl ^ 1], (uint32_t)(((it - 1) >> 1) & 1), kWaitCycles);
+                    if (ok) issue_u3();
+                }
+                if (ok && it + 1 < nitems) ok = gemm1(it + 1, 0);
+                ok = ok && gemm2(it, 1);
+                if (ok && it + 1 < nitems) ok = gemm1(it + 1, 1);
+            }
+            // the last item's commit: every MMA of this CTA has completed
+            if (ok) ok = tc::mbar_wait(&u3_free[(nitems - 1) & 1], (uint32_t)(((nitems - 1) >> 1) & 1), kWaitCycles);
+            if (!ok) {
+                atomicExch(err, (int)CPMDP_ETIMEOUT);
+                // let the MMAs and copies already issued finish before the CTA leaves
+                tc::commit(fin);
+                tc::mbar_wait(fin, 0, kWaitCycles);
+                for (int j = landed3; j < issued3; j++)
+                    tc::mbar_wait(&u3_full[j & 1], (uint32_t)((j >> 1) & 1), kWaitCycles);
+                for (int j = landed4; j < issued4; j++)
+                    tc::mbar_wait(&u4_full[j & 1], (uint32_t)((j >> 1) & 1), kWaitCycles);
+            }
         }
-        for (int c = 0; c < nchains && alive; c++, it++) {
-            const int buf = it & 1;
-            // prefetch the next item's factor tiles into the other buffer (its
-            // previous reader, item it-1, has completed)
+        __syncwarp();
+    } else if (nitems > 0) {
+        // ---------------- converter warps ----------------
+        const int row = tid & 127, cbase = kACols * (tid >> 7);   // accumulator row, first column
+        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+        const int s2 = row >> 6, r63 = row & 63;
+        // MN-major A2: this thread's row (s2, i3 = r63) -> k = i3, m = s2 * 64 + i4'
+        const uint32_t a2_off = (uint32_t)s2 * 8192u + (uint32_t)(r63 >> 3) * 1024u + (uint32_t)(r63 & 7) * 128u;
+        auto conv = [&](int p) {
+            float z[kACols];
+            tc::tmem_ld16(tmem + lane_off + 64 * p + cbase, z);
+#pragma unroll
+            for (int h = 0; h < kACols / 8; h++) {
+                uint32_t hi[4], lo[4];
+                tc::split8_bf16(z + 8 * h, hi, lo);
+                const uint32_t chunk = (uint32_t)((cbase >> 3) + h);
+                const uint32_t off = a2_off + (((chunk ^ (uint32_t)(r63 & 7)) & 7u) << 4);
+                *reinterpret_cast<uint4 *>(sA2 + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                *reinterpret_cast<uint4 *>(sA2 + kPairBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            }
+            tc::fence_proxy_async();
+            tc::fence_before();
+            tc::named_sync(kConvBar, kAConv);
             if (tid == 0) {
-                int nc = c + 1, ng = g;
-                if (nc == nchains) { nc = 0; ng = g + gridDim.x; }
-                if (ng < ngroups) {
-                    tc::mbar_expect_tx(&full[buf ^ 1], 4 * kTileBytes);
-                    tc::bulk_g2s(aU + (buf ^ 1) * 4 * kTileBytes, utile(U, nc, 2, 0), 4 * kTileBytes, &full[buf ^ 1]);
-                }
+                tc::mbar_arrive(&d1_empty[p]);
+                tc::mbar_arrive(&a2_full[p]);
             }
-            uint32_t &fph = buf ? fph1 : fph0;
-            if (!wait_all(&full[buf], fph, err)) { alive = false; break; }
-            sync_for_async();
-            const uint32_t u3 = aU + buf * 4 * kTileBytes, u4 = u3 + 2 * kTileBytes;
-            for (int p = 0; p < 2 && alive; p++) {
-                const uint32_t xa = aX + p * 2 * kPairBytes;
-                if (tid == 0) {
-                    tc::mma_bf16x3(tmem, xa, xa + kPairBytes, u4, u4 + kTileBytes, 0);
-                    tc::commit(mbar);
-                }
-                if (p == 0 && pend_c >= 0) write_quads(T, stage, pend_c, pend_b0, 0, kSlab / 2, tid, kAThreads);
-                if (!wait_all(mbar, phase, err)) { alive = false; break; }
-                tc::fence_after();
-                float z[kACols];
-                tc::tmem_ld16(tmem + lane_off + cbase, z);   // row = (s2, i3), cols i4' = cbase ..
-                {
-                    const uint32_t s2 = row >> 6, i3 = row & 63;
+        };
+        auto epi = [&](int p) {   // D2[p] -> stage slabs 2p + s2 (row = (s2, i4'), cols i3')
+            float y[kACols];
+            tc::tmem_ld16(tmem + lane_off + 128 + 64 * p + cbase, y);
+            const int s = 2 * p + s2;
 #pragma unroll
-                    for (int jj = 0; jj < kACols; jj++) {
-                        const uint32_t j = cbase + jj;
-                        __nv_bfloat16 h, l;
-                        tc::split_bf16(z[jj], h, l);
-                        put_bf16(sA2, s2 * 64 + j, i3, __bfloat16_as_ushort(h));
-                        put_bf16(sA2 + kPairBytes, s2 * 64 + j, i3, __bfloat16_as_ushort(l));
-                    }
-                }
-                sync_for_async();
-                if (tid == 0) {
-                    tc::mma_bf16x3(tmem + 64, aA2, aA2 + kPairBytes, u3, u3 + kTileBytes, 0);
-                    tc::commit(mbar);
-                }
-                if (p == 0 && pend_c >= 0) {
-                    write_quads(T, stage, pend_c, pend_b0, kSlab / 2, kSlab, tid, kAThreads);
-                    pend_c = -1;
-                }
-                // (the wait's barrier also orders every thread's reads of the
-                // stage buffer before it is overwritten below)
-                if (!wait_all(mbar, phase, err)) { alive = false; break; }
-                tc::fence_after();
-                float y[kACols];
-                tc::tmem_ld16(tmem + lane_off + 64 + cbase, y);   // row = (s2, i4'), cols i3' = cbase ..
-                {
-                    const int s = 2 * p + (row >> 6), i4 = row & 63;
-#pragma unroll
-                    for (int jj = 0; jj < kACols; jj++) stage[s * kSlab + (cbase + jj) * 64 + i4] = tc::pack_hilo(y[jj]);
-                }
-                tc::fence_before();
-                __syncthreads();
-                tc::fence_after();
+            for (int jj = 0; jj < kACols; jj++) stage[s * kSlab + (cbase + jj) * 64 + r63] = tc::pack_hilo(y[jj]);
+        };
+        bool ok = true;
+        stage_x(sX, V, Vbase, 4 * blockIdx.x, tid);
+        tc::fence_proxy_async();
+        tc::named_sync(kConvBar, kAConv);
+        if (tid == 0) tc::mbar_arrive(x_full);
+        int pend_c = -1, pend_b0 = 0;   // item whose slabs 2, 3 are still in D2[1]
+        for (int it = 0; it < nitems; it++) {
+            const int c = it % nchains, gi = it / nchains;
+            const int b0 = 4 * (blockIdx.x + gi * gridDim.x);
+            const uint32_t par = (uint32_t)(it & 1);
+            // CONV(p0): D1[0] ready; GEMM 2 of the previous item's p1 done (A2 free, D2[1] ready)
+            ok = conv_wait(&d1_full[0], par, lane);
+            if (ok && it >= 1) ok = conv_wait(&d2_full[1], par ^ 1u, lane);
+            if (!ok) break;
+            tc::fence_after();
+            conv(0);
+            // EPI(previous item, p1), then its quads
+            if (pend_c >= 0) {
+                epi(1);
+                tc::named_sync(kConvBar, kAConv);
+                write_quads(T, stage, pend_c, pend_b0, 0, kSlab, tid, kAConv);
             }
-            if (!alive) break;
-            // this item's quads go out during the next item's GEMMs
+            // CONV(p1): D1[1] ready; GEMM 2 of p0 done (A2 free, D2[0] ready)
+            ok = conv_wait(&d1_full[1], par, lane);
+            if (ok) ok = conv_wait(&d2_full[0], par, lane);
+            if (!ok) break;
+            tc::fence_after();
+            conv(1);   // (its barrier also ends the quads' reads of the stage)
+            epi(0);
             pend_c = c;
             pend_b0 = b0;
+            // last chain of the group: GEMM 1 of this item is complete, restage X
+            if (c == nchains - 1 && gi + 1 < my_groups) {
+                stage_x(sX, V, Vbase, 4 * (blockIdx.x + (gi + 1) * gridDim.x), tid);
+                tc::fence_proxy_async();
+                tc::named_sync(kConvBar, kAConv);
+                if (tid == 0) tc::mbar_arrive(x_full);
+            }
         }
-    }
-    // the last staged item
-    if (alive && pend_c >= 0) write_quads(T, stage, pend_c, pend_b0, 0, kSlab, tid, kAThreads);
-    // a prefetch may still be in flight when this CTA stopped early: wait for it
-    if (!alive && tid == 0) {
-        tc::mbar_wait(&full[0], fph0, kWaitCycles);
-        tc::mbar_wait(&full[1], fph1, kWaitCycles);
+        if (ok && pend_c >= 0) {
+            ok = conv_wait(&d2_full[1], (uint32_t)((nitems - 1) & 1), lane);
+            if (ok) {
+                tc::fence_after();
+                epi(1);
+                tc::named_sync(kConvBar, kAConv);
+                write_quads(T, stage, pend_c, pend_b0, 0, kSlab, tid, kAConv);
+            }
+        }
+        if (!ok && tid == 0) atomicExch(err, (int)CPMDP_ETIMEOUT);
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
 // ---------------------------------------------------------------------------

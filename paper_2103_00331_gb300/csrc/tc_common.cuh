@@ -35,9 +35,32 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
     return d;
 }
 
+// Descriptor of an MN-major 128B-swizzled bf16 tile: a 1024-byte atom holds
+// 8 K indices (128-byte rows) x 64 MN indices (8 chunks of 16 bytes, chunk c
+// of row r at position c ^ r); atoms along MN are `mn_stride` bytes apart
+// (leading byte offset), atoms along K 1024 bytes (stride byte offset).
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t addr, uint32_t mn_stride) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((mn_stride >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((1024u >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Byte offset of element (m, k) in an MN-major 128B-swizzled bf16 tile of
+// 128 MN indices x 64 K indices (two MN atoms 8192 bytes apart).
+__host__ __device__ __forceinline__ uint32_t sw128_mn_off(uint32_t m, uint32_t k) {
+    return (m >> 6) * 8192u + (k >> 3) * 1024u + (k & 7u) * 128u + (((((m >> 3) & 7u) ^ (k & 7u)) & 7u) << 4) +
+           ((m & 7u) << 1);
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both
 // K-major, N = 64, M = 128.
 constexpr uint32_t kIdescM128N64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+// The same with A MN-major (transpose-A bit).
+constexpr uint32_t kIdescM128N64AMN = kIdescM128N64 | (1u << 15);
 
 __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
     asm volatile(
@@ -57,6 +80,19 @@ __device__ __forceinline__ void mma_bf16x3(uint32_t d_tmem, uint32_t a_hi, uint3
         mma(d_tmem, sdesc(a_hi + o), sdesc(b_hi + o), kIdescM128N64, (accumulate || ks > 0) ? 1u : 0u);
         mma(d_tmem, sdesc(a_hi + o), sdesc(b_lo + o), kIdescM128N64, 1u);
         mma(d_tmem, sdesc(a_lo + o), sdesc(b_hi + o), kIdescM128N64, 1u);
+    }
+}
+
+// The same with A an MN-major 128 x 64 tile (sw128_mn_off): a K-step of 16
+// is two 1024-byte K atoms.
+__device__ __forceinline__ void mma_bf16x3_amn(uint32_t d_tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                               uint32_t b_lo, uint32_t accumulate) {
+#pragma unroll
+    for (int ks = 0; ks < 4; ks++) {
+        const uint32_t oa = ks * 2048, ob = ks * 32;
+        mma(d_tmem, sdesc_mn(a_hi + oa, 8192), sdesc(b_hi + ob), kIdescM128N64AMN, (accumulate || ks > 0) ? 1u : 0u);
+        mma(d_tmem, sdesc_mn(a_hi + oa, 8192), sdesc(b_lo + ob), kIdescM128N64AMN, 1u);
+        mma(d_tmem, sdesc_mn(a_lo + oa, 8192), sdesc(b_hi + ob), kIdescM128N64AMN, 1u);
     }
 }
 
@@ -99,6 +135,26 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 // Arrive on the mbarrier and expect `bytes` of transactions in this phase.
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+
+// Plain arrive (count 1) on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// Named barrier `id` over `n` threads (a multiple of 32), and the same with
+// an AND of a predicate over those threads.
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ bool named_and(uint32_t id, uint32_t n, bool pred) {
+    uint32_t out;
+    asm volatile(
+        "{\n.reg .pred p, q;\nsetp.ne.u32 p, %3, 0;\nbar.red.and.pred q, %1, %2, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(out)
+        : "r"(id), "r"(n), "r"((uint32_t)pred)
+        : "memory");
+    return out != 0;
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -174,6 +230,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
     hi = __float2bfloat16_rn(x);
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Eight values as bf16 hi and lo parts (split_bf16 on each), packed two per
+// 32-bit word in order: hi[0..3] and lo[0..3] hold x[0..7].
+__device__ __forceinline__ void split8_bf16(const float *x, uint32_t (&hi)[4], uint32_t (&lo)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(x[2 * i] - __low2float(h), x[2 * i + 1] - __high2float(h));
+        hi[i] = *reinterpret_cast<const uint32_t *>(&h);
+        lo[i] = *reinterpret_cast<const uint32_t *>(&l);
+    }
 }
 
 __device__ __forceinline__ uint32_t pack_hilo(float x) {
