@@ -257,15 +257,20 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
                 ok = tc::mbar_wait(&u3_full[sl], (uint32_t)((it >> 1) & 1), kWaitCycles);
                 if (!ok) break;
                 landed3++;
-                ok = gemm2(it, 0);
+                // the next item's GEMM 1 (p0) goes first (D1[0] is free as soon as
+                // A2 holds this item's p0), except at a group change, where X is
+                // restaged only after this item's CONV (p1)
+                const bool next = it + 1 < nitems, newgroup = next && (it + 1) % nchains == 0;
+                if (next && !newgroup) ok = gemm1(it + 1, 0);
+                ok = ok && gemm2(it, 0);
                 // U3 of item it+1 into the slot GEMM 2 (it-1) has finished with
-                if (ok && it >= 1 && it + 1 < nitems) {
+                if (ok && it >= 1 && next) {
                     ok = tc::mbar_wait(&u3_free[sl ^ 1], (uint32_t)(((it - 1) >> 1) & 1), kWaitCycles);
                     if (ok) issue_u3();
                 }
-                if (ok && it + 1 < nitems) ok = gemm1(it + 1, 0);
                 ok = ok && gemm2(it, 1);
-                if (ok && it + 1 < nitems) ok = gemm1(it + 1, 1);
+                if (ok && newgroup) ok = gemm1(it + 1, 0);
+                if (ok && next) ok = gemm1(it + 1, 1);
             }
             // the last item's commit: every MMA of this CTA has completed
             if (ok) ok = tc::mbar_wait(&u3_free[(nitems - 1) & 1], (uint32_t)(((nitems - 1) >> 1) & 1), kWaitCycles);
@@ -311,9 +316,15 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
         auto epi = [&](int p) {   // D2[p] -> stage slabs 2p + s2 (row = (s2, i4'), cols i3')
             float y[kACols];
             tc::tmem_ld16(tmem + lane_off + 128 + 64 * p + cbase, y);
-            const int s = 2 * p + s2;
+            uint32_t *dst = stage + (2 * p + s2) * kSlab + cbase * 64 + r63;
 #pragma unroll
-            for (int jj = 0; jj < kACols; jj++) stage[s * kSlab + (cbase + jj) * 64 + r63] = tc::pack_hilo(y[jj]);
+            for (int jj = 0; jj < kACols; jj += 2) {   // two columns per conversion; words (hi | lo << 16)
+                const __nv_bfloat162 h = __floats2bfloat162_rn(y[jj], y[jj + 1]);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(y[jj] - __low2float(h), y[jj + 1] - __high2float(h));
+                const uint32_t hw = *reinterpret_cast<const uint32_t *>(&h), lw = *reinterpret_cast<const uint32_t *>(&l);
+                dst[jj * 64] = __byte_perm(hw, lw, 0x5410);
+                dst[(jj + 1) * 64] = __byte_perm(hw, lw, 0x7632);
+            }
         };
         bool ok = true;
         stage_x(sX, V, Vbase, 4 * blockIdx.x, tid);
