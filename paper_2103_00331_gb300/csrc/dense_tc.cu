@@ -508,20 +508,23 @@ __global__ void __launch_bounds__(kBThreads, 2) dense_pass_b(const uint8_t *__re
                 float w1[kBCols];
                 tc::tmem_ld32(tmem + lane_off + cbase, w1);   // row = (s2, i1), cols i2' = cbase ..
                 {
-                    // the second GEMM's A operand, into the operand buffer
+                    // the second GEMM's A operand, MN-major into the operand
+                    // buffer: k = i1 (this thread's row), m = s2 * 64 + i2'
                     const uint32_t s2 = row >> 6, i1 = row & 63;
+                    const uint32_t a4_off = s2 * 8192u + (i1 >> 3) * 1024u + (i1 & 7u) * 128u;
 #pragma unroll
-                    for (int jj = 0; jj < kBCols; jj++) {
-                        const uint32_t j = cbase + jj;
-                        __nv_bfloat16 h, l;
-                        tc::split_bf16(w1[jj], h, l);
-                        put_bf16(sZ, s2 * 64 + j, i1, __bfloat16_as_ushort(h));
-                        put_bf16(sZ + kPairBytes, s2 * 64 + j, i1, __bfloat16_as_ushort(l));
+                    for (int h = 0; h < kBCols / 8; h++) {
+                        uint32_t hi[4], lo[4];
+                        tc::split8_bf16(w1 + 8 * h, hi, lo);
+                        const uint32_t chunk = (uint32_t)((cbase >> 3) + h);
+                        const uint32_t off = a4_off + (((chunk ^ (i1 & 7u)) & 7u) << 4);
+                        *reinterpret_cast<uint4 *>(sZ + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                        *reinterpret_cast<uint4 *>(sZ + kPairBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
                     }
                 }
                 sync_for_async();
                 if (tid == 0) {
-                    tc::mma_bf16x3(tmem + 64, aZ, aZ + kPairBytes, u1, u1 + kTileBytes, r > 0 ? 1u : 0u);
+                    tc::mma_bf16x3_amn(tmem + 64, aZ, aZ + kPairBytes, u1, u1 + kTileBytes, r > 0 ? 1u : 0u);
                     tc::commit(mbar);
                 }
                 if (!wait_all(mbar, mph, err)) { alive = false; break; }
