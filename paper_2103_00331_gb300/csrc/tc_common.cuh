@@ -105,12 +105,15 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
 }
 
+// One test of the phase; the thread may be suspended in hardware for up to
+// about 0.1 ms while the phase is still incomplete (woken when it completes),
+// so a waiting thread issues few instructions.
 __device__ __forceinline__ bool mbar_try(uint64_t *mbar, uint32_t phase) {
     uint32_t ok;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(smem_u32(mbar)), "r"(phase)
+        : "r"(smem_u32(mbar)), "r"(phase), "r"(100000u)
         : "memory");
     return ok != 0;
 }
