@@ -109,6 +109,8 @@ static void free_device(Factors &F) {
     F.march_graph = nullptr;
     if (F.dense_graph) cudaGraphExecDestroy(F.dense_graph);
     F.dense_graph = nullptr;
+    if (F.dense_pi_graph) cudaGraphExecDestroy(F.dense_pi_graph);
+    F.dense_pi_graph = nullptr;
     F.d_dense_loop = nullptr;
     F.d_arena = nullptr;
     F.d_code = nullptr; F.d_R32 = nullptr; F.d_R64 = nullptr; F.d_cell = nullptr;

@@ -734,6 +734,8 @@ cpmdp_status dense_certify(const Factors &F, const float *V, uint8_t *pi, double
 // first refresh, which subtracts and adds exact zeros). The host reads the
 // control block once, after the graph. The graph is recorded once per
 // (V, policy, tol, max_iter, certify, trace) and replayed.
+constexpr size_t kLoopCtlBytes = 256;   // device control block of the graph-driven loops
+
 struct DenseLoopCtl {
     int k;              // sweeps done
     int last_rebase;    // sweep of the last base refresh
@@ -945,7 +947,7 @@ cpmdp_status dense_tc_solve(const Factors &F, float *V, uint8_t *pi, const Solve
     if (s != CPMDP_OK) return s;
     Factors &M = const_cast<Factors &>(F);
     // buffers the recorded graph uses must exist before the recording
-    if (!M.d_dense_loop) CPMDP_CUDA(cudaMalloc(&M.d_dense_loop, sizeof(DenseLoopCtl)));
+    if (!M.d_dense_loop) CPMDP_CUDA(cudaMalloc(&M.d_dense_loop, kLoopCtlBytes));
     if (!M.d_Vd) CPMDP_CUDA(cudaMalloc(&M.d_Vd, (size_t)F.nstates * sizeof(double)));
     const int halve = F.gamma > 0.0 && F.gamma < 1.0 ? (int)ceil(log(2.0) / log(1.0 / F.gamma)) : 1;
     const bool same = M.dense_graph && M.dense_graph_V == (void *)V && M.dense_graph_pi == (void *)pi &&
@@ -1034,6 +1036,243 @@ __global__ void dense_improve_kernel(const float *__restrict__ Qold, const float
 // The FP32 base expectation is refreshed when an evaluation's residual
 // stops falling. With certify on, one FP64 backup of the result gives the
 // certified residual max |T(V) - V| (the policy is left as PI found it).
+// ---------------------------------------------------------------------------
+// BF16x3 policy iteration as one CUDA graph launch (nested conditional
+// nodes; the same steps and decisions as a host-driven loop):
+//   greedy sweep (max mode: the initial policy), then WHILE(round):
+//     round start (evaluation cap: partial_eval sweeps while the policy
+//     changes, max_eval_iter once a full evaluation is asked for)
+//     WHILE(eval): sweep V -> W in evaluation mode, control, IF(base
+//       refresh), IF(second: sweep W -> V, control, IF(base refresh))
+//     IF(odd count: copy W -> V)
+//     improvement: Q of the current action, best Q and its argmax, compare
+//     with the keep margin; round end (stop rules of modified PI)
+struct DensePiCtl {
+    int e;              // evaluation sweeps of this round
+    int cap;            // their limit this round
+    int ok;             // this round's evaluation reached eval_tol
+    int full;           // evaluations run to eval_tol (no cap)
+    int last_rebase;    // evaluation sweep of the last base refresh this round
+    int rebases;
+    int total;          // sweeps (greedy, evaluation, improvement)
+    int rounds;
+    int evals;          // evaluation sweeps of all rounds
+    int conv;
+    int stop;
+    int which;          // buffer of the current iterate: 0 = V, 1 = scratch
+    double res;         // last evaluation residual
+    double hist[8];     // this round's evaluation residuals (sweep j at j mod 8)
+};
+static_assert(sizeof(DensePiCtl) <= kLoopCtlBytes && sizeof(DenseLoopCtl) <= kLoopCtlBytes, "loop control block");
+
+__global__ void pi_init_kernel(DensePiCtl *c, const int *err, int max_rounds, cudaGraphConditionalHandle h_round) {
+    if (*(volatile const int *)err || max_rounds <= 0) c->stop = 1;
+    cudaGraphSetConditional(h_round, c->stop ? 0u : 1u);
+}
+
+__global__ void pi_round_start_kernel(DensePiCtl *c, int partial_eval, int max_eval_iter,
+                                      cudaGraphConditionalHandle h_eval) {
+    c->e = 0;
+    c->ok = 0;
+    c->last_rebase = 0;
+    c->which = 0;
+    c->cap = c->full ? max_eval_iter : min(partial_eval, max_eval_iter);
+    cudaGraphSetConditional(h_eval, c->cap > 0 ? 1u : 0u);
+}
+
+// After evaluation sweep `step` (0: V -> W, 1: W -> V).
+__global__ void pi_eval_ctl_kernel(DensePiCtl *c, unsigned long long *res_slot, const int *err, double eval_tol,
+                                   int step, cudaGraphConditionalHandle h_eval, cudaGraphConditionalHandle h_rebase,
+                                   cudaGraphConditionalHandle h_second) {
+    unsigned rebase = 0;
+    bool done;
+    if (*(volatile const int *)err) {
+        c->stop = 1;
+        done = true;
+    } else {
+        double r;
+        memcpy(&r, res_slot, sizeof(r));
+        *res_slot = 0ull;
+        c->hist[c->e & 7] = r;
+        c->e++;
+        c->total++;
+        c->res = r;
+        c->which = step == 0 ? 1 : 0;
+        done = false;
+        if (r < eval_tol) {
+            c->ok = 1;
+            done = true;
+        } else {
+            if (c->e - c->last_rebase >= 6 && r > 0.9 * c->hist[(c->e - 6) & 7] && c->rebases < 256) {
+                rebase = 1;
+                c->last_rebase = c->e;
+                c->rebases++;
+            }
+            if (c->e >= c->cap) done = true;
+        }
+    }
+    cudaGraphSetConditional(h_rebase, rebase);
+    if (step == 0) cudaGraphSetConditional(h_second, done ? 0u : 1u);
+    cudaGraphSetConditional(h_eval, done ? 0u : 1u);
+}
+
+__global__ void pi_after_eval_kernel(const DensePiCtl *c, cudaGraphConditionalHandle h_odd) {
+    cudaGraphSetConditional(h_odd, c->which == 1 ? 1u : 0u);
+}
+
+__global__ void pi_round_end_kernel(DensePiCtl *c, const unsigned *changed, const int *err, int max_rounds,
+                                    cudaGraphConditionalHandle h_round) {
+    const unsigned nchg = *changed;
+    c->evals += c->e;
+    c->total++;
+    c->rounds++;
+    if (*(volatile const int *)err) {
+        c->stop = 1;
+    } else if (nchg == 0) {
+        if (c->ok) {
+            c->conv = 1;
+            c->stop = 1;
+        } else if (c->full) {
+            c->stop = 1;
+        } else {
+            c->full = 1;
+        }
+    } else if (!c->ok && c->full) {
+        c->stop = 1;
+    }
+    if (c->rounds >= max_rounds) c->stop = 1;
+    cudaGraphSetConditional(h_round, c->stop ? 0u : 1u);
+}
+
+static cpmdp_status record_dense_pi(Factors &F, float *V, uint8_t *pi, const SolveOpts &o, cudaGraph_t *out) {
+    float *W = (float *)F.d_scratch;
+    unsigned long long *rb = &F.d_ctrl->res_slot[0];
+    unsigned *cb = &F.d_ctrl->changed_slot[0];
+    float *Qold = reinterpret_cast<float *>(F.d_pi_work), *Qbest = Qold + kS;
+    uint8_t *pib = reinterpret_cast<uint8_t *>(Qbest + kS);
+    DensePiCtl *c = reinterpret_cast<DensePiCtl *>(F.d_dense_loop);
+    const int grid = F.num_sms > 0 ? F.num_sms * 8 : 1216;
+    cudaGraph_t G = nullptr;
+    cudaStream_t cap = nullptr;
+    cpmdp_status s = CPMDP_OK;
+    cudaError_t e = cudaGraphCreate(&G, 0);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    cudaGraphConditionalHandle h_round = 0, h_eval = 0, h_odd = 0, h_reb0 = 0, h_second = 0, h_reb1 = 0;
+    cudaGraph_t rbody = nullptr, ebody = nullptr, obody = nullptr, sbody = nullptr;
+    cudaGraphNode_t n_round, n_eval, n_odd;
+    std::vector<cudaGraphNode_t> leaves;
+    // capture fn's work into g, after the nodes deps
+    auto capture = [&](cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, auto &&fn) -> cpmdp_status {
+        cudaError_t ce = cudaStreamBeginCaptureToGraph(cap, g, deps.empty() ? nullptr : deps.data(), nullptr,
+                                                       deps.size(), cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) return cuda_fail(ce, "begin capture");
+        cpmdp_status cs = fn();
+        cudaGraph_t gg = g;
+        ce = cudaStreamEndCapture(cap, &gg);
+        if (cs != CPMDP_OK) return cs;
+        if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
+        return CPMDP_OK;
+    };
+    auto launched = [&](const char *what) -> cpmdp_status {
+        cudaError_t ce = cudaGetLastError();
+        return ce == cudaSuccess ? CPMDP_OK : cuda_fail(ce, what);
+    };
+    // one evaluation sweep from `in` to `out` (each state's own action), then its control kernel
+    auto eval_ctl = [&](const float *in, float *outv, int step, cudaGraphConditionalHandle hr) -> cpmdp_status {
+        cudaError_t ce = cudaMemsetAsync(rb, 0, sizeof(*rb), cap);
+        if (ce != cudaSuccess) return cuda_fail(ce, "memset");
+        cpmdp_status cs = tc_sweep(F, in, outv, nullptr, true, rb, cap, pi);
+        if (cs != CPMDP_OK) return cs;
+        pi_eval_ctl_kernel<<<1, 1, 0, cap>>>(c, rb, F.d_tc_err, o.eval_tol, step, h_eval, hr, h_second);
+        return launched("evaluation control kernel");
+    };
+    auto rebase_body = [&](const float *cur) -> cpmdp_status {
+        cudaError_t ce = cudaMemcpyAsync(F.d_Vbase, cur, (size_t)kS * sizeof(float), cudaMemcpyDeviceToDevice, cap);
+        if (ce != cudaSuccess) return cuda_fail(ce, "base copy");
+        return dense_store_expectation(F, cur, F.d_EB, cap);
+    };
+    if (e != cudaSuccess) { s = cuda_fail(e, "graph setup"); goto done; }
+    if ((e = cudaGraphConditionalHandleCreate(&h_round, G, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    // root: greedy sweep (max mode: its argmax is the initial policy), the stop test, WHILE(round)
+    if ((s = capture(G, {}, [&]() -> cpmdp_status {
+             cpmdp_status cs = tc_sweep(F, V, W, pi, true, nullptr, cap);
+             if (cs != CPMDP_OK) return cs;
+             pi_init_kernel<<<1, 1, 0, cap>>>(c, F.d_tc_err, o.max_rounds, h_round);
+             return launched("init kernel");
+         })) != CPMDP_OK)
+        goto done;
+    if ((e = graph_leaves(G, leaves)) != cudaSuccess) goto fail;
+    if ((e = add_conditional(G, leaves, h_round, cudaGraphCondTypeWhile, &n_round, &rbody)) != cudaSuccess) goto fail;
+    // round body: start kernel, WHILE(eval), IF(odd: copy W -> V), improvement, end kernel
+    if ((e = cudaGraphConditionalHandleCreate(&h_eval, rbody, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    if ((e = cudaGraphConditionalHandleCreate(&h_odd, rbody, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    if ((s = capture(rbody, {}, [&]() -> cpmdp_status {
+             pi_round_start_kernel<<<1, 1, 0, cap>>>(c, o.partial_eval, o.max_eval_iter, h_eval);
+             return launched("round start kernel");
+         })) != CPMDP_OK)
+        goto done;
+    if ((e = graph_leaves(rbody, leaves)) != cudaSuccess) goto fail;
+    if ((e = add_conditional(rbody, leaves, h_eval, cudaGraphCondTypeWhile, &n_eval, &ebody)) != cudaSuccess) goto fail;
+    if ((s = capture(rbody, {n_eval}, [&]() -> cpmdp_status {
+             pi_after_eval_kernel<<<1, 1, 0, cap>>>(c, h_odd);
+             return launched("after-evaluation kernel");
+         })) != CPMDP_OK)
+        goto done;
+    if ((e = graph_leaves(rbody, leaves)) != cudaSuccess) goto fail;
+    if ((e = add_conditional(rbody, leaves, h_odd, cudaGraphCondTypeIf, &n_odd, &obody)) != cudaSuccess) goto fail;
+    if ((s = capture(obody, {}, [&]() -> cpmdp_status {
+             cudaError_t ce = cudaMemcpyAsync(V, W, (size_t)kS * sizeof(float), cudaMemcpyDeviceToDevice, cap);
+             return ce == cudaSuccess ? CPMDP_OK : cuda_fail(ce, "iterate copy");
+         })) != CPMDP_OK)
+        goto done;
+    if ((s = capture(rbody, {n_odd}, [&]() -> cpmdp_status {
+             cpmdp_status cs = tc_sweep(F, V, Qold, nullptr, true, nullptr, cap, pi);
+             if (cs != CPMDP_OK) return cs;
+             if ((cs = tc_sweep(F, V, Qbest, pib, true, nullptr, cap)) != CPMDP_OK) return cs;
+             cudaError_t ce = cudaMemsetAsync(cb, 0, sizeof(*cb), cap);
+             if (ce != cudaSuccess) return cuda_fail(ce, "memset");
+             dense_improve_kernel<<<grid, 256, 0, cap>>>(Qold, Qbest, pib, pi, 1e-6f, kS, cb);
+             if ((cs = launched("improvement kernel")) != CPMDP_OK) return cs;
+             pi_round_end_kernel<<<1, 1, 0, cap>>>(c, cb, F.d_tc_err, o.max_rounds, h_round);
+             return launched("round end kernel");
+         })) != CPMDP_OK)
+        goto done;
+    // evaluation body: sweep V -> W, control, IF(refresh from W), IF(second)
+    if ((e = cudaGraphConditionalHandleCreate(&h_reb0, ebody, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    if ((e = cudaGraphConditionalHandleCreate(&h_second, ebody, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    if ((s = capture(ebody, {}, [&] { return eval_ctl(V, W, 0, h_reb0); })) != CPMDP_OK) goto done;
+    {
+        cudaGraph_t b1, b2;
+        cudaGraphNode_t n1, n2;
+        if ((e = graph_leaves(ebody, leaves)) != cudaSuccess) goto fail;
+        if ((e = add_conditional(ebody, leaves, h_reb0, cudaGraphCondTypeIf, &n1, &b1)) != cudaSuccess) goto fail;
+        if ((e = add_conditional(ebody, {n1}, h_second, cudaGraphCondTypeIf, &n2, &b2)) != cudaSuccess) goto fail;
+        if ((s = capture(b1, {}, [&] { return rebase_body(W); })) != CPMDP_OK) goto done;
+        sbody = b2;
+    }
+    // second sweep W -> V, control, IF(refresh from V)
+    if ((e = cudaGraphConditionalHandleCreate(&h_reb1, sbody, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    if ((s = capture(sbody, {}, [&] { return eval_ctl(W, V, 1, h_reb1); })) != CPMDP_OK) goto done;
+    {
+        cudaGraph_t b1;
+        cudaGraphNode_t n1;
+        if ((e = graph_leaves(sbody, leaves)) != cudaSuccess) goto fail;
+        if ((e = add_conditional(sbody, leaves, h_reb1, cudaGraphCondTypeIf, &n1, &b1)) != cudaSuccess) goto fail;
+        if ((s = capture(b1, {}, [&] { return rebase_body(V); })) != CPMDP_OK) goto done;
+    }
+    goto done;
+fail:
+    s = cuda_fail(e, "recording the dense policy iteration graph");
+done:
+    if (cap) cudaStreamDestroy(cap);
+    if (s != CPMDP_OK) {
+        if (G) cudaGraphDestroy(G);
+        return s;
+    }
+    *out = G;
+    return CPMDP_OK;
+}
+
 cpmdp_status dense_tc_policy_iteration(const Factors &F, float *V, uint8_t *pi, const SolveOpts &o, Ctrl *hc,
                                        cudaStream_t st) {
     if (!dense_tc_supported(F)) {
@@ -1043,87 +1282,53 @@ cpmdp_status dense_tc_policy_iteration(const Factors &F, float *V, uint8_t *pi, 
     cpmdp_status s = tc_prepare(const_cast<Factors &>(F));
     if (s != CPMDP_OK) return s;
     Factors &M = const_cast<Factors &>(F);
+    // buffers the recorded graph uses must exist before the recording
     if (!M.d_pi_work) CPMDP_CUDA(cudaMalloc(&M.d_pi_work, (size_t)kS * (2 * sizeof(float) + 1)));
-    float *Qold = reinterpret_cast<float *>(M.d_pi_work), *Qbest = Qold + kS;
-    uint8_t *pib = reinterpret_cast<uint8_t *>(Qbest + kS);
-    CPMDP_CUDA(cudaMemsetAsync(F.d_tc_err, 0, sizeof(int), st));
-    float *W = (float *)F.d_scratch;
-    unsigned long long *rb = &F.d_ctrl->res_slot[0];
-    unsigned *cb = &F.d_ctrl->changed_slot[0];
-    float *cur = V, *nxt = W;
-    std::vector<double> hist;
-    int total = 0, rounds = 0, evals = 0, conv = 0, last_rebase = 0, rebases = 0;
-    bool base = false, full = o.partial_eval <= 0;
-    double res = INFINITY;
-    const int grid = F.num_sms > 0 ? F.num_sms * 8 : 1216;
-    // greedy start: the max sweep's argmax of the input V
-    s = tc_sweep(F, cur, nxt, pi, false, nullptr, st);
-    if (s != CPMDP_OK) return s;
-    total++;
-    while (rounds < o.max_rounds) {
-        const int cap = full ? o.max_eval_iter : std::min(o.partial_eval, o.max_eval_iter);
-        int e = 0, ok = 0;
-        hist.clear();
-        last_rebase = 0;
-        while (e < cap) {
-            CPMDP_CUDA(cudaMemsetAsync(rb, 0, sizeof(*rb), st));
-            s = tc_sweep(F, cur, nxt, nullptr, base, rb, st, pi);
-            if (s != CPMDP_OK) return s;
-            unsigned long long bits = 0;
-            CPMDP_CUDA(cudaMemcpyAsync(&bits, rb, sizeof(bits), cudaMemcpyDeviceToHost, st));
-            s = tc_check_err(F, st);
-            if (s != CPMDP_OK) return s;
-            memcpy(&res, &bits, sizeof(res));
-            float *t = cur; cur = nxt; nxt = t;
-            e++;
-            total++;
-            hist.push_back(res);
-            if (res < o.eval_tol) { ok = 1; break; }
-            const int k = (int)hist.size();
-            if (k - last_rebase >= 6 && res > 0.9 * hist[k - 6] && rebases < 256) {
-                CPMDP_CUDA(cudaMemcpyAsync(F.d_Vbase, cur, (size_t)kS * sizeof(float), cudaMemcpyDeviceToDevice, st));
-                s = dense_store_expectation(F, cur, F.d_EB, st);
-                if (s != CPMDP_OK) return s;
-                base = true;
-                last_rebase = k;
-                rebases++;
-            }
-        }
-        evals += e;
-        // improvement at the evaluated values
-        s = tc_sweep(F, cur, Qold, nullptr, base, nullptr, st, pi);
+    if (!M.d_dense_loop) CPMDP_CUDA(cudaMalloc(&M.d_dense_loop, kLoopCtlBytes));
+    const bool same = M.dense_pi_graph && M.dense_pi_graph_V == (void *)V && M.dense_pi_graph_pi == (void *)pi &&
+                      M.dense_pi_graph_eval_tol == o.eval_tol && M.dense_pi_graph_rounds == o.max_rounds &&
+                      M.dense_pi_graph_eval_iter == o.max_eval_iter && M.dense_pi_graph_partial == o.partial_eval;
+    if (!same) {
+        if (M.dense_pi_graph) { cudaGraphExecDestroy(M.dense_pi_graph); M.dense_pi_graph = nullptr; }
+        cudaGraph_t g = nullptr;
+        s = record_dense_pi(M, V, pi, o, &g);
         if (s != CPMDP_OK) return s;
-        s = tc_sweep(F, cur, Qbest, pib, base, nullptr, st);
-        if (s != CPMDP_OK) return s;
-        CPMDP_CUDA(cudaMemsetAsync(cb, 0, sizeof(*cb), st));
-        dense_improve_kernel<<<grid, 256, 0, st>>>(Qold, Qbest, pib, pi, 1e-6f, kS, cb);
-        CPMDP_CUDA(cudaGetLastError());
-        unsigned nchg = 0;
-        CPMDP_CUDA(cudaMemcpyAsync(&nchg, cb, sizeof(nchg), cudaMemcpyDeviceToHost, st));
-        s = tc_check_err(F, st);
-        if (s != CPMDP_OK) return s;
-        total++;
-        rounds++;
-        if (nchg == 0) {
-            if (ok) { conv = 1; break; }
-            if (full) break;
-            full = true;
-            continue;
-        }
-        if (!ok && full) break;
+        cudaError_t e = cudaGraphInstantiate(&M.dense_pi_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { M.dense_pi_graph = nullptr; CPMDP_CUDA(e); }
+        M.dense_pi_graph_V = (void *)V;
+        M.dense_pi_graph_pi = (void *)pi;
+        M.dense_pi_graph_eval_tol = o.eval_tol;
+        M.dense_pi_graph_rounds = o.max_rounds;
+        M.dense_pi_graph_eval_iter = o.max_eval_iter;
+        M.dense_pi_graph_partial = o.partial_eval;
     }
-    if (cur != V) CPMDP_CUDA(cudaMemcpyAsync(V, cur, (size_t)kS * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    // start: zero base (E of a zero base is zero), control block (one sweep: the greedy start)
+    DensePiCtl c0;
+    memset(&c0, 0, sizeof(c0));
+    c0.full = o.partial_eval <= 0;
+    c0.total = 1;
+    CPMDP_CUDA(cudaMemcpyAsync(M.d_dense_loop, &c0, sizeof(c0), cudaMemcpyHostToDevice, st));
+    CPMDP_CUDA(cudaMemsetAsync(F.d_Vbase, 0, (size_t)kS * sizeof(float), st));
+    CPMDP_CUDA(cudaMemsetAsync(F.d_EB, 0, (size_t)F.nactions * kS * sizeof(float), st));
+    CPMDP_CUDA(cudaMemsetAsync(&F.d_ctrl->res_slot[0], 0, sizeof(unsigned long long), st));
+    CPMDP_CUDA(cudaMemsetAsync(F.d_tc_err, 0, sizeof(int), st));
+    CPMDP_CUDA(cudaGraphLaunch(M.dense_pi_graph, st));
+    DensePiCtl c;
+    CPMDP_CUDA(cudaMemcpyAsync(&c, M.d_dense_loop, sizeof(c), cudaMemcpyDeviceToHost, st));
+    s = tc_check_err(F, st);
+    if (s != CPMDP_OK) return s;
     if (o.certify) {
         double *cert = (double *)((char *)F.d_ctrl + offsetof(Ctrl, certify_residual));
         s = dense_certify(F, V, nullptr, cert, st);
         if (s != CPMDP_OK) return s;
     }
-    hc->iterations = total;
-    hc->rounds = rounds;
-    hc->eval_sweeps = evals;
-    hc->converged = conv;
-    hc->last_residual = res;
-    hc->backups = (long long)(1 + rounds) * kS * F.nactions + (long long)evals * kS;
+    hc->iterations = c.total;
+    hc->rounds = c.rounds;
+    hc->eval_sweeps = c.evals;
+    hc->converged = c.conv;
+    hc->last_residual = c.rounds > 0 ? c.res : INFINITY;
+    hc->backups = (long long)(1 + c.rounds) * kS * F.nactions + (long long)c.evals * kS;
     return CPMDP_OK;
 }
 

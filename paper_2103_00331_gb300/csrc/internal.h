@@ -112,6 +112,13 @@ struct Factors {
     double dense_graph_tol = 0;
     int dense_graph_max_iter = 0;
     int dense_graph_certify = -1;
+    cudaGraphExec_t dense_pi_graph = nullptr;   // BF16X3 policy iteration, recorded once per (V, pi, options)
+    void *dense_pi_graph_V = nullptr;
+    void *dense_pi_graph_pi = nullptr;
+    double dense_pi_graph_eval_tol = 0;
+    int dense_pi_graph_rounds = 0;
+    int dense_pi_graph_eval_iter = 0;
+    int dense_pi_graph_partial = -1;
     int *d_tc_err = nullptr;           // error word of the tensor-core kernels
     // barrier-free FP32 solver (flow_solve.cu), allocated on first use
     void *d_flow = nullptr;            // arrival counters + four rings of |S| tagged words
