@@ -111,6 +111,8 @@ static void free_device(Factors &F) {
     F.dense_graph = nullptr;
     if (F.dense_pi_graph) cudaGraphExecDestroy(F.dense_pi_graph);
     F.dense_pi_graph = nullptr;
+    if (F.simt_graph) cudaGraphExecDestroy(F.simt_graph);
+    F.simt_graph = nullptr;
     F.d_dense_loop = nullptr;
     F.d_arena = nullptr;
     F.d_code = nullptr; F.d_R32 = nullptr; F.d_R64 = nullptr; F.d_cell = nullptr;

@@ -280,80 +280,215 @@ cpmdp_status dense_backup(const Factors &F, cpmdp_precision prec, const void *Vi
 // Value / policy iteration for dense models: each sweep is A*R*D launches
 // of milliseconds of work, so the loop runs on the host and reads the
 // residual (8 bytes) back once per sweep.
+// ---------------------------------------------------------------------------
+// The SIMT loops as one CUDA graph launch each (conditional nodes; the same
+// sweeps and stop rules as a host-driven loop, no residual read back per
+// sweep). Value iteration: WHILE { sweep V -> W, control, IF(second: sweep
+// W -> V, control) }, IF(odd count: copy W -> V), greedy policy. Policy
+// iteration: greedy start, WHILE(round) { start, WHILE(eval) { evaluation
+// sweeps as above }, IF(odd: copy), improvement sweep, round end }.
+
+// After value-iteration sweep `step` (0: V -> W, 1: W -> V).
+__global__ void simt_vi_ctl_kernel(DensePiCtl *c, unsigned long long *res_slot, double tol, int max_iter,
+                                   double *trace, int step, cudaGraphConditionalHandle h_loop,
+                                   cudaGraphConditionalHandle h_second) {
+    double r;
+    memcpy(&r, res_slot, sizeof(r));
+    *res_slot = 0ull;
+    if (trace) trace[c->total] = r;
+    c->total++;
+    c->res = r;
+    c->which = step == 0 ? 1 : 0;
+    if (r < tol) {
+        c->conv = 1;
+        c->stop = 1;
+    } else if (c->total >= max_iter) {
+        c->stop = 1;
+    }
+    if (step == 0) cudaGraphSetConditional(h_second, c->stop ? 0u : 1u);
+    cudaGraphSetConditional(h_loop, c->stop ? 0u : 1u);
+}
+
 template <typename T>
-static cpmdp_status dense_solve_t(const Factors &F, bool pim, T *V, uint8_t *pi, const SolveOpts &o,
-                                  Ctrl *hc, cudaStream_t st) {
+static cpmdp_status record_simt(Factors &F, bool pim, T *V, uint8_t *pi, const SolveOpts &o, cudaGraph_t *out) {
     T *W = (T *)F.d_scratch;
     unsigned long long *rb = &F.d_ctrl->res_slot[0];
     unsigned *cb = &F.d_ctrl->changed_slot[0];
     const double margin = std::is_same<T, double>::value ? 1e-12 : 1e-6;
-    T *cur = V, *nxt = W;
-    int total = 0, conv = 0, rounds = 0, evals = 0;
-    long long backups = 0;
-    double res = INFINITY;
-    const long long SA = (long long)F.nstates * F.nactions;
-    auto sweep_res = [&](int mode) -> cpmdp_status {
-        CPMDP_CUDA(cudaMemsetAsync(rb, 0, sizeof(*rb), st));
-        cpmdp_status s2 = dense_sweep<T>(F, cur, nxt, pi, mode, margin, rb, nullptr, st);
-        if (s2 != CPMDP_OK) return s2;
-        unsigned long long bits = 0;
-        CPMDP_CUDA(cudaMemcpyAsync(&bits, rb, sizeof(bits), cudaMemcpyDeviceToHost, st));
-        CPMDP_CUDA(cudaStreamSynchronize(st));
-        memcpy(&res, &bits, sizeof(res));
-        T *t = cur; cur = nxt; nxt = t;
-        total++;
-        backups += SA;
+    DensePiCtl *c = reinterpret_cast<DensePiCtl *>(F.d_dense_loop);
+    const int *err = F.d_tc_err;
+    cudaGraph_t G = nullptr;
+    cudaStream_t cap = nullptr;
+    cpmdp_status s = CPMDP_OK;
+    cudaError_t e = cudaGraphCreate(&G, 0);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    cudaGraphConditionalHandle h_outer = 0, h_eval = 0, h_second = 0, h_odd = 0;
+    cudaGraph_t lbody = nullptr, sbody = nullptr, obody = nullptr, rbody = nullptr;
+    cudaGraph_t host = nullptr;   // graph holding the evaluation WHILE and the odd-count copy
+    cudaGraphNode_t n_outer, n_loop, n_odd;
+    std::vector<cudaGraphNode_t> leaves;
+    auto capture = [&](cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, auto &&fn) -> cpmdp_status {
+        cudaError_t ce = cudaStreamBeginCaptureToGraph(cap, g, deps.empty() ? nullptr : deps.data(), nullptr,
+                                                       deps.size(), cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) return cuda_fail(ce, "begin capture");
+        cpmdp_status cs = fn();
+        cudaGraph_t gg = g;
+        ce = cudaStreamEndCapture(cap, &gg);
+        if (cs != CPMDP_OK) return cs;
+        if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
         return CPMDP_OK;
     };
-    cpmdp_status s2;
-    if (!pim) {
-        while (total < o.max_iter) {
-            if ((s2 = sweep_res(DM_VI)) != CPMDP_OK) return s2;
-            if (o.trace) CPMDP_CUDA(cudaMemcpyAsync(o.trace + total - 1, &res, sizeof(double), cudaMemcpyHostToDevice, st));
-            if (res < o.tol) { conv = 1; break; }
-        }
+    auto launched = [&](const char *what) -> cpmdp_status {
+        cudaError_t ce = cudaGetLastError();
+        return ce == cudaSuccess ? CPMDP_OK : cuda_fail(ce, what);
+    };
+    // one sweep from `in` to `outv` with its residual, then the step's control kernel
+    auto sweep_ctl = [&](T *in, T *outv, int step) -> cpmdp_status {
+        cudaError_t ce = cudaMemsetAsync(rb, 0, sizeof(*rb), cap);
+        if (ce != cudaSuccess) return cuda_fail(ce, "memset");
+        cpmdp_status cs = dense_sweep<T>(F, in, outv, pi, pim ? DM_EVAL : DM_VI, margin, rb, nullptr, cap);
+        if (cs != CPMDP_OK) return cs;
+        if (pim) pi_eval_ctl_kernel<<<1, 1, 0, cap>>>(c, rb, err, o.eval_tol, step, 0, h_eval, 0, h_second);
+        else simt_vi_ctl_kernel<<<1, 1, 0, cap>>>(c, rb, o.tol, o.max_iter, o.trace, step, h_eval, h_second);
+        return launched("control kernel");
+    };
+    if (e != cudaSuccess) { s = cuda_fail(e, "graph setup"); goto done; }
+    if (pim) {
+        // root: greedy start, stop test, WHILE(round)
+        if ((e = cudaGraphConditionalHandleCreate(&h_outer, G, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+        if ((s = capture(G, {}, [&]() -> cpmdp_status {
+                 cpmdp_status cs = dense_sweep<T>(F, V, nullptr, pi, DM_GREEDY, margin, nullptr, nullptr, cap);
+                 if (cs != CPMDP_OK) return cs;
+                 pi_init_kernel<<<1, 1, 0, cap>>>(c, err, o.max_rounds, h_outer);
+                 return launched("init kernel");
+             })) != CPMDP_OK)
+            goto done;
+        if ((e = graph_leaves(G, leaves)) != cudaSuccess) goto fail;
+        if ((e = add_conditional(G, leaves, h_outer, cudaGraphCondTypeWhile, &n_outer, &rbody)) != cudaSuccess) goto fail;
+        host = rbody;
+        if ((e = cudaGraphConditionalHandleCreate(&h_eval, host, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+        if ((s = capture(host, {}, [&]() -> cpmdp_status {
+                 pi_round_start_kernel<<<1, 1, 0, cap>>>(c, o.partial_eval, o.max_eval_iter, h_eval);
+                 return launched("round start kernel");
+             })) != CPMDP_OK)
+            goto done;
     } else {
-        if ((s2 = dense_sweep<T>(F, cur, nullptr, pi, DM_GREEDY, margin, nullptr, nullptr, st)) != CPMDP_OK) return s2;
-        total++;
-        backups += SA;
-        // modified policy iteration, as the GridWorld solvers
-        bool full = o.partial_eval <= 0;
-        while (rounds < o.max_rounds) {
-            const int cap = full ? o.max_eval_iter : std::min(o.partial_eval, o.max_eval_iter);
-            int e = 0, ok = 0;
-            while (e < cap) {
-                if ((s2 = sweep_res(DM_EVAL)) != CPMDP_OK) return s2;
-                e++;
-                if (res < o.eval_tol) { ok = 1; break; }
-            }
-            evals += e;
-            CPMDP_CUDA(cudaMemsetAsync(cb, 0, sizeof(*cb), st));
-            if ((s2 = dense_sweep<T>(F, cur, nullptr, pi, DM_IMPROVE, margin, nullptr, cb, st)) != CPMDP_OK) return s2;
-            unsigned nchg = 0;
-            CPMDP_CUDA(cudaMemcpyAsync(&nchg, cb, sizeof(nchg), cudaMemcpyDeviceToHost, st));
-            CPMDP_CUDA(cudaStreamSynchronize(st));
-            total++;
-            rounds++;
-            backups += SA;
-            if (nchg == 0) {
-                if (ok) { conv = 1; break; }
-                if (full) break;
-                full = true;
-                continue;
-            }
-            if (!ok && full) break;
-        }
+        host = G;
+        if ((e = cudaGraphConditionalHandleCreate(&h_eval, host, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+        if ((s = capture(host, {}, [&]() -> cpmdp_status {
+                 pi_init_kernel<<<1, 1, 0, cap>>>(c, err, o.max_iter, h_eval);
+                 return launched("init kernel");
+             })) != CPMDP_OK)
+            goto done;
     }
-    if (cur != V) CPMDP_CUDA(cudaMemcpyAsync(V, cur, sizeof(T) * F.nstates, cudaMemcpyDeviceToDevice, st));
-    if (!pim && pi) {
-        if ((s2 = dense_sweep<T>(F, V, nullptr, pi, DM_GREEDY, margin, nullptr, nullptr, st)) != CPMDP_OK) return s2;
+    // the sweep loop, then IF(odd count: copy W -> V)
+    if ((e = cudaGraphConditionalHandleCreate(&h_odd, host, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    if ((e = graph_leaves(host, leaves)) != cudaSuccess) goto fail;
+    if ((e = add_conditional(host, leaves, h_eval, cudaGraphCondTypeWhile, &n_loop, &lbody)) != cudaSuccess) goto fail;
+    if ((s = capture(host, {n_loop}, [&]() -> cpmdp_status {
+             pi_after_eval_kernel<<<1, 1, 0, cap>>>(c, h_odd);
+             return launched("after-loop kernel");
+         })) != CPMDP_OK)
+        goto done;
+    if ((e = graph_leaves(host, leaves)) != cudaSuccess) goto fail;
+    if ((e = add_conditional(host, leaves, h_odd, cudaGraphCondTypeIf, &n_odd, &obody)) != cudaSuccess) goto fail;
+    if ((s = capture(obody, {}, [&]() -> cpmdp_status {
+             cudaError_t ce = cudaMemcpyAsync(V, W, sizeof(T) * F.nstates, cudaMemcpyDeviceToDevice, cap);
+             return ce == cudaSuccess ? CPMDP_OK : cuda_fail(ce, "iterate copy");
+         })) != CPMDP_OK)
+        goto done;
+    if (pim) {
+        // improvement at the evaluated values, then the round's stop rules
+        if ((s = capture(host, {n_odd}, [&]() -> cpmdp_status {
+                 cudaError_t ce = cudaMemsetAsync(cb, 0, sizeof(*cb), cap);
+                 if (ce != cudaSuccess) return cuda_fail(ce, "memset");
+                 cpmdp_status cs = dense_sweep<T>(F, V, nullptr, pi, DM_IMPROVE, margin, nullptr, cb, cap);
+                 if (cs != CPMDP_OK) return cs;
+                 pi_round_end_kernel<<<1, 1, 0, cap>>>(c, cb, err, o.max_rounds, h_outer);
+                 return launched("round end kernel");
+             })) != CPMDP_OK)
+            goto done;
+    } else if (pi) {
+        // greedy policy of the returned values
+        if ((s = capture(host, {n_odd}, [&]() -> cpmdp_status {
+                 return dense_sweep<T>(F, V, nullptr, pi, DM_GREEDY, margin, nullptr, nullptr, cap);
+             })) != CPMDP_OK)
+            goto done;
     }
-    hc->iterations = total;
-    hc->rounds = rounds;
-    hc->eval_sweeps = evals;
-    hc->converged = conv;
-    hc->last_residual = res;
-    hc->backups = backups;
+    // loop body: sweep V -> W, control, IF(second: sweep W -> V, control)
+    if ((e = cudaGraphConditionalHandleCreate(&h_second, lbody, 0u, cudaGraphCondAssignDefault)) != cudaSuccess) goto fail;
+    if ((s = capture(lbody, {}, [&] { return sweep_ctl(V, W, 0); })) != CPMDP_OK) goto done;
+    {
+        cudaGraphNode_t n2;
+        if ((e = graph_leaves(lbody, leaves)) != cudaSuccess) goto fail;
+        if ((e = add_conditional(lbody, leaves, h_second, cudaGraphCondTypeIf, &n2, &sbody)) != cudaSuccess) goto fail;
+    }
+    if ((s = capture(sbody, {}, [&] { return sweep_ctl(W, V, 1); })) != CPMDP_OK) goto done;
+    goto done;
+fail:
+    s = cuda_fail(e, "recording the dense solve graph");
+done:
+    if (cap) cudaStreamDestroy(cap);
+    if (s != CPMDP_OK) {
+        if (G) cudaGraphDestroy(G);
+        return s;
+    }
+    *out = G;
+    return CPMDP_OK;
+}
+
+template <typename T>
+static cpmdp_status dense_solve_t(const Factors &F, bool pim, T *V, uint8_t *pi, const SolveOpts &o,
+                                  Ctrl *hc, cudaStream_t st) {
+    Factors &M = const_cast<Factors &>(F);
+    // buffers the recorded graph uses must exist before the recording
+    if (!M.d_dense_loop) CPMDP_CUDA(cudaMalloc(&M.d_dense_loop, kLoopCtlBytes));
+    if (!M.d_tc_err) CPMDP_CUDA(cudaMalloc(&M.d_tc_err, sizeof(int)));
+    const int prec = std::is_same<T, double>::value ? 1 : 0;
+    const bool same = M.simt_graph && M.simt_graph_V == (void *)V && M.simt_graph_pi == (void *)pi &&
+                      M.simt_graph_pim == (int)pim && M.simt_graph_prec == prec && M.simt_graph_tol == o.tol &&
+                      M.simt_graph_eval_tol == o.eval_tol && M.simt_graph_max_iter == o.max_iter &&
+                      M.simt_graph_rounds == o.max_rounds && M.simt_graph_eval_iter == o.max_eval_iter &&
+                      M.simt_graph_partial == o.partial_eval && M.simt_graph_trace == (void *)o.trace;
+    if (!same) {
+        if (M.simt_graph) { cudaGraphExecDestroy(M.simt_graph); M.simt_graph = nullptr; }
+        cudaGraph_t g = nullptr;
+        cpmdp_status s = record_simt<T>(M, pim, V, pi, o, &g);
+        if (s != CPMDP_OK) return s;
+        cudaError_t e = cudaGraphInstantiate(&M.simt_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { M.simt_graph = nullptr; CPMDP_CUDA(e); }
+        M.simt_graph_V = (void *)V;
+        M.simt_graph_pi = (void *)pi;
+        M.simt_graph_pim = (int)pim;
+        M.simt_graph_prec = prec;
+        M.simt_graph_tol = o.tol;
+        M.simt_graph_eval_tol = o.eval_tol;
+        M.simt_graph_max_iter = o.max_iter;
+        M.simt_graph_rounds = o.max_rounds;
+        M.simt_graph_eval_iter = o.max_eval_iter;
+        M.simt_graph_partial = o.partial_eval;
+        M.simt_graph_trace = (void *)o.trace;
+    }
+    DensePiCtl c0;
+    memset(&c0, 0, sizeof(c0));
+    if (pim) {
+        c0.full = o.partial_eval <= 0;
+        c0.total = 1;   // the greedy start
+    }
+    CPMDP_CUDA(cudaMemcpyAsync(M.d_dense_loop, &c0, sizeof(c0), cudaMemcpyHostToDevice, st));
+    CPMDP_CUDA(cudaMemsetAsync(&F.d_ctrl->res_slot[0], 0, sizeof(unsigned long long), st));
+    CPMDP_CUDA(cudaMemsetAsync(F.d_tc_err, 0, sizeof(int), st));
+    CPMDP_CUDA(cudaGraphLaunch(M.simt_graph, st));
+    DensePiCtl c;
+    CPMDP_CUDA(cudaMemcpyAsync(&c, M.d_dense_loop, sizeof(c), cudaMemcpyDeviceToHost, st));
+    CPMDP_CUDA(cudaStreamSynchronize(st));
+    hc->iterations = c.total;
+    hc->rounds = c.rounds;
+    hc->eval_sweeps = c.evals;
+    hc->converged = c.conv;
+    hc->last_residual = c.total > (pim ? 1 : 0) ? c.res : INFINITY;
+    hc->backups = (long long)c.total * F.nstates * F.nactions;
     return CPMDP_OK;
 }
 

@@ -653,7 +653,7 @@ static cpmdp_status tc_prepare(Factors &F) {
     CPMDP_CUDA(cudaMalloc(&Fm.d_T, (size_t)C * kS * sizeof(uint32_t)));
     CPMDP_CUDA(cudaMalloc(&Fm.d_EB, (size_t)F.nactions * kS * sizeof(float)));
     CPMDP_CUDA(cudaMalloc(&Fm.d_Vbase, (size_t)kS * sizeof(float)));
-    CPMDP_CUDA(cudaMalloc(&Fm.d_tc_err, sizeof(int)));
+    if (!Fm.d_tc_err) CPMDP_CUDA(cudaMalloc(&Fm.d_tc_err, sizeof(int)));
     CPMDP_CUDA(cudaFuncSetAttribute(dense_pass_a, cudaFuncAttributeMaxDynamicSharedMemorySize, kASmem));
     CPMDP_CUDA(cudaFuncSetAttribute(dense_pass_b, cudaFuncAttributeMaxDynamicSharedMemorySize, kBSmem));
     return CPMDP_OK;
@@ -734,7 +734,7 @@ cpmdp_status dense_certify(const Factors &F, const float *V, uint8_t *pi, double
 // first refresh, which subtracts and adds exact zeros). The host reads the
 // control block once, after the graph. The graph is recorded once per
 // (V, policy, tol, max_iter, certify, trace) and replayed.
-constexpr size_t kLoopCtlBytes = 256;   // device control block of the graph-driven loops
+static_assert(sizeof(DensePiCtl) <= kLoopCtlBytes, "loop control block");
 
 struct DenseLoopCtl {
     int k;              // sweeps done
@@ -748,6 +748,7 @@ struct DenseLoopCtl {
     double res;         // last working residual
     double hist[8];     // last eight working residuals (sweep k - 1 at k - 1 mod 8)
 };
+static_assert(sizeof(DenseLoopCtl) <= kLoopCtlBytes, "loop control block");
 
 __global__ void dense_loop_ctl_kernel(DenseLoopCtl *c, unsigned long long *res_slot, const int *err, double tol,
                                       int max_iter, int certify, int halve, double *trace, int step,
@@ -809,7 +810,7 @@ __global__ void dense_cert_check_kernel(DenseLoopCtl *c, const double *cert, dou
 }
 
 // Nodes of g that no other node depends on.
-static cudaError_t graph_leaves(cudaGraph_t g, std::vector<cudaGraphNode_t> &out) {
+cudaError_t graph_leaves(cudaGraph_t g, std::vector<cudaGraphNode_t> &out) {
     size_t n = 0;
     cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
     if (e != cudaSuccess) return e;
@@ -825,7 +826,7 @@ static cudaError_t graph_leaves(cudaGraph_t g, std::vector<cudaGraphNode_t> &out
 }
 
 // Add a conditional node (IF or WHILE) after `deps` in g; returns its body.
-static cudaError_t add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
+cudaError_t add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
                                    cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
                                    cudaGraphNode_t *node, cudaGraph_t *body) {
     cudaGraphNodeParams p = {};
@@ -1047,23 +1048,6 @@ __global__ void dense_improve_kernel(const float *__restrict__ Qold, const float
 //     IF(odd count: copy W -> V)
 //     improvement: Q of the current action, best Q and its argmax, compare
 //     with the keep margin; round end (stop rules of modified PI)
-struct DensePiCtl {
-    int e;              // evaluation sweeps of this round
-    int cap;            // their limit this round
-    int ok;             // this round's evaluation reached eval_tol
-    int full;           // evaluations run to eval_tol (no cap)
-    int last_rebase;    // evaluation sweep of the last base refresh this round
-    int rebases;
-    int total;          // sweeps (greedy, evaluation, improvement)
-    int rounds;
-    int evals;          // evaluation sweeps of all rounds
-    int conv;
-    int stop;
-    int which;          // buffer of the current iterate: 0 = V, 1 = scratch
-    double res;         // last evaluation residual
-    double hist[8];     // this round's evaluation residuals (sweep j at j mod 8)
-};
-static_assert(sizeof(DensePiCtl) <= kLoopCtlBytes && sizeof(DenseLoopCtl) <= kLoopCtlBytes, "loop control block");
 
 __global__ void pi_init_kernel(DensePiCtl *c, const int *err, int max_rounds, cudaGraphConditionalHandle h_round) {
     if (*(volatile const int *)err || max_rounds <= 0) c->stop = 1;
@@ -1081,9 +1065,10 @@ __global__ void pi_round_start_kernel(DensePiCtl *c, int partial_eval, int max_e
 }
 
 // After evaluation sweep `step` (0: V -> W, 1: W -> V).
+// can_rebase = 0 (SIMT paths): no base refresh, h_rebase is not touched.
 __global__ void pi_eval_ctl_kernel(DensePiCtl *c, unsigned long long *res_slot, const int *err, double eval_tol,
-                                   int step, cudaGraphConditionalHandle h_eval, cudaGraphConditionalHandle h_rebase,
-                                   cudaGraphConditionalHandle h_second) {
+                                   int step, int can_rebase, cudaGraphConditionalHandle h_eval,
+                                   cudaGraphConditionalHandle h_rebase, cudaGraphConditionalHandle h_second) {
     unsigned rebase = 0;
     bool done;
     if (*(volatile const int *)err) {
@@ -1103,7 +1088,7 @@ __global__ void pi_eval_ctl_kernel(DensePiCtl *c, unsigned long long *res_slot, 
             c->ok = 1;
             done = true;
         } else {
-            if (c->e - c->last_rebase >= 6 && r > 0.9 * c->hist[(c->e - 6) & 7] && c->rebases < 256) {
+            if (can_rebase && c->e - c->last_rebase >= 6 && r > 0.9 * c->hist[(c->e - 6) & 7] && c->rebases < 256) {
                 rebase = 1;
                 c->last_rebase = c->e;
                 c->rebases++;
@@ -1111,7 +1096,7 @@ __global__ void pi_eval_ctl_kernel(DensePiCtl *c, unsigned long long *res_slot, 
             if (c->e >= c->cap) done = true;
         }
     }
-    cudaGraphSetConditional(h_rebase, rebase);
+    if (can_rebase) cudaGraphSetConditional(h_rebase, rebase);
     if (step == 0) cudaGraphSetConditional(h_second, done ? 0u : 1u);
     cudaGraphSetConditional(h_eval, done ? 0u : 1u);
 }
@@ -1183,7 +1168,7 @@ static cpmdp_status record_dense_pi(Factors &F, float *V, uint8_t *pi, const Sol
         if (ce != cudaSuccess) return cuda_fail(ce, "memset");
         cpmdp_status cs = tc_sweep(F, in, outv, nullptr, true, rb, cap, pi);
         if (cs != CPMDP_OK) return cs;
-        pi_eval_ctl_kernel<<<1, 1, 0, cap>>>(c, rb, F.d_tc_err, o.eval_tol, step, h_eval, hr, h_second);
+        pi_eval_ctl_kernel<<<1, 1, 0, cap>>>(c, rb, F.d_tc_err, o.eval_tol, step, 1, h_eval, hr, h_second);
         return launched("evaluation control kernel");
     };
     auto rebase_body = [&](const float *cur) -> cpmdp_status {

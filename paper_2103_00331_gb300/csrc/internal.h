@@ -119,6 +119,18 @@ struct Factors {
     int dense_pi_graph_rounds = 0;
     int dense_pi_graph_eval_iter = 0;
     int dense_pi_graph_partial = -1;
+    cudaGraphExec_t simt_graph = nullptr;       // FP32 / FP64 dense VI or PI, recorded once per (buffers, options)
+    void *simt_graph_V = nullptr;
+    void *simt_graph_pi = nullptr;
+    void *simt_graph_trace = nullptr;
+    int simt_graph_pim = -1;
+    int simt_graph_prec = -1;
+    double simt_graph_tol = 0;
+    double simt_graph_eval_tol = 0;
+    int simt_graph_max_iter = 0;
+    int simt_graph_rounds = 0;
+    int simt_graph_eval_iter = 0;
+    int simt_graph_partial = -1;
     int *d_tc_err = nullptr;           // error word of the tensor-core kernels
     // barrier-free FP32 solver (flow_solve.cu), allocated on first use
     void *d_flow = nullptr;            // arrival counters + four rings of |S| tagged words
@@ -178,6 +190,45 @@ cpmdp_status dense_tc_backup(const Factors &F, const float *Vin, float *Vout, ui
 cpmdp_status dense_tc_solve(const Factors &F, float *V, uint8_t *pi, const SolveOpts &o, Ctrl *hc, cudaStream_t st);
 cpmdp_status dense_tc_policy_iteration(const Factors &F, float *V, uint8_t *pi, const SolveOpts &o, Ctrl *hc,
                                        cudaStream_t st);
+
+
+// ---------------------------------------------------------------------------
+// Graph-driven dense loops (dense_tc.cu, dense.cu): device control block of
+// policy iteration, its control kernels, and graph-building helpers.
+constexpr size_t kLoopCtlBytes = 256;   // size of the device control block buffer (d_dense_loop)
+
+// Policy-iteration state kept on the device between the graph's kernels.
+struct DensePiCtl {
+    int e;              // evaluation sweeps of this round
+    int cap;            // their limit this round
+    int ok;             // this round's evaluation reached eval_tol
+    int full;           // evaluations run to eval_tol (no cap)
+    int last_rebase;    // evaluation sweep of the last base refresh this round
+    int rebases;
+    int total;          // sweeps (greedy, evaluation, improvement)
+    int rounds;
+    int evals;          // evaluation sweeps of all rounds
+    int conv;
+    int stop;
+    int which;          // buffer of the current iterate: 0 = V, 1 = scratch
+    double res;         // last evaluation residual
+    double hist[8];     // this round's evaluation residuals (sweep j at j mod 8)
+};
+
+__global__ void pi_init_kernel(DensePiCtl *c, const int *err, int max_rounds, cudaGraphConditionalHandle h_round);
+__global__ void pi_round_start_kernel(DensePiCtl *c, int partial_eval, int max_eval_iter,
+                                      cudaGraphConditionalHandle h_eval);
+__global__ void pi_eval_ctl_kernel(DensePiCtl *c, unsigned long long *res_slot, const int *err, double eval_tol,
+                                   int step, int can_rebase, cudaGraphConditionalHandle h_eval,
+                                   cudaGraphConditionalHandle h_rebase, cudaGraphConditionalHandle h_second);
+__global__ void pi_after_eval_kernel(const DensePiCtl *c, cudaGraphConditionalHandle h_odd);
+__global__ void pi_round_end_kernel(DensePiCtl *c, const unsigned *changed, const int *err, int max_rounds,
+                                    cudaGraphConditionalHandle h_round);
+// Nodes of g that no other node depends on.
+cudaError_t graph_leaves(cudaGraph_t g, std::vector<cudaGraphNode_t> &out);
+// Add a conditional node (IF or WHILE) after `deps` in g; returns its body.
+cudaError_t add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
+                            cudaGraphConditionalNodeType type, cudaGraphNode_t *node, cudaGraph_t *body);
 
 }  // namespace cpmdp
 
