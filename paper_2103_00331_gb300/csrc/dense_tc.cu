@@ -83,18 +83,23 @@ __device__ __forceinline__ void sync_for_async() {
 constexpr int kQuadTileBytes = 16384;
 
 // Quads of one staged item (chain c, slab group starting at b0), those with
-// q in [q_lo, q_hi): written from the stage buffer ([slab][q], 32-bit hi/lo
-// words) as 16-byte units of the intermediate layout.
+// q in [q_lo, q_hi): the stage buffer holds the FP32 results ([slab][q]);
+// each quad is split into bf16 hi / lo parts (split_bf16 on each value) and
+// written as one 16-byte unit of the intermediate layout.
 __device__ __forceinline__ void write_quads(uint8_t *T, const uint32_t *stage, int c, int b0, int q_lo, int q_hi,
                                             int tid, int nthreads) {
     uint8_t *Tc = T + (size_t)c * kSlab * kQuadTileBytes + (size_t)((b0 >> 6) * 16 + ((b0 & 63) >> 2)) * 32;
     for (int q = q_lo + tid; q < q_hi; q += nthreads) {
-        const uint32_t w0 = stage[q], w1 = stage[kSlab + q], w2 = stage[2 * kSlab + q], w3 = stage[3 * kSlab + q];
+        const float x0 = __uint_as_float(stage[q]), x1 = __uint_as_float(stage[kSlab + q]);
+        const float x2 = __uint_as_float(stage[2 * kSlab + q]), x3 = __uint_as_float(stage[3 * kSlab + q]);
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(x0, x1), h23 = __floats2bfloat162_rn(x2, x3);
+        const __nv_bfloat162 l01 = __floats2bfloat162_rn(x0 - __low2float(h01), x1 - __high2float(h01));
+        const __nv_bfloat162 l23 = __floats2bfloat162_rn(x2 - __low2float(h23), x3 - __high2float(h23));
         uint4 v;
-        v.x = (w0 & 0xFFFFu) | (w1 << 16);
-        v.y = (w2 & 0xFFFFu) | (w3 << 16);
-        v.z = (w0 >> 16) | (w1 & 0xFFFF0000u);
-        v.w = (w2 >> 16) | (w3 & 0xFFFF0000u);
+        v.x = *reinterpret_cast<const uint32_t *>(&h01);
+        v.y = *reinterpret_cast<const uint32_t *>(&h23);
+        v.z = *reinterpret_cast<const uint32_t *>(&l01);
+        v.w = *reinterpret_cast<const uint32_t *>(&l23);
         *reinterpret_cast<uint4 *>(Tc + (size_t)(q >> 1) * (2 * kQuadTileBytes) + (q & 1) * 16) = v;
     }
 }
@@ -110,7 +115,7 @@ __device__ __forceinline__ void write_quads(uint8_t *T, const uint32_t *stage, i
 //   CONV: D1[p] -> A2 (bf16 hi/lo, MN-major: each thread writes its own
 //         accumulator row as 16-byte chunks, no transpose)
 //   GEMM 2 (D2[p]) = A2 U_3^T            rows (s2, i4'), cols i3'
-//   EPI: D2[p] -> stage (hi/lo words), then the item's quads -> T.
+//   EPI: D2[p] -> stage (FP32), then the item's quads (split to bf16 hi / lo) -> T.
 // The accumulators are double-buffered in TMEM (D1[0..1], D2[0..1]) and the
 // factor tiles in shared memory, so the tensor core runs the GEMMs of one
 // pair or item while the converters work on another: per item the
@@ -125,7 +130,7 @@ constexpr int kACols = 64 * 128 / kAConv;            // accumulator columns per 
 constexpr int kAOffX = 0;                            // 2 pairs x {hi, lo} x 16 KB, K-major
 constexpr int kAOffA2 = 4 * kPairBytes;              // {hi, lo} x 16 KB, MN-major
 constexpr int kAOffU = kAOffA2 + 2 * kPairBytes;     // U3 slots 0, 1 then U4 slots 0, 1 ({hi, lo} each)
-constexpr int kAOffStage = kAOffU + 2 * 4 * kTileBytes;  // 4 slabs x 4096 x 4 B
+constexpr int kAOffStage = kAOffU + 2 * 4 * kTileBytes;  // 4 slabs x 4096 FP32 results
 constexpr int kAOffBar = kAOffStage + 4 * kSlab * 4;
 constexpr int kASmem = kAOffBar + 160 + 1024;
 constexpr uint32_t kConvBar = 1;                     // named barrier of the converter warps
@@ -313,18 +318,12 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
                 tc::mbar_arrive(&a2_full[p]);
             }
         };
-        auto epi = [&](int p) {   // D2[p] -> stage slabs 2p + s2 (row = (s2, i4'), cols i3')
+        auto epi = [&](int p) {   // D2[p] -> stage slabs 2p + s2 (row = (s2, i4'), cols i3'), FP32
             float y[kACols];
             tc::tmem_ld16(tmem + lane_off + 128 + 64 * p + cbase, y);
             uint32_t *dst = stage + (2 * p + s2) * kSlab + cbase * 64 + r63;
 #pragma unroll
-            for (int jj = 0; jj < kACols; jj += 2) {   // two columns per conversion; words (hi | lo << 16)
-                const __nv_bfloat162 h = __floats2bfloat162_rn(y[jj], y[jj + 1]);
-                const __nv_bfloat162 l = __floats2bfloat162_rn(y[jj] - __low2float(h), y[jj + 1] - __high2float(h));
-                const uint32_t hw = *reinterpret_cast<const uint32_t *>(&h), lw = *reinterpret_cast<const uint32_t *>(&l);
-                dst[jj * 64] = __byte_perm(hw, lw, 0x5410);
-                dst[(jj + 1) * 64] = __byte_perm(hw, lw, 0x7632);
-            }
+            for (int jj = 0; jj < kACols; jj++) dst[jj * 64] = __float_as_uint(y[jj]);
         };
         bool ok = true;
         stage_x(sX, V, Vbase, 4 * blockIdx.x, tid);
