@@ -298,17 +298,22 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
         const int s2 = row >> 6, r63 = row & 63;
         // MN-major A2: this thread's row (s2, i3 = r63) -> k = i3, m = s2 * 64 + i4'
         const uint32_t a2_off = (uint32_t)s2 * 8192u + (uint32_t)(r63 >> 3) * 1024u + (uint32_t)(r63 & 7) * 128u;
-        auto conv = [&](int p) {
+        // D1[p] -> A2: the accumulator is loaded and split first, and only the
+        // stores wait for A2 to be free (the GEMM 2 that read it completed:
+        // a2_wait, nullable)
+        auto conv = [&](int p, uint64_t *a2_wait, uint32_t a2_par) -> bool {
             float z[kACols];
             tc::tmem_ld16(tmem + lane_off + 64 * p + cbase, z);
+            uint32_t hi[kACols / 8][4], lo[kACols / 8][4];
+#pragma unroll
+            for (int h = 0; h < kACols / 8; h++) tc::split8_bf16(z + 8 * h, hi[h], lo[h]);
+            if (a2_wait && !conv_wait(a2_wait, a2_par, lane)) return false;
 #pragma unroll
             for (int h = 0; h < kACols / 8; h++) {
-                uint32_t hi[4], lo[4];
-                tc::split8_bf16(z + 8 * h, hi, lo);
                 const uint32_t chunk = (uint32_t)((cbase >> 3) + h);
                 const uint32_t off = a2_off + (((chunk ^ (uint32_t)(r63 & 7)) & 7u) << 4);
-                *reinterpret_cast<uint4 *>(sA2 + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                *reinterpret_cast<uint4 *>(sA2 + kPairBytes + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                *reinterpret_cast<uint4 *>(sA2 + off) = make_uint4(hi[h][0], hi[h][1], hi[h][2], hi[h][3]);
+                *reinterpret_cast<uint4 *>(sA2 + kPairBytes + off) = make_uint4(lo[h][0], lo[h][1], lo[h][2], lo[h][3]);
             }
             tc::fence_proxy_async();
             tc::fence_before();
@@ -317,9 +322,11 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
                 tc::mbar_arrive(&d1_empty[p]);
                 tc::mbar_arrive(&a2_full[p]);
             }
+            return true;
         };
         auto epi = [&](int p) {   // D2[p] -> stage slabs 2p + s2 (row = (s2, i4'), cols i3'), FP32
             float y[kACols];
+            tc::fence_after();
             tc::tmem_ld16(tmem + lane_off + 128 + 64 * p + cbase, y);
             uint32_t *dst = stage + (2 * p + s2) * kSlab + cbase * 64 + r63;
 #pragma unroll
@@ -335,24 +342,25 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
             const int c = it % nchains, gi = it / nchains;
             const int b0 = 4 * (blockIdx.x + gi * gridDim.x);
             const uint32_t par = (uint32_t)(it & 1);
-            // CONV(p0): D1[0] ready; GEMM 2 of the previous item's p1 done (A2 free, D2[1] ready)
+            // CONV(p0): D1[0] ready; its stores once GEMM 2 of the previous item's p1 is done (A2
+            // free, D2[1] ready)
             ok = conv_wait(&d1_full[0], par, lane);
-            if (ok && it >= 1) ok = conv_wait(&d2_full[1], par ^ 1u, lane);
             if (!ok) break;
             tc::fence_after();
-            conv(0);
+            ok = conv(0, it >= 1 ? &d2_full[1] : nullptr, par ^ 1u);
+            if (!ok) break;
             // EPI(previous item, p1), then its quads
             if (pend_c >= 0) {
                 epi(1);
                 tc::named_sync(kConvBar, kAConv);
                 write_quads(T, stage, pend_c, pend_b0, 0, kSlab, tid, kAConv);
             }
-            // CONV(p1): D1[1] ready; GEMM 2 of p0 done (A2 free, D2[0] ready)
+            // CONV(p1): D1[1] ready; its stores once GEMM 2 of p0 is done (A2 free, D2[0] ready)
             ok = conv_wait(&d1_full[1], par, lane);
-            if (ok) ok = conv_wait(&d2_full[0], par, lane);
             if (!ok) break;
             tc::fence_after();
-            conv(1);   // (its barrier also ends the quads' reads of the stage)
+            ok = conv(1, &d2_full[0], par);   // (its barrier also ends the quads' reads of the stage)
+            if (!ok) break;
             epi(0);
             pend_c = c;
             pend_b0 = b0;
