@@ -301,13 +301,20 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
         // D1[p] -> A2: the accumulator is loaded and split first, and only the
         // stores wait for A2 to be free (the GEMM 2 that read it completed:
         // a2_wait, nullable)
-        auto conv = [&](int p, uint64_t *a2_wait, uint32_t a2_par) -> bool {
+        // pre >= 0: once A2 is free (so D2[pre] is complete), the epilogue's
+        // TMEM load of D2[pre] into yr is issued here and completes under the
+        // stores and the barrier (epi waits for it)
+        auto conv = [&](int p, uint64_t *a2_wait, uint32_t a2_par, int pre, uint32_t (&yr)[16]) -> bool {
             float z[kACols];
             tc::tmem_ld16(tmem + lane_off + 64 * p + cbase, z);
             uint32_t hi[kACols / 8][4], lo[kACols / 8][4];
 #pragma unroll
             for (int h = 0; h < kACols / 8; h++) tc::split8_bf16(z + 8 * h, hi[h], lo[h]);
             if (a2_wait && !conv_wait(a2_wait, a2_par, lane)) return false;
+            if (pre >= 0) {
+                tc::fence_after();
+                tc::tmem_ld16_async(tmem + lane_off + 128 + 64 * pre + cbase, yr);
+            }
 #pragma unroll
             for (int h = 0; h < kACols / 8; h++) {
                 const uint32_t chunk = (uint32_t)((cbase >> 3) + h);
@@ -324,14 +331,13 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
             }
             return true;
         };
-        auto epi = [&](int p) {   // D2[p] -> stage slabs 2p + s2 (row = (s2, i4'), cols i3'), FP32
-            float y[kACols];
-            tc::fence_after();
-            tc::tmem_ld16(tmem + lane_off + 128 + 64 * p + cbase, y);
+        auto epi = [&](int p, uint32_t (&yr)[16]) {   // D2[p] (loaded into yr) -> stage slabs 2p + s2, FP32
+            tc::tmem_wait16(yr);                        // (row = (s2, i4'), cols i3')
             uint32_t *dst = stage + (2 * p + s2) * kSlab + cbase * 64 + r63;
 #pragma unroll
-            for (int jj = 0; jj < kACols; jj++) dst[jj * 64] = __float_as_uint(y[jj]);
+            for (int jj = 0; jj < kACols; jj++) dst[jj * 64] = yr[jj];
         };
+        uint32_t yr[16];
         bool ok = true;
         stage_x(sX, V, Vbase, 4 * blockIdx.x, tid);
         tc::fence_proxy_async();
@@ -347,11 +353,11 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
             ok = conv_wait(&d1_full[0], par, lane);
             if (!ok) break;
             tc::fence_after();
-            ok = conv(0, it >= 1 ? &d2_full[1] : nullptr, par ^ 1u);
+            ok = conv(0, it >= 1 ? &d2_full[1] : nullptr, par ^ 1u, pend_c >= 0 ? 1 : -1, yr);
             if (!ok) break;
             // EPI(previous item, p1), then its quads
             if (pend_c >= 0) {
-                epi(1);
+                epi(1, yr);
                 tc::named_sync(kConvBar, kAConv);
                 write_quads(T, stage, pend_c, pend_b0, 0, kSlab, tid, kAConv);
             }
@@ -359,9 +365,9 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
             ok = conv_wait(&d1_full[1], par, lane);
             if (!ok) break;
             tc::fence_after();
-            ok = conv(1, &d2_full[0], par);   // (its barrier also ends the quads' reads of the stage)
+            ok = conv(1, &d2_full[0], par, 0, yr);   // (its barrier also ends the quads' reads of the stage)
             if (!ok) break;
-            epi(0);
+            epi(0, yr);
             pend_c = c;
             pend_b0 = b0;
             // last chain of the group: GEMM 1 of this item is complete, restage X
@@ -376,7 +382,8 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
             ok = conv_wait(&d2_full[1], (uint32_t)((nitems - 1) & 1), lane);
             if (ok) {
                 tc::fence_after();
-                epi(1);
+                tc::tmem_ld16_async(tmem + lane_off + 128 + 64 + cbase, yr);
+                epi(1, yr);
                 tc::named_sync(kConvBar, kAConv);
                 write_quads(T, stage, pend_c, pend_b0, 0, kSlab, tid, kAConv);
             }
