@@ -107,48 +107,49 @@ __device__ __forceinline__ void write_quads(uint8_t *T, const uint32_t *stage, i
 // ---------------------------------------------------------------------------
 // pass A: slabs of V (minus V_base when given) -> T_c for every chain c
 //
-// Warp-specialised: one control thread issues the GEMMs and the factor
-// copies; 16 converter warps move data between TMEM, shared memory and
-// global memory. An item is (slab group g, chain c); per item and pair p of
-// the group's two slab pairs:
-//   GEMM 1 (D1[p]) = X_p U_4^T           rows (s2, i3), cols i4'
-//   CONV: D1[p] -> A2 (bf16 hi/lo, MN-major: each thread writes its own
-//         accumulator row as 16-byte chunks, no transpose)
-//   GEMM 2 (D2[p]) = A2 U_3^T            rows (s2, i4'), cols i3'
-//   EPI: D2[p] -> stage (FP32), then the item's quads (split to bf16 hi / lo) -> T.
-// The accumulators are double-buffered in TMEM (D1[0..1], D2[0..1]) and the
-// factor tiles in shared memory, so the tensor core runs the GEMMs of one
-// pair or item while the converters work on another: per item the
-// converters run CONV(p0), EPI(previous item, p1) + its quads, CONV(p1),
-// EPI(p0). Every wait is bounded; a wait that runs out sets the error word
-// and every role leaves its loop (the converters decide together, so the
-// named barriers stay matched).
+// Warp-specialised in three roles. An item is (slab group g, chain c); per
+// item and pair p of the group's two slab pairs:
+//   GEMM 1 (D1[p]) = X_p U_4^T            rows (s2, i3), cols i4'
+//   CONV (group C): D1[p] -> A2 (bf16 hi/lo, MN-major: each thread writes
+//        its own accumulator row as 16-byte chunks, no transpose)
+//   GEMM 2 (D2[p]) = A2 U_3^T             rows (s2, i4'), cols i3'
+//   EPI (group E): D2[p] -> stage (FP32); after both pairs, the item's
+//        quads (split to bf16 hi / lo) -> T.
+// One control thread issues the GEMMs (the next item's GEMM 1 ahead of this
+// item's GEMM 2) and the factor copies (U_3 and U_4 rings, refilled as soon
+// as the GEMM that read a slot completes). The two converter groups (8 warps
+// each, two per TMEM lane quarter) never wait for each other: group C works
+// on one item's conversions while group E writes out another's quads, and
+// the tensor core runs the GEMMs in between. Within a group the warps decide
+// every wait together (named AND barrier of the group), so a wait that runs
+// out stops the whole group and no named barrier is left half-entered; the
+// error word is set and every role leaves its loop.
 
-constexpr int kAConv = 512;                          // converter threads
-constexpr int kAThreads = kAConv + 32;               // + the control warp
-constexpr int kACols = 64 * 128 / kAConv;            // accumulator columns per converter thread
+constexpr int kAGroup = 256;                         // threads of one converter group
+constexpr int kAThreads = 2 * kAGroup + 32;          // group C, group E, the control warp
+constexpr int kACols = 64 * 128 / kAGroup;           // accumulator columns per converter thread
 constexpr int kAOffX = 0;                            // 2 pairs x {hi, lo} x 16 KB, K-major
 constexpr int kAOffA2 = 4 * kPairBytes;              // {hi, lo} x 16 KB, MN-major
 constexpr int kAOffU = kAOffA2 + 2 * kPairBytes;     // U3 slots 0, 1 then U4 slots 0, 1 ({hi, lo} each)
 constexpr int kAOffStage = kAOffU + 2 * 4 * kTileBytes;  // 4 slabs x 4096 FP32 results
 constexpr int kAOffBar = kAOffStage + 4 * kSlab * 4;
-constexpr int kASmem = kAOffBar + 160 + 1024;
-constexpr uint32_t kConvBar = 1;                     // named barrier of the converter warps
+constexpr int kASmem = kAOffBar + 192 + 1024;
+constexpr uint32_t kBarC = 1, kBarE = 2;             // named barriers of the two groups
 
-// Converter-side wait: lane 0 of every converter warp polls the mbarrier
-// (bounded); the converters then agree on the outcome (named AND barrier),
-// so they all continue or all stop.
-__device__ __forceinline__ bool conv_wait(uint64_t *mbar, uint32_t parity, int lane) {
+// Group-side wait: lane 0 of every warp of the group polls the mbarrier
+// (bounded); the group then agrees on the outcome (named AND barrier).
+__device__ __forceinline__ bool group_wait(uint64_t *mbar, uint32_t parity, int lane, uint32_t bar) {
     bool ok = true;
     if (lane == 0) ok = tc::mbar_wait(mbar, parity, kWaitCycles);
     ok = __shfl_sync(0xFFFFFFFFu, ok ? 1 : 0, 0) != 0;
-    return tc::named_and(kConvBar, kAConv, ok);
+    return tc::named_and(bar, kAGroup, ok);
 }
 
 // Stage the group's 4 slabs (b0 .. b0+3) of V (- V_base) as two K-major
-// pair tiles, bf16 hi / lo: row = (s % 2) * 64 + i3, k = i4.
-__device__ __forceinline__ void stage_x(uint8_t *sX, const float *V, const float *Vbase, int b0, int tid) {
-    for (int e4 = tid; e4 < kSlab; e4 += kAConv) {   // 4 consecutive elements per step
+// pair tiles, bf16 hi / lo: row = (s % 2) * 64 + i3, k = i4 (by the
+// kAGroup threads of group C, gtid = 0 .. kAGroup - 1).
+__device__ __forceinline__ void stage_x(uint8_t *sX, const float *V, const float *Vbase, int b0, int gtid) {
+    for (int e4 = gtid; e4 < kSlab; e4 += kAGroup) {   // 4 consecutive elements per step
         const int s = e4 >> 10, rem = (e4 & 1023) * 4;
         const size_t gi = (size_t)(b0 + s) * kSlab + rem;
         float4 x = *reinterpret_cast<const float4 *>(V + gi);
@@ -177,13 +178,14 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
     uint8_t *sA2 = sm + kAOffA2;
     uint32_t *stage = reinterpret_cast<uint32_t *>(sm + kAOffStage);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kAOffBar);
-    uint64_t *d1_full = bars + 0, *d1_empty = bars + 2, *d2_full = bars + 4, *a2_full = bars + 6;
-    uint64_t *u3_full = bars + 8, *u3_free = bars + 10, *u4_full = bars + 12, *u4_free = bars + 14;
-    uint64_t *x_full = bars + 16, *fin = bars + 17;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kAOffBar + 144);
+    uint64_t *d1_full = bars + 0, *d1_empty = bars + 2, *d2_full = bars + 4, *d2_empty = bars + 6;
+    uint64_t *a2_full = bars + 8, *u3_full = bars + 10, *u3_free = bars + 12, *u4_full = bars + 14;
+    uint64_t *u4_free = bars + 16, *x_full = bars + 18, *fin = bars + 19;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kAOffBar + 160);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        for (int i = 0; i < 18; i++) tc::mbar_init(&bars[i], 1);
+        // d1_empty, d2_empty and a2_full take one arrival per warp of their group
+        for (int i = 0; i < 20; i++) tc::mbar_init(&bars[i], (i >= 2 && i < 4) || (i >= 6 && i < 10) ? kAGroup / 32 : 1);
     }
     if (warp == 0) tc::tmem_alloc(tslot, 256);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -194,14 +196,16 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
     const int ngroups = kSlab / 4;
     const int my_groups = blockIdx.x < ngroups ? (ngroups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int nitems = my_groups * nchains;
+    // converter threads: accumulator row (TMEM lane) and first column
+    const int row = tid & 127, cbase = kACols * ((warp >> 2) & 1);
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    const int s2 = row >> 6, r63 = row & 63;
 
-    if (warp == kAConv / 32) {
+    if (warp == 2 * kAGroup / 32) {
         // ---------------- control thread ----------------
         // Issue order: GEMM 1 of item 0, then per item it: GEMM 2 (it, p0),
-        // GEMM 1 (it+1, p0), GEMM 2 (it, p1), GEMM 1 (it+1, p1), so the next
-        // item's first GEMMs run while the converters work on this item.
-        // Factor rings: U4 of item j in slot j % 2 (free once GEMM 1 of item
-        // j completed), U3 of item j in slot j % 2 (free once GEMM 2 of j did).
+        // GEMM 1 (it+1, p0), GEMM 2 (it, p1), GEMM 1 (it+1, p1) (at a group
+        // change both GEMM 2 first: X is restaged after this item's CONV).
         if (lane == 0 && nitems > 0) {
             const uint32_t aX = tc::smem_u32(sX), aA2 = tc::smem_u32(sA2), aU = tc::smem_u32(sm + kAOffU);
             int issued3 = 0, landed3 = 0, issued4 = 0, landed4 = 0;   // factor copies issued / waited for
@@ -216,8 +220,8 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
                 tc::bulk_g2s(aU + (2 + sl) * 2 * kTileBytes, utile(U, j % nchains, 3, 0), 2 * kTileBytes,
                              &u4_full[sl]);
             };
-            // GEMM 1 (j, p) once D1[p] was read by CONV (j-1, p); for p = 0 also
-            // wait for X (first chain of a group) and for U4 of item j
+            // GEMM 1 (j, p) once group C has read D1[p] of item j-1; for p = 0
+            // also X (first chain of a group) and U4 of item j
             auto gemm1 = [&](int j, int p) -> bool {
                 const int sl = j & 1;
                 if (p == 0) {
@@ -234,9 +238,11 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
                 if (p == 1) tc::commit(&u4_free[sl]);
                 return true;
             };
+            // GEMM 2 (it, p) once group C wrote A2 and group E has read D2[p] of item it-1
             auto gemm2 = [&](int it, int p) -> bool {
                 const int sl = it & 1;
                 if (!tc::mbar_wait(&a2_full[p], (uint32_t)(it & 1), kWaitCycles)) return false;
+                if (!tc::mbar_wait(&d2_empty[p], (uint32_t)((it & 1) ^ 1), kWaitCycles)) return false;
                 tc::fence_after();
                 const uint32_t u3 = aU + sl * 2 * kTileBytes;
                 tc::mma_bf16x3_amn(tmem + 128 + 64 * p, aA2, aA2 + kPairBytes, u3, u3 + kTileBytes, 0);
@@ -262,17 +268,14 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
                 ok = tc::mbar_wait(&u3_full[sl], (uint32_t)((it >> 1) & 1), kWaitCycles);
                 if (!ok) break;
                 landed3++;
-                // the next item's GEMM 1 (p0) goes first (D1[0] is free as soon as
-                // A2 holds this item's p0), except at a group change, where X is
-                // restaged only after this item's CONV (p1)
                 const bool next = it + 1 < nitems, newgroup = next && (it + 1) % nchains == 0;
-                if (next && !newgroup) ok = gemm1(it + 1, 0);
-                ok = ok && gemm2(it, 0);
+                ok = gemm2(it, 0);
                 // U3 of item it+1 into the slot GEMM 2 (it-1) has finished with
                 if (ok && it >= 1 && next) {
                     ok = tc::mbar_wait(&u3_free[sl ^ 1], (uint32_t)(((it - 1) >> 1) & 1), kWaitCycles);
                     if (ok) issue_u3();
                 }
+                if (ok && next && !newgroup) ok = gemm1(it + 1, 0);
                 ok = ok && gemm2(it, 1);
                 if (ok && newgroup) ok = gemm1(it + 1, 0);
                 if (ok && next) ok = gemm1(it + 1, 1);
@@ -291,104 +294,80 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
             }
         }
         __syncwarp();
-    } else if (nitems > 0) {
-        // ---------------- converter warps ----------------
-        const int row = tid & 127, cbase = kACols * (tid >> 7);   // accumulator row, first column
-        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
-        const int s2 = row >> 6, r63 = row & 63;
+    } else if (warp < kAGroup / 32 && nitems > 0) {
+        // ---------------- group C: D1 -> A2 ----------------
         // MN-major A2: this thread's row (s2, i3 = r63) -> k = i3, m = s2 * 64 + i4'
         const uint32_t a2_off = (uint32_t)s2 * 8192u + (uint32_t)(r63 >> 3) * 1024u + (uint32_t)(r63 & 7) * 128u;
-        // D1[p] -> A2: the accumulator is loaded and split first, and only the
-        // stores wait for A2 to be free (the GEMM 2 that read it completed:
-        // a2_wait, nullable)
-        // pre >= 0: once A2 is free (so D2[pre] is complete), the epilogue's
-        // TMEM load of D2[pre] into yr is issued here and completes under the
-        // stores and the barrier (epi waits for it)
-        auto conv = [&](int p, uint64_t *a2_wait, uint32_t a2_par, int pre, uint32_t (&yr)[16]) -> bool {
-            float z[kACols];
-            tc::tmem_ld16(tmem + lane_off + 64 * p + cbase, z);
-            uint32_t hi[kACols / 8][4], lo[kACols / 8][4];
-#pragma unroll
-            for (int h = 0; h < kACols / 8; h++) tc::split8_bf16(z + 8 * h, hi[h], lo[h]);
-            if (a2_wait && !conv_wait(a2_wait, a2_par, lane)) return false;
-            if (pre >= 0) {
-                tc::fence_after();
-                tc::tmem_ld16_async(tmem + lane_off + 128 + 64 * pre + cbase, yr);
-            }
-#pragma unroll
-            for (int h = 0; h < kACols / 8; h++) {
-                const uint32_t chunk = (uint32_t)((cbase >> 3) + h);
-                const uint32_t off = a2_off + (((chunk ^ (uint32_t)(r63 & 7)) & 7u) << 4);
-                *reinterpret_cast<uint4 *>(sA2 + off) = make_uint4(hi[h][0], hi[h][1], hi[h][2], hi[h][3]);
-                *reinterpret_cast<uint4 *>(sA2 + kPairBytes + off) = make_uint4(lo[h][0], lo[h][1], lo[h][2], lo[h][3]);
-            }
-            tc::fence_proxy_async();
-            tc::fence_before();
-            tc::named_sync(kConvBar, kAConv);
-            if (tid == 0) {
-                tc::mbar_arrive(&d1_empty[p]);
-                tc::mbar_arrive(&a2_full[p]);
-            }
-            return true;
-        };
-        auto epi = [&](int p, uint32_t (&yr)[16]) {   // D2[p] (loaded into yr) -> stage slabs 2p + s2, FP32
-            tc::tmem_wait16(yr);                        // (row = (s2, i4'), cols i3')
-            uint32_t *dst = stage + (2 * p + s2) * kSlab + cbase * 64 + r63;
-#pragma unroll
-            for (int jj = 0; jj < kACols; jj++) dst[jj * 64] = yr[jj];
-        };
-        uint32_t yr[16];
         bool ok = true;
         stage_x(sX, V, Vbase, 4 * blockIdx.x, tid);
         tc::fence_proxy_async();
-        tc::named_sync(kConvBar, kAConv);
+        tc::named_sync(kBarC, kAGroup);
         if (tid == 0) tc::mbar_arrive(x_full);
-        int pend_c = -1, pend_b0 = 0;   // item whose slabs 2, 3 are still in D2[1]
-        for (int it = 0; it < nitems; it++) {
+        for (int it = 0; it < nitems && ok; it++) {
             const int c = it % nchains, gi = it / nchains;
-            const int b0 = 4 * (blockIdx.x + gi * gridDim.x);
-            const uint32_t par = (uint32_t)(it & 1);
-            // CONV(p0): D1[0] ready; its stores once GEMM 2 of the previous item's p1 is done (A2
-            // free, D2[1] ready)
-            ok = conv_wait(&d1_full[0], par, lane);
-            if (!ok) break;
-            tc::fence_after();
-            ok = conv(0, it >= 1 ? &d2_full[1] : nullptr, par ^ 1u, pend_c >= 0 ? 1 : -1, yr);
-            if (!ok) break;
-            // EPI(previous item, p1), then its quads
-            if (pend_c >= 0) {
-                epi(1, yr);
-                tc::named_sync(kConvBar, kAConv);
-                write_quads(T, stage, pend_c, pend_b0, 0, kSlab, tid, kAConv);
+            for (int p = 0; p < 2; p++) {
+                ok = group_wait(&d1_full[p], (uint32_t)(it & 1), lane, kBarC);
+                if (!ok) break;
+                tc::fence_after();
+                float z[kACols];
+                tc::tmem_ld32(tmem + lane_off + 64 * p + cbase, z);   // row (s2, i3), cols i4'
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&d1_empty[p]);
+                uint32_t hi[kACols / 8][4], lo[kACols / 8][4];
+#pragma unroll
+                for (int h = 0; h < kACols / 8; h++) tc::split8_bf16(z + 8 * h, hi[h], lo[h]);
+                // A2 is free once the GEMM 2 that read it last completed: (it-1, p1) before p0, (it, p0) before p1
+                if (p == 0 && it >= 1) ok = group_wait(&d2_full[1], (uint32_t)((it - 1) & 1), lane, kBarC);
+                if (p == 1) ok = group_wait(&d2_full[0], (uint32_t)(it & 1), lane, kBarC);
+                if (!ok) break;
+#pragma unroll
+                for (int h = 0; h < kACols / 8; h++) {
+                    const uint32_t chunk = (uint32_t)((cbase >> 3) + h);
+                    const uint32_t off = a2_off + (((chunk ^ (uint32_t)(r63 & 7)) & 7u) << 4);
+                    *reinterpret_cast<uint4 *>(sA2 + off) = make_uint4(hi[h][0], hi[h][1], hi[h][2], hi[h][3]);
+                    *reinterpret_cast<uint4 *>(sA2 + kPairBytes + off) =
+                        make_uint4(lo[h][0], lo[h][1], lo[h][2], lo[h][3]);
+                }
+                tc::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&a2_full[p]);
             }
-            // CONV(p1): D1[1] ready; its stores once GEMM 2 of p0 is done (A2 free, D2[0] ready)
-            ok = conv_wait(&d1_full[1], par, lane);
-            if (!ok) break;
-            tc::fence_after();
-            ok = conv(1, &d2_full[0], par, 0, yr);   // (its barrier also ends the quads' reads of the stage)
-            if (!ok) break;
-            epi(0, yr);
-            pend_c = c;
-            pend_b0 = b0;
-            // last chain of the group: GEMM 1 of this item is complete, restage X
-            if (c == nchains - 1 && gi + 1 < my_groups) {
+            // last chain of the group: both GEMM 1 of this item are complete, restage X
+            if (ok && c == nchains - 1 && gi + 1 < my_groups) {
                 stage_x(sX, V, Vbase, 4 * (blockIdx.x + (gi + 1) * gridDim.x), tid);
                 tc::fence_proxy_async();
-                tc::named_sync(kConvBar, kAConv);
+                tc::named_sync(kBarC, kAGroup);
                 if (tid == 0) tc::mbar_arrive(x_full);
             }
         }
-        if (ok && pend_c >= 0) {
-            ok = conv_wait(&d2_full[1], (uint32_t)((nitems - 1) & 1), lane);
-            if (ok) {
-                tc::fence_after();
-                tc::tmem_ld16_async(tmem + lane_off + 128 + 64 + cbase, yr);
-                epi(1, yr);
-                tc::named_sync(kConvBar, kAConv);
-                write_quads(T, stage, pend_c, pend_b0, 0, kSlab, tid, kAConv);
-            }
-        }
         if (!ok && tid == 0) atomicExch(err, (int)CPMDP_ETIMEOUT);
+    } else if (nitems > 0) {
+        // ---------------- group E: D2 -> stage -> quads of T ----------------
+        const int etid = tid - kAGroup;
+        bool ok = true;
+        for (int it = 0; it < nitems && ok; it++) {
+            const int c = it % nchains, gi = it / nchains;
+            const int b0 = 4 * (blockIdx.x + gi * gridDim.x);
+            for (int p = 0; p < 2; p++) {
+                ok = group_wait(&d2_full[p], (uint32_t)(it & 1), lane, kBarE);
+                if (!ok) break;
+                tc::fence_after();
+                float y[kACols];
+                tc::tmem_ld32(tmem + lane_off + 128 + 64 * p + cbase, y);   // row (s2, i4'), cols i3'
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&d2_empty[p]);
+                uint32_t *dst = stage + (2 * p + s2) * kSlab + cbase * 64 + r63;
+#pragma unroll
+                for (int jj = 0; jj < kACols; jj++) dst[jj * 64] = __float_as_uint(y[jj]);
+            }
+            if (!ok) break;
+            tc::named_sync(kBarE, kAGroup);   // the item's four slabs are staged
+            write_quads(T, stage, c, b0, 0, kSlab, etid, kAGroup);
+            tc::named_sync(kBarE, kAGroup);   // and read: the stage is free again
+        }
+        if (!ok && etid == 0) atomicExch(err, (int)CPMDP_ETIMEOUT);
     }
     tc::fence_before();
     __syncthreads();
