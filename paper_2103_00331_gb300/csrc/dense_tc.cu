@@ -118,16 +118,17 @@ __device__ __forceinline__ void write_quads(uint8_t *T, const uint32_t *stage, i
 // One control thread issues the GEMMs (the next item's GEMM 1 ahead of this
 // item's GEMM 2) and the factor copies (U_3 and U_4 rings, refilled as soon
 // as the GEMM that read a slot completes). The two converter groups (8 warps
-// each, two per TMEM lane quarter) never wait for each other: group C works
+// of 8 and 16 warps, two and four per TMEM lane quarter) never wait for each other: group C works
 // on one item's conversions while group E writes out another's quads, and
 // the tensor core runs the GEMMs in between. Within a group the warps decide
 // every wait together (named AND barrier of the group), so a wait that runs
 // out stops the whole group and no named barrier is left half-entered; the
 // error word is set and every role leaves its loop.
 
-constexpr int kAGroup = 256;                         // threads of one converter group
-constexpr int kAThreads = 2 * kAGroup + 32;          // group C, group E, the control warp
-constexpr int kACols = 64 * 128 / kAGroup;           // accumulator columns per converter thread
+constexpr int kAGroupC = 256;                        // group C: 8 warps, 32 accumulator columns per thread
+constexpr int kAGroupE = 512;                        // group E: 16 warps, 16 columns per thread
+constexpr int kAThreads = kAGroupC + kAGroupE + 32;  // + the control warp
+constexpr int kAColsC = 64 * 128 / kAGroupC, kAColsE = 64 * 128 / kAGroupE;
 constexpr int kAOffX = 0;                            // 2 pairs x {hi, lo} x 16 KB, K-major
 constexpr int kAOffA2 = 4 * kPairBytes;              // {hi, lo} x 16 KB, MN-major
 constexpr int kAOffU = kAOffA2 + 2 * kPairBytes;     // U3 slots 0, 1 then U4 slots 0, 1 ({hi, lo} each)
@@ -137,19 +138,20 @@ constexpr int kASmem = kAOffBar + 192 + 1024;
 constexpr uint32_t kBarC = 1, kBarE = 2;             // named barriers of the two groups
 
 // Group-side wait: lane 0 of every warp of the group polls the mbarrier
-// (bounded); the group then agrees on the outcome (named AND barrier).
-__device__ __forceinline__ bool group_wait(uint64_t *mbar, uint32_t parity, int lane, uint32_t bar) {
+// (bounded); the group (n threads) then agrees on the outcome (named AND
+// barrier).
+__device__ __forceinline__ bool group_wait(uint64_t *mbar, uint32_t parity, int lane, uint32_t bar, uint32_t n) {
     bool ok = true;
     if (lane == 0) ok = tc::mbar_wait(mbar, parity, kWaitCycles);
     ok = __shfl_sync(0xFFFFFFFFu, ok ? 1 : 0, 0) != 0;
-    return tc::named_and(bar, kAGroup, ok);
+    return tc::named_and(bar, n, ok);
 }
 
 // Stage the group's 4 slabs (b0 .. b0+3) of V (- V_base) as two K-major
 // pair tiles, bf16 hi / lo: row = (s % 2) * 64 + i3, k = i4 (by the
-// kAGroup threads of group C, gtid = 0 .. kAGroup - 1).
+// kAGroupC threads of group C, gtid = 0 .. kAGroupC - 1).
 __device__ __forceinline__ void stage_x(uint8_t *sX, const float *V, const float *Vbase, int b0, int gtid) {
-    for (int e4 = gtid; e4 < kSlab; e4 += kAGroup) {   // 4 consecutive elements per step
+    for (int e4 = gtid; e4 < kSlab; e4 += kAGroupC) {   // 4 consecutive elements per step
         const int s = e4 >> 10, rem = (e4 & 1023) * 4;
         const size_t gi = (size_t)(b0 + s) * kSlab + rem;
         float4 x = *reinterpret_cast<const float4 *>(V + gi);
@@ -185,7 +187,10 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         // d1_empty, d2_empty and a2_full take one arrival per warp of their group
-        for (int i = 0; i < 20; i++) tc::mbar_init(&bars[i], (i >= 2 && i < 4) || (i >= 6 && i < 10) ? kAGroup / 32 : 1);
+        for (int i = 0; i < 20; i++) {
+            const bool by_c = (i >= 2 && i < 4) || (i >= 8 && i < 10), by_e = i >= 6 && i < 8;
+            tc::mbar_init(&bars[i], by_c ? kAGroupC / 32 : by_e ? kAGroupE / 32 : 1);
+        }
     }
     if (warp == 0) tc::tmem_alloc(tslot, 256);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -196,12 +201,12 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
     const int ngroups = kSlab / 4;
     const int my_groups = blockIdx.x < ngroups ? (ngroups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int nitems = my_groups * nchains;
-    // converter threads: accumulator row (TMEM lane) and first column
-    const int row = tid & 127, cbase = kACols * ((warp >> 2) & 1);
+    // converter threads: accumulator row (TMEM lane; warp w reads lane quarter w % 4)
+    const int row = tid & 127;
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     const int s2 = row >> 6, r63 = row & 63;
 
-    if (warp == 2 * kAGroup / 32) {
+    if (warp == (kAGroupC + kAGroupE) / 32) {
         // ---------------- control thread ----------------
         // Issue order: GEMM 1 of item 0, then per item it: GEMM 2 (it, p0),
         // GEMM 1 (it+1, p0), GEMM 2 (it, p1), GEMM 1 (it+1, p1) (at a group
@@ -259,12 +264,6 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
             bool ok = gemm1(0, 0) && gemm1(0, 1);
             for (int it = 0; it < nitems && ok; it++) {
                 const int sl = it & 1;
-                // U4 of item it+2 into the slot GEMM 1 (it) has finished with
-                if (it + 2 < nitems) {
-                    ok = tc::mbar_wait(&u4_free[sl], (uint32_t)((it >> 1) & 1), kWaitCycles);
-                    if (!ok) break;
-                    issue_u4();
-                }
                 ok = tc::mbar_wait(&u3_full[sl], (uint32_t)((it >> 1) & 1), kWaitCycles);
                 if (!ok) break;
                 landed3++;
@@ -279,6 +278,12 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
                 ok = ok && gemm2(it, 1);
                 if (ok && newgroup) ok = gemm1(it + 1, 0);
                 if (ok && next) ok = gemm1(it + 1, 1);
+                // U4 of item it+2 into the slot GEMM 1 (it) has finished with (issued an item
+                // ago, so this wait rarely blocks; item it+2's GEMM 1 is an item away)
+                if (ok && it + 2 < nitems) {
+                    ok = tc::mbar_wait(&u4_free[sl], (uint32_t)((it >> 1) & 1), kWaitCycles);
+                    if (ok) issue_u4();
+                }
             }
             // the last item's commit: every MMA of this CTA has completed
             if (ok) ok = tc::mbar_wait(&u3_free[(nitems - 1) & 1], (uint32_t)(((nitems - 1) >> 1) & 1), kWaitCycles);
@@ -294,41 +299,50 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
             }
         }
         __syncwarp();
-    } else if (warp < kAGroup / 32 && nitems > 0) {
+    } else if (warp < kAGroupC / 32 && nitems > 0) {
         // ---------------- group C: D1 -> A2 ----------------
+        // columns cbase .. cbase + 31 of this thread's row, in two halves of 16
+        const int cbase = kAColsC * ((warp >> 2) & 1);
         // MN-major A2: this thread's row (s2, i3 = r63) -> k = i3, m = s2 * 64 + i4'
         const uint32_t a2_off = (uint32_t)s2 * 8192u + (uint32_t)(r63 >> 3) * 1024u + (uint32_t)(r63 & 7) * 128u;
+        auto store_a2 = [&](int col0, const uint32_t (&hi)[2][4], const uint32_t (&lo)[2][4]) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t chunk = (uint32_t)((col0 >> 3) + h);
+                const uint32_t off = a2_off + (((chunk ^ (uint32_t)(r63 & 7)) & 7u) << 4);
+                *reinterpret_cast<uint4 *>(sA2 + off) = make_uint4(hi[h][0], hi[h][1], hi[h][2], hi[h][3]);
+                *reinterpret_cast<uint4 *>(sA2 + kPairBytes + off) = make_uint4(lo[h][0], lo[h][1], lo[h][2], lo[h][3]);
+            }
+        };
         bool ok = true;
         stage_x(sX, V, Vbase, 4 * blockIdx.x, tid);
         tc::fence_proxy_async();
-        tc::named_sync(kBarC, kAGroup);
+        tc::named_sync(kBarC, kAGroupC);
         if (tid == 0) tc::mbar_arrive(x_full);
         for (int it = 0; it < nitems && ok; it++) {
             const int c = it % nchains, gi = it / nchains;
             for (int p = 0; p < 2; p++) {
-                ok = group_wait(&d1_full[p], (uint32_t)(it & 1), lane, kBarC);
+                ok = group_wait(&d1_full[p], (uint32_t)(it & 1), lane, kBarC, kAGroupC);
                 if (!ok) break;
                 tc::fence_after();
-                float z[kACols];
-                tc::tmem_ld32(tmem + lane_off + 64 * p + cbase, z);   // row (s2, i3), cols i4'
+                float z0[16], z1[16];
+                tc::tmem_ld16(tmem + lane_off + 64 * p + cbase, z0);        // row (s2, i3), cols i4'
+                tc::tmem_ld16(tmem + lane_off + 64 * p + cbase + 16, z1);
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&d1_empty[p]);
-                uint32_t hi[kACols / 8][4], lo[kACols / 8][4];
+                uint32_t hi0[2][4], lo0[2][4], hi1[2][4], lo1[2][4];
 #pragma unroll
-                for (int h = 0; h < kACols / 8; h++) tc::split8_bf16(z + 8 * h, hi[h], lo[h]);
-                // A2 is free once the GEMM 2 that read it last completed: (it-1, p1) before p0, (it, p0) before p1
-                if (p == 0 && it >= 1) ok = group_wait(&d2_full[1], (uint32_t)((it - 1) & 1), lane, kBarC);
-                if (p == 1) ok = group_wait(&d2_full[0], (uint32_t)(it & 1), lane, kBarC);
-                if (!ok) break;
-#pragma unroll
-                for (int h = 0; h < kACols / 8; h++) {
-                    const uint32_t chunk = (uint32_t)((cbase >> 3) + h);
-                    const uint32_t off = a2_off + (((chunk ^ (uint32_t)(r63 & 7)) & 7u) << 4);
-                    *reinterpret_cast<uint4 *>(sA2 + off) = make_uint4(hi[h][0], hi[h][1], hi[h][2], hi[h][3]);
-                    *reinterpret_cast<uint4 *>(sA2 + kPairBytes + off) =
-                        make_uint4(lo[h][0], lo[h][1], lo[h][2], lo[h][3]);
+                for (int h = 0; h < 2; h++) {
+                    tc::split8_bf16(z0 + 8 * h, hi0[h], lo0[h]);
+                    tc::split8_bf16(z1 + 8 * h, hi1[h], lo1[h]);
                 }
+                // A2 is free once the GEMM 2 that read it last completed: (it-1, p1) before p0, (it, p0) before p1
+                if (p == 0 && it >= 1) ok = group_wait(&d2_full[1], (uint32_t)((it - 1) & 1), lane, kBarC, kAGroupC);
+                if (p == 1) ok = group_wait(&d2_full[0], (uint32_t)(it & 1), lane, kBarC, kAGroupC);
+                if (!ok) break;
+                store_a2(cbase, hi0, lo0);
+                store_a2(cbase + 16, hi1, lo1);
                 tc::fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&a2_full[p]);
@@ -337,35 +351,36 @@ __global__ void __launch_bounds__(kAThreads, 1) dense_pass_a(const float *__rest
             if (ok && c == nchains - 1 && gi + 1 < my_groups) {
                 stage_x(sX, V, Vbase, 4 * (blockIdx.x + (gi + 1) * gridDim.x), tid);
                 tc::fence_proxy_async();
-                tc::named_sync(kBarC, kAGroup);
+                tc::named_sync(kBarC, kAGroupC);
                 if (tid == 0) tc::mbar_arrive(x_full);
             }
         }
         if (!ok && tid == 0) atomicExch(err, (int)CPMDP_ETIMEOUT);
-    } else if (nitems > 0) {
+    } else if (warp < (kAGroupC + kAGroupE) / 32 && nitems > 0) {
         // ---------------- group E: D2 -> stage -> quads of T ----------------
-        const int etid = tid - kAGroup;
+        const int etid = tid - kAGroupC;
+        const int cbase = kAColsE * ((warp - kAGroupC / 32) >> 2);
         bool ok = true;
         for (int it = 0; it < nitems && ok; it++) {
             const int c = it % nchains, gi = it / nchains;
             const int b0 = 4 * (blockIdx.x + gi * gridDim.x);
             for (int p = 0; p < 2; p++) {
-                ok = group_wait(&d2_full[p], (uint32_t)(it & 1), lane, kBarE);
+                ok = group_wait(&d2_full[p], (uint32_t)(it & 1), lane, kBarE, kAGroupE);
                 if (!ok) break;
                 tc::fence_after();
-                float y[kACols];
-                tc::tmem_ld32(tmem + lane_off + 128 + 64 * p + cbase, y);   // row (s2, i4'), cols i3'
+                float y[kAColsE];
+                tc::tmem_ld16(tmem + lane_off + 128 + 64 * p + cbase, y);   // row (s2, i4'), cols i3'
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&d2_empty[p]);
                 uint32_t *dst = stage + (2 * p + s2) * kSlab + cbase * 64 + r63;
 #pragma unroll
-                for (int jj = 0; jj < kACols; jj++) dst[jj * 64] = __float_as_uint(y[jj]);
+                for (int jj = 0; jj < kAColsE; jj++) dst[jj * 64] = __float_as_uint(y[jj]);
             }
             if (!ok) break;
-            tc::named_sync(kBarE, kAGroup);   // the item's four slabs are staged
-            write_quads(T, stage, c, b0, 0, kSlab, etid, kAGroup);
-            tc::named_sync(kBarE, kAGroup);   // and read: the stage is free again
+            tc::named_sync(kBarE, kAGroupE);   // the item's four slabs are staged
+            write_quads(T, stage, c, b0, 0, kSlab, etid, kAGroupE);
+            tc::named_sync(kBarE, kAGroupE);   // and read: the stage is free again
         }
         if (!ok && etid == 0) atomicExch(err, (int)CPMDP_ETIMEOUT);
     }
