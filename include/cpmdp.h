@@ -82,8 +82,10 @@ typedef enum {
     CPMDP_SOLVER_BARRIER_FREE = 2,  /* fused FP32 GridWorld solver without a barrier in its sweep loop */
     CPMDP_SOLVER_DENSE = 3,         /* dense CP solver */
     CPMDP_SOLVER_BATCH = 4,         /* batched value iteration */
-    CPMDP_SOLVER_MARCH_GRAPH = 5    /* FP32 value iteration of a 3-D grid of 2^23+ states: plane-marching
+    CPMDP_SOLVER_MARCH_GRAPH = 5,   /* FP32 value iteration of a 3-D grid of 2^23+ states: plane-marching
                                        sweeps replayed from a CUDA graph, stopping rule taken on the device */
+    CPMDP_SOLVER_BATCH_RESIDENT = 6 /* batched value iteration with every instance held in the shared memory
+                                       of one CTA or of one thread-block cluster for its whole solve */
 } cpmdp_solver;
 
 /*

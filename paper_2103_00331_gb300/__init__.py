@@ -24,6 +24,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT = 0, 1, 2, 3, 4, 5
 F32, F64, BF16X3 = 0, 1, 2
 GRIDWORLD, DENSE_CP = 0, 1
 SOLVER_PLAIN, SOLVER_GRID_BARRIER, SOLVER_BARRIER_FREE, SOLVER_DENSE, SOLVER_BATCH, SOLVER_MARCH_GRAPH = 0, 1, 2, 3, 4, 5
+SOLVER_BATCH_RESIDENT = 6
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT"}
 
 

@@ -420,7 +420,8 @@ namespace cpmdp {
 static void free_batch_device(cpmdp_batch &B) {
     void *ptrs[] = {B.d_inst, B.d_tiles, B.d_code, B.d_R, B.d_W, B.d_res, B.d_done, B.d_ctrl,
                     B.d_ring, B.d_p2ctr, B.d_p2tab, B.d_p2hdr, B.d_p2epoch, B.d_p2res,
-                    B.d_R64, B.d_instw, B.d_cert};
+                    B.d_R64, B.d_instw, B.d_cert, B.d_Rp, B.d_codep, B.d_rparts, B.d_rmulti,
+                    B.d_rsolo, B.d_rhdr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (B.graph) cudaGraphExecDestroy(B.graph);
@@ -768,20 +769,45 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
     if (cudaSetDevice(B->device) != cudaSuccess) { set_error("cannot select CUDA device %d", B->device); return CPMDP_ECUDA; }
     struct Restore { int p; ~Restore() { if (p >= 0) cudaSetDevice(p); } } restore{prev};
     cudaStream_t st = (cudaStream_t)stream;
-    if (!B->tuned) {
-        // first solve: pick block and tile sizes on this batch
-        cpmdp_status s = autotune(*B, st);
+    // fused = 1: every instance resident in shared memory when all fit (one
+    // CTA, or a cluster of CTAs, per instance); otherwise, and for fused = 4,
+    // the batched kernel with the barrier-free tail; fused = 2: the batched
+    // kernel to the end
+    bool resident = false;
+    if (o.fused == 1) {
+        cpmdp_status s = batch_resident_prepare(*B);
         if (s != CPMDP_OK) return s;
-        B->tuned = true;
+        resident = B->res_ok;
     }
-    prepare_tail(*B);
-    // record the solve (state resets + the cooperative launch) into a CUDA
-    // graph once per (V, stream, options) and replay it; if recording is
-    // refused, launch directly
-    const bool tail = o.fused != 2;
+    if (resident) {
+        if (!B->res_planned || B->res_planned_for != B->res_est) {
+            cpmdp_status s = batch_resident_plan(*B, o.tol, o.max_iter);
+            if (s != CPMDP_OK) return s;
+        }
+    } else {
+        if (!B->tuned) {
+            // first solve: pick block and tile sizes on this batch
+            cpmdp_status s = autotune(*B, st);
+            if (s != CPMDP_OK) return s;
+            B->tuned = true;
+        }
+        prepare_tail(*B);
+    }
+    // record the solve (state resets + the launches) into a CUDA graph once
+    // per (V, stream, options) and replay it; if recording is refused,
+    // launch directly
+    const bool tail = !resident && o.fused != 2;
+    const int kind = resident ? 2 : (tail ? 1 : 0);
+    auto enqueue = [&](cudaStream_t s2, int *grid) -> cudaError_t {
+        if (resident) {
+            *grid = B->res_grid;
+            return batch_resident_enqueue(*B, V, o.tol, o.max_iter, s2);
+        }
+        return enqueue_batch(*B, V, o.tol, o.max_iter, o.timeout_s, B->block, B->spl, s2, grid, tail);
+    };
     const bool same = B->graph && B->graph_V == (void *)V && B->graph_stream == st && B->graph_tol == o.tol &&
                       B->graph_max_iter == o.max_iter && B->graph_timeout == o.timeout_s &&
-                      B->graph_tail == (tail ? 1 : 0);
+                      B->graph_kind == kind;
     if (!same && !B->graph_failed) {
         if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
         cudaStream_t cap;
@@ -789,7 +815,7 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         int grid = 0;
-        if (e == cudaSuccess) e = enqueue_batch(*B, V, o.tol, o.max_iter, o.timeout_s, B->block, B->spl, cap, &grid, tail);
+        if (e == cudaSuccess) e = enqueue(cap, &grid);
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         cudaStreamDestroy(cap);
         if (e == cudaSuccess && e2 == cudaSuccess && g) e = cudaGraphInstantiate(&B->graph, g, 0);
@@ -806,7 +832,7 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
             B->graph_tol = o.tol;
             B->graph_max_iter = o.max_iter;
             B->graph_timeout = o.timeout_s;
-            B->graph_tail = tail ? 1 : 0;
+            B->graph_kind = kind;
         }
     }
     cudaEvent_t e0, e1;
@@ -817,7 +843,7 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
         CPMDP_CUDA(cudaGraphLaunch(B->graph, st));
     } else {
         int grid = 0;
-        CPMDP_CUDA(enqueue_batch(*B, V, o.tol, o.max_iter, o.timeout_s, B->block, B->spl, st, &grid, tail));
+        CPMDP_CUDA(enqueue(st, &grid));
     }
     CPMDP_CUDA(cudaEventRecord(e1, st));
     Ctrl hc;
@@ -853,6 +879,7 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
         if (hc.handoff && sweeps > hc.handoff_sweeps && !p2res.empty()) memcpy(&r, &p2res[(size_t)i], sizeof(double));
         else if (sweeps > 0) memcpy(&r, &res[(size_t)((sweeps - 1) % 3) * B->ninst + i], sizeof(double));
         if (iterations_out) iterations_out[i] = sweeps;
+        if (resident) B->res_est[(size_t)i] = sweeps;
         if (residual_out) residual_out[i] = r;
         worst = r > worst ? r : worst;
         backups += (long long)sweeps * B->inst[(size_t)i].nstates * B->inst_actions[(size_t)i];
@@ -867,7 +894,7 @@ cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *B, float *V, const cpmdp_s
         info->error_bound = -1.0;
         info->backups = backups;
         info->elapsed_ms = ms;
-        info->solver = CPMDP_SOLVER_BATCH;
+        info->solver = resident ? CPMDP_SOLVER_BATCH_RESIDENT : CPMDP_SOLVER_BATCH;
         info->tail_from = hc.handoff ? hc.handoff_sweeps : 0;
     }
     if (not_conv) {

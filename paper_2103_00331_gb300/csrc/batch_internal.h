@@ -38,6 +38,47 @@ struct alignas(16) BatchTile {
     float w_move, w_perp, w_stay, gamma;
 };
 
+// Shared-memory-resident batched solve (batch_resident.cu): one part of an
+// instance held by one CTA, slices [z0, z0 + nsl) of its leading dimension
+// (3-D: y-x planes, 2-D: rows, 1-D: the one row), rows padded to nxp states.
+struct ResPart {
+    long long goff;        // packed index of the part's first state
+    long long poff;        // index of the part's first state in the padded reward / code copies
+    int inst;
+    int D, nx, nxp, ny, P; // dimensions; row, padded row, rows per slice, padded states per slice
+    int nsl;               // slices held
+    int base;              // shared-memory state offset (a multiple of 128)
+    int nchunks;           // 128-state chunks
+    int has_prev, has_next;  // the adjacent slice lives in the CTA of rank - 1 / rank + 1
+    int prev_off;          // state offset of that CTA's last slice (rank - 1)
+    unsigned prev_addr, next_addr;  // shared::cluster addresses (set in the kernel)
+    float wm, wp, wst, g;
+};
+
+struct ResArgs {
+    const ResPart *parts;
+    const int2 *multi;     // cluster bundles: (first part, parts), part r on cluster rank r
+    const int2 *solo;      // solo bundles: (first part, parts), all in one CTA
+    const int *hdr;        // [0] cluster bundles, [1] solo bundles
+    int *ctr;              // [0], [1]: queue counters, zeroed before each launch
+    const float *Rp;       // padded FP32 rewards
+    const uint8_t *codep;  // padded move codes (padding: obstacle)
+    float *V;              // packed values, start in / result out
+    int *done_at;          // per instance: sweeps done (negative: stopped at max_iter)
+    unsigned long long *res;  // [3][ninst]: residual of the last sweep (bits of a double) at (sweeps - 1) % 3
+    int ninst;
+    unsigned tol_bits;     // bits of the largest float below tol
+    int max_iter;
+    Ctrl *ctrl;            // iterations = most sweeps of any instance
+};
+
+}  // namespace cpmdp
+
+struct cpmdp_batch;
+namespace cpmdp {
+cpmdp_status batch_resident_prepare(cpmdp_batch &B);
+cpmdp_status batch_resident_plan(cpmdp_batch &B, double tol, int max_iter);
+cudaError_t batch_resident_enqueue(const cpmdp_batch &B, float *V, double tol, int max_iter, cudaStream_t st);
 }  // namespace cpmdp
 
 struct cpmdp_batch {
@@ -70,7 +111,6 @@ struct cpmdp_batch {
     double graph_tol = 0;
     int graph_max_iter = 0;
     double graph_timeout = 0;
-    int graph_tail = 0;
     std::vector<cpmdp::BatchTile> tiles_host;
     // barrier-free tail (batch_flow.cu), allocated on the first solve
     bool flow_tried = false;
@@ -85,5 +125,22 @@ struct cpmdp_batch {
     double *d_R64 = nullptr;
     double *d_instw = nullptr;
     unsigned long long *d_cert = nullptr;
+    // shared-memory-resident solve (batch_resident.cu), set up on the first solve
+    bool res_tried = false;
+    bool res_ok = false;
+    int res_C = 1;                         // CTAs per cluster
+    int res_grid = 0;                      // CTAs launched (co-resident clusters x res_C)
+    float *d_Rp = nullptr;
+    uint8_t *d_codep = nullptr;
+    cpmdp::ResPart *d_rparts = nullptr;
+    int2 *d_rmulti = nullptr;
+    int2 *d_rsolo = nullptr;
+    int *d_rhdr = nullptr;
+    std::vector<long long> res_pad;        // per instance: offset in the padded copies
+    std::vector<int> res_est;              // per instance: sweeps of the last solve (0: unknown)
+    std::vector<int> res_planned_for;      // res_est the current bundles were made for
+    bool res_planned = false;
+    int res_nmulti = 0, res_nsolo = 0;
+    int graph_kind = -1;                   // recorded graph: 0 batched, 1 batched + tail, 2 resident
 };
 

@@ -133,9 +133,10 @@ def test_batch_k_sweeps_match_oracle(cp, k):
 
 
 def test_batch_tail_equals_batched_kernel(cp):
-    """Once the running instances fit one co-resident grid, the batch goes on
-    barrier-free, each instance at its own pace. Same sweeps, values and
-    residuals, bit for bit, as the batched kernel run to the end (fused=2)."""
+    """fused=4: once the running instances fit one co-resident grid, the
+    batched kernel hands them to the barrier-free tail, each instance at its
+    own pace. Same sweeps, values and residuals, bit for bit, as the batched
+    kernel run to the end (fused=2)."""
     import torch
     inst = ci.batch_gridworlds(count=300, seed=11)
     inst.append(ci.gridworld((37,), p=0.9, gamma=0.95, step_reward=-0.04, goal_rewards=[1.0], seed=1))
@@ -143,24 +144,70 @@ def test_batch_tail_equals_batched_kernel(cp):
                              obstacle_rate=0.1, seed=2))
     B = cp.batch_build(inst, device=0)
     out = {}
-    for fused in (1, 2):
+    for fused in (4, 2):
         V = torch.zeros(int(B.total_states), dtype=torch.float32, device="cuda")
         r, it, res = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=5000, fused=fused))
         out[fused] = (V.cpu().numpy(), it, res, r)
-    (Va, ia, ra, xa), (Vb, ib, rb, xb) = out[1], out[2]
+    (Va, ia, ra, xa), (Vb, ib, rb, xb) = out[4], out[2]
     assert xa["tail_from"] > 0 and xb["tail_from"] == 0
     assert np.array_equal(ia, ib)
     assert np.array_equal(ra, rb)
     assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
     assert xa["iterations"] == xb["iterations"]
     # max_iter inside the tail: the same partial result
-    for fused in (1, 2):
+    for fused in (4, 2):
         V = torch.zeros(int(B.total_states), dtype=torch.float32, device="cuda")
         r, it, res = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=xa["tail_from"] + 5, fused=fused),
                                               raise_on_noconv=False)
         out[fused] = (V.cpu().numpy(), it, res, r)
-    (Va, ia, ra, xa), (Vb, ib, rb, xb) = out[1], out[2]
+    (Va, ia, ra, xa), (Vb, ib, rb, xb) = out[4], out[2]
     assert xa["status"] == cp.ENOCONV and np.array_equal(ia, ib) and np.array_equal(ra, rb)
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+    B.close()
+
+
+def test_batch_resident_equals_batched_kernel(cp):
+    """fused=1 (default): every instance held in shared memory for its whole
+    solve, in one CTA (several small instances per CTA in lockstep) or cut
+    into slices over the CTAs of a cluster (the slices next to a part read
+    through distributed shared memory). Same per-state arithmetic as the
+    batched kernel: sweeps, values and residuals equal those of fused=2 bit
+    for bit, on the first solve (bundles from a gamma-based guess), on the
+    second (bundles re-made from the first solve's sweep counts) and with
+    max_iter stopping part of the instances."""
+    import torch
+    inst = ci.batch_gridworlds(count=160, seed=13)
+    extra = [(48, 48, 48), (40, 47, 45), (33, 37, 28), (128, 128), (127, 101), (3, 129), (37,), (1,), (8, 8),
+             (2, 3, 4), (9, 1, 6), (45, 30, 21)]
+    for j, s in enumerate(extra):
+        inst.append(ci.gridworld(s, p=0.6 + 0.03 * j, gamma=0.9 + 0.008 * j, step_reward=-0.04,
+                                 goal_rewards=[1.0, -1.0][:min(2, int(np.prod(s)) - 1)] or [1.0],
+                                 obstacle_rate=0.05 if int(np.prod(s)) > 2 else 0.0, seed=300 + j))
+    inst.append(ci.GridWorld(shape=(4, 4), p=0.8, gamma=0.9, cell=np.ones((4, 4), np.uint8),
+                             reward=np.zeros((4, 4))))
+    B = cp.batch_build(inst, device=0)
+    nS = int(B.total_states)
+
+    def solve(fused, max_iter=5000):
+        V = torch.zeros(nS, dtype=torch.float32, device="cuda")
+        r, it, res = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=max_iter, fused=fused),
+                                              raise_on_noconv=False)
+        return V.cpu().numpy(), it, res, r
+
+    Vb, ib, rb, xb = solve(2)
+    for rep in range(2):
+        Va, ia, ra, xa = solve(1)
+        assert xa["solver"] == cp.SOLVER_BATCH_RESIDENT and xb["solver"] == cp.SOLVER_BATCH
+        assert xa["status"] == cp.OK
+        assert np.array_equal(ia, ib), (rep, np.nonzero(ia != ib)[0][:5])
+        assert np.array_equal(ra, rb)
+        assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+        assert xa["iterations"] == xb["iterations"] and xa["backups"] == xb["backups"]
+    k = int(np.median(ib))
+    Vb, ib, rb, xb = solve(2, k)
+    Va, ia, ra, xa = solve(1, k)
+    assert xa["status"] == cp.ENOCONV and xb["status"] == cp.ENOCONV
+    assert np.array_equal(ia, ib) and np.array_equal(ra, rb)
     assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
     B.close()
 
