@@ -874,7 +874,8 @@ def kernel_case(name, reps=3):
     solve64b / pi64b = the same on the grid-barrier solver; ws512 = the warm-start network on
     512 x 16^3 coarse cells (six tensor-core convolutions); batch1024 = batched value iteration of
     1024 uneven GridWorlds (batched kernel, then the barrier-free tail); batch4096 = the 4096-instance
-    batch, shared-memory-resident solver (fused=1) and batched kernel with tail (fused=4); batchcert = the FP64
+    batch, shared-memory-resident solver (fused=1) and batched kernel with tail (fused=4); batchres1024 = the
+    resident solver on 1024 instances; batchcert = the FP64
     certifying sweep of that batch after its solve."""
     import torch
     import paper_2103_00331_gb300 as cp
@@ -933,6 +934,16 @@ def kernel_case(name, reps=3):
                 r, iters, _ = cp.batch_value_iteration(B, V, opts=opts)
                 print(f"batch of 4096, fused={fused}: {r['elapsed_ms']:.3f} ms, {r['iterations']} sweeps, "
                       f"solver {r['solver']}")
+        B.close()
+    elif name == "batchres1024":
+        inst = ci.batch_gridworlds(count=1024, seed=0)
+        B = cp.batch_build(inst, device=0)
+        V = torch.zeros(int(B.total_states), dtype=torch.float32, device=dev)
+        opts = cp.default_opts(tol=TOL, max_iter=5000)
+        for _ in range(reps):
+            V.zero_()
+            r, iters, _ = cp.batch_value_iteration(B, V, opts=opts)
+            print(f"batch of 1024, resident: {r['elapsed_ms']:.3f} ms, {r['iterations']} sweeps, solver {r['solver']}")
         B.close()
     elif name == "batch1024":
         inst = ci.batch_gridworlds(count=1024, seed=0)
@@ -1003,7 +1014,7 @@ def main():
     ap.add_argument("--skip-dense", action="store_true")
     ap.add_argument("--skip-warmstart", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--kernel-case", choices=["sweep512", "sweep320", "solve64", "pi64", "solve64b", "pi64b", "dense64", "batch4096",
+    ap.add_argument("--kernel-case", choices=["sweep512", "sweep320", "solve64", "pi64", "solve64b", "pi64b", "dense64", "batch4096", "batchres1024",
                                               "dense64tc", "ws512", "batch1024", "batchcert"],
                     default=None,
                     help="run one kernel workload a few times (profiling) and exit")

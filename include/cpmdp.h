@@ -146,7 +146,9 @@ typedef struct {
                                 one-thread check kernel after each sweep raises a flag on which every
                                 later kernel returns at once), 32 sweeps recorded once into a CUDA
                                 graph that is replayed until the flag is up (the host reads it once
-                                per 32 sweeps); 0 and 3 run value iteration only */
+                                per 32 sweeps); 0 and 3 run value iteration only. Batches
+                                (cpmdp_batch_value_iteration): 1 shared-memory-resident solver,
+                                4 batched kernel with the barrier-free tail, 2 batched kernel only */
     double eval_tol;         /* policy iteration: evaluation stops below this residual
                                 (default: tol for F32, 1e-10 for F64) */
     int32_t max_eval_iter;   /* policy iteration: evaluation sweep limit per round (default 100000) */
@@ -321,20 +323,36 @@ cpmdp_status cpmdp_batch_info(const cpmdp_batch *batch, int32_t *count, int64_t 
 
 /*
  * FP32 value iteration of every instance of the batch (fused backup of
- * cpmdp_value_iteration, one cooperative persistent launch, per-instance
- * stopping at opts->tol or opts->max_iter). V: device, packed values (start
- * in, result out), 16-byte aligned. iterations_out / residual_out: host
- * arrays of `count` (may be NULL): sweeps and last residual per instance.
- * info (may be NULL): iterations = launch-wide sweeps, backups = sum over
- * instances, elapsed_ms, rounds = 1 when the solve was replayed from a CUDA
- * graph. The first call tunes block and tile sizes on the batch (a few
- * sweeps on a temporary buffer) and records the solve into a CUDA graph,
- * replayed by later calls with the same V, stream and options. Once the
- * instances still running fit one co-resident grid (one warp per 128
- * states), they continue without the grid barrier, each instance at its own
- * pace (same sweeps and values; info->tail_from tells when); opts->fused = 2
- * keeps the whole solve on the batched kernel. Synchronises with `stream`.
- * Errors: EINVAL, ECUDA, ENOCONV (some instance hit max_iter), ETIMEOUT.
+ * cpmdp_value_iteration, per-instance stopping at opts->tol or
+ * opts->max_iter). V: device, packed values (start in, result out), 16-byte
+ * aligned. iterations_out / residual_out: host arrays of `count` (may be
+ * NULL): sweeps and last residual per instance. info (may be NULL):
+ * iterations = most sweeps of any instance, backups = sum over instances,
+ * elapsed_ms, rounds = 1 when the solve was replayed from a CUDA graph,
+ * solver = CPMDP_SOLVER_BATCH_RESIDENT or CPMDP_SOLVER_BATCH.
+ * opts->fused selects the solver (same sweeps, values and residuals, bit for
+ * bit, whichever runs):
+ *   1 (default) every instance held in shared memory for its whole solve,
+ *     one persistent launch of 1024-thread CTAs (up to 27,648 states per
+ *     CTA): small instances packed several to a CTA, larger ones cut into
+ *     slices over the CTAs of a thread-block cluster (2, 4 or 8, the
+ *     smallest that every instance fits) that read the slices next to their
+ *     part through distributed shared memory. The work is scheduled from
+ *     the previous solve's sweep counts of each instance (the first solve of
+ *     a batch from a gamma-based guess). Batches with an instance that does
+ *     not fit eight CTAs run as with fused = 4.
+ *   4 one cooperative persistent launch over all instances (one grid barrier
+ *     per sweep); once the instances still running fit one co-resident grid
+ *     (one warp per 128 states) they continue without the grid barrier, each
+ *     instance at its own pace (info->tail_from tells when). The first call
+ *     tunes block and tile sizes on the batch (a few sweeps on a temporary
+ *     buffer).
+ *   2 as 4, without the barrier-free tail.
+ * Each solve is recorded once into a CUDA graph, replayed by later calls
+ * with the same V, stream and options. Synchronises with `stream`.
+ * Errors: EINVAL, ECUDA, ENOCONV (some instance hit max_iter), ETIMEOUT
+ * (fused = 2 / 4: a device-side wait ran out; the resident solver waits only
+ * at hardware CTA and cluster barriers).
  */
 cpmdp_status cpmdp_batch_value_iteration(cpmdp_batch *batch, float *V, const cpmdp_solve_opts *opts,
                                          int32_t *iterations_out, double *residual_out, cpmdp_result *info,

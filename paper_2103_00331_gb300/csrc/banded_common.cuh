@@ -109,26 +109,45 @@ __device__ __forceinline__ void perp_of(const TA (&nb)[2 * D], TA (&perp)[D]) {
     for (int d = D - 1; d >= 0; d--) { perp[d] += acc; acc += P[d]; }
 }
 
+// Larger of a and b: fmaxf for float (one instruction); for double the
+// compare-select form (GB300's narrow FP64 pipe takes either as one op).
+template <typename TA> __device__ __forceinline__ TA vmax(TA a, TA b) { return b > a ? b : a; }
+template <> __device__ __forceinline__ float vmax<float>(float a, float b) { return fmaxf(a, b); }
+
 // Value-iteration backup of one state from its blocked-move-resolved
 // neighbour values nb (Eq. 1). Because w_move, w_perp and gamma are >= 0 and
 // rounding is monotone, max_sigma E_(d,sigma) is E at max(N_{d,-}, N_{d,+})
 // and max_a fl(R + gamma E_a) = fl(R + gamma max_a E_a): the same value (and
 // the same lowest-index argmax) as evaluating every action, with D instead
-// of 2D expectation chains. Terminals keep R, obstacles 0.
-template <typename TA, int D>
+// of 2D expectation chains. Terminals keep R, obstacles 0. ARG = false
+// leaves arg unset and takes both maxima with vmax (the same values; only
+// the sign of a zero maximum may differ from the compare-select form).
+template <typename TA, int D, bool ARG = true>
 __device__ __forceinline__ TA vi_state(TA self, const TA (&nb)[2 * D], unsigned c, TA r, TA wm, TA wp, TA wst, TA g,
                                        int &arg) {
     TA perp[D];
     perp_of<TA, D>(nb, perp);
     const TA stay = (D == 1) ? wst * self : (TA)0;
     TA bestE = 0;
-    arg = 0;
+    if (ARG) arg = 0;
 #pragma unroll
     for (int d = 0; d < D; d++) {
-        const bool up = nb[2 * d + 1] > nb[2 * d];
-        const TA m = up ? nb[2 * d + 1] : nb[2 * d];
-        const TA e = wm * m + wp * perp[d] + stay;
-        if (d == 0 || e > bestE) { bestE = e; arg = 2 * d + (up ? 1 : 0); }
+        TA m, e;
+        bool up = false;
+        if (ARG) {
+            up = nb[2 * d + 1] > nb[2 * d];
+            m = up ? nb[2 * d + 1] : nb[2 * d];
+        } else {
+            m = vmax<TA>(nb[2 * d], nb[2 * d + 1]);
+        }
+        // D = 1: the slip stays in place with weight w_stay; D >= 2 has none
+        if (D == 1) e = wm * m + wp * perp[d] + stay;
+        else e = wm * m + wp * perp[d];
+        if (ARG) {
+            if (d == 0 || e > bestE) { bestE = e; arg = 2 * d + (up ? 1 : 0); }
+        } else {
+            bestE = d == 0 ? e : vmax<TA>(bestE, e);
+        }
     }
     TA v = r + g * bestE;
     if (c & (1u << (2 * D + 1))) v = r;
@@ -266,7 +285,7 @@ struct Segment {
 #pragma unroll
             for (int j = 0; j < NB; j++) nbk[j] = nb[j][k];
             int arg;
-            const TA v = vi_state<TA, D>(self[k], nbk, c, r[k], wm, wp, wst, g, arg);
+            const TA v = vi_state<TA, D, WITH_PI>(self[k], nbk, c, r[k], wm, wp, wst, g, arg);
             out[k] = v;
             if (WITH_PI) pi[s0 + k] = (c & (OBST | TERM)) ? (uint8_t)255 : (uint8_t)arg;
             if (!(c & OBST)) {

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) march_kernel(MarchArgs m, const float *__
                 nb[4] = (c & 16u) ? self : left;
                 nb[5] = (c & 32u) ? self : right;
                 int arg;
-                const TA v = vi_state<TA, D>(self, nb, c, rc.r[k], wm, wp, wst, g, arg);
+                const TA v = vi_state<TA, D, WITH_PI>(self, nb, c, rc.r[k], wm, wp, wst, g, arg);
                 out[k] = v;
                 pol |= ((c & (OBST | TERM)) ? 255u : (unsigned)arg) << (8 * k);
                 if (!(c & OBST)) {

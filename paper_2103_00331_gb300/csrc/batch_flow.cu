@@ -207,7 +207,7 @@ __device__ void run_instance(const P2Args &a, const BatchInst &I, int inst, int 
             nb[NRR] = ((c >> NRR) & 1u) ? cur[k] : left;
             nb[NRR + 1] = ((c >> (NRR + 1)) & 1u) ? cur[k] : right;
             int arg;
-            const float v = vi_state<float, D>(cur[k], nb, c, R[k], wm, wp, wst, g, arg);
+            const float v = vi_state<float, D, false>(cur[k], nb, c, R[k], wm, wp, wst, g, arg);
             nxt[k] = v;
             if (valid && !(c & OBST)) {
                 const float dv = abs_diff(v, cur[k]);

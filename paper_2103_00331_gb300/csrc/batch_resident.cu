@@ -110,14 +110,37 @@ __device__ __forceinline__ unsigned cluster_ctarank() {
 // is never below).
 __device__ __forceinline__ bool res_below(unsigned bits, unsigned tol_bits) { return bits <= tol_bits; }
 
+// What a segment's backup needs of its part, in registers (loaded once per
+// part, not once per segment: the stores of the sweep go to shared memory,
+// which the compiler cannot tell apart from the part table).
+struct SegGeo {
+    long long poff;
+    int base, P, nslp, nxp;
+    unsigned prev_addr, next_addr;   // 0: the instance ends there (a wall)
+    float wm, wp, wst, g;
+    __device__ __forceinline__ void load(const ResPart &pt) {
+        poff = pt.poff;
+        base = pt.base;
+        P = pt.P;
+        nslp = pt.nsl * pt.P;
+        nxp = pt.nxp;
+        prev_addr = pt.has_prev ? pt.prev_addr : 0u;
+        next_addr = pt.has_next ? pt.next_addr : 0u;
+        wm = pt.wm;
+        wp = pt.wp;
+        wst = pt.wst;
+        g = pt.g;
+    }
+};
+
 // Backup of the segment of part pt at shared-memory state o (4 states,
 // 16-byte aligned), from buffer cur into nxt. Returns the segment's
 // residual (0 for padding and obstacles).
 template <int D>
-__device__ __forceinline__ float res_segment(const ResPart &pt, const float *cur, float *nxt, unsigned bufoff,
+__device__ __forceinline__ float res_segment(const SegGeo &pt, const float *cur, float *nxt, unsigned bufoff,
                                              const float *Rp, const uint8_t *codep, int o) {
     const int rel = o - pt.base;
-    const int nslp = pt.nsl * pt.P;
+    const int nslp = pt.nslp;
     Segment<float, float, D, 4> sg;
     if (rel < nslp) {
         load_pack<uint8_t, 4>(codep + pt.poff + rel, sg.code);
@@ -136,14 +159,14 @@ __device__ __forceinline__ float res_segment(const ResPart &pt, const float *cur
         // instance ends: the code blocks the move, any value will do)
         const int P = pt.P;
         if (rel < P) {
-            if (pt.has_prev) ld_cluster4(pt.prev_addr + bufoff + 4u * (unsigned)rel, sg.rows[0]);
+            if (pt.prev_addr) ld_cluster4(pt.prev_addr + bufoff + 4u * (unsigned)rel, sg.rows[0]);
             else load_pack<float, 4>(cur + o, sg.rows[0]);
         } else {
             load_pack<float, 4>(cur + o - P, sg.rows[0]);
         }
         const int lastrel = rel - nslp + P;
         if (lastrel >= 0) {
-            if (pt.has_next) ld_cluster4(pt.next_addr + bufoff + 4u * (unsigned)lastrel, sg.rows[1]);
+            if (pt.next_addr) ld_cluster4(pt.next_addr + bufoff + 4u * (unsigned)lastrel, sg.rows[1]);
             else load_pack<float, 4>(cur + o, sg.rows[1]);
         } else {
             load_pack<float, 4>(cur + o + P, sg.rows[1]);
@@ -164,9 +187,9 @@ __device__ __forceinline__ float res_segment(const ResPart &pt, const float *cur
     return sg.template finish_vi<false>(a, nxt, nullptr, o);
 }
 
-__device__ __forceinline__ float res_chunk(const ResPart &pt, const float *cur, float *nxt, unsigned bufoff,
+__device__ __forceinline__ float res_chunk(int D, const SegGeo &pt, const float *cur, float *nxt, unsigned bufoff,
                                            const float *Rp, const uint8_t *codep, int o) {
-    switch (pt.D) {
+    switch (D) {
     case 1: return res_segment<1>(pt, cur, nxt, bufoff, Rp, codep, o);
     case 2: return res_segment<2>(pt, cur, nxt, bufoff, Rp, codep, o);
     default: return res_segment<3>(pt, cur, nxt, bufoff, Rp, codep, o);
@@ -238,10 +261,17 @@ __device__ void res_solo(const ResArgs &a, ResShared &S, float *buf) {
             const float *cur = buf + (q & 1) * kResCap;
             float *nxt = buf + ((q + 1) & 1) * kResCap;
             bool worked = false;
+            int gp = -1, gD = 3;
+            SegGeo geo;
             for (int c = warp; c < nch; c += kResWarps) {
                 const int p = S.chunk_part[c];
                 if (q > 0 && (q >= a.max_iter || res_below(S.slot[p][(q - 1) % 3], a.tol_bits))) continue;
-                const float r = res_chunk(S.part[p], cur, nxt, 0u, a.Rp, a.codep, c * kResChunk + 4 * lane);
+                if (p != gp) {
+                    geo.load(S.part[p]);
+                    gD = S.part[p].D;
+                    gp = p;
+                }
+                const float r = res_chunk(gD, geo, cur, nxt, 0u, a.Rp, a.codep, c * kResChunk + 4 * lane);
                 const unsigned mx = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(r));
                 if (lane == 0) atomicMax(&S.slot[p][q % 3], mx);
                 worked = true;
@@ -269,8 +299,11 @@ __device__ void res_solo(const ResArgs &a, ResShared &S, float *buf) {
 }
 
 // Cluster bundles: one instance over the C CTAs of the cluster, part r on
-// rank r (ranks past the bundle's parts only keep the barriers).
-__device__ void res_cluster(const ResArgs &a, ResShared &S, float *buf) {
+// rank r (ranks past the bundle's parts only keep the barriers). Every CTA
+// sends its residual of a sweep to the slot of every CTA (C remote max
+// reductions), so after the cluster barrier each CTA reads the instance's
+// residual from its own shared memory.
+__device__ void res_cluster(const ResArgs &a, ResShared &S, float *buf, int C) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned rank = cluster_ctarank();
     const unsigned job_addr0 = cluster_map(smem_addr(&S.job), 0);
@@ -287,7 +320,7 @@ __device__ void res_cluster(const ResArgs &a, ResShared &S, float *buf) {
         const bool have = (int)rank < bd.y;
         if (tid == 0) {
             S.slot[0][0] = S.slot[0][1] = S.slot[0][2] = 0u;
-            S.local = 0u;
+            S.slot[1][0] = S.slot[1][1] = 0u;   // this CTA's residual of the sweep, by parity
             if (have) {
                 ResPart pt = a.parts[bd.x + rank];
                 const unsigned b0 = smem_addr(buf);
@@ -298,45 +331,46 @@ __device__ void res_cluster(const ResArgs &a, ResShared &S, float *buf) {
         }
         __syncthreads();
         if (have) res_load(S.part[0], buf, a.V);
-        // the lead's residual slots (rank 0 holds the first part)
-        const unsigned slot_addr0 = cluster_map(smem_addr(&S.slot[0][0]), 0);
+        SegGeo geo;
+        geo.load(S.part[0]);
+        const int D = S.part[0].D, inst = S.part[0].inst;
+        // lane t < C of warp 0 sends to rank t's slots
+        const unsigned slot_remote = tid < C ? cluster_map(smem_addr(&S.slot[0][0]), (unsigned)tid) : 0u;
         cluster_sync_all();
         const int nch = have ? S.part[0].nchunks : 0;
         int sweeps = 0;
-        bool running = have;
         for (int q = 0;; q++) {
             if (q > 0) {
-                // every thread reads the same slot after the same barrier
-                const unsigned v = ld_cluster_u32(slot_addr0 + 4u * (unsigned)((q - 1) % 3));
-                const bool stop = q >= a.max_iter || res_below(v, a.tol_bits);
-                if (stop) {
-                    if (rank == 0 && tid == 0)
-                        res_record(a, S.part[0].inst, res_below(v, a.tol_bits) ? q : -q, v, q - 1);
+                // the residual of sweep q - 1, complete in every CTA's own slot
+                const unsigned v = S.slot[0][(q - 1) % 3];
+                const bool below = res_below(v, a.tol_bits);
+                if (below || q >= a.max_iter) {
+                    if (rank == 0 && tid == 0) res_record(a, inst, below ? q : -q, v, q - 1);
                     sweeps = q;
                     break;
                 }
             }
-            if (rank == 0 && tid == 0) S.slot[0][(q + 1) % 3] = 0u;
+            if (tid == 0) {
+                S.slot[0][(q + 1) % 3] = 0u;
+                S.slot[1][(q + 1) & 1] = 0u;
+            }
             const float *cur = buf + (q & 1) * kResCap;
             float *nxt = buf + ((q + 1) & 1) * kResCap;
             const unsigned bufoff = (unsigned)((q & 1) * kResCap * 4);
-            if (running) {
+            if (have) {
                 for (int c = warp; c < nch; c += kResWarps) {
-                    const float r = res_chunk(S.part[0], cur, nxt, bufoff, a.Rp, a.codep, c * kResChunk + 4 * lane);
+                    const float r = res_chunk(D, geo, cur, nxt, bufoff, a.Rp, a.codep, c * kResChunk + 4 * lane);
                     const unsigned mx = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(r));
-                    if (lane == 0) atomicMax(&S.local, mx);
+                    if (lane == 0) atomicMax(&S.slot[1][q & 1], mx);
                 }
             }
             __syncthreads();
-            if (tid == 0 && running) {
-                red_cluster_max(slot_addr0 + 4u * (unsigned)(q % 3), S.local);
-                S.local = 0u;
-            }
+            if (tid < C && have) red_cluster_max(slot_remote + 4u * (unsigned)(q % 3), S.slot[1][q & 1]);
             cluster_sync_all();
         }
         if (have) res_store(S.part[0], buf + (sweeps & 1) * kResCap, a.V);
-        // rank 0 overwrites its job word and slots only after this CTA's
-        // last remote read: the next bundle's first cluster barrier
+        // every CTA reads only its own slots now, and rank 0's job word was
+        // read before the bundle's sweeps
         __syncthreads();
     }
 }
@@ -346,7 +380,11 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_vi_kernel(ResArgs a) 
     extern __shared__ __align__(16) float res_smem[];
     float *buf = res_smem;
     ResShared &S = *reinterpret_cast<ResShared *>(res_smem + 2 * kResCap);
-    if (CLUSTER) res_cluster(a, S, buf);
+    if (CLUSTER) {
+        unsigned nrank;
+        asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(nrank));
+        res_cluster(a, S, buf, (int)nrank);
+    }
     res_solo(a, S, buf);
 }
 
@@ -473,7 +511,7 @@ cpmdp_status batch_resident_prepare(cpmdp_batch &B) {
 // gamma-based guess before the first): instances whose solo solve would
 // set the length of the whole launch are cut over a cluster; the others are
 // packed, most sweeps first, into CTAs as long as the bundle's time stays
-// under the launch's lower bound.
+// under about a third of the launch's average load per CTA.
 cpmdp_status batch_resident_plan(cpmdp_batch &B, double tol, int max_iter) {
     const int n = B.ninst, C = B.res_C;
     std::vector<double> est((size_t)n);
@@ -520,7 +558,9 @@ cpmdp_status batch_resident_plan(cpmdp_batch &B, double tol, int max_iter) {
             if (t > avg) split[(size_t)i] = 1;
         }
     }
-    const double target = std::max(crit, work / std::max(1, B.res_grid));
+    // solo bundles run after the cluster bundles: keeping each one well
+    // under the launch's average load lets the last ones even out the end
+    const double target = std::max(crit, 0.35 * work / std::max(1, B.res_grid));
     std::vector<int> order((size_t)n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return est[(size_t)x] > est[(size_t)y]; });

@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_vi_kernel(Fl
                 sg.nbk(sg.cur, rows, hl, hr, i, k, nb);
                 const unsigned c = (sg.code[i] >> (8 * k)) & 0xFFu;
                 int arg;
-                const float v = vi_state<float, D>(sg.cur[i][k], nb, c, sg.R[i][k], wm, wp, wst, g, arg);
+                const float v = vi_state<float, D, false>(sg.cur[i][k], nb, c, sg.R[i][k], wm, wp, wst, g, arg);
                 nxt[i][k] = v;
                 if (sg.valid[i] && !(c & OBST)) {
                     const float dv = abs_diff(v, sg.cur[i][k]);
