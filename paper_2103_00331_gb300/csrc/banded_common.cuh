@@ -114,40 +114,51 @@ __device__ __forceinline__ void perp_of(const TA (&nb)[2 * D], TA (&perp)[D]) {
 template <typename TA> __device__ __forceinline__ TA vmax(TA a, TA b) { return b > a ? b : a; }
 template <> __device__ __forceinline__ float vmax<float>(float a, float b) { return fmaxf(a, b); }
 
+// max over actions of E_a at one state, from its blocked-move-resolved
+// neighbour values (value iteration without the argmax; see vi_state).
+template <typename TA, int D>
+__device__ __forceinline__ TA vi_best_e(TA self, const TA (&nb)[2 * D], TA wm, TA wp, TA wst) {
+    TA perp[D];
+    perp_of<TA, D>(nb, perp);
+    const TA stay = (D == 1) ? wst * self : (TA)0;
+    TA bestE = 0;
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+        const TA m = vmax<TA>(nb[2 * d], nb[2 * d + 1]);
+        // D = 1: the slip stays in place with weight w_stay; D >= 2 has none
+        const TA e = (D == 1) ? wm * m + wp * perp[d] + stay : wm * m + wp * perp[d];
+        bestE = d == 0 ? e : vmax<TA>(bestE, e);
+    }
+    return bestE;
+}
+
 // Value-iteration backup of one state from its blocked-move-resolved
 // neighbour values nb (Eq. 1). Because w_move, w_perp and gamma are >= 0 and
 // rounding is monotone, max_sigma E_(d,sigma) is E at max(N_{d,-}, N_{d,+})
 // and max_a fl(R + gamma E_a) = fl(R + gamma max_a E_a): the same value (and
 // the same lowest-index argmax) as evaluating every action, with D instead
 // of 2D expectation chains. Terminals keep R, obstacles 0. ARG = false
-// leaves arg unset and takes both maxima with vmax (the same values; only
-// the sign of a zero maximum may differ from the compare-select form).
+// leaves arg unset and takes both maxima with vmax (vi_best_e: the same
+// values; only the sign of a zero maximum may differ from the compare-select
+// form).
 template <typename TA, int D, bool ARG = true>
 __device__ __forceinline__ TA vi_state(TA self, const TA (&nb)[2 * D], unsigned c, TA r, TA wm, TA wp, TA wst, TA g,
                                        int &arg) {
-    TA perp[D];
-    perp_of<TA, D>(nb, perp);
-    const TA stay = (D == 1) ? wst * self : (TA)0;
     TA bestE = 0;
-    if (ARG) arg = 0;
+    if (ARG) {
+        TA perp[D];
+        perp_of<TA, D>(nb, perp);
+        const TA stay = (D == 1) ? wst * self : (TA)0;
+        arg = 0;
 #pragma unroll
-    for (int d = 0; d < D; d++) {
-        TA m, e;
-        bool up = false;
-        if (ARG) {
-            up = nb[2 * d + 1] > nb[2 * d];
-            m = up ? nb[2 * d + 1] : nb[2 * d];
-        } else {
-            m = vmax<TA>(nb[2 * d], nb[2 * d + 1]);
-        }
-        // D = 1: the slip stays in place with weight w_stay; D >= 2 has none
-        if (D == 1) e = wm * m + wp * perp[d] + stay;
-        else e = wm * m + wp * perp[d];
-        if (ARG) {
+        for (int d = 0; d < D; d++) {
+            const bool up = nb[2 * d + 1] > nb[2 * d];
+            const TA m = up ? nb[2 * d + 1] : nb[2 * d];
+            const TA e = (D == 1) ? wm * m + wp * perp[d] + stay : wm * m + wp * perp[d];
             if (d == 0 || e > bestE) { bestE = e; arg = 2 * d + (up ? 1 : 0); }
-        } else {
-            bestE = d == 0 ? e : vmax<TA>(bestE, e);
         }
+    } else {
+        bestE = vi_best_e<TA, D>(self, nb, wm, wp, wst);
     }
     TA v = r + g * bestE;
     if (c & (1u << (2 * D + 1))) v = r;

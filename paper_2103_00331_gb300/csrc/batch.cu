@@ -420,7 +420,7 @@ namespace cpmdp {
 static void free_batch_device(cpmdp_batch &B) {
     void *ptrs[] = {B.d_inst, B.d_tiles, B.d_code, B.d_R, B.d_W, B.d_res, B.d_done, B.d_ctrl,
                     B.d_ring, B.d_p2ctr, B.d_p2tab, B.d_p2hdr, B.d_p2epoch, B.d_p2res,
-                    B.d_R64, B.d_instw, B.d_cert, B.d_Rp, B.d_codep, B.d_rparts, B.d_rmulti,
+                    B.d_R64, B.d_instw, B.d_cert, B.d_Rp, B.d_Gp, B.d_codep, B.d_rparts, B.d_rmulti,
                     B.d_rsolo, B.d_rhdr};
     for (void *p : ptrs)
         if (p) cudaFree(p);

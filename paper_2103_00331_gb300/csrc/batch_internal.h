@@ -61,7 +61,8 @@ struct ResArgs {
     const int2 *solo;      // solo bundles: (first part, parts), all in one CTA
     const int *hdr;        // [0] cluster bundles, [1] solo bundles
     int *ctr;              // [0], [1]: queue counters, zeroed before each launch
-    const float *Rp;       // padded FP32 rewards
+    const float *Rp;       // padded FP32 rewards (0 on obstacles)
+    const float *Gp;       // padded multipliers of max_a E_a: gamma on free states, else 0
     const uint8_t *codep;  // padded move codes (padding: obstacle)
     float *V;              // packed values, start in / result out
     int *done_at;          // per instance: sweeps done (negative: stopped at max_iter)
@@ -131,6 +132,7 @@ struct cpmdp_batch {
     int res_C = 1;                         // CTAs per cluster
     int res_grid = 0;                      // CTAs launched (co-resident clusters x res_C)
     float *d_Rp = nullptr;
+    float *d_Gp = nullptr;
     uint8_t *d_codep = nullptr;
     cpmdp::ResPart *d_rparts = nullptr;
     int2 *d_rmulti = nullptr;

@@ -135,20 +135,27 @@ struct SegGeo {
 
 // Backup of the segment of part pt at shared-memory state o (4 states,
 // 16-byte aligned), from buffer cur into nxt. Returns the segment's
-// residual (0 for padding and obstacles).
+// residual. Terminals and obstacles need no select: the padded copies hold,
+// per state, R (0 on obstacles) and the multiplier of the expectation (gamma,
+// 0 on terminals, obstacles and padding), so V' = R + g_s max_a E_a is R on
+// a terminal and 0 on an obstacle; obstacle values are loaded as 0, so an
+// obstacle's |V' - V| is 0 (no state reads an obstacle's value: a move into
+// one is blocked). Free states get vi_state's arithmetic exactly.
 template <int D>
 __device__ __forceinline__ float res_segment(const SegGeo &pt, const float *cur, float *nxt, unsigned bufoff,
-                                             const float *Rp, const uint8_t *codep, int o) {
+                                             const ResArgs &a, int o) {
     const int rel = o - pt.base;
     const int nslp = pt.nslp;
     Segment<float, float, D, 4> sg;
+    float gs[4];
     if (rel < nslp) {
-        load_pack<uint8_t, 4>(codep + pt.poff + rel, sg.code);
-        load_pack<float, 4>(Rp + pt.poff + rel, sg.r);
+        load_pack<uint8_t, 4>(a.codep + pt.poff + rel, sg.code);
+        load_pack<float, 4>(a.Rp + pt.poff + rel, sg.r);
+        load_pack<float, 4>(a.Gp + pt.poff + rel, gs);
     } else {
-        // padding up to the part's last chunk: obstacles (value 0, no residual)
+        // padding up to the part's last chunk: every move blocked, value 0
 #pragma unroll
-        for (int k = 0; k < 4; k++) { sg.code[k] = 0xFF; sg.r[k] = 0.f; }
+        for (int k = 0; k < 4; k++) { sg.code[k] = 0xFF; sg.r[k] = 0.f; gs[k] = 0.f; }
     }
     load_pack<float, 4>(cur + o, sg.vs);
     sg.halo_m = cur[o > 0 ? o - 1 : 0];
@@ -179,20 +186,28 @@ __device__ __forceinline__ float res_segment(const SegGeo &pt, const float *cur,
         load_pack<float, 4>(cur + (m < 0 ? 0 : m), sg.rows[2]);
         load_pack<float, 4>(cur + (p > kResCap - 4 ? kResCap - 4 : p), sg.rows[3]);
     }
-    BandArgs a;
-    a.wf_move = pt.wm;
-    a.wf_perp = pt.wp;
-    a.wf_stay = pt.wst;
-    a.wf_gamma = pt.g;
-    return sg.template finish_vi<false>(a, nxt, nullptr, o);
+    float self[4], nb[2 * D][4];
+    sg.neighbours(self, nb);
+    float out[4], res = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        float nbk[2 * D];
+#pragma unroll
+        for (int j = 0; j < 2 * D; j++) nbk[j] = nb[j][k];
+        const float v = sg.r[k] + gs[k] * vi_best_e<float, D>(self[k], nbk, pt.wm, pt.wp, pt.wst);
+        out[k] = v;
+        res = fmaxf(res, fabsf(v - self[k]));
+    }
+    store_pack<float, 4>(nxt + o, out);
+    return res;
 }
 
 __device__ __forceinline__ float res_chunk(int D, const SegGeo &pt, const float *cur, float *nxt, unsigned bufoff,
-                                           const float *Rp, const uint8_t *codep, int o) {
+                                           const ResArgs &a, int o) {
     switch (D) {
-    case 1: return res_segment<1>(pt, cur, nxt, bufoff, Rp, codep, o);
-    case 2: return res_segment<2>(pt, cur, nxt, bufoff, Rp, codep, o);
-    default: return res_segment<3>(pt, cur, nxt, bufoff, Rp, codep, o);
+    case 1: return res_segment<1>(pt, cur, nxt, bufoff, a, o);
+    case 2: return res_segment<2>(pt, cur, nxt, bufoff, a, o);
+    default: return res_segment<3>(pt, cur, nxt, bufoff, a, o);
     }
 }
 
@@ -206,11 +221,14 @@ __device__ __forceinline__ long long res_global(const ResPart &pt, int rel) {
     return pt.goff + ((long long)zl * pt.ny + y) * pt.nx + x;
 }
 
-__device__ __forceinline__ void res_load(const ResPart &pt, float *buf0, const float *V) {
+// The part's values into buffer 0: padding and obstacles as 0 (an
+// obstacle's value is never read and its result is 0).
+__device__ __forceinline__ void res_load(const ResPart &pt, float *buf0, const float *V, const uint8_t *codep) {
     const int n = pt.nchunks * kResChunk;
+    const unsigned obst = 1u << (2 * pt.D);
     for (int rel = threadIdx.x; rel < n; rel += blockDim.x) {
         const long long g = res_global(pt, rel);
-        buf0[pt.base + rel] = g >= 0 ? V[g] : 0.f;
+        buf0[pt.base + rel] = g >= 0 && !(codep[pt.poff + rel] & obst) ? V[g] : 0.f;
     }
 }
 
@@ -254,7 +272,7 @@ __device__ void res_solo(const ResArgs &a, ResShared &S, float *buf) {
             const ResPart &lastp = S.part[np - 1];
             nch = lastp.base / kResChunk + lastp.nchunks;
         }
-        for (int p = 0; p < np; p++) res_load(S.part[p], buf, a.V);
+        for (int p = 0; p < np; p++) res_load(S.part[p], buf, a.V, a.codep);
         __syncthreads();
         for (int q = 0;; q++) {
             if (tid < np) S.slot[tid][(q + 1) % 3] = 0u;
@@ -271,7 +289,7 @@ __device__ void res_solo(const ResArgs &a, ResShared &S, float *buf) {
                     gD = S.part[p].D;
                     gp = p;
                 }
-                const float r = res_chunk(gD, geo, cur, nxt, 0u, a.Rp, a.codep, c * kResChunk + 4 * lane);
+                const float r = res_chunk(gD, geo, cur, nxt, 0u, a, c * kResChunk + 4 * lane);
                 const unsigned mx = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(r));
                 if (lane == 0) atomicMax(&S.slot[p][q % 3], mx);
                 worked = true;
@@ -330,7 +348,7 @@ __device__ void res_cluster(const ResArgs &a, ResShared &S, float *buf, int C) {
             }
         }
         __syncthreads();
-        if (have) res_load(S.part[0], buf, a.V);
+        if (have) res_load(S.part[0], buf, a.V, a.codep);
         SegGeo geo;
         geo.load(S.part[0]);
         const int D = S.part[0].D, inst = S.part[0].inst;
@@ -359,7 +377,7 @@ __device__ void res_cluster(const ResArgs &a, ResShared &S, float *buf, int C) {
             const unsigned bufoff = (unsigned)((q & 1) * kResCap * 4);
             if (have) {
                 for (int c = warp; c < nch; c += kResWarps) {
-                    const float r = res_chunk(D, geo, cur, nxt, bufoff, a.Rp, a.codep, c * kResChunk + 4 * lane);
+                    const float r = res_chunk(D, geo, cur, nxt, bufoff, a, c * kResChunk + 4 * lane);
                     const unsigned mx = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(r));
                     if (lane == 0) atomicMax(&S.slot[1][q & 1], mx);
                 }
@@ -388,25 +406,31 @@ __global__ void __launch_bounds__(kResThreads, 1) resident_vi_kernel(ResArgs a) 
     res_solo(a, S, buf);
 }
 
-// Padded copies of the rewards and codes: instance i at pad_off[i], its
-// leading slices one after another, rows padded to nxp with obstacle codes.
+// Padded copies of the rewards, the expectation multipliers and the codes:
+// instance i at pad_off[i], its leading slices one after another, rows
+// padded to nxp with obstacle codes. Multiplier: gamma on free states, 0 on
+// terminals, obstacles and padding; reward 0 on obstacles and padding.
 __global__ void res_pad_kernel(const BatchInst *inst, const long long *pad_off, const float *R, const uint8_t *code,
-                               float *Rp, uint8_t *codep) {
+                               float *Rp, float *Gp, uint8_t *codep) {
     const BatchInst I = inst[blockIdx.x];
     const int nx = I.shape[I.ndim - 1], nxp = (nx + 3) & ~3;
     const int ny = I.ndim == 3 ? I.shape[1] : 1;
     const int L = I.ndim == 1 ? 1 : I.shape[0];
     const int P = ny * nxp;
+    const unsigned obst = 1u << (2 * I.ndim), term = 1u << (2 * I.ndim + 1);
     const long long n = (long long)L * P, base = pad_off[blockIdx.x];
     for (long long idx = threadIdx.x; idx < n; idx += blockDim.x) {
         const int zl = (int)(idx / P), rem = (int)(idx - (long long)zl * P);
         const int y = rem / nxp, x = rem - y * nxp;
         if (x < nx) {
             const long long g = I.offset + ((long long)zl * ny + y) * nx + x;
-            Rp[base + idx] = R[g];
-            codep[base + idx] = code[g];
+            const unsigned c = code[g];
+            Rp[base + idx] = (c & obst) ? 0.f : R[g];
+            Gp[base + idx] = (c & (obst | term)) ? 0.f : I.gamma;
+            codep[base + idx] = (uint8_t)c;
         } else {
             Rp[base + idx] = 0.f;
+            Gp[base + idx] = 0.f;
             codep[base + idx] = 0xFF;
         }
     }
@@ -487,6 +511,7 @@ cpmdp_status batch_resident_prepare(cpmdp_batch &B) {
     }
     const size_t nparts_max = (size_t)B.ninst * C;
     CPMDP_CUDA(cudaMalloc(&B.d_Rp, sizeof(float) * (size_t)off));
+    CPMDP_CUDA(cudaMalloc(&B.d_Gp, sizeof(float) * (size_t)off));
     CPMDP_CUDA(cudaMalloc(&B.d_codep, (size_t)off));
     CPMDP_CUDA(cudaMalloc(&B.d_rparts, sizeof(ResPart) * nparts_max));
     CPMDP_CUDA(cudaMalloc(&B.d_rmulti, sizeof(int2) * (size_t)B.ninst));
@@ -496,7 +521,7 @@ cpmdp_status batch_resident_prepare(cpmdp_batch &B) {
     CPMDP_CUDA(cudaMalloc(&d_pad, sizeof(long long) * (size_t)B.ninst));
     struct FreePad { long long *p; ~FreePad() { cudaFree(p); } } free_pad{d_pad};
     CPMDP_CUDA(cudaMemcpy(d_pad, pad.data(), sizeof(long long) * (size_t)B.ninst, cudaMemcpyHostToDevice));
-    res_pad_kernel<<<B.ninst, 256>>>(B.d_inst, d_pad, B.d_R, B.d_code, B.d_Rp, B.d_codep);
+    res_pad_kernel<<<B.ninst, 256>>>(B.d_inst, d_pad, B.d_R, B.d_code, B.d_Rp, B.d_Gp, B.d_codep);
     CPMDP_CUDA(cudaGetLastError());
     CPMDP_CUDA(cudaDeviceSynchronize());
     B.res_pad = pad;
@@ -684,6 +709,7 @@ cudaError_t batch_resident_enqueue(const cpmdp_batch &B, float *V, double tol, i
     a.hdr = B.d_rhdr;
     a.ctr = B.d_rhdr + 2;
     a.Rp = B.d_Rp;
+    a.Gp = B.d_Gp;
     a.codep = B.d_codep;
     a.V = V;
     a.done_at = B.d_done;
