@@ -212,6 +212,43 @@ def test_batch_resident_equals_batched_kernel(cp):
     B.close()
 
 
+@pytest.mark.parametrize("shapes", [
+    # 2-D grids larger than one CTA (cut into row ranges over a cluster of 2), small ones beside them
+    [(150, 200), (201, 140), (9, 7), (64, 64), (3, 5, 7)],
+    # a 3-D grid that needs 6 CTAs (clusters of 8), 1-D and 2-D instances beside it
+    [(100, 40, 40), (40, 47, 45), (37,), (120, 9), (8, 8, 8)],
+])
+def test_batch_resident_cluster_sizes(cp, shapes):
+    """The resident solver's cluster size is the smallest power of two that
+    fits every instance (2 and 8 here); parts of one instance on
+    neighbouring ranks exchange their edge slices (rows in 2-D, planes in
+    3-D). Sweeps, values and residuals equal the batched kernel's (fused=2)
+    bit for bit, and every instance matches the FP64 oracle within the value
+    bound of the first test."""
+    import torch
+    from oracle import cpfactor as oc
+    inst = [ci.gridworld(s, p=0.7 + 0.04 * j, gamma=0.93 + 0.01 * j, step_reward=-0.04,
+                         goal_rewards=[1.0, -1.0], obstacle_rate=0.05, seed=700 + j) for j, s in enumerate(shapes)]
+    B = cp.batch_build(inst, device=0)
+    out = {}
+    for fused in (1, 2):
+        V = torch.zeros(int(B.total_states), dtype=torch.float32, device="cuda")
+        r, it, res = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=5000, fused=fused))
+        out[fused] = (V.cpu().numpy(), it, res, r)
+    (Va, ia, ra, xa), (Vb, ib, rb, xb) = out[1], out[2]
+    assert xa["solver"] == cp.SOLVER_BATCH_RESIDENT
+    assert np.array_equal(ia, ib) and np.array_equal(ra, rb)
+    assert np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+    Vh = Va.astype(np.float64)
+    for i, gw in enumerate(inst):
+        lo, n = int(B.offsets[i]), gw.nstates
+        Vo, _, ko, _ = oc.value_iteration(gw, tol=1e-6, max_iter=5000)
+        eps = 14 * U32 * (np.abs(gw.reward).max() + np.abs(Vo).max())
+        bound = (2 * gw.gamma * 1e-6 + eps) / (1 - gw.gamma)
+        assert np.abs(Vh[lo:lo + n] - Vo).max() <= bound, (i, gw.shape)
+    B.close()
+
+
 def test_batch_certify_policy_matches_oracle(cp):
     """cpmdp_batch_certify after a batched solve: per instance the certified
     residual equals the oracle's own FP64 backup of the returned values
