@@ -53,6 +53,9 @@ struct ResPart {
     int prev_off;          // state offset of that CTA's last slice (rank - 1)
     unsigned prev_addr, next_addr;  // shared::cluster addresses (set in the kernel)
     float wm, wp, wst, g;
+    int bidx;              // cluster bundles: index of the part's instance in the bundle
+    int nbinst;            //   instances in the bundle (each over consecutive ranks)
+    int lead;              //   rank of the instance's first part (records its result)
 };
 
 struct ResArgs {

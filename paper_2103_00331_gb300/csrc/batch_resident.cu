@@ -18,11 +18,11 @@
 //    sweep in lockstep (one __syncthreads per sweep), each stopping on its
 //    own residual (its chunks are skipped from then on).
 //  * A cluster bundle is one instance cut into C parts of consecutive
-//    slices, one per CTA of a cluster of C; the slices adjacent to a part
-//    are read from the neighbouring CTA's buffer through distributed shared
-//    memory, the residual of a sweep is combined in the shared memory of the
-//    CTA holding the first part, and the cluster barrier (hardware, release
-//    / acquire) separates the sweeps.
+//    slices, one per CTA of a cluster of C (or two instances of C / 2 parts
+//    each); the slices adjacent to a part are read from the neighbouring
+//    CTA's buffer through distributed shared memory, each CTA's residual of
+//    a sweep goes to its instance's slot in every CTA of the cluster, and
+//    the cluster barrier (hardware, release / acquire) separates the sweeps.
 //
 // The backup of a 4-state segment is Segment::finish_vi, the arithmetic of
 // the batched kernel: values, sweep counts and residuals equal that
@@ -62,9 +62,9 @@ constexpr int kResWarps = kResThreads / 32;
 
 struct ResShared {
     ResPart part[kResMaxParts];
-    unsigned slot[kResMaxParts][3];   // residual bits of sweep q in slot q % 3 (cluster: slot[0] of the lead)
+    unsigned slot[kResMaxParts][3];   // residual bits of sweep q in slot q % 3 (cluster: slot[b] of instance b)
     int done[kResMaxParts];           // sweeps done (negative: stopped at max_iter)
-    unsigned local;                   // cluster bundles: this CTA's residual of the sweep
+    unsigned lmax[2];                 // cluster bundles: this CTA's residual of the sweep, by parity
     int job;
     uint8_t chunk_part[kResChunks];
 };
@@ -316,11 +316,14 @@ __device__ void res_solo(const ResArgs &a, ResShared &S, float *buf) {
     }
 }
 
-// Cluster bundles: one instance over the C CTAs of the cluster, part r on
-// rank r (ranks past the bundle's parts only keep the barriers). Every CTA
-// sends its residual of a sweep to the slot of every CTA (C remote max
-// reductions), so after the cluster barrier each CTA reads the instance's
-// residual from its own shared memory.
+// Cluster bundles: one instance over the C CTAs of the cluster, or two
+// instances over C / 2 consecutive ranks each (part r on rank r). Every CTA
+// sends its residual of a sweep to its instance's slot in every CTA of the
+// cluster (C remote max reductions), so after the cluster barrier each CTA
+// reads every instance's residual from its own shared memory: an instance
+// stops on its own (its CTAs keep the barriers until the bundle ends, and
+// its slots, no longer written, read as below tol from then on), and the
+// bundle ends when none runs.
 __device__ void res_cluster(const ResArgs &a, ResShared &S, float *buf, int C) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned rank = cluster_ctarank();
@@ -336,9 +339,9 @@ __device__ void res_cluster(const ResArgs &a, ResShared &S, float *buf, int C) {
         }
         const int2 bd = a.multi[job];
         const bool have = (int)rank < bd.y;
+        if (tid < 8) S.slot[tid][0] = S.slot[tid][1] = S.slot[tid][2] = 0u;
         if (tid == 0) {
-            S.slot[0][0] = S.slot[0][1] = S.slot[0][2] = 0u;
-            S.slot[1][0] = S.slot[1][1] = 0u;   // this CTA's residual of the sweep, by parity
+            S.lmax[0] = S.lmax[1] = 0u;
             if (have) {
                 ResPart pt = a.parts[bd.x + rank];
                 const unsigned b0 = smem_addr(buf);
@@ -352,38 +355,46 @@ __device__ void res_cluster(const ResArgs &a, ResShared &S, float *buf, int C) {
         SegGeo geo;
         geo.load(S.part[0]);
         const int D = S.part[0].D, inst = S.part[0].inst;
-        // lane t < C of warp 0 sends to rank t's slots
-        const unsigned slot_remote = tid < C ? cluster_map(smem_addr(&S.slot[0][0]), (unsigned)tid) : 0u;
+        const int bidx = have ? S.part[0].bidx : 0, nb = have ? S.part[0].nbinst : 1;
+        const bool lead = have && (int)rank == S.part[0].lead;
+        // lane t < C of warp 0 sends to rank t's slot of this CTA's instance
+        const unsigned slot_remote =
+            tid < C ? cluster_map(smem_addr(&S.slot[bidx][0]), (unsigned)tid) : 0u;
         cluster_sync_all();
         const int nch = have ? S.part[0].nchunks : 0;
         int sweeps = 0;
+        bool running = have;
         for (int q = 0;; q++) {
             if (q > 0) {
-                // the residual of sweep q - 1, complete in every CTA's own slot
-                const unsigned v = S.slot[0][(q - 1) % 3];
-                const bool below = res_below(v, a.tol_bits);
-                if (below || q >= a.max_iter) {
-                    if (rank == 0 && tid == 0) res_record(a, inst, below ? q : -q, v, q - 1);
-                    sweeps = q;
-                    break;
+                // every instance's residual of sweep q - 1, complete in this
+                // CTA's own slots (every CTA reads the same values)
+                bool any = false;
+                for (int b = 0; b < nb; b++) {
+                    const unsigned v = S.slot[b][(q - 1) % 3];
+                    const bool stop = res_below(v, a.tol_bits) || q >= a.max_iter;
+                    any |= !stop;
+                    if (b == bidx && stop && running) {
+                        running = false;
+                        sweeps = q;
+                        if (lead && tid == 0) res_record(a, inst, res_below(v, a.tol_bits) ? q : -q, v, q - 1);
+                    }
                 }
+                if (!any) break;
             }
-            if (tid == 0) {
-                S.slot[0][(q + 1) % 3] = 0u;
-                S.slot[1][(q + 1) & 1] = 0u;
-            }
+            if (tid < nb) S.slot[tid][(q + 1) % 3] = 0u;
+            if (tid == 0) S.lmax[(q + 1) & 1] = 0u;
             const float *cur = buf + (q & 1) * kResCap;
             float *nxt = buf + ((q + 1) & 1) * kResCap;
             const unsigned bufoff = (unsigned)((q & 1) * kResCap * 4);
-            if (have) {
+            if (running) {
                 for (int c = warp; c < nch; c += kResWarps) {
                     const float r = res_chunk(D, geo, cur, nxt, bufoff, a, c * kResChunk + 4 * lane);
                     const unsigned mx = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(r));
-                    if (lane == 0) atomicMax(&S.slot[1][q & 1], mx);
+                    if (lane == 0) atomicMax(&S.lmax[q & 1], mx);
                 }
             }
             __syncthreads();
-            if (tid < C && have) red_cluster_max(slot_remote + 4u * (unsigned)(q % 3), S.slot[1][q & 1]);
+            if (tid < C && running) red_cluster_max(slot_remote + 4u * (unsigned)(q % 3), S.lmax[q & 1]);
             cluster_sync_all();
         }
         if (have) res_store(S.part[0], buf + (sweeps & 1) * kResCap, a.V);
@@ -613,31 +624,64 @@ cpmdp_status batch_resident_plan(cpmdp_batch &B, double tol, int max_iter) {
         p.g = I.gamma;
         return p;
     };
-    // cluster bundles, longest first
-    std::vector<std::pair<double, int>> mlist;
-    for (int i : order)
-        if (split[(size_t)i]) {
-            const InstGeo &g = geo[(size_t)i];
-            const int per = (g.L + C - 1) / C;
-            mlist.push_back({est[(size_t)i] * sweep_cost(chunks_of((long long)per * g.P), true), i});
-        }
-    std::stable_sort(mlist.begin(), mlist.end(), [](const std::pair<double, int> &x, const std::pair<double, int> &y) {
-        return x.first > y.first;
-    });
-    for (const auto &m : mlist) {
-        const int i = m.second;
+    // cluster bundles, longest first: an instance that needs at most C / 2
+    // CTAs for its size goes with another such instance of similar sweep
+    // count, C / 2 ranks each (half the barriers per instance); the others,
+    // and the solo-sized instances cut for the length of the launch, take
+    // all C ranks
+    auto cluster_parts = [&](int i, int r0, int k, int bidx, int nb) {
         const InstGeo &g = geo[(size_t)i];
-        const int first = (int)parts.size();
         int z0 = 0;
-        std::vector<int> nsl((size_t)C);
-        for (int r = 0; r < C; r++) nsl[(size_t)r] = g.L / C + (r < g.L % C ? 1 : 0);
-        for (int r = 0; r < C; r++) {
+        std::vector<int> nsl((size_t)k);
+        for (int r = 0; r < k; r++) nsl[(size_t)r] = g.L / k + (r < g.L % k ? 1 : 0);
+        for (int r = 0; r < k; r++) {
             ResPart p = make_part(i, z0, nsl[(size_t)r], 0);
             p.has_prev = r > 0 ? 1 : 0;
-            p.has_next = r + 1 < C ? 1 : 0;
+            p.has_next = r + 1 < k ? 1 : 0;
             p.prev_off = r > 0 ? (nsl[(size_t)r - 1] - 1) * g.P : 0;
+            p.bidx = bidx;
+            p.nbinst = nb;
+            p.lead = r0;
             parts.push_back(p);
             z0 += nsl[(size_t)r];
+        }
+    };
+    std::vector<int> halves;
+    std::vector<std::pair<double, std::pair<int, int>>> mlist;   // (time, (instance, partner or -1))
+    for (int i : order) {
+        if (!split[(size_t)i]) continue;
+        const InstGeo &g = geo[(size_t)i];
+        if (C >= 4 && g.kmin >= 2 && 2 * g.kmin <= C) {
+            halves.push_back(i);
+        } else {
+            const int per = (g.L + C - 1) / C;
+            mlist.push_back({est[(size_t)i] * sweep_cost(chunks_of((long long)per * g.P), true), {i, -1}});
+        }
+    }
+    for (size_t h = 0; h < halves.size(); h += 2) {
+        const int i = halves[h];
+        const InstGeo &g = geo[(size_t)i];
+        if (h + 1 < halves.size()) {
+            const int j2 = halves[h + 1];
+            const InstGeo &g2 = geo[(size_t)j2];
+            const int per = std::max((g.L + C / 2 - 1) / (C / 2) * g.P, (g2.L + C / 2 - 1) / (C / 2) * g2.P);
+            mlist.push_back({est[(size_t)i] * sweep_cost(chunks_of(per), true), {i, j2}});
+        } else {
+            const int per = (g.L + C - 1) / C;
+            mlist.push_back({est[(size_t)i] * sweep_cost(chunks_of((long long)per * g.P), true), {i, -1}});
+        }
+    }
+    std::stable_sort(mlist.begin(), mlist.end(),
+                     [](const std::pair<double, std::pair<int, int>> &x, const std::pair<double, std::pair<int, int>> &y) {
+                         return x.first > y.first;
+                     });
+    for (const auto &m : mlist) {
+        const int first = (int)parts.size();
+        if (m.second.second < 0) {
+            cluster_parts(m.second.first, 0, C, 0, 1);
+        } else {
+            cluster_parts(m.second.first, 0, C / 2, 0, 2);
+            cluster_parts(m.second.second, C / 2, C / 2, 1, 2);
         }
         multi.push_back(make_int2(first, C));
     }
