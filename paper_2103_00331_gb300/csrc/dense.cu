@@ -61,6 +61,26 @@ __global__ void __launch_bounds__(256) mode_product_kernel(const T *__restrict__
     for (int a = 0; a < 4; a++)
 #pragma unroll
         for (int b = 0; b < 4; b++) acc[a][b] = 0;
+    // The columns this thread loads are the same in every K step: their
+    // offsets (l N Rt + r for column c = l Rt + r) are computed once, with no
+    // 64-bit division inside the loop. Rt > 1: one column (tid % TC), rows
+    // tid / TC + 4 m; Rt == 1: rows tid % TK, columns tid / TK + 16 m.
+    constexpr int kLd = TK * TC / 256;   // X elements a thread loads per K step
+    long long xoff[kLd];
+    bool xok[kLd];
+#pragma unroll
+    for (int m = 0; m < kLd; m++) {
+        const int cc = Rt == 1 ? tid / TK + (256 / TK) * m : tid % TC;
+        const long long c = c0 + cc;
+        xok[m] = c < ncols;
+        if (Rt == 1) {
+            xoff[m] = c * N;
+        } else {
+            const long long l = c / Rt, r = c - l * Rt;
+            xoff[m] = l * N * Rt + r;
+        }
+        if (Rt != 1) break;   // one column: xoff[0]
+    }
 
     for (int j0 = 0; j0 < N; j0 += TK) {
         // U tile: 64 rows x 16 columns, loaded along j
@@ -70,17 +90,14 @@ __global__ void __launch_bounds__(256) mode_product_kernel(const T *__restrict__
             sU[jj][ii] = (i < N && j < N) ? U[(long long)i * N + j] : (T)0;
         }
         // X tile: 16 x 64; coalesce along r when Rt > 1, along j when Rt == 1
-        for (int e = tid; e < TK * TC; e += 256) {
-            int jj, cc;
-            if (Rt == 1) { jj = e % TK; cc = e / TK; }
-            else { cc = e % TC; jj = e / TC; }
+#pragma unroll
+        for (int m = 0; m < kLd; m++) {
+            const int jj = Rt == 1 ? tid % TK : tid / TC + (256 / TC) * m;
+            const int cc = Rt == 1 ? tid / TK + (256 / TK) * m : tid % TC;
             const int j = j0 + jj;
-            const long long c = c0 + cc;
+            const int mi = Rt == 1 ? m : 0;
             T v = 0;
-            if (j < N && c < ncols) {
-                const long long l = c / Rt, r = c - l * Rt;
-                v = X[(l * N + j) * Rt + r];
-            }
+            if (j < N && xok[mi]) v = X[xoff[mi] + (long long)j * (Rt == 1 ? 1 : Rt)];
             sX[jj][cc] = v;
         }
         __syncthreads();
@@ -101,6 +118,13 @@ __global__ void __launch_bounds__(256) mode_product_kernel(const T *__restrict__
 
     double local_res = 0.0;
     unsigned local_chg = 0;
+    long long sbase[4];   // state of (i = 0, column c): l N Rt + r
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+        const long long c = c0 + tx + 16 * b;
+        const long long l = Rt == 1 ? c : c / Rt, r = c - l * Rt;
+        sbase[b] = l * N * Rt + r;
+    }
 #pragma unroll
     for (int a = 0; a < 4; a++) {
         const int i = i0 + ty + 16 * a;
@@ -109,8 +133,7 @@ __global__ void __launch_bounds__(256) mode_product_kernel(const T *__restrict__
         for (int b = 0; b < 4; b++) {
             const long long c = c0 + tx + 16 * b;
             if (c >= ncols) continue;
-            const long long l = c / Rt, r = c - l * Rt;
-            const long long s = (l * N + i) * Rt + r;
+            const long long s = sbase[b] + (long long)i * Rt;
             if (!ep.enabled) { Y[s] = acc[a][b]; continue; }
             T *E = (T *)ep.E;
             const T e = (ep.first_rank ? (T)0 : E[s]) + (T)ep.lambda * acc[a][b];
