@@ -1,6 +1,7 @@
 // C ABI entry points of libcpmdp: problem validation, CP factor
 // construction (host), device upload, and dispatch to the solvers.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -180,7 +181,10 @@ static void build_gridworld(Factors &F) {
     }
 }
 
-static cpmdp_status validate(const cpmdp_problem *p) {
+// per_state: also check every reward and cell code on the host (device
+// GridWorld builds check them on the device instead, in the kernels that
+// convert the rewards and derive the move codes).
+static cpmdp_status validate(const cpmdp_problem *p, bool per_state) {
     if (!p) { set_error("problem is NULL"); return CPMDP_EINVAL; }
     if (p->ndim < 1 || p->ndim > CPMDP_MAX_DIM) { set_error("ndim %d outside [1, %d]", p->ndim, CPMDP_MAX_DIM); return CPMDP_EINVAL; }
     double S = 1;
@@ -191,7 +195,7 @@ static cpmdp_status validate(const cpmdp_problem *p) {
     if (S >= 2147483648.0) { set_error("|S| = %.0f exceeds 2^31 - 1", S); return CPMDP_EINVAL; }
     if (!(p->gamma >= 0.0 && p->gamma <= 1.0)) { set_error("gamma %g outside [0, 1]", p->gamma); return CPMDP_EINVAL; }
     if (!p->reward) { set_error("reward is NULL"); return CPMDP_EINVAL; }
-    {
+    if (per_state) {
         // a double is not finite exactly when its exponent bits are all ones:
         // one branch-free integer pass, then a search only when it failed
         const uint64_t *bits = reinterpret_cast<const uint64_t *>(p->reward);
@@ -204,7 +208,7 @@ static cpmdp_status validate(const cpmdp_problem *p) {
     if (p->kind == CPMDP_GRIDWORLD) {
         if (p->nactions != 2 * p->ndim) { set_error("GridWorld needs nactions = 2*ndim = %d (got %d)", 2 * p->ndim, p->nactions); return CPMDP_EINVAL; }
         if (!(p->p_success >= 0.0 && p->p_success <= 1.0)) { set_error("p_success %g outside [0, 1]", p->p_success); return CPMDP_EINVAL; }
-        if (p->cell) {
+        if (p->cell && per_state) {
             uint8_t top = 0;
             for (int64_t s = 0; s < (int64_t)S; s++) top = p->cell[s] > top ? p->cell[s] : top;
             if (top > CPMDP_CELL_TERMINAL)
@@ -227,6 +231,19 @@ static cpmdp_status validate(const cpmdp_problem *p) {
 
 // Code of blocked moves of one state (the same rule as build_gridworld), for
 // host queries on factors whose codes live on the device only.
+static const uint8_t *host_cells(const Factors &F) {
+    if ((int64_t)F.cell.size() != F.nstates) {
+        F.cell.resize((size_t)F.nstates);
+        DeviceGuard g(F.device);
+        if (cudaMemcpy(F.cell.data(), F.d_cell, (size_t)F.nstates, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            (void)cudaGetLastError();
+            F.cell.clear();
+            return nullptr;
+        }
+    }
+    return F.cell.data();
+}
+
 static uint32_t code_of(const Factors &F, int64_t s) {
     const int D = F.ndim;
     const uint32_t all_dirs = (uint32_t)((1ull << (2 * D)) - 1);
@@ -252,13 +269,16 @@ struct CodeGeom {
 // Per-state codes of blocked moves from the cell kinds (device copy of the
 // rule in build_gridworld), stored in `cb` bytes per state. |S| < 2^31 is
 // validated, so 32-bit coordinates suffice (64-bit division is emulated).
-__global__ void codes_kernel(const uint8_t *__restrict__ cell, CodeGeom g, int S, int cb, uint8_t *__restrict__ out) {
+// bad (nullable): set to 1 + the index of a cell code other than 0, 1, 2.
+__global__ void codes_kernel(const uint8_t *__restrict__ cell, CodeGeom g, int S, int cb, uint8_t *__restrict__ out,
+                             unsigned long long *bad) {
     const int D = g.ndim;
     const uint32_t all_dirs = (uint32_t)((1ull << (2 * D)) - 1);
     // the loop index is 64-bit so the stride step cannot overflow near |S| = 2^31
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < S; i += (long long)gridDim.x * blockDim.x) {
         const int s = (int)i;
         const uint8_t k = cell[s];
+        if (bad && k > CPMDP_CELL_TERMINAL) atomicCAS(bad, 0ull, (unsigned long long)s + 1ull);
         uint32_t c;
         if (k == CPMDP_CELL_OBSTACLE) {
             c = all_dirs | (1u << (2 * D));
@@ -280,14 +300,24 @@ __global__ void codes_kernel(const uint8_t *__restrict__ cell, CodeGeom g, int S
     }
 }
 
-__global__ void to_f32_kernel(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        b[i] = (float)a[i];
+// bad (nullable): set to 1 + the index of a value that is not finite (all
+// exponent bits set; an integer test, no FP64 instruction).
+__global__ void to_f32_kernel(const double *__restrict__ a, float *__restrict__ b, int64_t n,
+                              unsigned long long *bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = a[i];
+        if (bad && ((__double_as_longlong(x) >> 52) & 0x7FF) == 0x7FF) atomicCAS(bad, 0ull, (unsigned long long)i + 1ull);
+        b[i] = (float)x;
+    }
 }
 
 // reward: the caller's rewards (device GridWorld builds keep no host copy),
-// or F.reward.
-static cpmdp_status upload(Factors &F, const double *reward) {
+// or F.reward; cell: the caller's cell kinds (NULL: all free) or F.cell.
+// The copies and kernels go to the legacy default stream in order; device
+// GridWorld builds check every reward (finite) and cell code (0, 1, 2) in
+// the conversion and code kernels, and the one synchronising read of the
+// build reads those checks.
+static cpmdp_status upload(Factors &F, const double *reward, const uint8_t *cell) {
     DeviceGuard g(F.device);
     if (!g.ok) { set_error("cannot select CUDA device %d", F.device); return CPMDP_ECUDA; }
     CPMDP_CUDA(cudaDeviceGetAttribute(&F.num_sms, cudaDevAttrMultiProcessorCount, F.device));
@@ -319,26 +349,39 @@ static cpmdp_status upload(Factors &F, const double *reward) {
         F.d_flow = arena + o_flow;
         F.flow_in_arena = true;
         F.flow_base = 0;
-        CPMDP_CUDA(cudaMemset(static_cast<char *>(F.d_flow) + flow_counter_bytes(), 0xFF,
-                              flow_bytes(F) - flow_counter_bytes()));
+        CPMDP_CUDA(cudaMemsetAsync(static_cast<char *>(F.d_flow) + flow_counter_bytes(), 0xFF,
+                                   flow_bytes(F) - flow_counter_bytes(), 0));
     }
-    CPMDP_CUDA(cudaMemcpy(F.d_R64, reward, S * sizeof(double), cudaMemcpyHostToDevice));
-    to_f32_kernel<<<blocks, 256>>>(F.d_R64, F.d_R32, F.nstates);
+    const bool check = F.kind == CPMDP_GRIDWORLD;
+    CPMDP_CUDA(cudaMemsetAsync(F.d_ctrl, 0, sizeof(Ctrl), 0));
+    CPMDP_CUDA(cudaMemcpyAsync(F.d_R64, reward, S * sizeof(double), cudaMemcpyHostToDevice, 0));
+    to_f32_kernel<<<blocks, 256>>>(F.d_R64, F.d_R32, F.nstates, check ? &F.d_ctrl->bad_reward : nullptr);
     CPMDP_CUDA(cudaGetLastError());
-    CPMDP_CUDA(cudaMemcpy(F.d_cell, F.cell.data(), S, cudaMemcpyHostToDevice));
-    CPMDP_CUDA(cudaMemset(F.d_ctrl, 0, sizeof(Ctrl)));
+    if (cell) CPMDP_CUDA(cudaMemcpyAsync(F.d_cell, cell, S, cudaMemcpyHostToDevice, 0));
+    else CPMDP_CUDA(cudaMemsetAsync(F.d_cell, CPMDP_CELL_FREE, S, 0));
     if (F.kind == CPMDP_GRIDWORLD) {
         CodeGeom geo{};
         geo.ndim = F.ndim;
         for (int d = 0; d < F.ndim; d++) { geo.shape[d] = (int)F.shape[d]; geo.stride[d] = (int)F.stride[d]; }
-        codes_kernel<<<blocks, 256>>>(F.d_cell, geo, (int)F.nstates, (int)cb, static_cast<uint8_t *>(F.d_code));
+        codes_kernel<<<blocks, 256>>>(F.d_cell, geo, (int)F.nstates, (int)cb, static_cast<uint8_t *>(F.d_code),
+                                      &F.d_ctrl->bad_cell);
         CPMDP_CUDA(cudaGetLastError());
     } else {
         cpmdp_status st = dense_prepare(F);
         if (st != CPMDP_OK) return st;
     }
-    // building is synchronous: the codes and FP32 rewards are complete on return
-    CPMDP_CUDA(cudaStreamSynchronize(0));
+    // building is synchronous: this read waits for the codes and FP32
+    // rewards and returns the device-side checks
+    unsigned long long bad[2] = {0ull, 0ull};
+    static_assert(offsetof(Ctrl, bad_cell) == offsetof(Ctrl, bad_reward) + sizeof(unsigned long long),
+                  "bad_reward and bad_cell are adjacent");
+    CPMDP_CUDA(cudaMemcpy(bad, &F.d_ctrl->bad_reward, sizeof(bad), cudaMemcpyDeviceToHost));
+    if (bad[0]) { set_error("reward[%lld] is not finite", (long long)(bad[0] - 1)); return CPMDP_EINVAL; }
+    if (bad[1]) {
+        const long long b = (long long)(bad[1] - 1);
+        set_error("cell[%lld] = %d is not 0, 1 or 2", b, cell ? (int)cell[b] : -1);
+        return CPMDP_EINVAL;
+    }
     return CPMDP_OK;
 }
 
@@ -371,7 +414,9 @@ cpmdp_status cpmdp_build_factors(const cpmdp_problem *p, int device, cpmdp_facto
     g_err[0] = 0;
     if (!out) { set_error("out is NULL"); return CPMDP_EINVAL; }
     *out = nullptr;
-    cpmdp_status st = validate(p);
+    // device GridWorld builds check the rewards and cell codes on the device
+    const bool device_gw = device >= 0 && p && p->kind == CPMDP_GRIDWORLD;
+    cpmdp_status st = validate(p, !device_gw);
     if (st != CPMDP_OK) return st;
     cpmdp_factors *h = new (std::nothrow) cpmdp_factors();
     if (!h) { set_error("host allocation failed"); return CPMDP_ENOMEM; }
@@ -390,8 +435,12 @@ cpmdp_status cpmdp_build_factors(const cpmdp_problem *p, int device, cpmdp_facto
         // device GridWorld builds upload the caller's rewards directly; host-only
         // factors (batches) and dense models keep a host copy
         if (device < 0 || p->kind != CPMDP_GRIDWORLD) F.reward.assign(p->reward, p->reward + S);
-        if (p->cell) F.cell.assign(p->cell, p->cell + S);
-        else F.cell.assign((size_t)S, (uint8_t)CPMDP_CELL_FREE);
+        // device GridWorld builds upload the caller's cell kinds directly (a
+        // host copy is made on the first host query that needs one)
+        if (!device_gw) {
+            if (p->cell) F.cell.assign(p->cell, p->cell + S);
+            else F.cell.assign((size_t)S, (uint8_t)CPMDP_CELL_FREE);
+        }
         if (F.kind == CPMDP_GRIDWORLD) {
             build_gridworld(F);
         } else {
@@ -437,7 +486,7 @@ cpmdp_status cpmdp_build_factors(const cpmdp_problem *p, int device, cpmdp_facto
         return CPMDP_ENOMEM;
     }
     if (device >= 0) {
-        st = upload(F, F.reward.empty() ? p->reward : F.reward.data());
+        st = upload(F, F.reward.empty() ? p->reward : F.reward.data(), device_gw ? p->cell : F.cell.data());
         if (st != CPMDP_OK) {
             DeviceGuard g(device);
             free_device(F);
@@ -476,7 +525,9 @@ cpmdp_status cpmdp_components(const cpmdp_factors *h, int64_t s, int32_t a, int6
     if (s < 0 || s >= F.nstates || a < 0 || a >= F.nactions) { set_error("state or action out of range"); return CPMDP_EINVAL; }
     if (cap > 0 && (!next || !prob)) { set_error("next/prob NULL with cap > 0"); return CPMDP_EINVAL; }
     *count = 0;
-    if (F.cell[(size_t)s] != CPMDP_CELL_FREE) return CPMDP_OK;
+    const uint8_t *cells = host_cells(F);
+    if (!cells) { set_error("cannot read the cell kinds back from the device"); return CPMDP_ECUDA; }
+    if (cells[(size_t)s] != CPMDP_CELL_FREE) return CPMDP_OK;
     const int D = F.ndim;
     const uint32_t code = F.code.empty() ? code_of(F, s) : F.code[(size_t)s];
     std::map<int64_t, double> acc;

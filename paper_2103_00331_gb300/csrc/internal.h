@@ -39,6 +39,8 @@ struct Ctrl {
     int handoff;                   // batch: 1 when the batched kernel stopped for the barrier-free tail
     int handoff_sweeps;            // batch: sweeps done before the hand-off
     int plain_stop;                // plain baseline, device-checked variant: stop every later kernel
+    unsigned long long bad_reward; // factor build: 1 + index of a reward that is not finite (0: none)
+    unsigned long long bad_cell;   // factor build: 1 + index of a cell code other than 0, 1, 2 (0: none)
 };
 
 struct Factors {
@@ -57,7 +59,10 @@ struct Factors {
     int code_bytes = 1;
 
     // host copies
-    std::vector<uint8_t> cell;
+    // host copy of the cell kinds: host-only factors keep one from the build;
+    // device GridWorld factors fill it from the device on the first host
+    // query that needs it (cpmdp_components)
+    mutable std::vector<uint8_t> cell;
     std::vector<double> reward;
     std::vector<uint32_t> code;        // banded code per state (host, widened)
     std::vector<double> dense_factors; // [a][r][d] blocks

@@ -377,3 +377,36 @@ def test_device_factors_components_match_host(cp, shape):
             assert cp.components(fd, s, a) == cp.components(fh, s, a)
     fd.close()
     fh.close()
+
+
+def test_device_build_checks_inputs_on_the_device(cp):
+    """A device GridWorld build checks every reward (finite) and cell code
+    (0, 1 or 2) in its conversion and code kernels instead of on the host:
+    the same EINVAL and message as a host-only build, and the device stays
+    usable (the next build and solve succeed)."""
+    import torch
+    base = ci.gridworld((6, 7, 9), p=0.8, gamma=0.95, step_reward=-0.04, goal_rewards=[1.0], obstacle_rate=0.1,
+                        seed=5)
+    r = np.asarray(base.reward, dtype=np.float64).reshape(-1).copy()
+    r[123] = np.nan
+    pr = cp.make_problem(shape=base.shape, nactions=6, kind=cp.GRIDWORLD, reward=r, gamma=0.95, p_success=0.8,
+                         cell=np.asarray(base.cell, dtype=np.uint8).reshape(-1))
+    with pytest.raises(cp.CpmdpError) as ei:
+        cp.build_factors(pr, device=0)
+    assert ei.value.status == cp.EINVAL and "reward[123] is not finite" in cp.last_error()
+    c = np.asarray(base.cell, dtype=np.uint8).reshape(-1).copy()
+    c[200] = 7
+    pr = cp.make_problem(shape=base.shape, nactions=6, kind=cp.GRIDWORLD,
+                         reward=np.asarray(base.reward, dtype=np.float64).reshape(-1), gamma=0.95, p_success=0.8, cell=c)
+    with pytest.raises(cp.CpmdpError) as ei:
+        cp.build_factors(pr, device=0)
+    assert ei.value.status == cp.EINVAL and "cell[200] = 7" in cp.last_error()
+    # the device is fine: a valid build solves, and its host query reads the cells back from the device
+    f = cp.build_factors(base, device=0)
+    V = torch.zeros(base.nstates, dtype=torch.float32, device="cuda")
+    res = cp.value_iteration(f, cp.F32, V, None, opts=cp.default_opts(max_iter=5000))
+    assert res["status"] == cp.OK
+    free = int(np.flatnonzero(np.asarray(base.cell).reshape(-1) == 0)[0])
+    comps = cp.components(f, free, 0)
+    assert comps and abs(sum(pr_ for _, pr_ in comps) - 1.0) < 1e-12
+    f.close()
