@@ -301,3 +301,38 @@ def test_batch_certify_policy_matches_oracle(cp):
         compared += int(sure_o.sum())
     assert compared > 1000
     B.close()
+
+
+def test_batch_full_4096_certified_and_sampled(cp):
+    """The full 4096-instance batch (2-D sides 8..128, 3-D sides 8..48) in the
+    configuration the benchmark times (shared-memory-resident solver,
+    default options, second solve scheduled from the first's sweep counts):
+    every instance converges, its FP64 certified residual (the FP64 backup
+    of the returned values) is at most tol plus one FP32 backup's rounding
+    bound eps = 14 u (max|R| + max|V|), and every 128th instance plus the
+    slowest one equal the FP64 oracle's value iteration within the value
+    bound of the first test."""
+    import torch
+    from oracle import cpfactor as oc
+    inst = ci.batch_gridworlds(count=4096, seed=0)
+    B = cp.batch_build(inst, device=0)
+    V = torch.zeros(int(B.total_states), dtype=torch.float32, device="cuda")
+    cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=5000))
+    V.zero_()
+    r, iters, res = cp.batch_value_iteration(B, V, opts=cp.default_opts(max_iter=5000))
+    assert r["status"] == cp.OK and r["solver"] == cp.SOLVER_BATCH_RESIDENT and np.all(res < 1e-6)
+    cert = cp.batch_certify(B, V)
+    Vh = V.double().cpu().numpy()
+    for i, gw in enumerate(inst):
+        lo, n = int(B.offsets[i]), gw.nstates
+        eps = 14 * U32 * (np.abs(gw.reward).max() + np.abs(Vh[lo:lo + n]).max())
+        assert cert[i] <= 1e-6 + eps, (i, cert[i], eps)
+    picks = sorted(set(range(0, 4096, 128)) | {int(np.argmax(iters))})
+    for i in picks:
+        gw = inst[i]
+        lo, n = int(B.offsets[i]), gw.nstates
+        Vo, _, ko, _ = oc.value_iteration(gw, tol=1e-6, max_iter=5000)
+        eps = 14 * U32 * (np.abs(gw.reward).max() + np.abs(Vo).max())
+        bound = (2 * gw.gamma * 1e-6 + eps) / (1 - gw.gamma)
+        assert np.abs(Vh[lo:lo + n] - Vo).max() <= bound, (i, gw.shape)
+    B.close()
