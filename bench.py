@@ -891,7 +891,9 @@ def hbm_sweep(cp, dev, stream, peak):
 
 def kernel_case(name, reps=3):
     """Run one kernel workload a few times and exit (for ncu captures):
-    sweep512 / sweep320 = fused FP32 backup of a 512^3 / 320^3 GridWorld; solve64 / pi64 = fused
+    sweep512 / sweep320 = fused FP32 backup of a 512^3 / 320^3 GridWorld; dense64 / dense64f64 = one
+    FP32 / FP64 SIMT sweep of the 64^4 dense CP model; dense64tc = one BF16x3 tensor-core sweep of it;
+    solve64 / pi64 = fused
     FP32 value / policy iteration of the 64^3 instance (barrier-free solver);
     solve64b / pi64b = the same on the grid-barrier solver; ws512 = the warm-start network on
     512 x 16^3 coarse cells (six tensor-core convolutions); batch1024 = batched value iteration of
@@ -930,6 +932,21 @@ def kernel_case(name, reps=3):
             flops = 2.0 * 64 * 4 * dc.nstates * dc.nactions * dc.rank
             print(f"dense 64^4 BF16x3 tcgen05 sweep: {ms:.3f} ms, {flops / ms / 1e9:.1f} TFLOP/s (FP32-equivalent), "
                   f"{3 * flops / ms / 1e9:.1f} TFLOP/s bf16")
+            Va, Vb = Vb, Va
+    elif name == "dense64f64":
+        dc = ci.config_dense_4d(side=64, seed=0)
+        f = cp.build_factors(dc, device=0)
+        Va = torch.as_tensor(ci.random_values(dc.shape, seed=2).reshape(-1)).to(dev)
+        Vb = torch.empty_like(Va)
+        res = torch.zeros(1, dtype=torch.float64, device=dev)
+        for i in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            cp.bellman_backup(f, cp.F64, Va, Vb, None, res)
+            e1.record()
+            torch.cuda.synchronize()
+            flops = 2.0 * 64 * 4 * dc.nstates * dc.nactions * dc.rank
+            print(f"dense 64^4 FP64 SIMT sweep: {e0.elapsed_time(e1):.3f} ms, {flops / e0.elapsed_time(e1) / 1e9:.3f} TFLOP/s")
             Va, Vb = Vb, Va
     elif name == "dense64":
         dc = ci.config_dense_4d(side=64, seed=0)
@@ -1036,7 +1053,7 @@ def main():
     ap.add_argument("--skip-dense", action="store_true")
     ap.add_argument("--skip-warmstart", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--kernel-case", choices=["sweep512", "sweep320", "solve64", "pi64", "solve64b", "pi64b", "dense64", "batch4096", "batchres1024",
+    ap.add_argument("--kernel-case", choices=["sweep512", "sweep320", "solve64", "pi64", "solve64b", "pi64b", "dense64", "dense64f64", "batch4096", "batchres1024",
                                               "dense64tc", "ws512", "batch1024", "batchcert"],
                     default=None,
                     help="run one kernel workload a few times (profiling) and exit")
