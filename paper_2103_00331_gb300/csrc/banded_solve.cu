@@ -138,6 +138,139 @@ __global__ void __launch_bounds__(256) solve_pi_kernel(BandArgs a, T *V, T *Wbuf
 }
 
 
+// Grids that one block covers (at most 256 segments, where the kernels
+// above run a single block anyway): the same solvers with the value
+// ping-pong in shared memory and each sweep's residual and stop decision
+// taken in shared memory (one block barrier per sweep, no global atomics or
+// control-block round trips). Same per-state arithmetic and stopping rules,
+// so the same values, sweep counts and residuals as the kernels above.
+constexpr int kSmallMaxItems = 256;
+
+template <typename T, int D, int VEC>
+__global__ void __launch_bounds__(256) small_vi_kernel(BandArgs a, T *V, SolveParams sp, Ctrl *ctrl,
+                                                       double *trace) {
+    typedef T TA;
+    extern __shared__ __align__(16) unsigned char small_raw[];
+    __shared__ unsigned shm[64];
+    __shared__ unsigned long long s_mb;
+    T *cur = reinterpret_cast<T *>(small_raw), *nxt = cur + a.nstates;
+    const int nitems = a.nstates / VEC;
+    for (int i = threadIdx.x; i < a.nstates; i += blockDim.x) cur[i] = V[i];
+    __syncthreads();
+    int k = 0, converged = 0;
+    unsigned long long last = 0ull;
+    while (k < sp.max_iter) {
+        TA r = 0;
+        for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
+            Segment<T, TA, D, VEC> sg;
+            sg.template load<M_VI>(a, cur, nullptr, i * VEC);
+            const TA x = sg.template finish_vi<false>(a, nxt, nullptr, i * VEC);
+            r = x > r ? x : r;
+        }
+        const unsigned long long mb = block_max_bits(r, shm);
+        if (threadIdx.x == 0) s_mb = mb;
+        __syncthreads();   // the sweep's writes and its residual, for every thread
+        const unsigned long long m = s_mb;
+        if (trace && threadIdx.x == 0) trace[k] = __longlong_as_double((long long)m);
+        last = m;
+        k++;
+        T *t = cur; cur = nxt; nxt = t;
+        if (below_tol(m, sp.tol)) { converged = 1; break; }
+    }
+    for (int i = threadIdx.x; i < a.nstates; i += blockDim.x) V[i] = cur[i];
+    if (threadIdx.x == 0) {
+        ctrl->iterations = k;
+        ctrl->converged = converged;
+        ctrl->last_residual = __longlong_as_double((long long)last);
+        ctrl->backups = (long long)k * a.nstates * sp.nactions;
+    }
+}
+
+template <typename T, int D, int VEC>
+__global__ void __launch_bounds__(256) small_pi_kernel(BandArgs a, T *V, uint8_t *pi, SolveParams sp, Ctrl *ctrl) {
+    typedef T TA;
+    extern __shared__ __align__(16) unsigned char small_raw[];
+    __shared__ unsigned shm[64];
+    __shared__ unsigned shu[32];
+    __shared__ unsigned long long s_mb;
+    __shared__ unsigned s_c;
+    T *cur = reinterpret_cast<T *>(small_raw), *nxt = cur + a.nstates;
+    const int nitems = a.nstates / VEC;
+    for (int i = threadIdx.x; i < a.nstates; i += blockDim.x) cur[i] = V[i];
+    __syncthreads();
+    int total = 0, round = 0, evals = 0, converged = 0;
+    long long backups = 0;
+    unsigned long long last = 0ull;
+    unsigned changed_total = 0, dummy = 0;
+    // initial policy: greedy with respect to the input V
+    for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
+        Segment<T, TA, D, VEC> sg;
+        sg.template load<M_GREEDY>(a, cur, pi, i * VEC);
+        sg.template finish_pi<M_GREEDY>(a, nullptr, pi, (TA)0, i * VEC, dummy);
+    }
+    __syncthreads();
+    total++;
+    backups += (long long)a.nstates * sp.nactions;
+    // modified policy iteration: evaluations capped at partial_eval sweeps
+    // until an improvement changes no action, full evaluations after that
+    bool full = sp.partial_eval <= 0;
+    while (round < sp.max_rounds) {
+        const int cap = full ? sp.max_eval_iter : min(sp.partial_eval, sp.max_eval_iter);
+        int e = 0, eval_ok = 0;
+        while (e < cap) {
+            TA r = 0;
+            for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
+                Segment<T, TA, D, VEC> sg;
+                sg.template load<M_EVAL>(a, cur, pi, i * VEC);
+                const TA x = sg.template finish_pi<M_EVAL>(a, nxt, pi, (TA)0, i * VEC, dummy);
+                r = x > r ? x : r;
+            }
+            const unsigned long long mb = block_max_bits(r, shm);
+            if (threadIdx.x == 0) s_mb = mb;
+            __syncthreads();
+            const unsigned long long m = s_mb;
+            last = m;
+            e++;
+            total++;
+            backups += a.nstates;
+            T *t = cur; cur = nxt; nxt = t;
+            if (below_tol(m, sp.eval_tol)) { eval_ok = 1; break; }
+        }
+        evals += e;
+        unsigned changed = 0;
+        for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
+            Segment<T, TA, D, VEC> sg;
+            sg.template load<M_IMPROVE>(a, cur, pi, i * VEC);
+            sg.template finish_pi<M_IMPROVE>(a, nullptr, pi, (TA)sp.margin, i * VEC, changed);
+        }
+        const unsigned c0 = block_sum(changed, shu);
+        if (threadIdx.x == 0) s_c = c0;
+        __syncthreads();   // the policy changes and their count, for every thread
+        const unsigned c = s_c;
+        changed_total += c;
+        total++;
+        round++;
+        backups += (long long)a.nstates * sp.nactions;
+        if (c == 0) {
+            if (eval_ok) { converged = 1; break; }
+            if (full) break;   // the evaluation limit ran out
+            full = true;       // evaluate this policy to eval_tol before deciding
+            continue;
+        }
+        if (!eval_ok && full) break;
+    }
+    for (int i = threadIdx.x; i < a.nstates; i += blockDim.x) V[i] = cur[i];
+    if (threadIdx.x == 0) {
+        ctrl->rounds = round;
+        ctrl->eval_sweeps = evals;
+        ctrl->iterations = total;
+        ctrl->converged = converged;
+        ctrl->last_residual = __longlong_as_double((long long)last);
+        ctrl->backups = backups;
+        ctrl->changed_total = changed_total;
+    }
+}
+
 template <typename K>
 static cudaError_t coop_grid(K kern, const Factors &F, int nitems, int &cache, int &grid) {
     if (cache <= 0) {
@@ -188,13 +321,29 @@ static cudaError_t launch_pi(const Factors &F, T *V, T *W, uint8_t *pi, const So
 }
 
 
+template <typename T, int D, int VEC>
+static cudaError_t launch_small(const Factors &F, bool pim, T *V, uint8_t *pi, const SolveParams &sp, double *trace,
+                                cudaStream_t st) {
+    BandArgs a = make_band_args(F);
+    const size_t smem = 2 * (size_t)F.nstates * sizeof(T);
+    if (pim) small_pi_kernel<T, D, VEC><<<1, 256, smem, st>>>(a, V, pi, sp, F.d_ctrl);
+    else small_vi_kernel<T, D, VEC><<<1, 256, smem, st>>>(a, V, sp, F.d_ctrl, trace);
+    return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t solve_t(const Factors &F, bool pim, T *V, uint8_t *pi, const SolveParams &sp, double *trace,
-                           cudaStream_t st) {
+                           bool small_ok, cudaStream_t st) {
     T *W = (T *)F.d_scratch;
     const int vec = band_pick_vec(F, sizeof(T), V, W);
     constexpr int V2 = (int)(16 / sizeof(T));
     cudaError_t e = cudaErrorInvalidValue;
+    // one block's worth of segments, values within the default 48 KB of shared memory
+    if (small_ok && F.nstates / vec <= kSmallMaxItems && 2 * (size_t)F.nstates * sizeof(T) <= 48 * 1024) {
+        if (vec == 1) { CPMDP_DISPATCH_D(F.ndim, e = (launch_small<T, DD, 1>(F, pim, V, pi, sp, trace, st))); }
+        else { CPMDP_DISPATCH_D(F.ndim, e = (launch_small<T, DD, V2>(F, pim, V, pi, sp, trace, st))); }
+        return e;
+    }
     if (pim) {
         if (vec == 1) { CPMDP_DISPATCH_D(F.ndim, e = (launch_pi<T, DD, 1>(F, V, W, pi, sp, st))); }
         else { CPMDP_DISPATCH_D(F.ndim, e = (launch_pi<T, DD, V2>(F, V, W, pi, sp, st))); }
@@ -243,9 +392,12 @@ cpmdp_status banded_solve(const Factors &F, cpmdp_precision prec, bool policy_it
         CPMDP_CUDA(march_solve(F, (float *)V, o.tol, o.max_iter, o.trace, st));
         return CPMDP_OK;
     }
+    // grids one block covers: the shared-memory single-block kernels
+    // (fused = 2 keeps the grid-barrier kernels; the stall aid needs their barrier)
+    const bool small_ok = o.fused == 1 && !o.inject_stall;
     cudaError_t e;
-    if (prec == CPMDP_F64) e = solve_t<double>(F, policy_iteration, (double *)V, pi, sp, o.trace, st);
-    else e = solve_t<float>(F, policy_iteration, (float *)V, pi, sp, o.trace, st);
+    if (prec == CPMDP_F64) e = solve_t<double>(F, policy_iteration, (double *)V, pi, sp, o.trace, small_ok, st);
+    else e = solve_t<float>(F, policy_iteration, (float *)V, pi, sp, o.trace, small_ok, st);
     CPMDP_CUDA(e);
     return CPMDP_OK;
 }

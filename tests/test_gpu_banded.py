@@ -410,3 +410,37 @@ def test_device_build_checks_inputs_on_the_device(cp):
     comps = cp.components(f, free, 0)
     assert comps and abs(sum(pr_ for _, pr_ in comps) - 1.0) < 1e-12
     f.close()
+
+
+@pytest.mark.parametrize("shape,prec", [((10, 10), 1), ((10, 10), 0), ((37,), 1), ((5, 6, 7), 1), ((3, 9, 5), 0),
+                                         ((21, 23), 1), ((2, 2), 1)])
+def test_single_block_solver_equals_grid_barrier(cp, shape, prec):
+    """Grids one block covers (at most 256 segments) run value and policy
+    iteration in a single block with the values in shared memory (fused=1);
+    the grid-barrier kernels (fused=2) run the same per-state arithmetic and
+    stopping rules through global memory: values, policies, sweep, round and
+    evaluation counts and the last residual equal, bit for bit (FP64 and
+    FP32, rows of odd and even length, 1-D to 3-D)."""
+    import torch
+    gw = ci.gridworld(shape, p=0.8, gamma=0.93, step_reward=-0.04,
+                      goal_rewards=[1.0, -1.0][:min(2, int(np.prod(shape)) - 1)], obstacle_rate=0.1, seed=41)
+    f = cp.build_factors(gw, device=0)
+    dt = torch.float64 if prec == 1 else torch.float32
+    pr = cp.F64 if prec == 1 else cp.F32
+    out = {}
+    for fused in (1, 2):
+        V = torch.zeros(gw.nstates, dtype=dt, device="cuda")
+        pi = torch.zeros(gw.nstates, dtype=torch.uint8, device="cuda")
+        r = cp.value_iteration(f, pr, V, pi, opts=cp.default_opts(max_iter=5000, fused=fused))
+        V2 = torch.zeros(gw.nstates, dtype=dt, device="cuda")
+        pi2 = torch.zeros(gw.nstates, dtype=torch.uint8, device="cuda")
+        r2 = cp.policy_iteration(f, pr, V2, pi2, opts=cp.default_opts(max_iter=5000, fused=fused))
+        out[fused] = (V.cpu().numpy(), pi.cpu().numpy(), r, V2.cpu().numpy(), pi2.cpu().numpy(), r2)
+    a, b = out[1], out[2]
+    assert np.array_equal(a[0].view(np.uint8), b[0].view(np.uint8)) and np.array_equal(a[1], b[1])
+    assert a[2]["iterations"] == b[2]["iterations"] and a[2]["residual"] == b[2]["residual"]
+    assert a[2]["certified_residual"] == b[2]["certified_residual"]
+    assert np.array_equal(a[3].view(np.uint8), b[3].view(np.uint8)) and np.array_equal(a[4], b[4])
+    for k in ("iterations", "rounds", "eval_sweeps", "residual"):
+        assert a[5][k] == b[5][k], (k, a[5][k], b[5][k])
+    f.close()
