@@ -131,7 +131,10 @@ typedef struct {
     int32_t max_iter;        /* sweep limit (default 1000, the paper's maxIter) */
     int32_t certify;         /* 1 (default): after F32 solves, one FP64 sweep of the result gives the
                                 certified residual and the policy (FP64 argmax) */
-    int32_t fused;           /* 1 (default): fused device-resident solver; FP32 GridWorld solves of
+    int32_t fused;           /* 1 (default): fused device-resident solver; GridWorlds one block covers
+                                (at most 256 segments of the vector width) run in a single block with
+                                the values in shared memory (same values and sweep counts as the
+                                grid-barrier solver); FP32 GridWorld solves of
                                 1 to 3 dimensions whose rows are a multiple of 4 states and that fit
                                 one co-resident grid at one thread per column of 1, 2 or 4 segments of
                                 4 states run barrier-free (sweeps synchronised through sweep-tagged
