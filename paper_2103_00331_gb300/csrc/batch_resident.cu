@@ -24,9 +24,12 @@
 //    a sweep goes to its instance's slot in every CTA of the cluster, and
 //    the cluster barrier (hardware, release / acquire) separates the sweeps.
 //
-// The backup of a 4-state segment is Segment::finish_vi, the arithmetic of
-// the batched kernel: values, sweep counts and residuals equal that
-// kernel's, bit for bit. Stopping: an instance stops after the first sweep
+// The backup of a 4-state segment resolves blocked moves with
+// Segment::neighbours and takes max_a E_a with vi_best_e, the arithmetic of
+// the batched kernel's value iteration; terminals and obstacles take a
+// per-state multiplier of max_a E_a (0 on them) instead of selects. Values,
+// sweep counts and residuals equal the batched kernel's, bit for bit.
+// Stopping: an instance stops after the first sweep
 // whose residual is below tol (or after max_iter sweeps); per instance the
 // residual of sweep q goes to slot q % 3 (slot q + 1 is cleared during
 // sweep q, after every reader of its previous use passed the barrier of
