@@ -1009,19 +1009,19 @@ def kernel_case(name, reps=3):
         B.close()
     elif name == "ws512":
         from paper_2103_00331_gb300 import warmstart as ws
-        path = os.path.join(ROOT, "paper_2103_00331_gb300", "data", "warmstart_weights.npz")
-        net = ws.WarmStartNet.load(path, device=0)
+        # six layers with dilations up to 4 (random weights: the time does not depend on them)
+        net = ws.WarmStartNet(device=0, seed=0, dilations=(1, 2, 4, 2, 1, 1))
         dims = (512, 16, 16, 16)
         nv = int(np.prod(dims))
         feat = torch.zeros((nv, 64), dtype=torch.bfloat16, device=dev)
-        feat[:, :4] = torch.as_tensor(ci.random_values((nv, 4), seed=5).astype(np.float32)).to(dev)
+        feat[:, :net.n_feat] = torch.as_tensor(ci.random_values((nv, net.n_feat), seed=5).astype(np.float32)).to(dev)
         for i in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             net.predict(feat, dims)
             e1.record()
             ws.ws_sync()
-            flops = 2.0 * nv * 27 * 64 * 64 * ws.LAYERS
+            flops = 2.0 * nv * 27 * 64 * 64 * net.layers
             print(f"warm-start network, 512 x 16^3 coarse cells: {e0.elapsed_time(e1):.3f} ms, "
                   f"{flops / e0.elapsed_time(e1) / 1e9:.1f} TFLOP/s bf16 (tcgen05 convolutions)")
     elif name in ("solve64", "pi64", "solve64b", "pi64b"):

@@ -388,7 +388,7 @@ cpmdp_status cpmdp_batch_certify(const cpmdp_batch *batch, const float *V, uint8
  * caller-owned; all calls asynchronous on `stream`; errors EINVAL / ECUDA.
  *
  * cpmdp_ws_features: coarse features of batch instances first..first+count-1
- *   (3-D, one shape, contiguous): per 4x4x4 cell the mean reward of its
+ *   (3-D, one shape): per 4x4x4 cell the mean reward of its
  *   non-obstacle states, its obstacle fraction, its largest terminal reward
  *   (0 if none), -log(1 - gamma) / 5; channels 4..63 zero.
  * cpmdp_ws_coarse_vi: value iteration of a coarsened copy of every instance
@@ -406,6 +406,14 @@ cpmdp_status cpmdp_batch_certify(const cpmdp_batch *batch, const float *V, uint8
  * cpmdp_ws_upsample: V (packed batch layout) = coarse + base (base NULL = 0)
  *   at the cell centres, interpolated trilinearly to every free state
  *   (clamped to the outermost centres); R(t) on terminals, 0 on obstacles.
+ * cpmdp_ws_fine_loss_grad: the loss of a coarse estimate on the full grid.
+ *   With Vh = the upsampling of pred + base (as cpmdp_ws_upsample) and
+ *   n = count * states per instance: r(s) = Vh(s) - V_target(s) on free
+ *   states, 0 on terminals and obstacles (written to resid, float
+ *   [count][states per instance], caller-owned scratch); *loss += sum r^2 / n
+ *   (loss device float, or NULL); dy channel 0 (bf16 [count][cells][64]) =
+ *   dloss/dpred = 2/n times the transpose of the interpolation applied to r,
+ *   channels 1..63 zero. V_target is in the packed batch layout.
  */
 cpmdp_status cpmdp_ws_features(const cpmdp_batch *batch, int32_t first, int32_t count, uint16_t *feat, void *stream);
 cpmdp_status cpmdp_ws_coarse_vi(const cpmdp_batch *batch, int32_t first, int32_t count, float tol, int32_t max_sweeps,
@@ -414,9 +422,16 @@ cpmdp_status cpmdp_ws_targets(const cpmdp_batch *batch, const float *V, int32_t 
                               float *target, float *mask, void *stream);
 cpmdp_status cpmdp_ws_upsample(const cpmdp_batch *batch, const float *coarse, const float *base, int32_t first,
                                int32_t count, float *V, void *stream);
+cpmdp_status cpmdp_ws_fine_loss_grad(const cpmdp_batch *batch, const float *V_target, int32_t first, int32_t count,
+                                     const float *pred, const float *base, float *resid, uint16_t *dy, float *loss,
+                                     void *stream);
 /* y = conv(x, W) + b (ReLU if relu); wf = the forward weight tiles written by cpmdp_ws_cast_weights;
  * y0 (nullable) gets channel 0 in FP32. Runs on the tcgen05 tensor cores (bf16 operands, FP32
- * accumulation): 128 voxels x 64 channels per CTA, 27 taps x K = 64. */
+ * accumulation in TMEM): persistent CTAs, tiles of 128 voxels x 64 channels, 27 taps x K = 64,
+ * inputs brought in by tensor copies (zero fill outside the grid). x and y 16-byte aligned; x is read
+ * through a tensor map, so the call fails with ECUDA where the driver offers none. Errors: EINVAL
+ * (dimensions, null pointers), ECUDA; a tensor-core wait that runs out is reported by
+ * cpmdp_ws_sync. */
 cpmdp_status cpmdp_conv3d_forward(const uint16_t *x, const uint16_t *wf, const float *bias, uint16_t *y, float *y0,
                                   int32_t n, int32_t z, int32_t y_, int32_t x_, int32_t dilation, int32_t relu,
                                   void *stream);

@@ -174,6 +174,26 @@ def coarse_target(gw, V):
     return t, m
 
 
+def _corners(p3, cshape):
+    """The eight (cell, weight) pairs of the trilinear interpolation at fine
+    coordinate p3: a coordinate p sits at (p + 0.5) / FACTOR - 0.5 in cell
+    units, clamped to the outermost centres (where the clamp folds two
+    corners onto one cell both pairs name it)."""
+    lo, hi, t = [], [], []
+    for p, n in zip(p3, cshape):
+        u = min(max((p + 0.5) / FACTOR - 0.5, 0.0), n - 1.0)
+        a = int(np.floor(u))
+        lo.append(a)
+        hi.append(min(a + 1, n - 1))
+        t.append(u - a)
+    out = []
+    for k in range(8):
+        pick = tuple((hi if (k >> (2 - d)) & 1 else lo)[d] for d in range(3))
+        w = np.prod([t[d] if (k >> (2 - d)) & 1 else 1.0 - t[d] for d in range(3)])
+        out.append((pick, w))
+    return out
+
+
 def upsample(gw, coarse):
     """Warm start on the full grid: the coarse values sit at the cell
     centres; a free state at fine coordinate x is at (x + 0.5) / FACTOR - 0.5
@@ -186,22 +206,34 @@ def upsample(gw, coarse):
     for z in range(shape[0]):
         for y in range(shape[1]):
             for x in range(shape[2]):
-                lo, hi, t = [], [], []
-                for p, n in zip((z, y, x), C.shape):
-                    u = min(max((p + 0.5) / FACTOR - 0.5, 0.0), n - 1.0)
-                    a = int(np.floor(u))
-                    lo.append(a)
-                    hi.append(min(a + 1, n - 1))
-                    t.append(u - a)
-                v = 0.0
-                for k in range(8):
-                    pick = [(hi if (k >> (2 - d)) & 1 else lo)[d] for d in range(3)]
-                    w = np.prod([t[d] if (k >> (2 - d)) & 1 else 1.0 - t[d] for d in range(3)])
-                    v += w * C[tuple(pick)]
-                V0[z, y, x] = v
+                V0[z, y, x] = sum(w * C[c] for c, w in _corners((z, y, x), C.shape))
     cell = np.asarray(gw.cell)
     V0 = np.where(cell == 2, np.asarray(gw.reward), V0)
     return np.where(cell == 1, 0.0, V0)
+
+
+def fine_loss_grad(gw, V_target, coarse, n=None):
+    """Loss of a coarse estimate on the full grid and its gradient:
+    r = upsample(coarse) - V_target on the free states (terminals and
+    obstacles are exact), loss = sum r^2 / n, and d loss / d coarse[c] =
+    2 / n * sum over free states of (interpolation weight of c) * r (the
+    transpose of the interpolation). n defaults to the instance's state
+    count."""
+    shape = gw.shape
+    C = np.asarray(coarse, dtype=np.float64)
+    Vt = np.asarray(V_target, dtype=np.float64).reshape(shape)
+    n = float(np.prod(shape)) if n is None else float(n)
+    Vh = upsample(gw, C)
+    free = np.asarray(gw.cell) == 0
+    r = np.where(free, Vh - Vt, 0.0)
+    grad = np.zeros(C.shape)
+    for z in range(shape[0]):
+        for y in range(shape[1]):
+            for x in range(shape[2]):
+                if r[z, y, x] != 0.0:
+                    for c, w in _corners((z, y, x), C.shape):
+                        grad[c] += 2.0 / n * w * r[z, y, x]
+    return float((r * r).sum() / n), grad
 
 
 def coarse_gridworld(gw):

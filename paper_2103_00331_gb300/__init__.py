@@ -107,6 +107,7 @@ def _load():
             ("cpmdp_ws_coarse_vi", [vp, i32, i32, ctypes.c_float, i32, vp, vp, vp]),
             ("cpmdp_ws_targets", [vp, vp, i32, i32, vp, vp, vp, vp]),
             ("cpmdp_ws_upsample", [vp, vp, vp, i32, i32, vp, vp]),
+            ("cpmdp_ws_fine_loss_grad", [vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]),
             ("cpmdp_conv3d_forward", [vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, i32, vp]),
             ("cpmdp_conv3d_backward_data", [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]),
             ("cpmdp_conv3d_backward_weight", [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]),
@@ -131,7 +132,7 @@ EXPORTED = ["cpmdp_default_opts", "cpmdp_build_factors", "cpmdp_free_factors", "
             "cpmdp_policy_iteration", "cpmdp_value_iteration_static", "cpmdp_batch_build",
             "cpmdp_batch_free", "cpmdp_batch_info", "cpmdp_batch_value_iteration", "cpmdp_batch_certify",
             "cpmdp_ws_features", "cpmdp_ws_coarse_vi",
-            "cpmdp_ws_targets", "cpmdp_ws_upsample", "cpmdp_conv3d_forward", "cpmdp_conv3d_backward_data",
+            "cpmdp_ws_targets", "cpmdp_ws_upsample", "cpmdp_ws_fine_loss_grad", "cpmdp_conv3d_forward", "cpmdp_conv3d_backward_data",
             "cpmdp_conv3d_backward_weight", "cpmdp_ws_loss_grad", "cpmdp_adam_step", "cpmdp_ws_cast_weights",
             "cpmdp_ws_sync", "cpmdp_last_error", "cpmdp_version"]
 
@@ -392,6 +393,14 @@ def ws_targets(batch, V, first, count, target, mask, base=None, stream=None):
 def ws_upsample(batch, coarse, first, count, V, base=None, stream=None):
     _check(lib.cpmdp_ws_upsample(batch.handle, _ptr(coarse), _ptr(base), int(first), int(count), _ptr(V),
                                  _stream(stream)))
+
+
+def ws_fine_loss_grad(batch, V_target, first, count, pred, base, resid, dy, loss=None, stream=None):
+    """``cpmdp_ws_fine_loss_grad``: loss of upsample(pred + base) against
+    V_target on the full grid (added to ``loss``) and its gradient with
+    respect to pred in channel 0 of ``dy``."""
+    _check(lib.cpmdp_ws_fine_loss_grad(batch.handle, _ptr(V_target), int(first), int(count), _ptr(pred), _ptr(base),
+                                       _ptr(resid), _ptr(dy), _ptr(loss), _stream(stream)))
 
 
 def conv3d_forward(x, wf, bias, y, y0, dims, dilation, relu, stream=None):
