@@ -742,14 +742,6 @@ __global__ void fine_grad_kernel(const BatchInst *__restrict__ inst, int first, 
 constexpr int kCoarseThreads = 512;
 constexpr int kMaxCoarseCells = 8192;
 
-__device__ __forceinline__ unsigned float_key(float f) {
-    const unsigned b = __float_as_uint(f);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float key_float(unsigned k) {
-    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
-}
-
 __global__ void __launch_bounds__(kCoarseThreads) coarse_vi_kernel(const BatchInst *__restrict__ inst,
                                                                    const uint8_t *__restrict__ code,
                                                                    const float *__restrict__ R, int first, int cells,
@@ -757,50 +749,64 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_vi_kernel(const BatchIn
                                                                    float *__restrict__ coarse_v,
                                                                    __nv_bfloat16 *__restrict__ feat) {
     extern __shared__ uint8_t smem_raw[];
-    int *n_obst = reinterpret_cast<int *>(smem_raw);                 // later: V (even sweeps)
-    int *n_free = n_obst + cells;                                    // later: V (odd sweeps)
-    float *rsum = reinterpret_cast<float *>(n_free + cells);         // later: coarse reward
-    unsigned *tkey = reinterpret_cast<unsigned *>(rsum + cells);     // largest terminal reward (0: none)
-    uint8_t *kind = reinterpret_cast<uint8_t *>(tkey + cells);      // bits 0-5 blocked moves, 6 obstacle, 7 terminal
+    float *va = reinterpret_cast<float *>(smem_raw);                 // V (even sweeps)
+    float *vb = va + cells;                                          // V (odd sweeps)
+    float *rsum = vb + cells;                                        // coarse reward
+    uint8_t *kind = reinterpret_cast<uint8_t *>(rsum + cells);      // bits 0-5 blocked moves, 6 obstacle, 7 terminal
     const int tid = threadIdx.x;
     const int i = blockIdx.x;
     const BatchInst I = inst[first + i];
     const int zc = (I.shape[0] + kF - 1) / kF, yc = (I.shape[1] + kF - 1) / kF, xc = (I.shape[2] + kF - 1) / kF;
-    for (int c = tid; c < cells; c += kCoarseThreads) {
-        n_obst[c] = 0;
-        n_free[c] = 0;
-        rsum[c] = 0.f;
-        tkey[c] = 0u;
-    }
-    __syncthreads();
     const unsigned ob = 1u << (2 * I.ndim), tb = 1u << (2 * I.ndim + 1);
-    for (int s = tid; s < I.nstates; s += kCoarseThreads) {   // coalesced over the fine states
-        const int z = s / I.stride[0], y = (s / I.stride[1]) % I.shape[1], x = s % I.shape[2];
-        const int c = ((z / kF) * yc + y / kF) * xc + x / kF;
-        const unsigned cs = code[I.offset + s];
-        if (cs & ob) { atomicAdd(&n_obst[c], 1); continue; }
-        const float r = R[I.offset + s];
-        if (cs & tb) { atomicMax(&tkey[c], float_key(r)); continue; }
-        atomicAdd(&n_free[c], 1);
-        atomicAdd(&rsum[c], r);
-    }
-    __syncthreads();
     const float g = I.gamma;
     const float gc = g * g * g * g, steps = 1.f + g + g * g + g * g * g;
+    // per cell, over its rows of up to 4 fine states (one 16-byte reward load
+    // and one 4-byte code load where the row is a full aligned group of 4)
     for (int c = tid; c < cells; c += kCoarseThreads) {
         const int cz = c / (yc * xc), cy = (c / xc) % yc, cx = c % xc;
-        const int n = (min((cz + 1) * kF, I.shape[0]) - cz * kF) * (min((cy + 1) * kF, I.shape[1]) - cy * kF) *
-                      (min((cx + 1) * kF, I.shape[2]) - cx * kF);
+        const int x0 = cx * kF, x1 = min(x0 + kF, I.shape[2]);
+        const bool vec = x1 - x0 == kF && I.shape[2] % 4 == 0 && I.offset % 4 == 0;
+        int n = 0, n_obst = 0, n_free = 0, any_t = 0;
+        float rs = 0.f, tmax = 0.f;
+        for (int z = cz * kF; z < min((cz + 1) * kF, I.shape[0]); z++)
+            for (int y = cy * kF; y < min((cy + 1) * kF, I.shape[1]); y++) {
+                const long long row = I.offset + (long long)z * I.stride[0] + (long long)y * I.stride[1];
+                float r4[kF];
+                unsigned c4[kF];
+                if (vec) {
+                    const float4 rv = *reinterpret_cast<const float4 *>(R + row + x0);
+                    const unsigned cw = *reinterpret_cast<const unsigned *>(code + row + x0);
+                    r4[0] = rv.x; r4[1] = rv.y; r4[2] = rv.z; r4[3] = rv.w;
+#pragma unroll
+                    for (int k = 0; k < kF; k++) c4[k] = (cw >> (8 * k)) & 0xFFu;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kF; k++) {
+                        const bool in = x0 + k < x1;
+                        r4[k] = in ? R[row + x0 + k] : 0.f;
+                        c4[k] = in ? code[row + x0 + k] : 0xFFFFFFFFu;   // outside the grid
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < kF; k++) {
+                    const unsigned cs = c4[k];
+                    if (cs == 0xFFFFFFFFu) continue;
+                    n++;
+                    if (cs & ob) { n_obst++; continue; }
+                    if (cs & tb) { tmax = any_t ? fmaxf(tmax, r4[k]) : r4[k]; any_t = 1; continue; }
+                    n_free++;
+                    rs += r4[k];
+                }
+            }
         uint8_t k = 0;
         float r = 0.f;
-        if (2 * n_obst[c] >= n) k = 0x40;
-        else if (tkey[c]) { k = 0x80; r = key_float(tkey[c]); }
-        else r = n_free[c] ? rsum[c] / (float)n_free[c] * steps : 0.f;
+        if (2 * n_obst >= n) k = 0x40;
+        else if (any_t) { k = 0x80; r = tmax; }
+        else r = n_free ? rs / (float)n_free * steps : 0.f;
         kind[c] = k;
         rsum[c] = r;
     }
     __syncthreads();
-    float *va = reinterpret_cast<float *>(n_obst), *vb = reinterpret_cast<float *>(n_free);
     for (int c = tid; c < cells; c += kCoarseThreads) {
         const int cz = c / (yc * xc), cy = (c / xc) % yc, cx = c % xc;
         uint8_t k = kind[c];
@@ -1029,7 +1035,7 @@ cpmdp_status cpmdp_ws_coarse_vi(const cpmdp_batch *B, int32_t first, int32_t cou
         return CPMDP_EINVAL;
     }
     if (!coarse_v || !(tol > 0.f) || max_sweeps < 1) { set_error("coarse_v, tol > 0 and max_sweeps >= 1 required"); return CPMDP_EINVAL; }
-    const size_t smem = (size_t)cells * 17;
+    const size_t smem = (size_t)cells * 13;
     CPMDP_CUDA(cudaFuncSetAttribute(coarse_vi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     coarse_vi_kernel<<<count, kCoarseThreads, smem, (cudaStream_t)stream>>>(B->d_inst, B->d_code, B->d_R, first, cells,
                                                                           tol, max_sweeps, coarse_v,
