@@ -160,12 +160,15 @@ typedef struct {
     double *trace;           /* optional device buffer of max_iter doubles: residual of each sweep
                                 (value iteration, fused path only; the barrier-free solver zeroes it
                                 first and also fills the entries of its two dropped sweeps) */
-    int32_t partial_eval;    /* policy iteration (default 8): while the policy keeps changing, each
+    int32_t partial_eval;    /* policy iteration (default 4): while the policy keeps changing, each
                                 round's evaluation stops after at most this many sweeps (modified
-                                policy iteration); once an improvement changes no action, every
-                                later round evaluates to eval_tol, and the solve stops only when
-                                an improvement after such a full evaluation changes no action.
-                                0: every round evaluates to eval_tol */
+                                policy iteration); once an improvement changes no action after a
+                                capped evaluation, every later round evaluates to eval_tol. The
+                                solve stops when an improvement changes no action and its own
+                                values are within eval_tol of its input. 0: every round evaluates
+                                to eval_tol. Dense models take the same caps with an improvement
+                                that writes no values: they stop after an evaluation to eval_tol
+                                whose improvement changes no action */
     int32_t inject_stall;    /* testing aid (default 0): 1 makes one block of the fused GridWorld
                                 solver leave at once (without arriving at its first grid barrier, or,
                                 barrier-free, without publishing its values), so the other blocks'
@@ -260,11 +263,15 @@ cpmdp_status cpmdp_value_iteration(const cpmdp_factors *factors, cpmdp_precision
 /*
  * Policy iteration (background section): start from the greedy policy of
  * the input V (device, in/out), then alternate evaluation of the fixed
- * policy (backup sweeps without the max, until opts->eval_tol) and greedy
- * improvement (an action changes only when another beats it by more than
- * 1e-6 (F32) or 1e-12 (F64) times 1 + |Q|); stop when no action changes.
- * V receives the value of the final policy, policy (device, |S|, not NULL)
- * the final policy. Synchronises with `stream` before returning.
+ * policy (backup sweeps without the max, until opts->eval_tol or the
+ * partial_eval cap) and greedy improvement (an action changes only when
+ * another beats it by more than 1e-6 (F32) or 1e-12 (F64) times 1 + |Q|).
+ * GridWorld models: the improvement sweep also writes the new policy's
+ * first evaluation step (Q of the action kept or taken, as in modified
+ * policy iteration), and the solve stops when it changes no action and
+ * moves no value by eval_tol or more. V receives the value of the final
+ * policy, policy (device, |S|, not NULL) the final policy. Synchronises
+ * with `stream` before returning.
  * BF16X3 (dense models, 64^4): evaluation sweeps are the tensor-core backup
  * with each state's own action (defect correction against an FP32 base, as
  * in value iteration); an improvement takes an evaluation-mode sweep, a max

@@ -403,7 +403,7 @@ void cpmdp_default_opts(cpmdp_solve_opts *o) {
     o->max_rounds = 1000;
     o->timeout_s = 2.0;
     o->trace = nullptr;
-    o->partial_eval = 8;
+    o->partial_eval = 4;
 }
 
 const char *cpmdp_last_error(void) { return g_err; }

@@ -315,8 +315,9 @@ struct Segment {
 
     // Policy-iteration sweeps: EVAL (V' = Q of the fixed action, returns the
     // residual), IMPROVE (switch to the argmax when it beats the current
-    // action by more than margin (1 + |Q|), count switches) and GREEDY
-    // (policy = argmax, lowest index on ties).
+    // action by more than margin (1 + |Q|), count switches; V' = Q of the
+    // action kept or taken, the first evaluation step of the new policy,
+    // and its residual) and GREEDY (policy = argmax, lowest index on ties).
     template <int MODE>
     __device__ __forceinline__ TA finish_pi(const BandArgs &a, T *W, uint8_t *pi, TA margin, int s0,
                                             unsigned &changed) const {
@@ -335,6 +336,7 @@ struct Segment {
             perp_sums(nb, k, perp);
             const TA stay = wst * self[k];
             TA v = self[k];
+            int na = (int)act[k];   // IMPROVE: the action after this sweep
             if (MODE == M_EVAL) {
                 TA nbk[NB];
 #pragma unroll
@@ -357,16 +359,26 @@ struct Segment {
                 }
                 if (MODE == M_IMPROVE) {
                     const TA thr = margin * ((TA)1 + (qold < 0 ? -qold : qold));
-                    if (arg != old && best > qold + thr) { pi[s] = (uint8_t)arg; changed++; }
+                    if (arg != old && best > qold + thr) { pi[s] = (uint8_t)arg; changed++; na = arg; }
                 } else {
                     pi[s] = (uint8_t)arg;
                 }
             } else if (MODE == M_GREEDY) {
                 pi[s] = 255;
             }
+            if (MODE == M_IMPROVE) {
+                TA nbk[NB];
+#pragma unroll
+                for (int j = 0; j < NB; j++) nbk[j] = nb[j][k];
+                v = eval_state<TA, D>(self[k], nbk, c, rk, na, wm, wp, wst, g);
+                if (!(c & OBST)) {
+                    const TA dv = abs_diff(v, self[k]);
+                    res = dv > res ? dv : res;
+                }
+            }
             out[k] = v;
         }
-        if (MODE == M_EVAL) {
+        if (MODE == M_EVAL || MODE == M_IMPROVE) {
             T o[VEC];
 #pragma unroll
             for (int k = 0; k < VEC; k++) o[k] = (T)out[k];

@@ -7,7 +7,9 @@
 // ends in a grid barrier whose arrival atomic also reports whether the
 // block's residual is still >= tol (VI, evaluation) or whether the block
 // changed an action (improvement): every block learns the stopping decision
-// from the barrier itself, with no extra round trip. The residual value goes
+// from the barrier itself, with no extra round trip (an improvement sweep,
+// which also writes the new policy's first evaluation step, adds its
+// residual through the slot below, read after the barrier). The residual value goes
 // to res_slot[k % 3] by atomic max (slot k+1 is cleared by block 0 during
 // sweep k, after every block has passed the barrier of sweep k-1, so nobody
 // still reads it); it is read for the trace and at the end. The host reads
@@ -105,20 +107,33 @@ __global__ void __launch_bounds__(256) solve_pi_kernel(BandArgs a, T *V, T *Wbuf
             if (open == 0) { eval_ok = 1; break; }
         }
         evals += e;
+        // improvement, and the new policy's first evaluation step V' = Q of
+        // the action kept or taken (modified policy iteration)
         unsigned changed = 0;
-        sweep_all<T, TA, D, VEC, M_IMPROVE, true>(a, cur, nullptr, pi, (TA)sp.margin, changed);
+        const TA r = sweep_all<T, TA, D, VEC, M_IMPROVE, true>(a, cur, nxt, pi, (TA)sp.margin, changed);
         const unsigned c = block_sum(changed, shu);
-        if (threadIdx.x == 0 && c) atomicAdd(&ctrl->changed_total, c);
+        const unsigned long long mb = block_max_bits(r, shm);
+        if (threadIdx.x == 0) {
+            if (c) atomicAdd(&ctrl->changed_total, c);
+            if (mb) atomicMax(&ctrl->res_slot[ks % 3], mb);
+        }
+        if (lead) ctrl->res_slot[(ks + 1) % 3] = 0ull;
         const long long moved = grid_sync_count(ctrl, nbar++, nb, threadIdx.x == 0 && c > 0, sp.timeout_ns,
                                                 ph0, ph1, false);
         if (moved < 0) return;
+        const bool open =
+            !below_tol(*(volatile unsigned long long *)&ctrl->res_slot[ks % 3], sp.eval_tol);
+        ks++;
         total++;
         round++;
         backups += (long long)a.nstates * sp.nactions;
+        T *t = cur; cur = nxt; nxt = t;
         if (moved == 0) {
-            if (eval_ok) { converged = 1; break; }
-            if (full) break;   // the evaluation limit ran out
-            full = true;       // evaluate this policy to eval_tol before deciding
+            if (!open) { converged = 1; break; }   // stable policy, V' within eval_tol of V
+            if (!eval_ok) {
+                if (full) break;   // the evaluation limit ran out
+                full = true;       // evaluate this policy to eval_tol before deciding
+            }
             continue;
         }
         if (!eval_ok && full) break;
@@ -237,24 +252,37 @@ __global__ void __launch_bounds__(256) small_pi_kernel(BandArgs a, T *V, uint8_t
             if (below_tol(m, sp.eval_tol)) { eval_ok = 1; break; }
         }
         evals += e;
+        // improvement, and the new policy's first evaluation step V' = Q of
+        // the action kept or taken (modified policy iteration)
         unsigned changed = 0;
+        TA r = 0;
         for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
             Segment<T, TA, D, VEC> sg;
             sg.template load<M_IMPROVE>(a, cur, pi, i * VEC);
-            sg.template finish_pi<M_IMPROVE>(a, nullptr, pi, (TA)sp.margin, i * VEC, changed);
+            const TA x = sg.template finish_pi<M_IMPROVE>(a, nxt, pi, (TA)sp.margin, i * VEC, changed);
+            r = x > r ? x : r;
         }
         const unsigned c0 = block_sum(changed, shu);
-        if (threadIdx.x == 0) s_c = c0;
-        __syncthreads();   // the policy changes and their count, for every thread
+        const unsigned long long mb = block_max_bits(r, shm);
+        if (threadIdx.x == 0) {
+            s_c = c0;
+            s_mb = mb;
+        }
+        __syncthreads();   // the policy changes, their count and V', for every thread
         const unsigned c = s_c;
+        const unsigned long long m = s_mb;
+        last = m;
         changed_total += c;
         total++;
         round++;
         backups += (long long)a.nstates * sp.nactions;
+        T *t = cur; cur = nxt; nxt = t;
         if (c == 0) {
-            if (eval_ok) { converged = 1; break; }
-            if (full) break;   // the evaluation limit ran out
-            full = true;       // evaluate this policy to eval_tol before deciding
+            if (below_tol(m, sp.eval_tol)) { converged = 1; break; }   // stable policy, V' within eval_tol
+            if (!eval_ok) {
+                if (full) break;   // the evaluation limit ran out
+                full = true;       // evaluate this policy to eval_tol before deciding
+            }
             continue;
         }
         if (!eval_ok && full) break;

@@ -2,7 +2,8 @@
 // GridWorld factors of 1 to 3 dimensions (background section: value
 // iteration repeats the Eq. 1 backup until it converges; policy iteration
 // alternates evaluation of a fixed policy with greedy improvement until no
-// action changes).
+// action changes; here in its modified form, whose improvement sweep also
+// takes the new policy's first evaluation step).
 //
 // The grid-barrier solver (banded_solve.cu) ends every sweep with a
 // grid-wide barrier. When the whole value tensor sits in L2 (64^3: 1 MB),
@@ -94,18 +95,20 @@ struct Arrivals {
     unsigned na = 0;    // arrivals made
     unsigned nchk = 0;  // arrivals checked (always in order)
 
-    __device__ __forceinline__ void arrive(bool flag) {
+    __device__ __forceinline__ void arrive(bool flag) { arrive_count(flag ? 1u : 0u); }
+    // Arrive adding `count` to the arrival's flag total (the checks return
+    // the sum over warps).
+    __device__ __forceinline__ void arrive_count(unsigned count) {
         if ((threadIdx.x & 31) == 0)
-            red_add_rlx(ctr + ((na % kSlots) * kNC + (unsigned)gw % kNC) * kLineWords,
-                        1ull | ((u64)(flag ? 1u : 0u) << 32));
+            red_add_rlx(ctr + ((na % kSlots) * kNC + (unsigned)gw % kNC) * kLineWords, 1ull | ((u64)count << 32));
         na++;
     }
     __device__ __forceinline__ u64 peek(unsigned i) const {
         const int lane = threadIdx.x & 31;
         return lane < kNC ? ld_rlx(ctr + ((i % kSlots) * kNC + lane) * kLineWords) : 0ull;
     }
-    // Warps that raised their flag at arrival i, or -1 if some warp has not
-    // reported it yet (then nothing is recorded). After A arrivals with F
+    // Warps that raised their flag at arrival i (the sum of their counts),
+    // or -1 if some warp has not reported it yet (then nothing is recorded). After A arrivals with F
     // raised flags a counter holds A + F * 2^32 as a 64-bit integer, carries
     // from the low half included, so with A known from i the check needs
     // only the low halves and F = (v - A) >> 32.
@@ -708,8 +711,12 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
             if (arv.check_next(ctrl, sp.timeout_ns) < 0) return;
         const unsigned hq = q;  // highest tag sequence written so far
         // sg.cur now holds V_rq, the values of this evaluation
-        // improvement on V_rq (tag base + rq, buffer rq mod kRing)
+        // improvement on V_rq (tag base + rq, buffer rq mod kRing), and the
+        // new policy's first evaluation step V' = Q of the action kept or
+        // taken (modified policy iteration)
         unsigned changed = 0;
+        float nxt[ZS][4];
+        float r = 0.f;
         {
             float rows[ZS][NR][4], hl[ZS], hr[ZS];
             if (!sg.gather(f, rq, base, sg.cur, rows, hl, hr, ctrl, sp.timeout_ns)) return;
@@ -725,6 +732,12 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
                     const int a = improve_state<D>(nb, sg.cur[i][k], c, sg.R[i][k], old, false, margin, wm, wp, wst,
                                                    g, ch);
                     act |= (unsigned)a << (8 * k);
+                    const float v = eval_state<float, D>(sg.cur[i][k], nb, c, sg.R[i][k], a, wm, wp, wst, g);
+                    nxt[i][k] = v;
+                    if (sg.valid[i] && !(c & OBST)) {
+                        const float dv = abs_diff(v, sg.cur[i][k]);
+                        r = dv > r ? dv : r;
+                    }
                 }
                 if (sg.valid[i]) {
                     sg.act[i] = act;
@@ -732,19 +745,29 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
                 }
             }
         }
-        // the next evaluation starts from V_rq republished as sequence hq + 1
+        // the next evaluation starts from V' published as sequence hq + 1
         q = hq + 1;
-        sg.publish(f, q, base, sg.cur);
+        sg.publish(f, q, base, nxt);
+#pragma unroll
+        for (int i = 0; i < ZS; i++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) sg.cur[i][k] = nxt[i][k];
+        rres = r;
         const unsigned wc = __reduce_add_sync(FULL, changed);
         if (lane == 0 && wc) atomicAdd(&ctrl->changed_total, wc);
-        arv.arrive(wc > 0);
+        // one arrival carries both counts: warps whose actions changed (low
+        // 16 bits) and warps whose residual is at or above eval_tol (high 16)
+        const bool wopen = warp_open(r, f.eval_tol_bits);
+        arv.arrive_count((wc > 0 ? 1u : 0u) + (wopen ? 65536u : 0u));
         const int moved = arv.check_next(ctrl, sp.timeout_ns);
         if (moved < 0) return;
         round++;
-        if (moved == 0) {
-            if (eval_ok) { conv = 1; break; }
-            if (full) break;   // the evaluation limit ran out
-            full = true;       // evaluate this policy to eval_tol before deciding
+        if ((moved & 0xFFFF) == 0) {
+            if ((moved >> 16) == 0) { conv = 1; break; }   // stable policy, V' within eval_tol
+            if (!eval_ok) {
+                if (full) break;   // the evaluation limit ran out
+                full = true;       // evaluate this policy to eval_tol before deciding
+            }
             continue;
         }
         if (!eval_ok && full) break;
