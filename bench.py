@@ -43,7 +43,8 @@ SIDE = 64
 TOL = 1e-6
 BYTES_VI = 13      # per state per VI sweep: V 4 + R 4 + code 1 + V' 4
 BYTES_EVAL = 14    # + policy read
-BYTES_IMPROVE = 10 # V 4 + R 4 + code 1 + policy 1
+BYTES_IMPROVE = 14 # V 4 + R 4 + code 1 + policy 1 + V' 4 (the new policy's first evaluation step)
+BYTES_GREEDY = 10  # V 4 + R 4 + code 1 + policy 1 (the initial greedy sweep writes no values)
 
 
 def workload(seed):
@@ -304,7 +305,7 @@ def run_ours(args, rank, world, local, pg):
         vi_iters.append(rv["iterations"])
         pi_iters.append(rp["iterations"])
         vi_bytes += rv["iterations"] * S * BYTES_VI
-        pi_bytes += rp["eval_sweeps"] * S * BYTES_EVAL + (rp["rounds"] + 1) * S * BYTES_IMPROVE
+        pi_bytes += rp["eval_sweeps"] * S * BYTES_EVAL + rp["rounds"] * S * BYTES_IMPROVE + S * BYTES_GREEDY
     torch.cuda.synchronize()
     clocks = sampler.stop()
     if pg is not None:
