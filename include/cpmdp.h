@@ -160,7 +160,9 @@ typedef struct {
     double *trace;           /* optional device buffer of max_iter doubles: residual of each sweep
                                 (value iteration, fused path only; the barrier-free solver zeroes it
                                 first and also fills the entries of its two dropped sweeps) */
-    int32_t partial_eval;    /* policy iteration (default 4): while the policy keeps changing, each
+    int32_t partial_eval;    /* policy iteration (default -1: 2 on GridWorld models, 4 on dense ones,
+                                the caps measured fastest; other values below -1 are EINVAL):
+                                while the policy keeps changing, each
                                 round's evaluation stops after at most this many sweeps (modified
                                 policy iteration); once an improvement changes no action after a
                                 capped evaluation, every later round evaluates to eval_tol. The

@@ -430,6 +430,27 @@ __device__ __forceinline__ int improve_state(const float (&nb)[2 * D], float sel
     return old;
 }
 
+// The decision after an improvement sweep of policy iteration, from its
+// arrival (warps that changed an action in the low 16 bits, warps whose
+// residual is >= eval_tol in the high 16) and whether the evaluation before
+// it reached eval_tol (the same rules as the grid-barrier solver): 0 go on
+// (after a stable policy whose evaluation was capped: evaluate to eval_tol
+// from now on, full = true and the running phase's cap raised), 1 converged,
+// 2 stop (the evaluation limit ran out).
+__device__ __forceinline__ int pi_decide(int moved, int prev_ok, bool &full, int &cap, int max_eval) {
+    const int nchg = moved & 0xFFFF, nopen = moved >> 16;
+    if (nchg == 0) {
+        if (nopen == 0) return 1;
+        if (!prev_ok) {
+            if (full) return 2;
+            full = true;
+            cap = max_eval;
+        }
+        return 0;
+    }
+    return (!prev_ok && full) ? 2 : 0;
+}
+
 // Final bookkeeping: every warp adds its residual and arrives; the lead
 // waits for all warps, then fills the control block.
 __device__ __forceinline__ void flow_finish(Ctrl *ctrl, float rres, u64 timeout_ns, int NW, bool lead,
@@ -624,23 +645,34 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
             sg.act[i] = act;
         }
     }
-    int evals = 0, round = 0, conv = 0;
+    int evals = 0, round = 0, conv = 0, stop = 0;
     float rres = 0.f;
     // modified policy iteration: evaluations capped at partial_eval sweeps
     // until an improvement changes no action, full evaluations after that
-    // (the same rule as the grid-barrier solver, so the same rounds)
+    // (the same rule as the grid-barrier solver, so the same rounds).
+    // After an evaluation that ran to its cap, the improvement's arrival is
+    // not waited for: the next evaluation phase starts at once and takes the
+    // improvement's decision at its first lagged check (sweep q0 + 2, before
+    // the ring the improvement read is overwritten); when that decision is
+    // to stop, the warp returns to V' (its own ring words, still intact) and
+    // the phase's sweeps are dropped.
     bool full = sp.partial_eval <= 0;
+    bool pend = false;          // an improvement's arrival not checked yet
+    unsigned pend_seq = 0;      // sequence of its V'
+    float pend_r = 0.f;         // its residual
+    int pend_ok = 0;            // whether the evaluation before it reached eval_tol
     while (round < sp.max_rounds) {
-        const int cap = full ? sp.max_eval_iter : min(sp.partial_eval, sp.max_eval_iter);
+        int cap = full ? sp.max_eval_iter : min(sp.partial_eval, sp.max_eval_iter);
         // evaluation of the current policy from V_q (tag base + q)
         const unsigned q0 = q;
+        unsigned qs = pend ? q0 - 1 : q0;   // first sweep whose arrival is unchecked
         unsigned rq = q;
         int e = 0, eval_ok = 0;
         float rh[kLag];
 #pragma unroll
         for (int i = 0; i < kLag; i++) rh[i] = 0.f;
         for (;;) {
-            const bool chk = q - q0 >= (unsigned)kLag;
+            const bool chk = q - qs >= (unsigned)kLag;
             const u64 pk = chk ? arv.peek(arv.nchk) : 0ull;
             float rows[ZS][NR][4], hl[ZS], hr[ZS];
             if (!sg.gather(f, q, base, sg.cur, rows, hl, hr, ctrl, sp.timeout_ns)) return;
@@ -664,7 +696,15 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
             if (chk) {
                 const int nf = arv.check(pk, ctrl, sp.timeout_ns);
                 if (nf < 0) return;
-                if (nf == 0) {  // sweep q - kLag met eval_tol: its result is V_{q-kLag+1}
+                if (pend) {     // this arrival is the pending improvement's (sweep q0 - 1)
+                    pend = false;
+                    stop = pi_decide(nf, pend_ok, full, cap, sp.max_eval_iter);
+                    if (stop) {
+                        sg.own_values_all(f, pend_seq, sg.cur);
+                        rres = pend_r;
+                        break;
+                    }
+                } else if (nf == 0) {  // sweep q - kLag met eval_tol: its result is V_{q-kLag+1}
                     sg.own_values_all(f, q - kLag + 1, sg.cur);
                     rres = rh[kLag - 1];
                     rq = q - kLag + 1;
@@ -683,6 +723,18 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
             rh[0] = r;
             q++;
             e++;
+            if (e == cap && pend) {   // short phases end before their first lagged check
+                const int moved = arv.check_next(ctrl, sp.timeout_ns);
+                if (moved < 0) return;
+                pend = false;
+                qs = q0;   // if the phase goes on (cap raised), its own sweeps are next in line
+                stop = pi_decide(moved, pend_ok, full, cap, sp.max_eval_iter);
+                if (stop) {
+                    sg.own_values_all(f, pend_seq, sg.cur);
+                    rres = pend_r;
+                    break;
+                }
+            }
             if (e == cap) {
                 rres = rh[0];
                 rq = q;
@@ -705,6 +757,7 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
                 break;
             }
         }
+        if (stop) break;   // the pending improvement ended the solve
         evals += (int)(rq - q0);
         // every earlier arrival is settled before the improvement's own
         while (arv.nchk < arv.na)
@@ -759,19 +812,32 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
         // 16 bits) and warps whose residual is at or above eval_tol (high 16)
         const bool wopen = warp_open(r, f.eval_tol_bits);
         arv.arrive_count((wc > 0 ? 1u : 0u) + (wopen ? 65536u : 0u));
+        round++;
+        if (rq == hq) {
+            // the improvement read ring hq, which the next phase overwrites
+            // only with its third sweep: its decision is taken there (or
+            // below, after the last round)
+            pend = true;
+            pend_seq = q;
+            pend_r = r;
+            pend_ok = eval_ok;
+        } else {
+            // an evaluation that stopped early leaves the improvement reading
+            // an older ring, one the next phase's first sweeps overwrite
+            const int moved = arv.check_next(ctrl, sp.timeout_ns);
+            if (moved < 0) return;
+            int cap_unused = 0;
+            stop = pi_decide(moved, eval_ok, full, cap_unused, sp.max_eval_iter);
+            if (stop) break;
+        }
+    }
+    if (pend) {   // the round limit came first: the last improvement's decision
         const int moved = arv.check_next(ctrl, sp.timeout_ns);
         if (moved < 0) return;
-        round++;
-        if ((moved & 0xFFFF) == 0) {
-            if ((moved >> 16) == 0) { conv = 1; break; }   // stable policy, V' within eval_tol
-            if (!eval_ok) {
-                if (full) break;   // the evaluation limit ran out
-                full = true;       // evaluate this policy to eval_tol before deciding
-            }
-            continue;
-        }
-        if (!eval_ok && full) break;
+        int cap_unused = 0;
+        stop = pi_decide(moved, pend_ok, full, cap_unused, sp.max_eval_iter);
     }
+    conv = stop == 1;
 #pragma unroll
     for (int i = 0; i < ZS; i++)
         if (sg.valid[i]) {

@@ -42,6 +42,7 @@ def test_version_and_defaults(cp):
     assert "sm_103a" in cp.version()
     o = cp.default_opts()
     assert o.tol == 1e-6 and o.max_iter == 1000 and o.certify == 1 and o.fused == 1
+    assert o.partial_eval == -1   # the per-model default evaluation cap
 
 
 CASES = [

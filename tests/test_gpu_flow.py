@@ -128,7 +128,7 @@ def test_pi_equals_grid_barrier_solver(cp, shape):
     f.close()
 
 
-@pytest.mark.parametrize("partial", [0, 3, 8])
+@pytest.mark.parametrize("partial", [0, 1, 2, 3, 4, 8])
 def test_pi_partial_evaluation_same_in_both_solvers(cp, partial):
     """Modified policy iteration (evaluations capped at partial_eval sweeps
     until an improvement changes no action; 0 = every evaluation to
