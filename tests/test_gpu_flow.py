@@ -108,7 +108,8 @@ def test_k_sweeps_match_oracle(cp, oc, k):
     f.close()
 
 
-@pytest.mark.parametrize("shape", [(12, 20), (37, 64), (5, 9, 12), (64, 64, 64)])
+@pytest.mark.parametrize("shape", [(400,), (3000,), (12, 20), (37, 64), (24, 160), (5, 9, 12), (20, 36, 8),
+                                   (64, 64, 64)])
 def test_pi_equals_grid_barrier_solver(cp, shape):
     import torch
     gw = _world(shape, seed=11 + shape[0])
