@@ -84,8 +84,8 @@ __global__ void __launch_bounds__(256) solve_pi_kernel(BandArgs a, T *V, T *Wbuf
     if (grid_sync_count(ctrl, nbar++, nb, 0, sp.timeout_ns, ph0, ph1, stall) < 0) return;
     total++;
     backups += (long long)a.nstates * sp.nactions;
-    // modified policy iteration: evaluations capped at partial_eval sweeps
-    // until an improvement changes no action, full evaluations after that
+    // modified policy iteration: evaluations of exactly partial_eval sweeps
+    // until an improvement changes no action, evaluations to eval_tol after that
     bool full = sp.partial_eval <= 0;
     while (round < sp.max_rounds) {
         const int cap = full ? sp.max_eval_iter : min(sp.partial_eval, sp.max_eval_iter);
@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(256) solve_pi_kernel(BandArgs a, T *V, T *Wbuf
             ks++; e++; total++;
             backups += a.nstates;
             T *t = cur; cur = nxt; nxt = t;
-            if (open == 0) { eval_ok = 1; break; }
+            // a capped evaluation runs all its sweeps; one to eval_tol stops there
+            if (open == 0 && full) { eval_ok = 1; break; }
         }
         evals += e;
         // improvement, and the new policy's first evaluation step V' = Q of
@@ -226,8 +227,8 @@ __global__ void __launch_bounds__(256) small_pi_kernel(BandArgs a, T *V, uint8_t
     __syncthreads();
     total++;
     backups += (long long)a.nstates * sp.nactions;
-    // modified policy iteration: evaluations capped at partial_eval sweeps
-    // until an improvement changes no action, full evaluations after that
+    // modified policy iteration: evaluations of exactly partial_eval sweeps
+    // until an improvement changes no action, evaluations to eval_tol after that
     bool full = sp.partial_eval <= 0;
     while (round < sp.max_rounds) {
         const int cap = full ? sp.max_eval_iter : min(sp.partial_eval, sp.max_eval_iter);
@@ -249,7 +250,8 @@ __global__ void __launch_bounds__(256) small_pi_kernel(BandArgs a, T *V, uint8_t
             total++;
             backups += a.nstates;
             T *t = cur; cur = nxt; nxt = t;
-            if (below_tol(m, sp.eval_tol)) { eval_ok = 1; break; }
+            // a capped evaluation runs all its sweeps; one to eval_tol stops there
+            if (full && below_tol(m, sp.eval_tol)) { eval_ok = 1; break; }
         }
         evals += e;
         // improvement, and the new policy's first evaluation step V' = Q of

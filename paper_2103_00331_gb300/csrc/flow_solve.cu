@@ -647,32 +647,36 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
     }
     int evals = 0, round = 0, conv = 0, stop = 0;
     float rres = 0.f;
-    // modified policy iteration: evaluations capped at partial_eval sweeps
-    // until an improvement changes no action, full evaluations after that
-    // (the same rule as the grid-barrier solver, so the same rounds).
-    // After an evaluation that ran to its cap, the improvement's arrival is
-    // not waited for: the next evaluation phase starts at once and takes the
-    // improvement's decision at its first lagged check (sweep q0 + 2, before
-    // the ring the improvement read is overwritten); when that decision is
-    // to stop, the warp returns to V' (its own ring words, still intact) and
-    // the phase's sweeps are dropped.
+    // modified policy iteration, the same schedule as the grid-barrier
+    // solver (so the same rounds and sweeps): while the policy changes, each
+    // evaluation runs exactly partial_eval sweeps; once an improvement after
+    // such a capped evaluation changes no action, evaluations run to
+    // eval_tol. Every store of sequence x first checks the arrivals of the
+    // sequences up to x - 3 (four rings: nobody still reads the ring it
+    // overwrites). A capped evaluation needs no other check: its improvement
+    // follows at once, on its last sweep, and the improvement's decision
+    // (stop, evaluate to eval_tol, go on) is read when its arrival comes up
+    // in that order, at the latest when the next evaluation reaches its cap;
+    // a "stop" returns every warp to the improvement's values (its own ring
+    // words, still intact) and drops what followed.
     bool full = sp.partial_eval <= 0;
+    unsigned chk_out = 1;       // output sequence of the next unchecked arrival
     bool pend = false;          // an improvement's arrival not checked yet
-    unsigned pend_seq = 0;      // sequence of its V'
+    unsigned pend_seq = 0;      // its output sequence (V')
     float pend_r = 0.f;         // its residual
     int pend_ok = 0;            // whether the evaluation before it reached eval_tol
     while (round < sp.max_rounds) {
         int cap = full ? sp.max_eval_iter : min(sp.partial_eval, sp.max_eval_iter);
         // evaluation of the current policy from V_q (tag base + q)
         const unsigned q0 = q;
-        unsigned qs = pend ? q0 - 1 : q0;   // first sweep whose arrival is unchecked
         unsigned rq = q;
         int e = 0, eval_ok = 0;
         float rh[kLag];
 #pragma unroll
         for (int i = 0; i < kLag; i++) rh[i] = 0.f;
         for (;;) {
-            const bool chk = q - qs >= (unsigned)kLag;
+            // the check due before this iteration's store of q + 1: sequence q - 2
+            const bool chk = chk_out + 2u <= q;
             const u64 pk = chk ? arv.peek(arv.nchk) : 0ull;
             float rows[ZS][NR][4], hl[ZS], hr[ZS];
             if (!sg.gather(f, q, base, sg.cur, rows, hl, hr, ctrl, sp.timeout_ns)) return;
@@ -696,7 +700,8 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
             if (chk) {
                 const int nf = arv.check(pk, ctrl, sp.timeout_ns);
                 if (nf < 0) return;
-                if (pend) {     // this arrival is the pending improvement's (sweep q0 - 1)
+                const unsigned s = chk_out++;
+                if (pend && s == pend_seq) {   // the last improvement's decision
                     pend = false;
                     stop = pi_decide(nf, pend_ok, full, cap, sp.max_eval_iter);
                     if (stop) {
@@ -704,13 +709,15 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
                         rres = pend_r;
                         break;
                     }
-                } else if (nf == 0) {  // sweep q - kLag met eval_tol: its result is V_{q-kLag+1}
-                    sg.own_values_all(f, q - kLag + 1, sg.cur);
+                } else if (full && s > q0 && nf == 0) {
+                    // the sweep that produced V_s met eval_tol (s = q - 2): V_s ends the evaluation
+                    sg.own_values_all(f, s, sg.cur);
                     rres = rh[kLag - 1];
-                    rq = q - kLag + 1;
+                    rq = s;
                     eval_ok = 1;
                     break;
                 }
+                // otherwise an evaluation sweep of a capped phase: its check only orders the rings
             }
             sg.publish(f, q + 1, base, nxt);
             arv.arrive(warp_open(r, f.eval_tol_bits));
@@ -723,45 +730,64 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
             rh[0] = r;
             q++;
             e++;
-            if (e == cap && pend) {   // short phases end before their first lagged check
-                const int moved = arv.check_next(ctrl, sp.timeout_ns);
-                if (moved < 0) return;
-                pend = false;
-                qs = q0;   // if the phase goes on (cap raised), its own sweeps are next in line
-                stop = pi_decide(moved, pend_ok, full, cap, sp.max_eval_iter);
+            if (e == cap && pend) {
+                // the last improvement's decision is still out: take it now
+                while (pend) {
+                    const int nf = arv.check_next(ctrl, sp.timeout_ns);
+                    if (nf < 0) return;
+                    const unsigned s = chk_out++;
+                    if (s == pend_seq) {
+                        pend = false;
+                        stop = pi_decide(nf, pend_ok, full, cap, sp.max_eval_iter);
+                    }
+                }
                 if (stop) {
                     sg.own_values_all(f, pend_seq, sg.cur);
                     rres = pend_r;
                     break;
                 }
+                if (e < cap) continue;   // cap raised: this evaluation runs to eval_tol
             }
             if (e == cap) {
                 rres = rh[0];
                 rq = q;
-                // arrivals of this phase are its sweeps q0, q0 + 1, ... in order
-                const unsigned na0 = arv.na - (unsigned)e;
-                while (arv.nchk < arv.na) {
-                    const unsigned sweep = q0 + (arv.nchk - na0);
-                    const int nf = arv.check_next(ctrl, sp.timeout_ns);
-                    if (nf < 0) return;
-                    if (nf == 0 && !eval_ok) {
-                        eval_ok = 1;
-                        rq = sweep + 1;
-                        if (rq != q) sg.own_values_all(f, rq, sg.cur);
-                        const unsigned back = q - 1 - sweep;   // 0 .. kLag-1
+                if (full) {
+                    // an evaluation to eval_tol that reached max_eval_iter:
+                    // whether one of its last sweeps met eval_tol after all
+                    while (chk_out <= q) {
+                        const int nf = arv.check_next(ctrl, sp.timeout_ns);
+                        if (nf < 0) return;
+                        const unsigned s = chk_out++;
+                        if (s > q0 && nf == 0 && !eval_ok) {
+                            eval_ok = 1;
+                            rq = s;
+                            if (rq != q) sg.own_values_all(f, rq, sg.cur);
+                            const unsigned back = q - s;   // 0 .. kLag-1
 #pragma unroll
-                        for (int i2 = 0; i2 < kLag; i2++)
-                            if ((unsigned)i2 == back) rres = rh[i2];
+                            for (int i2 = 0; i2 < kLag; i2++)
+                                if ((unsigned)i2 == back) rres = rh[i2];
+                        }
                     }
                 }
                 break;
             }
         }
-        if (stop) break;   // the pending improvement ended the solve
+        if (stop) break;   // the last improvement ended the solve
         evals += (int)(rq - q0);
-        // every earlier arrival is settled before the improvement's own
-        while (arv.nchk < arv.na)
-            if (arv.check_next(ctrl, sp.timeout_ns) < 0) return;
+        if (full) {
+            // every earlier arrival is settled before the improvement (it
+            // reads V_rq, possibly an older ring than the last one written)
+            while (chk_out <= q) {
+                if (arv.check_next(ctrl, sp.timeout_ns) < 0) return;
+                chk_out++;
+            }
+        } else {
+            // the checks due before the improvement's store of q + 1
+            while (chk_out + 2u <= q) {
+                if (arv.check_next(ctrl, sp.timeout_ns) < 0) return;
+                chk_out++;
+            }
+        }
         const unsigned hq = q;  // highest tag sequence written so far
         // sg.cur now holds V_rq, the values of this evaluation
         // improvement on V_rq (tag base + rq, buffer rq mod kRing), and the
@@ -814,28 +840,34 @@ __global__ void __launch_bounds__(32 * ColWarps<ZS>::value, 1) flow_pi_kernel(Fl
         arv.arrive_count((wc > 0 ? 1u : 0u) + (wopen ? 65536u : 0u));
         round++;
         if (rq == hq) {
-            // the improvement read ring hq, which the next phase overwrites
-            // only with its third sweep: its decision is taken there (or
-            // below, after the last round)
+            // the improvement read ring hq, which later stores overwrite only
+            // from sequence hq + 4 on: its decision is read in order (or below,
+            // after the last round)
             pend = true;
             pend_seq = q;
             pend_r = r;
             pend_ok = eval_ok;
         } else {
-            // an evaluation that stopped early leaves the improvement reading
-            // an older ring, one the next phase's first sweeps overwrite
+            // an evaluation to eval_tol that stopped early leaves the
+            // improvement reading an older ring, one the next stores overwrite
+            // sooner: every arrival before its own was settled above
             const int moved = arv.check_next(ctrl, sp.timeout_ns);
             if (moved < 0) return;
+            chk_out++;
             int cap_unused = 0;
             stop = pi_decide(moved, eval_ok, full, cap_unused, sp.max_eval_iter);
             if (stop) break;
         }
     }
-    if (pend) {   // the round limit came first: the last improvement's decision
-        const int moved = arv.check_next(ctrl, sp.timeout_ns);
-        if (moved < 0) return;
-        int cap_unused = 0;
-        stop = pi_decide(moved, pend_ok, full, cap_unused, sp.max_eval_iter);
+    while (pend) {   // the round limit came first: the last improvement's decision
+        const int nf = arv.check_next(ctrl, sp.timeout_ns);
+        if (nf < 0) return;
+        const unsigned s = chk_out++;
+        if (s == pend_seq) {
+            pend = false;
+            int cap_unused = 0;
+            stop = pi_decide(nf, pend_ok, full, cap_unused, sp.max_eval_iter);
+        }
     }
     conv = stop == 1;
 #pragma unroll
