@@ -163,8 +163,8 @@ typedef struct {
     int32_t partial_eval;    /* policy iteration (default -1: 2 on GridWorld models, 4 on dense ones,
                                 the caps measured fastest; other values below -1 are EINVAL):
                                 while the policy keeps changing, each
-                                round's evaluation stops after at most this many sweeps (modified
-                                policy iteration); once an improvement changes no action after a
+                                round's evaluation runs exactly this many sweeps (modified policy
+                                iteration); once an improvement changes no action after such a
                                 capped evaluation, every later round evaluates to eval_tol. The
                                 solve stops when an improvement changes no action and its own
                                 values are within eval_tol of its input. 0: every round evaluates
